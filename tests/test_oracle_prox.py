@@ -1,0 +1,148 @@
+"""Pins for oracle/prox.py against brute force and optimality conditions.
+
+The set table (Sec. "Software and numerical examples") defines the sets;
+Eq. proj_prob defines the projection as the nearest point; Eq. prox_sq_dist
+gives the prox of the squared distance in closed form.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import prox
+
+
+def _rand(n, seed):
+    return np.random.default_rng(seed).standard_normal(n) * 2.0
+
+
+def test_bounds_is_nearest_point_per_entry():
+    w = _rand(50, 1)
+    y = prox.proj_bounds(w, -0.5, 1.25)
+    for wi, yi in zip(w, y):
+        cands = np.linspace(-0.5, 1.25, 2001)
+        best = cands[np.argmin(np.abs(cands - wi))]
+        assert abs(yi - wi) <= abs(best - wi) + 1e-12
+        assert -0.5 <= yi <= 1.25
+    assert np.array_equal(prox.proj_bounds(w, 0.0, math.inf), np.maximum(w, 0.0))
+    with pytest.raises(ValueError):
+        prox.proj_bounds(w, 1.0, 0.0)
+
+
+def test_l2_ball_projection_optimality():
+    g = np.random.default_rng(2)
+    for n, sigma in ((1, 0.3), (5, 1.0), (40, 3.0)):
+        w = g.standard_normal(n) * 3
+        y = prox.proj_l2(w, sigma)
+        assert np.linalg.norm(y) <= sigma * (1 + 1e-14) or np.allclose(y, w)
+        # variational inequality: <w - y, z - y> <= 0 for all z in the ball
+        for _ in range(200):
+            z = g.standard_normal(n)
+            z *= g.uniform(0, sigma) / np.linalg.norm(z)
+            assert float((w - y) @ (z - y)) <= 1e-12
+    w = np.array([3.0, 4.0])
+    assert np.allclose(prox.proj_l2(w, 1.0), [0.6, 0.8])
+    assert np.array_equal(prox.proj_l2(w, 5.0), w)
+
+
+def _theta_by_bisection(w, tau):
+    """theta >= 0 with sum max(|w| - theta, 0) = tau, by bisection (an
+    independent route to the l1-ball KKT conditions)."""
+    a = np.abs(w)
+    if a.sum() <= tau:
+        return 0.0
+    lo, hi = 0.0, float(a.max())
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.maximum(a - mid, 0).sum() > tau:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 10, 64])
+def test_l1_threshold_matches_bisection(n):
+    for seed in range(5):
+        w = _rand(n, 100 + seed)
+        for frac in (0.0, 0.1, 0.5, 0.9, 1.0, 1.5):
+            tau = frac * float(np.abs(w).sum())
+            th = prox.l1_threshold(w, tau)
+            ref = _theta_by_bisection(w, tau)
+            assert th == pytest.approx(ref, rel=1e-12, abs=1e-12)
+            y = prox.proj_l1(w, tau)
+            if frac < 1.0:
+                assert np.abs(y).sum() == pytest.approx(tau, rel=1e-12, abs=1e-12)
+            else:
+                assert np.array_equal(y, w)
+
+
+def test_l1_projection_brute_force_support_enumeration():
+    """For n <= 8 enumerate every support set S and sign pattern fixed by w:
+    on S, y = sign(w)(|w| - t) with t = (sum_S |w| - tau)/|S|; keep the
+    feasible candidate nearest to w (the projection is unique)."""
+    g = np.random.default_rng(11)
+    for n in range(1, 9):
+        for _ in range(10):
+            w = g.standard_normal(n) * 2
+            tau = g.uniform(0.05, 0.95) * np.abs(w).sum()
+            best, best_d = None, np.inf
+            for r in range(1, n + 1):
+                for S in itertools.combinations(range(n), r):
+                    S = list(S)
+                    t = (np.abs(w[S]).sum() - tau) / r
+                    if t < 0:
+                        continue
+                    y = np.zeros(n)
+                    y[S] = np.sign(w[S]) * (np.abs(w[S]) - t)
+                    if np.any(np.sign(y[S]) != np.sign(w[S])) or np.any(np.abs(w[S]) < t):
+                        continue
+                    d = np.linalg.norm(y - w)
+                    if np.abs(y).sum() <= tau * (1 + 1e-12) and d < best_d:
+                        best, best_d = y, d
+            y = prox.proj_l1(w, tau)
+            assert np.allclose(y, best, atol=1e-12)
+
+
+def test_l1_special_cases():
+    w = np.array([1.0, -2.0, 3.0])
+    assert np.array_equal(prox.proj_l1(w, 0.0), np.zeros(3))
+    assert np.array_equal(prox.proj_l1(w, 10.0), w)
+    # tau = 1 against sorted |w| = 3, 2, 1: theta = 2, only the 3 survives
+    assert np.allclose(prox.proj_l1(w, 1.0), [0.0, 0.0, 1.0])
+    # ties in |w| do not matter for the threshold
+    assert np.allclose(prox.proj_l1(np.array([2.0, -2.0]), 2.0), [1.0, -1.0])
+
+
+def test_card_brute_force_over_subsets():
+    g = np.random.default_rng(5)
+    for n in range(1, 11):
+        for k in range(0, n + 2):
+            w = g.standard_normal(n)
+            best_S, best_d = None, np.inf
+            for S in itertools.combinations(range(n), min(k, n)):
+                y = np.zeros(n)
+                y[list(S)] = w[list(S)]
+                d = np.linalg.norm(y - w)
+                if d < best_d:
+                    best_S, best_d = set(S), d
+            assert set(prox.card_support(w, k).tolist()) == best_S
+            assert np.linalg.norm(prox.proj_card(w, k) - w) == pytest.approx(best_d, abs=1e-14)
+
+
+def test_card_tie_rule_prefers_lower_index():
+    w = np.array([1.0, -3.0, 3.0, 0.5, -3.0])
+    assert prox.card_support(w, 2).tolist() == [1, 2]
+    assert prox.card_support(w, 3).tolist() == [1, 2, 4]
+    assert prox.card_support(w, 0).tolist() == []
+    assert np.array_equal(prox.proj_card(w, 9), w)
+
+
+def test_prox_dist_is_minimiser():
+    g = np.random.default_rng(9)
+    m, w = g.standard_normal(20), g.standard_normal(20)
+    for rho in (0.1, 1.0, 7.5):
+        z = prox.prox_dist(w, m, rho)
+        # gradient of 1/2||z - m||^2 + rho/2 ||z - w||^2 vanishes at z
+        assert np.allclose((z - m) + rho * (z - w), 0, atol=1e-14)
