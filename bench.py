@@ -1,0 +1,297 @@
+"""Throughput of the PARSDMM hot path on GB300.
+
+Workload: the 2D 512 x 1024 layered model with five sets (bounds; TV l1 ball
+tau = 0.3 TV(m); l2 ball on D_x x, sigma = 0.5 ||D_x m||; card(D_z x) <= 2%
+of N; D_z x in [-0.1, 0.5]), FP32 storage with FP64 reductions, adaptive
+rho, gamma = 1.5, 500 iterations, 5 CG steps.  One step = one projection
+(500 PARSDMM iterations) of one model resident in HBM.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PARSDMM iter/s & projections/s at 1e-4 rel err; % HBM peak; p50/p99 latency"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload():
+    from paper_1902_09699_gb300 import workloads as W
+    return W.layered_2d()
+
+
+def config_dict(c, extra=None):
+    d = {"workload": c["name"], "grid": list(c["grid"]["n"]), "sets": len(c["sets"]),
+         "iterations": c["opts"]["max_iter"], "cg_steps": c["opts"]["cg_iters"],
+         "adapt": "rho", "gamma": c["opts"]["gamma0"], "l2_between_steps": "flushed (512 MB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/sip_clocks.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self, dev=0):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9 and parts[0] == str(dev):
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- reference arm / cpu baseline
+def oracle_sample(iters, dtype_f32=True):
+    """Time the FP64 oracle (as it stands) on the first ``iters`` iterations of
+    the workload, single-threaded, in a fresh process."""
+    code = (
+        "import sys, time, json, numpy as np; sys.path.insert(0, %r)\n"
+        "from paper_1902_09699_gb300 import workloads as W\n"
+        "from oracle import parsdmm as P\n"
+        "c = W.layered_2d(); m = c['m'].astype(np.float32).astype(np.float64) if %r else c['m']\n"
+        "o = P.options(**dict(c['opts'], max_iter=%d))\n"
+        "t = time.perf_counter(); P.parsdmm(m, c['grid'], c['sets'], o); dt = time.perf_counter() - t\n"
+        "print(json.dumps({'seconds': dt}))\n" % (ROOT, dtype_f32, iters))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    secs = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
+    return iters / secs, secs
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    c = workload()
+    its = 12
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, _ = oracle_sample(its)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    sample = "first %d of %d iterations of the workload per step (FP64 numpy oracle, 1 thread)" % (
+        its, c["opts"]["max_iter"])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(c), "projections_per_s": v / c["opts"]["max_iter"],
+            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1902_09699_gb300 import sip
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    c = workload()
+    its = c["opts"]["max_iter"]
+    pr = sip.Projector(c["grid"], c["sets"], dtype=args.dtype, **c["opts"])
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    # independent replicas: each rank projects its own models (seeded per rank)
+    from paper_1902_09699_gb300 import workloads as W
+    models = [torch.as_tensor(c["m"] if (rank == 0 and i == 0) else W.layered((512, 1024), seed=5000 + 7 * rank + i),
+                              dtype=tdt, device=dev) for i in range(4)]
+    x = torch.empty_like(models[0])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        pr.project(models[i % len(models)], x, info=False)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time per step with CUDA events, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(st)
+        pr.project(models[i % len(models)], x, info=False)
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop(local)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * its * args.steps / (total_ms / 1000.0)
+
+    # ---- accuracy of this form against the FP64 GPU loop (projections/s at 1e-4)
+    x32, _ = pr.project(models[0], None)
+    pr64 = sip.Projector(c["grid"], c["sets"], dtype="f64", **c["opts"])
+    x64, _ = pr64.project(models[0].double())
+    rel_err = float((x32.double() - x64).norm() / x64.norm())
+    # plain FP64 GPU loop throughput (one step, same workload)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1.0)
+    e0.record(st)
+    pr64.project(models[0].double(), x64, info=False)
+    e1.record(st)
+    torch.cuda.synchronize()
+    f64_ms = e0.elapsed_time(e1)
+    pr64.close()
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    hm = [m.cpu().pin_memory() for m in models]
+    hx = torch.empty(x.numel(), dtype=tdt).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    dm = torch.empty_like(models[0])
+    for i in range(e2e_steps):
+        dm.copy_(hm[i % len(hm)], non_blocking=True)
+        pr.project(dm, x, info=False)
+        hx.copy_(x, non_blocking=True)
+    t1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / e2e_steps
+    e2e_value = world * its / (e2e_ms / 1000.0)
+
+    # ---- per-kernel device time (CUDA events around every launch, no graph)
+    pr.set_timing(True)
+    flush.fill_(2.0)
+    pr.project(models[1], x, info=True)
+    kt = pr.kernel_times()
+    pr.set_timing(False)
+    dom = max(kt, key=lambda k: kt[k]["ms"])
+    d = kt[dom]
+    avg_s = d["ms"] / max(d["launches"], 1) / 1000.0
+    peak, peak_src = peaks()
+    achieved = d["bytes_per_launch"] / avg_s / 1e9 if avg_s > 0 else 0.0
+    launches_per_step = sum(v["launches"] for v in kt.values()) + 2   # + init, norms
+    bpi = pr.bytes_per_iter()
+    pct_hbm = bpi * (value / world) / 1e9 / peak
+
+    out = None
+    if rank == 0:
+        cpu_v, cpu_s = oracle_sample(args.cpu_iters)
+        out = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": config_dict(c, {"parallelism": "replicas" if world > 1 else "single"}),
+            "projections_per_s": value / its,
+            "projections_per_s_at_1e-4": (value / its) if rel_err <= 1e-4 else 0.0,
+            "rel_err_vs_f64_gpu": rel_err,
+            "f64_gpu_loop": {"ms_per_projection": f64_ms, "iter_per_s": its / (f64_ms / 1000.0)},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "bytes_per_iter": bpi, "pct_hbm_peak": pct_hbm, "hbm_peak_gbs": peak,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "kernel_ms_per_launch": avg_s * 1000.0},
+            "kernel_breakdown_ms_per_step": {k: v["ms"] for k, v in kt.items()},
+            "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": models[0].numel() * models[0].element_size(),
+                    "d2h_bytes_per_step": x.numel() * x.element_size()},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "cpu_baseline": {"value": cpu_v, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                             "sample": "first %d of %d iterations of the workload (FP64 numpy oracle, %.1f s)" % (
+                                 args.cpu_iters, its, cpu_s)},
+        }
+        print(json.dumps(out))
+    pr.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--cpu-iters", type=int, default=30)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

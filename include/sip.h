@@ -1,0 +1,248 @@
+/*
+ * sip.h -- C ABI of a GB300 (sm_103a) implementation of PARSDMM, the
+ * projection onto an intersection of sets of arXiv:1902.09699.
+ *
+ * Problem (Eq. proj_intersect, Eq. proj_intersect_indicator):
+ *     x = argmin_x 1/2 ||x - m||_2^2   s.t.  A_i x in C_i,  i = 1..p,
+ * with A_i an identity or finite-difference operator on a regular 2D/3D grid
+ * and C_i a simple set (bounds, l1 ball, l2 ball, cardinality; set table of
+ * Sec. "Software and numerical examples").  The user gives m and the pairs
+ * (A_i, C_i); the library adds the identity block and the prox of the
+ * squared distance (Sec. "Software and numerical examples") and runs
+ * Algorithm PARSDMM with Algorithm adapt-rho-gamma and the stopping rule of
+ * Eq. stopping_conditions, optionally inside Algorithm ML-PARSDMM.
+ *
+ * Layout: every grid vector is contiguous with z the fastest index,
+ * linear index iz + n_z*(ix + n_x*iy) (Sec. "Notation").  The output of a
+ * forward difference along an axis has one sample fewer along that axis
+ * (Eq. FD_mat) and the same z-fastest layout on its own grid; the TV
+ * operator stacks D_z, D_x (, D_y) outputs in that order.
+ *
+ * Precision: SIP_F64 stores and computes everything in binary64;
+ * SIP_F32 stores vectors in binary32 and accumulates every inner product,
+ * norm and l1 running sum in binary64.  Device buffers passed to the library
+ * hold elements of the handle's dtype.
+ *
+ * Errors: every call returns a sip_status; nothing throws across the ABI.
+ * sip_last_error() gives a thread-local message for the last failure of
+ * the calling thread.  A failed call leaves a handle usable.
+ *
+ * Threads / streams: calls on one handle must not overlap; distinct
+ * handles are independent.  Device work is ordered on the caller's stream
+ * (a cudaStream_t passed as void*, NULL for the legacy default stream).
+ */
+#ifndef SIP_H
+#define SIP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIP_MAX_SETS 16
+
+typedef enum {
+    SIP_OK = 0,
+    SIP_ERR_INVALID_ARG = 1, /* bad pointer, size, set parameter or option */
+    SIP_ERR_OOM = 2,         /* device or host allocation failed */
+    SIP_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    SIP_ERR_TIMEOUT = 4,     /* a bounded wait gave up */
+    SIP_ERR_NONFINITE = 5,   /* NaN/Inf met in the model */
+    SIP_ERR_BUDGET = 6,      /* request exceeds a memory budget */
+    SIP_ERR_INTERNAL = 7     /* a device-side consistency check failed */
+} sip_status;
+
+/* Linear operators A_i (Eq. FD_mat; set table). */
+typedef enum {
+    SIP_OP_I = 0,   /* identity, M = N */
+    SIP_OP_DZ = 1,  /* (x[iz+1]-x[iz])/h_z, output (n_z-1) x n_x (x n_y) */
+    SIP_OP_DX = 2,  /* (x[ix+1]-x[ix])/h_x, output n_z x (n_x-1) (x n_y) */
+    SIP_OP_DY = 3,  /* (x[iy+1]-x[iy])/h_y, 3D only */
+    SIP_OP_TV = 4   /* anisotropic TV stack [D_z; D_x (; D_y)] */
+} sip_op;
+
+/* Simple sets C_i (set table). */
+typedef enum {
+    SIP_SET_BOUNDS = 0, /* lo <= (Ax)[j] <= hi; lo/hi may be -/+INFINITY */
+    SIP_SET_L1 = 1,     /* ||Ax||_1 <= sigma */
+    SIP_SET_L2 = 2,     /* ||Ax||_2 <= sigma */
+    SIP_SET_CARD = 3    /* card(Ax) <= k; ties: larger |.| first, then lower index */
+} sip_set_type;
+
+typedef enum { SIP_F64 = 0, SIP_F32 = 1 } sip_dtype;
+
+/* SIP_FORM_ALG1: the paper's iteration with the identity block p+1
+ * (Eqs. PARSDMM_1, SDMM_adaptive).  SIP_FORM_DIRECT: the distance term kept
+ * in the x-step, (I + sum rho_i A_i^T A_i) x = m + sum A_i^T(rho_i y_i + v_i),
+ * no block p+1. */
+typedef enum { SIP_FORM_ALG1 = 0, SIP_FORM_DIRECT = 1 } sip_form;
+
+typedef struct {
+    int ndim;     /* 2 or 3 */
+    int64_t n[3]; /* n_z, n_x, n_y (n[2] ignored in 2D); every n >= 1 */
+    double h[3];  /* grid spacing per axis, > 0 (Eq. FD_mat) */
+} sip_grid;
+
+typedef struct {
+    int op;           /* sip_op */
+    int type;         /* sip_set_type */
+    double lo, hi;    /* SIP_SET_BOUNDS, lo <= hi */
+    double sigma;     /* SIP_SET_L1 / L2 radius (>= 0), used when sigma_rel == 0 */
+    double sigma_rel; /* > 0: radius = sigma_rel * ||A m|| (l1 or l2 norm of the
+                         set), resolved on the device from each model m */
+    int64_t k;        /* SIP_SET_CARD, >= 0, used when k_frac == 0 */
+    double k_frac;    /* > 0: k = floor(k_frac * N) with N the grid size */
+} sip_set;
+
+typedef struct {
+    int max_iter;       /* iterations of Algorithm PARSDMM (>= 1) */
+    int cg_iters;       /* > 0: fixed CG steps per x-update; 0: Eq. cg_stop
+                           rule ||r_j|| < 0.1 ||r_0||, at most cg_max steps */
+    int cg_max;
+    double eps_feas;    /* Eq. stopping_conditions (paper: 1e-3) */
+    double eps_evol;    /* Eq. stopping_conditions (paper: 1e-2) */
+    int check_every;    /* feasibility / evolution tested when k % check_every == 0 */
+    int evol_hist;      /* s of Eq. obj_stop, 1..8 */
+    int stop;           /* 0: run max_iter; 1: Eq. stopping_conditions; 2: feasibility only */
+    int adapt;          /* 0: fixed rho, gamma; 1: adapt rho; 2: adapt rho and gamma */
+    int adapt_every;    /* adapt when k % adapt_every == 1 % adapt_every */
+    double rho0, gamma0;
+    double eps_corr;    /* Algorithm adapt-rho-gamma (0.3) */
+    double rho_ratio_max; /* rho_i kept in [rho_{p+1}/R, rho_{p+1} R] */
+    double gamma_max;   /* gamma kept below 2 (1.99) */
+    int form;           /* sip_form */
+    int dtype;          /* sip_dtype */
+    int levels;         /* 1, or 2 for two-level ML-PARSDMM */
+    int coarse_iter;    /* iterations on the coarse level (0: max_iter) */
+    /* Optional host arrays [max_iter][nblocks] of rho_i / gamma_i used in
+     * iteration k (row k-1); nblocks = nsets + (form == ALG1).  When set, the
+     * values are replayed instead of adapted.  Read during sip_project. */
+    const double *rho_schedule;
+    const double *gamma_schedule;
+    /* Optional host array [max_iter][2*nblocks + 2 + nsets] filled by
+     * sip_project (single-level only): per iteration the rho_i and gamma_i
+     * used, the CG steps, r_evol and r_feas_i (NaN when not a check
+     * iteration). */
+    double *trace;
+} sip_options;
+
+typedef struct {
+    int iters;          /* iterations run (finest level) */
+    int cg_steps_total; /* CG steps summed over iterations (finest level) */
+    int stop_reason;    /* 0: max_iter reached; 1: stopping rule held */
+    int nblocks;
+    double r_evol;      /* last computed Eq. obj_stop value */
+    double r_feas[SIP_MAX_SETS]; /* last computed Eq. feas_stop values */
+    double rho[SIP_MAX_SETS + 1];
+    double gamma[SIP_MAX_SETS + 1];
+    double sigma[SIP_MAX_SETS];  /* resolved radii (finest level) */
+    int64_t k[SIP_MAX_SETS];     /* resolved cardinalities (finest level) */
+    float ms;           /* device time of the projection (CUDA events) */
+} sip_info;
+
+typedef struct sip_handle sip_handle;
+
+/* Fill *opts with the defaults (paper values where the paper gives one):
+ * max_iter 200, cg_iters 5, cg_max 100, eps_feas 1e-3, eps_evol 1e-2,
+ * check_every 5, evol_hist 5, stop 0, adapt 1, adapt_every 2, rho0 1,
+ * gamma0 1.5, eps_corr 0.3, rho_ratio_max 1e3, gamma_max 1.99,
+ * form ALG1, dtype F32, levels 1. */
+void sip_options_default(sip_options *opts);
+
+/* Build a projector for one grid and set list.  Validates every argument,
+ * resolves the operator / set layout and allocates the device arena that
+ * holds x, y_i, v_i, the CG vectors, the adapt state and all scratch
+ * (allocation happens here only).  nsets in [1, 16].  Returns
+ * SIP_ERR_INVALID_ARG for: NULL pointers, ndim not 2/3, n < 1, h <= 0,
+ * unknown op/type, an op that needs an axis of length >= 2 on a shorter
+ * axis, lo > hi, sigma < 0, k < 0, k_frac or sigma_rel < 0, bad options. */
+sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets,
+                      const sip_options *opts, sip_handle **out);
+
+/* Project the device vector m_dev (N elements of the handle's dtype) and
+ * write the result to x_dev (N elements).  Stream-ordered on `stream`;
+ * returns without synchronising unless info != NULL, a trace or schedule
+ * is requested, or the stopping rule is on.  m_dev must stay valid until
+ * the work completes.  State (x, y_i, v_i) starts from zero on the coarsest
+ * level each call. */
+sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev,
+                       void *stream, sip_info *info);
+
+sip_status sip_destroy(sip_handle *h);
+
+const char *sip_last_error(const sip_handle *h);
+
+/* Bytes of device memory the handle holds. */
+int64_t sip_device_bytes(const sip_handle *h);
+
+/* Algorithmic bytes one PARSDMM iteration must move at the handle's
+ * precision (state read and written once per phase; the figure the roofline
+ * uses), finest level. */
+double sip_bytes_per_iter(const sip_handle *h);
+
+/* Per-kernel device timing.  With timing on, sip_project launches every
+ * kernel directly (no CUDA graph) between CUDA events on the caller's stream
+ * and sip_project synchronises; sip_kernel_times returns, per kernel
+ * category (see sip_kernel_name, 0..SIP_KERNEL_CATEGORIES-1), the summed
+ * device milliseconds, the launch count since timing was switched on, and
+ * the algorithmic bytes one launch moves (the roofline numerator). */
+#define SIP_KERNEL_CATEGORIES 8
+sip_status sip_set_timing(sip_handle *h, int on);
+sip_status sip_kernel_times(const sip_handle *h, double *ms, int64_t *launches,
+                            double *bytes_per_launch);
+const char *sip_kernel_name(int category);
+
+/* ---------------------------------------------------------------------
+ * Single-step entry points.  Each runs the same device code the loop uses
+ * on caller buffers, so every step can be checked alone.  All pointers are
+ * device pointers of `dtype` elements unless stated; all calls are
+ * stream-ordered and synchronise only to return host scalars.
+ * ------------------------------------------------------------------- */
+
+/* s = A x (op on grid; Eq. FD_mat).  s has sip_op_rows(grid, op) entries. */
+sip_status sip_apply_op(const sip_grid *grid, int op, int dtype,
+                        const void *x_dev, void *s_dev, void *stream);
+/* x = A^T s. */
+sip_status sip_apply_op_t(const sip_grid *grid, int op, int dtype,
+                          const void *s_dev, void *x_dev, void *stream);
+/* Number of rows of A (M_i), or -1 for an invalid grid/op. */
+int64_t sip_op_rows(const sip_grid *grid, int op);
+
+/* out = C x with C = c_identity I + sum_i rho_i A_i^T A_i (Eq. sys_mat),
+ * applied as a matrix-free stencil.  ops/rhos are host arrays of nops. */
+sip_status sip_system_apply(const sip_grid *grid, const int *ops,
+                            const double *rhos, int nops, double c_identity,
+                            int dtype, const void *x_dev, void *out_dev,
+                            void *stream);
+
+/* y = P_C(w) for one simple set on n entries (set table), computed with the
+ * loop's kernels: clip, l2 radial scaling, l1-ball threshold by radix
+ * selection with binary64 running sums, top-k by radix selection with the
+ * index tie rule.  set->sigma / set->k are used as given (sigma_rel and
+ * k_frac ignored).  *scalar_out (host, may be NULL) receives the l1
+ * threshold theta, the l2 scale, or for card the |.| of the k-th kept
+ * entry. */
+sip_status sip_project_set(const sip_set *set, int dtype, const void *w_dev,
+                           int64_t n, void *y_dev, void *stream,
+                           double *scalar_out);
+
+/* *out (host) = ||A m||_1 (type L1) or ||A m||_2 (type L2), accumulated in
+ * binary64: the norm that relative radii (sigma_rel) refer to. */
+sip_status sip_op_norm(const sip_grid *grid, int op, int type, int dtype,
+                       const void *m_dev, void *stream, double *out);
+
+/* Coarse model for ML-PARSDMM: average over 2x2(x2) blocks; the coarse
+ * grid has n_c = ceil(n/2) and twice the spacing (Sec. "Multilevel
+ * PARSDMM").  mc_dev has the coarse grid's N entries. */
+sip_status sip_restrict(const sip_grid *fine, int dtype, const void *m_dev,
+                        void *mc_dev, void *stream);
+/* Linear interpolation of a vector on op's output grid from the coarse grid
+ * of `fine` to `fine` (same op), extrapolating linearly at the ends. */
+sip_status sip_prolong(const sip_grid *fine, int op, int dtype,
+                       const void *uc_dev, void *uf_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIP_H */

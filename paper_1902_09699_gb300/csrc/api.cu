@@ -1,0 +1,631 @@
+// C ABI of libsip.so: handle life cycle, layout of the device arena, launch
+// sequencing of Algorithm PARSDMM / ML-PARSDMM, and the single-step entry
+// points.  Every argument check happens here, on the host, before any
+// device work; kernels assume validated layouts.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sip.h"
+#include "sip_dev.cuh"
+#include "sip_kernels.h"
+#include "sip_host.h"
+
+namespace sip {
+
+thread_local std::string g_err;
+
+sip_status fail(sip_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(SIP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static size_t esize(int dtype) { return dtype == SIP_F64 ? 8 : 4; }
+static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// ----------------------------------------------------------------------------
+// grid and operator geometry
+// ----------------------------------------------------------------------------
+GridDesc grid_desc(const sip_grid &g) {
+  GridDesc d;
+  d.ndim = g.ndim;
+  d.n[0] = g.n[0];
+  d.n[1] = g.n[1];
+  d.n[2] = g.ndim == 3 ? g.n[2] : 1;
+  d.h[0] = g.h[0];
+  d.h[1] = g.h[1];
+  d.h[2] = g.ndim == 3 ? g.h[2] : 1.0;
+  return d;
+}
+
+std::vector<int> op_parts(const GridDesc &g, int op) {
+  switch (op) {
+    case SIP_OP_I: return {SEG_I};
+    case SIP_OP_DZ: return {SEG_DZ};
+    case SIP_OP_DX: return {SEG_DX};
+    case SIP_OP_DY: return {SEG_DY};
+    default:
+      if (g.ndim == 3) return {SEG_DZ, SEG_DX, SEG_DY};
+      return {SEG_DZ, SEG_DX};
+  }
+}
+
+int64_t part_rows(const GridDesc &g, int kind) {
+  switch (kind) {
+    case SEG_DZ: return (g.n[0] - 1) * g.n[1] * g.n[2];
+    case SEG_DX: return g.n[0] * (g.n[1] - 1) * g.n[2];
+    case SEG_DY: return g.n[0] * g.n[1] * (g.n[2] - 1);
+    default: return g.N();
+  }
+}
+
+int64_t op_rows(const GridDesc &g, int op) {
+  int64_t m = 0;
+  for (int k : op_parts(g, op)) m += part_rows(g, k);
+  return m;
+}
+
+// output-grid dims (nz, nx, ny) of one part and the staggered axis
+void part_dims(const GridDesc &g, int kind, int64_t d[3], int &stag) {
+  d[0] = g.n[0];
+  d[1] = g.n[1];
+  d[2] = g.n[2];
+  stag = -1;
+  if (kind == SEG_DZ) { d[0] -= 1; stag = 0; }
+  if (kind == SEG_DX) { d[1] -= 1; stag = 1; }
+  if (kind == SEG_DY) { d[2] -= 1; stag = 2; }
+}
+
+static sip_status check_grid(const sip_grid *g) {
+  if (!g) return fail(SIP_ERR_INVALID_ARG, "grid is NULL");
+  if (g->ndim != 2 && g->ndim != 3) return fail(SIP_ERR_INVALID_ARG, "grid.ndim must be 2 or 3 (got %d)", g->ndim);
+  for (int a = 0; a < g->ndim; ++a) {
+    if (g->n[a] < 1) return fail(SIP_ERR_INVALID_ARG, "grid.n[%d] = %lld < 1", a, (long long)g->n[a]);
+    if (!(g->h[a] > 0.0) || !std::isfinite(g->h[a]))
+      return fail(SIP_ERR_INVALID_ARG, "grid.h[%d] must be finite and > 0", a);
+  }
+  const GridDesc d = grid_desc(*g);
+  if (d.N() >= (int64_t(1) << 31) / 4) return fail(SIP_ERR_INVALID_ARG, "grid too large (N = %lld)", (long long)d.N());
+  return SIP_OK;
+}
+
+static sip_status check_op(const GridDesc &g, int op) {
+  if (op < SIP_OP_I || op > SIP_OP_TV) return fail(SIP_ERR_INVALID_ARG, "unknown operator %d", op);
+  if (op == SIP_OP_DY && g.ndim != 3) return fail(SIP_ERR_INVALID_ARG, "D_y needs a 3D grid");
+  if ((op == SIP_OP_DZ || op == SIP_OP_TV) && g.n[0] < 2) return fail(SIP_ERR_INVALID_ARG, "operator needs n_z >= 2");
+  if ((op == SIP_OP_DX || op == SIP_OP_TV) && g.n[1] < 2) return fail(SIP_ERR_INVALID_ARG, "operator needs n_x >= 2");
+  if ((op == SIP_OP_DY || (op == SIP_OP_TV && g.ndim == 3)) && g.n[2] < 2)
+    return fail(SIP_ERR_INVALID_ARG, "operator needs n_y >= 2");
+  return SIP_OK;
+}
+
+static sip_status check_set(const GridDesc &g, const sip_set &s, int i) {
+  sip_status st = check_op(g, s.op);
+  if (st) return fail(st, "set %d: %s", i, g_err.c_str());
+  switch (s.type) {
+    case SIP_SET_BOUNDS:
+      if (std::isnan(s.lo) || std::isnan(s.hi) || s.lo > s.hi)
+        return fail(SIP_ERR_INVALID_ARG, "set %d: bounds need lo <= hi", i);
+      break;
+    case SIP_SET_L1:
+    case SIP_SET_L2:
+      if (!(s.sigma >= 0.0) || !std::isfinite(s.sigma)) return fail(SIP_ERR_INVALID_ARG, "set %d: sigma < 0", i);
+      if (!(s.sigma_rel >= 0.0) || !std::isfinite(s.sigma_rel))
+        return fail(SIP_ERR_INVALID_ARG, "set %d: sigma_rel < 0", i);
+      break;
+    case SIP_SET_CARD:
+      if (s.k < 0) return fail(SIP_ERR_INVALID_ARG, "set %d: k < 0", i);
+      if (!(s.k_frac >= 0.0) || !(s.k_frac <= 1.0)) return fail(SIP_ERR_INVALID_ARG, "set %d: k_frac not in [0, 1]", i);
+      break;
+    default:
+      return fail(SIP_ERR_INVALID_ARG, "set %d: unknown set type %d", i, s.type);
+  }
+  return SIP_OK;
+}
+
+static sip_status check_opts(const sip_options &o) {
+  if (o.max_iter < 1) return fail(SIP_ERR_INVALID_ARG, "max_iter must be >= 1");
+  if (o.cg_iters < 0 || o.cg_max < 1 || o.cg_iters > 1000 || o.cg_max > 1000)
+    return fail(SIP_ERR_INVALID_ARG, "cg_iters in [0, 1000], cg_max in [1, 1000]");
+  if (o.check_every < 1) return fail(SIP_ERR_INVALID_ARG, "check_every must be >= 1");
+  if (o.evol_hist < 1 || o.evol_hist > kMaxHist) return fail(SIP_ERR_INVALID_ARG, "evol_hist must be in [1, %d]", kMaxHist);
+  if (o.stop < 0 || o.stop > 2) return fail(SIP_ERR_INVALID_ARG, "stop must be 0, 1 or 2");
+  if (o.adapt < 0 || o.adapt > 2) return fail(SIP_ERR_INVALID_ARG, "adapt must be 0, 1 or 2");
+  if (o.adapt_every < 1) return fail(SIP_ERR_INVALID_ARG, "adapt_every must be >= 1");
+  if (!(o.rho0 > 0.0) || !std::isfinite(o.rho0)) return fail(SIP_ERR_INVALID_ARG, "rho0 must be > 0");
+  if (!(o.gamma0 > 0.0) || !(o.gamma0 < 2.0)) return fail(SIP_ERR_INVALID_ARG, "gamma0 must be in (0, 2)");
+  if (!(o.rho_ratio_max >= 1.0)) return fail(SIP_ERR_INVALID_ARG, "rho_ratio_max must be >= 1");
+  if (!(o.gamma_max > 0.0) || !(o.gamma_max < 2.0)) return fail(SIP_ERR_INVALID_ARG, "gamma_max must be in (0, 2)");
+  if (o.form != SIP_FORM_ALG1 && o.form != SIP_FORM_DIRECT) return fail(SIP_ERR_INVALID_ARG, "unknown form");
+  if (o.dtype != SIP_F64 && o.dtype != SIP_F32) return fail(SIP_ERR_INVALID_ARG, "unknown dtype");
+  if (o.levels != 1 && o.levels != 2) return fail(SIP_ERR_INVALID_ARG, "levels must be 1 or 2");
+  if (o.coarse_iter < 0) return fail(SIP_ERR_INVALID_ARG, "coarse_iter < 0");
+  if (o.levels == 2 && (o.rho_schedule || o.gamma_schedule || o.trace))
+    return fail(SIP_ERR_INVALID_ARG, "schedules and traces are single-level only");
+  if (o.gamma_schedule && !o.rho_schedule) return fail(SIP_ERR_INVALID_ARG, "gamma_schedule needs rho_schedule");
+  return SIP_OK;
+}
+
+sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const sip_options *opts) {
+  sip_status st = check_grid(grid);
+  if (st) return st;
+  if (!sets) return fail(SIP_ERR_INVALID_ARG, "sets is NULL");
+  if (!opts) return fail(SIP_ERR_INVALID_ARG, "opts is NULL");
+  if (nsets < 1 || nsets > kMaxSets) return fail(SIP_ERR_INVALID_ARG, "nsets must be in [1, %d]", kMaxSets);
+  const GridDesc g = grid_desc(*grid);
+  for (int i = 0; i < nsets; ++i)
+    if ((st = check_set(g, sets[i], i))) return st;
+  return check_opts(*opts);
+}
+
+// ----------------------------------------------------------------------------
+// instance layout (host description; device pointers filled at placement)
+// ----------------------------------------------------------------------------
+InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const sip_options &o) {
+  InstLayout L;
+  L.g = g;
+  L.opts = o;
+  InstDev &d = L.dev;
+  memset(&d, 0, sizeof d);
+  d.nz = (int32_t)g.n[0];
+  d.nx = (int32_t)g.n[1];
+  d.ny = (int32_t)g.n[2];
+  d.ndim = g.ndim;
+  d.ihz = 1.0 / g.h[0];
+  d.ihx = 1.0 / g.h[1];
+  d.ihy = 1.0 / g.h[2];
+  d.N = g.N();
+  d.p = nsets;
+  d.alg1 = o.form == SIP_FORM_ALG1 ? 1 : 0;
+  d.nb = nsets + d.alg1;
+  d.hist = o.evol_hist;
+  d.max_iter = o.max_iter;
+  d.cg_iters = o.cg_iters;
+  d.cg_max = o.cg_max;
+  d.check_every = o.check_every;
+  d.stop = o.stop;
+  d.adapt = o.adapt;
+  d.adapt_every = o.adapt_every;
+  d.eps_feas = o.eps_feas;
+  d.eps_evol = o.eps_evol;
+  d.rho0 = o.rho0;
+  d.gamma0 = o.gamma0;
+  d.eps_corr = o.eps_corr;
+  d.rho_ratio_max = o.rho_ratio_max;
+  d.gamma_max = o.gamma_max;
+
+  int64_t yoff = 0, woff = 0, soff = 0;
+  int nseg = 0;
+  for (int b = 0; b < d.nb; ++b) {
+    BlockDev &bd = d.blk[b];
+    if (b < nsets) {
+      const sip_set &s = sets[b];
+      bd.op = s.op;
+      bd.type = s.type == SIP_SET_BOUNDS ? BT_BOUNDS : s.type == SIP_SET_L1 ? BT_L1 : s.type == SIP_SET_L2 ? BT_L2 : BT_CARD;
+      bd.lo = s.lo;
+      bd.hi = s.hi;
+      bd.sigma_abs = s.sigma;
+      bd.sigma_rel = (s.type == SIP_SET_L1 || s.type == SIP_SET_L2) ? s.sigma_rel : 0.0;
+      bd.k_abs = s.k;
+      bd.k_frac = s.type == SIP_SET_CARD ? s.k_frac : 0.0;
+    } else {
+      bd.op = SIP_OP_I;
+      bd.type = BT_DIST;
+    }
+    bd.M = op_rows(g, bd.op);
+    bd.yoff = yoff;
+    yoff += bd.M;
+    bd.woff = bd.soff = -1;
+    bd.job_w = bd.job_s = -1;
+    if (bd.type == BT_L1 || bd.type == BT_L2 || bd.type == BT_CARD) {
+      bd.woff = woff;
+      woff += bd.M;
+    }
+    if (bd.type == BT_L1 || bd.type == BT_CARD) {
+      bd.soff = soff;
+      soff += bd.M;
+    }
+    bd.seg0 = nseg;
+    int64_t row0 = 0;
+    for (int kind : op_parts(g, bd.op)) {
+      SegDev &sg = d.seg[nseg++];
+      sg.kind = kind;
+      sg.block = b;
+      sg.row0 = row0;
+      sg.len = part_rows(g, kind);
+      row0 += sg.len;
+    }
+    bd.nseg = nseg - bd.seg0;
+  }
+  SegDev &ring = d.seg[nseg++];
+  ring.kind = SEG_RING;
+  ring.block = -1;
+  ring.row0 = 0;
+  ring.len = d.N;
+  d.nseg = nseg;
+  L.Mtot = yoff;
+  L.Mw = woff;
+  L.Ms = soff;
+  // selection jobs (local numbering; made global at placement)
+  for (int b = 0; b < d.nb; ++b) {
+    BlockDev &bd = d.blk[b];
+    if (bd.type != BT_L1 && bd.type != BT_CARD) continue;
+    for (int feas = 0; feas < 2; ++feas) {
+      JobDev j;
+      memset(&j, 0, sizeof j);
+      j.block = b;
+      j.kind = bd.type == BT_L1 ? JOB_L1 : JOB_TOPK;
+      j.feas = feas;
+      j.M = bd.M;
+      j.data_off = feas ? bd.soff : bd.woff;
+      j.ntiles = (int32_t)((bd.M + kTile - 1) / kTile);
+      (feas ? bd.job_s : bd.job_w) = (int)L.jobs.size();
+      L.jobs.push_back(j);
+    }
+  }
+  return L;
+}
+
+// Algorithmic bytes per iteration of the fused schedule (see sip.h).
+double layout_bytes_per_iter(const InstLayout &L, int dtype) {
+  const InstDev &d = L.dev;
+  const double W = (double)esize(dtype);
+  const double N = (double)d.N, Mp = (double)L.Mtot;
+  const int ncg = L.opts.cg_iters > 0 ? L.opts.cg_iters : 5;
+  const int rsel = select_passes(dtype);
+  double words = 2 * Mp + 2 * N + (d.alg1 ? 0 : N);  // rhs: y, v, x read; r write (+ m)
+  words += ncg * 10.0 * N;                            // CG: p, q, x, r traffic per step
+  words += 4 * Mp + N + (d.alg1 ? N : 0);             // set pass: x, y, v read, y, v write (+ m)
+  double feas = 0.0;
+  for (int b = 0; b < d.nb; ++b) {
+    const BlockDev &bd = d.blk[b];
+    if (bd.type == BT_L2) words += 2.0 * bd.M;
+    if (bd.type == BT_L1 || bd.type == BT_CARD) {
+      words += (2.0 + rsel) * bd.M;
+      feas += (1.0 + rsel) * bd.M;
+    }
+  }
+  words += 2 * N;                                      // x history write + read
+  if (L.opts.adapt && !L.opts.rho_schedule) words += 8 * Mp / L.opts.adapt_every;
+  words += (feas + d.hist * N) / L.opts.check_every;
+  return words * W;
+}
+
+// ----------------------------------------------------------------------------
+// plan: one or more instances placed in one device arena
+// ----------------------------------------------------------------------------
+static void push_tiles(std::vector<Tile> &v, int inst, int item, int64_t n) {
+  int seq = 0;
+  for (int64_t s = 0; s < n; s += kTile, ++seq) {
+    Tile t;
+    t.inst = inst;
+    t.item = item;
+    t.start = s;
+    t.len = (int32_t)(n - s < kTile ? n - s : kTile);
+    t.seq = seq;
+    v.push_back(t);
+  }
+}
+
+void Plan::release() {
+  if (graph) cudaGraphExecDestroy(graph);
+  graph = nullptr;
+  if (arena) cudaFree(arena);
+  arena = nullptr;
+}
+
+sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m) {
+  P.dtype = dtype;
+  P.ninst = (int)insts.size();
+  const size_t W = esize(dtype);
+  // ---- sizes
+  int64_t njobs = 0, ntie = 0;
+  std::vector<Tile> tn, tset, tsel, tfin;
+  P.any_card = P.any_fin = false;
+  P.cg_launch = 0;
+  P.max_iter = 0;
+  P.check_every = 1 << 30;
+  P.any_stop = false;
+  for (int i = 0; i < P.ninst; ++i) {
+    InstLayout &L = insts[i];
+    InstDev &d = L.dev;
+    d.job0 = (int32_t)njobs;
+    d.njob = (int32_t)L.jobs.size();
+    for (int b = 0; b < d.nb; ++b) {
+      if (d.blk[b].job_w >= 0) d.blk[b].job_w += (int32_t)njobs;
+      if (d.blk[b].job_s >= 0) d.blk[b].job_s += (int32_t)njobs;
+    }
+    for (auto &j : L.jobs) {
+      j.inst = i;
+      j.hist_off = (int64_t)(njobs++) * kBins;
+      j.tie_off = ntie;
+      ntie += j.ntiles;
+    }
+    const size_t b0 = tn.size();
+    push_tiles(tn, i, 0, d.N);
+    d.nt_n = (int32_t)(tn.size() - b0);
+    const size_t b1 = tset.size();
+    for (int s = 0; s < d.nseg; ++s) push_tiles(tset, i, s, d.seg[s].len);
+    d.nt_set = (int32_t)(tset.size() - b1);
+    const size_t b2 = tfin.size();
+    for (int b = 0; b < d.nb; ++b) {
+      const int t = d.blk[b].type;
+      if (t == BT_L1 || t == BT_L2 || t == BT_CARD) {
+        push_tiles(tfin, i, b, d.blk[b].M);
+        P.any_fin = true;
+      }
+      if (t == BT_CARD) P.any_card = true;
+    }
+    d.nt_fin = (int32_t)(tfin.size() - b2);
+    for (int j = 0; j < (int)L.jobs.size(); ++j) push_tiles(tsel, i, d.job0 + j, L.jobs[j].M);
+    const int cgl = L.opts.cg_iters > 0 ? L.opts.cg_iters : L.opts.cg_max;
+    if (cgl > P.cg_launch) P.cg_launch = cgl;
+    if (L.opts.max_iter > P.max_iter) P.max_iter = L.opts.max_iter;
+    if (L.opts.check_every < P.check_every) P.check_every = L.opts.check_every;
+    if (L.opts.stop) P.any_stop = true;
+  }
+  P.nt_n = (int)tn.size();
+  P.nt_set = (int)tset.size();
+  P.nt_sel = (int)tsel.size();
+  P.nt_fin = (int)tfin.size();
+  P.njobs = (int)njobs;
+
+  // ---- arena layout
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    const int64_t o = off;
+    off = align_up(off + (bytes > 0 ? bytes : 0), 256);
+    return o;
+  };
+  struct Offs {
+    int64_t x, y, v, r, p0, p1, q, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace;
+  };
+  std::vector<Offs> offs(P.ninst);
+  // warm state (x, y, v) of all instances first, then the rest of the state,
+  // then everything else: memsets stay contiguous
+  for (int i = 0; i < P.ninst; ++i) {
+    offs[i].x = take(insts[i].dev.N * W);
+    offs[i].y = take(insts[i].Mtot * W);
+    offs[i].v = take(insts[i].Mtot * W);
+  }
+  P.warm_end = off;
+  for (int i = 0; i < P.ninst; ++i) {
+    const InstLayout &L = insts[i];
+    const int64_t N = L.dev.N;
+    const bool ad = L.opts.adapt != 0;
+    offs[i].r = take(N * W);
+    offs[i].p0 = take(N * W);
+    offs[i].p1 = take(N * W);
+    offs[i].q = take(N * W);
+    offs[i].ring = take((int64_t)L.dev.hist * N * W);
+    offs[i].w = take(L.Mw * W);
+    offs[i].s = take(L.Ms * W);
+    offs[i].k0s = ad ? take(L.Mtot * W) : -1;
+    offs[i].k0vh = ad ? take(L.Mtot * W) : -1;
+    offs[i].k0y = ad ? take(L.Mtot * W) : -1;
+    offs[i].k0v = ad ? take(L.Mtot * W) : -1;
+  }
+  P.state_end = off;
+  for (int i = 0; i < P.ninst; ++i) {
+    const InstLayout &L = insts[i];
+    offs[i].m = own_m ? take(L.dev.N * W) : -1;
+    offs[i].sched_r = L.opts.rho_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
+    offs[i].sched_g = L.opts.gamma_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
+    offs[i].trace = L.opts.trace ? take((int64_t)L.opts.max_iter * (2 * L.dev.nb + 2 + L.dev.p) * 8) : -1;
+  }
+  const int64_t o_insts = take((int64_t)P.ninst * sizeof(InstDev));
+  const int64_t o_scal = take((int64_t)P.ninst * sizeof(InstScal));
+  const int64_t o_jobs = take((int64_t)njobs * sizeof(JobDev));
+  const int64_t o_jscal = take((int64_t)njobs * sizeof(JobScal));
+  P.hist_begin = off;
+  const int64_t o_hcnt = take((int64_t)njobs * kBins * 4);
+  const int64_t o_hs1 = take((int64_t)njobs * kBins * 8);
+  const int64_t o_hs2 = take((int64_t)njobs * kBins * 8);
+  P.hist_end = off;
+  const int64_t o_ties = take(ntie * 4);
+  const int64_t o_tn = take((int64_t)tn.size() * sizeof(Tile));
+  const int64_t o_tset = take((int64_t)tset.size() * sizeof(Tile));
+  const int64_t o_tsel = take((int64_t)tsel.size() * sizeof(Tile));
+  const int64_t o_tfin = take((int64_t)tfin.size() * sizeof(Tile));
+  P.arena_bytes = off;
+
+  if (cudaMalloc(&P.arena, (size_t)off) != cudaSuccess) {
+    cudaGetLastError();
+    P.arena = nullptr;
+    return fail(SIP_ERR_OOM, "device allocation of %lld bytes failed", (long long)off);
+  }
+  char *base = (char *)P.arena;
+  auto at = [&](int64_t o) -> void * { return o < 0 ? nullptr : (void *)(base + o); };
+  P.h_insts.resize(P.ninst);
+  P.layouts = insts;
+  for (int i = 0; i < P.ninst; ++i) {
+    InstDev &d = insts[i].dev;
+    const Offs &o = offs[i];
+    d.x = at(o.x);
+    d.y = at(o.y);
+    d.v = at(o.v);
+    d.r = at(o.r);
+    d.p0 = at(o.p0);
+    d.p1 = at(o.p1);
+    d.q = at(o.q);
+    d.ring = at(o.ring);
+    d.w = at(o.w);
+    d.s = at(o.s);
+    d.k0s = at(o.k0s);
+    d.k0vh = at(o.k0vh);
+    d.k0y = at(o.k0y);
+    d.k0v = at(o.k0v);
+    d.m = at(o.m);
+    d.rho_sched = (const double *)at(o.sched_r);
+    d.gamma_sched = (const double *)at(o.sched_g);
+    d.trace = (double *)at(o.trace);
+    d.trace_w = 2 * d.nb + 2 + d.p;
+    P.h_insts[i] = d;
+    P.layouts[i] = insts[i];
+  }
+  P.m_own = own_m;
+  P.d_insts = (InstDev *)at(o_insts);
+  P.d_scal = (InstScal *)at(o_scal);
+  P.d_jobs = (JobDev *)at(o_jobs);
+  P.d_jscal = (JobScal *)at(o_jscal);
+  P.d_hcnt = (uint32_t *)at(o_hcnt);
+  P.d_hs1 = (double *)at(o_hs1);
+  P.d_hs2 = (double *)at(o_hs2);
+  P.d_ties = (uint32_t *)at(o_ties);
+  P.d_tn = (Tile *)at(o_tn);
+  P.d_tset = (Tile *)at(o_tset);
+  P.d_tsel = (Tile *)at(o_tsel);
+  P.d_tfin = (Tile *)at(o_tfin);
+
+  std::vector<JobDev> jobs;
+  for (auto &L : insts)
+    for (auto &j : L.jobs) jobs.push_back(j);
+  CK(cudaMemset(P.arena, 0, (size_t)off));
+  CK(cudaMemcpy(P.d_insts, P.h_insts.data(), P.ninst * sizeof(InstDev), cudaMemcpyHostToDevice));
+  if (njobs) CK(cudaMemcpy(P.d_jobs, jobs.data(), njobs * sizeof(JobDev), cudaMemcpyHostToDevice));
+  if (!tn.empty()) CK(cudaMemcpy(P.d_tn, tn.data(), tn.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  if (!tset.empty()) CK(cudaMemcpy(P.d_tset, tset.data(), tset.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  if (!tsel.empty()) CK(cudaMemcpy(P.d_tsel, tsel.data(), tsel.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  if (!tfin.empty()) CK(cudaMemcpy(P.d_tfin, tfin.data(), tfin.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  return SIP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// launch sequencing
+// ----------------------------------------------------------------------------
+static sip_status enqueue_iteration(Plan &P, cudaStream_t st, KernelTimer *tm) {
+  const Launch L{P.dtype, st};
+  auto T0 = [&](int c) { if (tm) tm->begin(c, st); };
+  auto T1 = [&](int c) { if (tm) tm->end(c, st); };
+  T0(KT_RHS);
+  CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
+  T1(KT_RHS);
+  for (int j = 0; j < P.cg_launch; ++j) {
+    T0(KT_CG_DIR);
+    CK(launch_cg_dir(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
+    T1(KT_CG_DIR);
+    T0(KT_CG_UPD);
+    CK(launch_cg_upd(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
+    T1(KT_CG_UPD);
+  }
+  T0(KT_SETPASS);
+  CK(launch_setpass(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs));
+  T1(KT_SETPASS);
+  if (P.nt_sel) {
+    const int np = select_passes(P.dtype);
+    for (int pass = 0; pass < np; ++pass) {
+      T0(KT_SELECT);
+      CK(launch_select(L, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
+                       pass));
+      T1(KT_SELECT);
+    }
+  }
+  if (P.any_card) {
+    T0(KT_TIES);
+    CK(launch_ties(L, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
+    T1(KT_TIES);
+  }
+  if (P.nt_fin) {
+    T0(KT_FINAL);
+    CK(launch_final(L, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
+    T1(KT_FINAL);
+  }
+  T0(KT_TAIL);
+  CK(launch_tail(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst));
+  T1(KT_TAIL);
+  return SIP_OK;
+}
+
+static sip_status build_graph(Plan &P, cudaStream_t cap, int iters) {
+  if (P.graph && P.graph_iters == iters) return SIP_OK;
+  if (P.graph) {
+    cudaGraphExecDestroy(P.graph);
+    P.graph = nullptr;
+  }
+  CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  sip_status st = SIP_OK;
+  for (int i = 0; i < iters && st == SIP_OK; ++i) st = enqueue_iteration(P, cap, nullptr);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap, &g);
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(SIP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&P.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    P.graph = nullptr;
+    return fail(SIP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  P.graph_iters = iters;
+  return SIP_OK;
+}
+
+// Run `iters` iterations (kernels no-op once an instance is done).
+sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,
+                          KernelTimer *tm) {
+  if (tm) {
+    for (int i = 0; i < iters; ++i) {
+      sip_status s = enqueue_iteration(P, st, tm);
+      if (s) return s;
+    }
+    return SIP_OK;
+  }
+  const int chunk = poll ? P.check_every : (iters < 10 ? iters : 10);
+  sip_status s = build_graph(P, cap, chunk);
+  if (s) return s;
+  int done_iters = 0;
+  while (done_iters < iters) {
+    CK(cudaGraphLaunch(P.graph, st));
+    done_iters += chunk;
+    if (poll && done_iters < iters) {
+      // all instances done?  (one flag per instance; single-instance plans)
+      CK(cudaMemcpyAsync(pinned_flag, &P.d_scal[0].done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (*pinned_flag) break;
+    }
+  }
+  return SIP_OK;
+}
+
+sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm) {
+  const Launch L{P.dtype, st};
+  char *base = (char *)P.arena;
+  if (warm) {
+    CK(cudaMemsetAsync(base + P.warm_end, 0, (size_t)(P.state_end - P.warm_end), st));
+    for (int i = 0; i < P.ninst; ++i)  // x^0 into the history ring
+      CK(cudaMemcpyAsync(P.h_insts[i].ring, P.h_insts[i].x, (size_t)P.h_insts[i].N * esize(P.dtype),
+                         cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK(cudaMemsetAsync(base, 0, (size_t)P.state_end, st));
+  }
+  CK(cudaMemsetAsync(base + P.hist_begin, 0, (size_t)(P.hist_end - P.hist_begin), st));
+  CK(launch_init(L, P.d_insts, P.d_scal, P.ninst));
+  CK(launch_norms(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal));
+  return SIP_OK;
+}
+
+sip_status plan_set_m(Plan &P, int inst, const void *m, cudaStream_t st) {
+  P.h_insts[inst].m = m;
+  CK(cudaMemcpyAsync(&P.d_insts[inst].m, &P.h_insts[inst].m, sizeof(void *), cudaMemcpyHostToDevice, st));
+  return SIP_OK;
+}
+
+}  // namespace sip

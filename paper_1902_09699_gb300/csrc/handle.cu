@@ -1,0 +1,538 @@
+// extern "C" entry points of libsip.so (declared in include/sip.h).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sip.h"
+#include "sip_dev.cuh"
+#include "sip_host.h"
+#include "sip_kernels.h"
+
+using namespace sip;
+
+struct sip_handle {
+  Plan lev[2];      // lev[0]: finest grid; lev[1]: coarse grid (two-level ML)
+  int levels = 1;
+  sip_options opts;
+  sip_grid grid;
+  std::vector<sip_set> sets;
+  cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+  int32_t *pinned = nullptr;   // pinned flag for the stopping-rule poll
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timing = false;
+  KernelTimer timer;
+  std::string err;
+};
+
+namespace {
+
+#define CKH(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(SIP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t esz(int dtype) { return dtype == SIP_F64 ? 8 : 4; }
+
+sip_status keep(sip_handle *h, sip_status s) {
+  if (h && s != SIP_OK) h->err = g_err;
+  return s;
+}
+
+sip_grid coarse_of(const sip_grid &g) {
+  sip_grid c = g;
+  for (int a = 0; a < g.ndim; ++a) {
+    c.n[a] = (g.n[a] + 1) / 2;
+    c.h[a] = 2.0 * g.h[a];
+  }
+  return c;
+}
+
+// minimal InstDev describing one grid and the parts of one operator
+InstDev op_inst(const GridDesc &g, int op) {
+  InstDev d;
+  memset(&d, 0, sizeof d);
+  d.nz = (int32_t)g.n[0];
+  d.nx = (int32_t)g.n[1];
+  d.ny = (int32_t)g.n[2];
+  d.ndim = g.ndim;
+  d.ihz = 1.0 / g.h[0];
+  d.ihx = 1.0 / g.h[1];
+  d.ihy = 1.0 / g.h[2];
+  d.N = g.N();
+  int64_t row0 = 0;
+  for (int kind : op_parts(g, op)) {
+    SegDev &s = d.seg[d.nseg++];
+    s.kind = kind;
+    s.block = 0;
+    s.row0 = row0;
+    s.len = part_rows(g, kind);
+    row0 += s.len;
+  }
+  return d;
+}
+
+// Temporary device copy of a small host struct (single-step calls only).
+template <typename S>
+struct DevCopy {
+  S *p = nullptr;
+  cudaError_t make(const S &h) {
+    cudaError_t e = cudaMalloc(&p, sizeof(S));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(p, &h, sizeof(S), cudaMemcpyHostToDevice);
+  }
+  ~DevCopy() {
+    if (p) cudaFree(p);
+  }
+};
+
+sip_status check_grid_op(const sip_grid *grid, int op) {
+  if (!grid) return fail(SIP_ERR_INVALID_ARG, "grid is NULL");
+  sip_set s;
+  memset(&s, 0, sizeof s);
+  s.op = op;
+  s.type = SIP_SET_BOUNDS;
+  s.lo = -INFINITY;
+  s.hi = INFINITY;
+  sip_options o;
+  sip_options_default(&o);
+  return validate(grid, &s, 1, &o);
+}
+
+}  // namespace
+
+extern "C" {
+
+void sip_options_default(sip_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->max_iter = 200;
+  o->cg_iters = 5;
+  o->cg_max = 100;
+  o->eps_feas = 1e-3;
+  o->eps_evol = 1e-2;
+  o->check_every = 5;
+  o->evol_hist = 5;
+  o->stop = 0;
+  o->adapt = 1;
+  o->adapt_every = 2;
+  o->rho0 = 1.0;
+  o->gamma0 = 1.5;
+  o->eps_corr = 0.3;
+  o->rho_ratio_max = 1e3;
+  o->gamma_max = 1.99;
+  o->form = SIP_FORM_ALG1;
+  o->dtype = SIP_F32;
+  o->levels = 1;
+  o->coarse_iter = 0;
+}
+
+const char *sip_last_error(const sip_handle *h) {
+  if (h && !h->err.empty()) return h->err.c_str();
+  return g_err.c_str();
+}
+
+sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets, const sip_options *opts,
+                      sip_handle **out) {
+  if (!out) return fail(SIP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  sip_status st = validate(grid, sets, nsets, opts);
+  if (st) return st;
+  sip_grid cgrid;
+  if (opts->levels == 2) {
+    cgrid = coarse_of(*grid);
+    if ((st = validate(&cgrid, sets, nsets, opts))) return fail(st, "coarse level: %s", g_err.c_str());
+  }
+  sip_handle *h = new (std::nothrow) sip_handle();
+  if (!h) return fail(SIP_ERR_OOM, "host allocation failed");
+  h->opts = *opts;
+  h->grid = *grid;
+  h->sets.assign(sets, sets + nsets);
+  h->levels = opts->levels;
+  auto bail = [&](sip_status s) {
+    sip_destroy(h);
+    return s;
+  };
+  {
+    std::vector<InstLayout> L{make_layout(grid_desc(*grid), sets, nsets, *opts)};
+    if ((st = plan_build(h->lev[0], L, opts->dtype, false))) return bail(st);
+  }
+  if (opts->levels == 2) {
+    sip_options oc = *opts;
+    oc.max_iter = opts->coarse_iter > 0 ? opts->coarse_iter : opts->max_iter;
+    std::vector<InstLayout> L{make_layout(grid_desc(cgrid), sets, nsets, oc)};
+    if ((st = plan_build(h->lev[1], L, opts->dtype, true))) return bail(st);
+  }
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&h->pinned, sizeof(int32_t)) != cudaSuccess || cudaEventCreate(&h->ev0) != cudaSuccess ||
+      cudaEventCreate(&h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(SIP_ERR_CUDA, "stream/event set-up failed"));
+  }
+  *out = h;
+  return SIP_OK;
+}
+
+sip_status sip_destroy(sip_handle *h) {
+  if (!h) return SIP_OK;
+  for (auto &P : h->lev) P.release();
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+  return SIP_OK;
+}
+
+int64_t sip_device_bytes(const sip_handle *h) {
+  if (!h) return 0;
+  return h->lev[0].arena_bytes + h->lev[1].arena_bytes;
+}
+
+double sip_bytes_per_iter(const sip_handle *h) {
+  if (!h || h->lev[0].layouts.empty()) return 0.0;
+  return layout_bytes_per_iter(h->lev[0].layouts[0], h->opts.dtype);
+}
+
+static sip_status prolong_state(Plan &C, Plan &F, cudaStream_t st) {
+  const Launch L{F.dtype, st};
+  const InstLayout &lc = C.layouts[0], &lf = F.layouts[0];
+  const InstDev &dc = C.h_insts[0], &df = F.h_insts[0];
+  const size_t W = esz(F.dtype);
+  int64_t cd[3], fd[3];
+  int stag;
+  part_dims(lc.g, SEG_I, cd, stag);
+  part_dims(lf.g, SEG_I, fd, stag);
+  CKH(launch_prolong(L, cd, fd, -1, dc.x, df.x));
+  for (int b = 0; b < dc.nb; ++b) {
+    const BlockDev &bc = dc.blk[b], &bf = df.blk[b];
+    for (int s = 0; s < bc.nseg; ++s) {
+      const SegDev &sc = dc.seg[bc.seg0 + s], &sf = df.seg[bf.seg0 + s];
+      part_dims(lc.g, sc.kind, cd, stag);
+      part_dims(lf.g, sf.kind, fd, stag);
+      const int64_t oc = (bc.yoff + sc.row0) * W, of = (bf.yoff + sf.row0) * W;
+      CKH(launch_prolong(L, cd, fd, stag, (char *)dc.y + oc, (char *)df.y + of));
+      CKH(launch_prolong(L, cd, fd, stag, (char *)dc.v + oc, (char *)df.v + of));
+    }
+  }
+  return SIP_OK;
+}
+
+static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cudaStream_t st, sip_info *info) {
+  Plan &F = h->lev[0];
+  const sip_options &o = h->opts;
+  const size_t W = esz(o.dtype);
+  const InstDev &df = F.h_insts[0];
+  KernelTimer *tm = h->timing ? &h->timer : nullptr;
+  CKH(cudaEventRecord(h->ev0, st));
+  if (h->levels == 2) {
+    Plan &C = h->lev[1];
+    const Launch L{o.dtype, st};
+    int64_t fd[3], cd[3];
+    int stag;
+    part_dims(F.layouts[0].g, SEG_I, fd, stag);
+    part_dims(C.layouts[0].g, SEG_I, cd, stag);
+    CKH(launch_restrict(L, fd, cd, m_dev, (void *)C.h_insts[0].m));
+    sip_status s = plan_prepare(C, st, false);
+    if (!s) s = run_iterations(C, st, h->cap, C.max_iter, o.stop != 0, h->pinned, tm);
+    if (!s) s = prolong_state(C, F, st);
+    if (!s) s = plan_set_m(F, 0, m_dev, st);
+    if (!s) s = plan_prepare(F, st, true);
+    if (s) return s;
+  } else {
+    sip_status s = plan_set_m(F, 0, m_dev, st);
+    if (s) return s;
+    const int nb = df.nb;
+    if (o.rho_schedule)
+      CKH(cudaMemcpyAsync((void *)df.rho_sched, o.rho_schedule, (size_t)o.max_iter * nb * 8, cudaMemcpyHostToDevice, st));
+    if (o.gamma_schedule)
+      CKH(cudaMemcpyAsync((void *)df.gamma_sched, o.gamma_schedule, (size_t)o.max_iter * nb * 8,
+                          cudaMemcpyHostToDevice, st));
+    if ((s = plan_prepare(F, st, false))) return s;
+  }
+  sip_status s = run_iterations(F, st, h->cap, F.max_iter, o.stop != 0, h->pinned, tm);
+  if (s) return s;
+  CKH(cudaMemcpyAsync(x_dev, df.x, (size_t)df.N * W, cudaMemcpyDeviceToDevice, st));
+  CKH(cudaEventRecord(h->ev1, st));
+  const bool sync = info || o.trace || tm;
+  if (!sync) return SIP_OK;
+  CKH(cudaStreamSynchronize(st));
+  if (tm) tm->collect();
+  InstScal sc;
+  CKH(cudaMemcpy(&sc, F.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
+  if (o.trace) CKH(cudaMemcpy(o.trace, df.trace, (size_t)o.max_iter * df.trace_w * 8, cudaMemcpyDeviceToHost));
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->iters = sc.iters;
+    info->cg_steps_total = sc.cg_total;
+    info->stop_reason = sc.stop_reason;
+    info->nblocks = df.nb;
+    info->r_evol = sc.r_evol;
+    for (int b = 0; b < df.p; ++b) {
+      info->r_feas[b] = sc.r_feas[b];
+      info->sigma[b] = sc.sigma[b];
+      info->k[b] = sc.kcard[b];
+    }
+    for (int b = 0; b < df.nb; ++b) {
+      info->rho[b] = sc.rho[b];
+      info->gamma[b] = sc.gamma[b];
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->ms = ms;
+  }
+  if (sc.stop_reason < 0) return fail(SIP_ERR_NONFINITE, "the model holds NaN or Inf");
+  return SIP_OK;
+}
+
+sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev, void *stream, sip_info *info) {
+  if (!h) return fail(SIP_ERR_INVALID_ARG, "handle is NULL");
+  if (!m_dev || !x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "m_dev / x_dev is NULL"));
+  h->err.clear();
+  return keep(h, project_impl(h, m_dev, x_dev, (cudaStream_t)stream, info));
+}
+
+// ----------------------------------------------------------------------------
+// per-kernel timing
+// ----------------------------------------------------------------------------
+static const char *kKernelNames[KT_COUNT] = {"rhs", "cg_dir", "cg_upd", "setpass", "select", "ties", "final", "tail"};
+
+const char *sip_kernel_name(int i) { return (i >= 0 && i < KT_COUNT) ? kKernelNames[i] : ""; }
+
+sip_status sip_set_timing(sip_handle *h, int on) {
+  if (!h) return fail(SIP_ERR_INVALID_ARG, "handle is NULL");
+  h->timing = on != 0;
+  h->timer.reset();
+  return SIP_OK;
+}
+
+sip_status sip_kernel_times(const sip_handle *h, double *ms, int64_t *launches, double *bytes_per_launch) {
+  if (!h) return fail(SIP_ERR_INVALID_ARG, "handle is NULL");
+  const InstLayout &L = h->lev[0].layouts[0];
+  const InstDev &d = L.dev;
+  const double W = (double)esz(h->opts.dtype), N = (double)d.N, Mp = (double)L.Mtot;
+  double Mpw = 0.0, Mms = 0.0, Msel = 0.0;
+  for (int b = 0; b < d.nb; ++b) {
+    const int t = d.blk[b].type;
+    if (t == BT_BOUNDS || t == BT_DIST) Mpw += (double)d.blk[b].M;
+    if (t == BT_L1 || t == BT_L2 || t == BT_CARD) Mms += (double)d.blk[b].M;
+    if (t == BT_L1 || t == BT_CARD) Msel += (double)d.blk[b].M;
+  }
+  const double ad = (h->opts.adapt && !h->opts.rho_schedule) ? 1.0 / h->opts.adapt_every : 0.0;
+  double bytes[KT_COUNT] = {};
+  bytes[KT_RHS] = W * (2 * Mp + 2 * N + (d.alg1 ? 0 : N));
+  bytes[KT_CG_DIR] = W * 4 * N;
+  bytes[KT_CG_UPD] = W * 6 * N;
+  bytes[KT_SETPASS] = W * (N + 2 * Mp + 2 * Mpw + Mms + (d.alg1 ? N : 0) + 2 * N + ad * (4 * Mp + 2 * Mpw));
+  bytes[KT_SELECT] = W * Msel;
+  bytes[KT_TIES] = 0.0;
+  bytes[KT_FINAL] = W * (3 * Mms + ad * 4 * Mms);
+  bytes[KT_TAIL] = 0.0;
+  for (int c = 0; c < KT_COUNT; ++c) {
+    if (ms) ms[c] = h->timer.ms[c];
+    if (launches) launches[c] = h->timer.launches[c];
+    if (bytes_per_launch) bytes_per_launch[c] = bytes[c];
+  }
+  return SIP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// single-step entry points
+// ----------------------------------------------------------------------------
+int64_t sip_op_rows(const sip_grid *grid, int op) {
+  if (check_grid_op(grid, op) != SIP_OK) return -1;
+  return op_rows(grid_desc(*grid), op);
+}
+
+sip_status sip_apply_op(const sip_grid *grid, int op, int dtype, const void *x_dev, void *s_dev, void *stream) {
+  sip_status st = check_grid_op(grid, op);
+  if (st) return st;
+  if (dtype != SIP_F64 && dtype != SIP_F32) return fail(SIP_ERR_INVALID_ARG, "unknown dtype");
+  if (!x_dev || !s_dev) return fail(SIP_ERR_INVALID_ARG, "NULL buffer");
+  const GridDesc g = grid_desc(*grid);
+  DevCopy<InstDev> d;
+  CKH(d.make(op_inst(g, op)));
+  CKH(launch_apply_op(Launch{dtype, (cudaStream_t)stream}, d.p, x_dev, s_dev, op_rows(g, op)));
+  CKH(cudaStreamSynchronize((cudaStream_t)stream));
+  return SIP_OK;
+}
+
+sip_status sip_apply_op_t(const sip_grid *grid, int op, int dtype, const void *s_dev, void *x_dev, void *stream) {
+  sip_status st = check_grid_op(grid, op);
+  if (st) return st;
+  if (dtype != SIP_F64 && dtype != SIP_F32) return fail(SIP_ERR_INVALID_ARG, "unknown dtype");
+  if (!x_dev || !s_dev) return fail(SIP_ERR_INVALID_ARG, "NULL buffer");
+  const GridDesc g = grid_desc(*grid);
+  DevCopy<InstDev> d;
+  CKH(d.make(op_inst(g, op)));
+  CKH(launch_apply_op_t(Launch{dtype, (cudaStream_t)stream}, d.p, s_dev, x_dev, g.N()));
+  CKH(cudaStreamSynchronize((cudaStream_t)stream));
+  return SIP_OK;
+}
+
+sip_status sip_system_apply(const sip_grid *grid, const int *ops, const double *rhos, int nops, double c_identity,
+                            int dtype, const void *x_dev, void *out_dev, void *stream) {
+  sip_status st = check_grid_op(grid, SIP_OP_I);
+  if (st) return st;
+  if (dtype != SIP_F64 && dtype != SIP_F32) return fail(SIP_ERR_INVALID_ARG, "unknown dtype");
+  if (!x_dev || !out_dev || (nops > 0 && (!ops || !rhos)) || nops < 0)
+    return fail(SIP_ERR_INVALID_ARG, "NULL buffer or bad nops");
+  const GridDesc g = grid_desc(*grid);
+  InstScal sc;
+  memset(&sc, 0, sizeof sc);
+  double c0 = c_identity, cz = 0, cx = 0, cy = 0;
+  for (int i = 0; i < nops; ++i) {
+    if ((st = check_grid_op(grid, ops[i]))) return st;
+    switch (ops[i]) {
+      case SIP_OP_I: c0 += rhos[i]; break;
+      case SIP_OP_DZ: cz += rhos[i]; break;
+      case SIP_OP_DX: cx += rhos[i]; break;
+      case SIP_OP_DY: cy += rhos[i]; break;
+      default: cz += rhos[i]; cx += rhos[i]; if (g.ndim == 3) cy += rhos[i]; break;
+    }
+  }
+  sc.c0 = c0;
+  sc.cz = cz / (g.h[0] * g.h[0]);
+  sc.cx = cx / (g.h[1] * g.h[1]);
+  sc.cy = cy / (g.h[2] * g.h[2]);
+  DevCopy<InstDev> d;
+  DevCopy<InstScal> ds;
+  CKH(d.make(op_inst(g, SIP_OP_I)));
+  CKH(ds.make(sc));
+  CKH(launch_system_apply(Launch{dtype, (cudaStream_t)stream}, d.p, ds.p, x_dev, out_dev, g.N()));
+  CKH(cudaStreamSynchronize((cudaStream_t)stream));
+  return SIP_OK;
+}
+
+sip_status sip_project_set(const sip_set *set, int dtype, const void *w_dev, int64_t n, void *y_dev, void *stream,
+                           double *scalar_out) {
+  if (!set || !w_dev || !y_dev) return fail(SIP_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(SIP_ERR_INVALID_ARG, "n must be >= 1");
+  sip_set s = *set;
+  s.op = SIP_OP_I;
+  s.sigma_rel = 0.0;
+  s.k_frac = 0.0;
+  sip_grid g;
+  memset(&g, 0, sizeof g);
+  g.ndim = 2;
+  g.n[0] = n;
+  g.n[1] = 1;
+  g.h[0] = g.h[1] = 1.0;
+  sip_options o;
+  sip_options_default(&o);
+  o.dtype = dtype;
+  o.form = SIP_FORM_DIRECT;
+  o.adapt = 0;
+  o.max_iter = 1;
+  o.gamma0 = 1.0;
+  o.rho0 = 1.0;
+  o.check_every = 1 << 30;
+  sip_status st = validate(&g, &s, 1, &o);
+  if (st) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Plan P;
+  std::vector<InstLayout> L{make_layout(grid_desc(g), &s, 1, o)};
+  if ((st = plan_build(P, L, dtype, false))) return st;
+  struct Rel {
+    Plan &p;
+    ~Rel() { p.release(); }
+  } rel{P};
+  const InstDev &d = P.h_insts[0];
+  const Launch Ln{dtype, cs};
+  if ((st = plan_set_m(P, 0, w_dev, cs))) return st;
+  if ((st = plan_prepare(P, cs, false))) return st;
+  CKH(cudaMemcpyAsync(d.x, w_dev, (size_t)n * esz(dtype), cudaMemcpyDeviceToDevice, cs));
+  CKH(launch_setpass(Ln, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs));
+  if (P.nt_sel)
+    for (int pass = 0; pass < select_passes(dtype); ++pass)
+      CKH(launch_select(Ln, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
+                        pass));
+  if (P.any_card) CKH(launch_ties(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
+  if (P.nt_fin) CKH(launch_final(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
+  CKH(cudaMemcpyAsync(y_dev, d.y, (size_t)n * esz(dtype), cudaMemcpyDeviceToDevice, cs));
+  CKH(cudaStreamSynchronize(cs));
+  if (scalar_out) {
+    *scalar_out = 0.0;
+    if (s.type == SIP_SET_L2) {
+      InstScal sc;
+      CKH(cudaMemcpy(&sc, P.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
+      *scalar_out = sc.l2scale[0];
+    } else if (s.type == SIP_SET_L1 || s.type == SIP_SET_CARD) {
+      JobScal js;
+      CKH(cudaMemcpy(&js, P.d_jscal + d.blk[0].job_w, sizeof js, cudaMemcpyDeviceToHost));
+      if (js.mode == JM_SELECT) *scalar_out = s.type == SIP_SET_L1 ? js.theta : js.kval;
+    }
+  }
+  return SIP_OK;
+}
+
+sip_status sip_op_norm(const sip_grid *grid, int op, int type, int dtype, const void *m_dev, void *stream,
+                       double *out) {
+  if (!out || !m_dev) return fail(SIP_ERR_INVALID_ARG, "NULL argument");
+  if (type != SIP_SET_L1 && type != SIP_SET_L2) return fail(SIP_ERR_INVALID_ARG, "type must be L1 or L2");
+  sip_set s;
+  memset(&s, 0, sizeof s);
+  s.op = op;
+  s.type = type;
+  s.sigma_rel = 1.0;
+  sip_options o;
+  sip_options_default(&o);
+  o.dtype = dtype;
+  o.form = SIP_FORM_DIRECT;
+  o.adapt = 0;
+  o.max_iter = 1;
+  sip_status st = validate(grid, &s, 1, &o);
+  if (st) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Plan P;
+  std::vector<InstLayout> L{make_layout(grid_desc(*grid), &s, 1, o)};
+  if ((st = plan_build(P, L, dtype, false))) return st;
+  struct Rel {
+    Plan &p;
+    ~Rel() { p.release(); }
+  } rel{P};
+  if ((st = plan_set_m(P, 0, m_dev, cs))) return st;
+  if ((st = plan_prepare(P, cs, false))) return st;
+  CKH(cudaStreamSynchronize(cs));
+  InstScal sc;
+  CKH(cudaMemcpy(&sc, P.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
+  *out = sc.sigma[0];
+  return SIP_OK;
+}
+
+sip_status sip_restrict(const sip_grid *fine, int dtype, const void *m_dev, void *mc_dev, void *stream) {
+  sip_status st = check_grid_op(fine, SIP_OP_I);
+  if (st) return st;
+  if (!m_dev || !mc_dev) return fail(SIP_ERR_INVALID_ARG, "NULL buffer");
+  const GridDesc f = grid_desc(*fine), c = grid_desc(coarse_of(*fine));
+  CKH(launch_restrict(Launch{dtype, (cudaStream_t)stream}, f.n, c.n, m_dev, mc_dev));
+  CKH(cudaStreamSynchronize((cudaStream_t)stream));
+  return SIP_OK;
+}
+
+sip_status sip_prolong(const sip_grid *fine, int op, int dtype, const void *uc_dev, void *uf_dev, void *stream) {
+  sip_status st = check_grid_op(fine, op);
+  if (st) return st;
+  const sip_grid cg = coarse_of(*fine);
+  if ((st = check_grid_op(&cg, op))) return fail(st, "coarse grid: %s", g_err.c_str());
+  if (!uc_dev || !uf_dev) return fail(SIP_ERR_INVALID_ARG, "NULL buffer");
+  const GridDesc f = grid_desc(*fine), c = grid_desc(cg);
+  const Launch L{dtype, (cudaStream_t)stream};
+  int64_t oc = 0, of = 0;
+  for (int kind : op_parts(f, op)) {
+    int64_t cd[3], fd[3];
+    int stag;
+    part_dims(c, kind, cd, stag);
+    part_dims(f, kind, fd, stag);
+    CKH(launch_prolong(L, cd, fd, stag, (const char *)uc_dev + oc * esz(dtype), (char *)uf_dev + of * esz(dtype)));
+    oc += part_rows(c, kind);
+    of += part_rows(f, kind);
+  }
+  CKH(cudaStreamSynchronize((cudaStream_t)stream));
+  return SIP_OK;
+}
+
+}  // extern "C"

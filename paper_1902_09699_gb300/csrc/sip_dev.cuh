@@ -1,0 +1,164 @@
+// Device-side data model of the PARSDMM engine (internal to libsip.so).
+//
+// One "instance" is one projection problem (grid, blocks, state arena).  A
+// plan holds one or many instances of one dtype; every kernel walks a tile
+// list in which each tile names its instance, so one launch serves a single
+// large grid or a ragged batch of small ones alike.
+//
+// Blocks follow the paper's stacked variables (Eq. conc_variables): blocks
+// 0..p-1 are the user's sets (A_i, C_i); in the paper's form block p is the
+// identity block A_{p+1} = I_N with the prox of the squared distance
+// (Eq. prox_sq_dist).  A block's rows y_i, v_i are contiguous in the
+// instance's y / v arrays at offset yoff.  A block whose operator is the TV
+// stack has one segment per difference operator; every other block has one
+// segment.  Segment rows decompose on the operator's own output grid, z
+// fastest (Eq. FD_mat).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sip.h"
+
+namespace sip {
+
+constexpr int kMaxSets = SIP_MAX_SETS;
+constexpr int kMaxBlocks = kMaxSets + 1;
+constexpr int kMaxSegs = kMaxBlocks * 3 + 1;
+constexpr int kMaxHist = 8;          // s of Eq. obj_stop, upper limit
+constexpr int kThreads = 256;        // threads per CTA for the streaming kernels
+constexpr int kPerThread = 4;
+constexpr int kTile = kThreads * kPerThread;
+constexpr int kDigitBits = 11;       // radix digit of the selection passes
+constexpr int kBins = 1 << kDigitBits;
+
+enum SegKind : int32_t { SEG_I = 0, SEG_DZ = 1, SEG_DX = 2, SEG_DY = 3, SEG_RING = 4 };
+enum BlkType : int32_t { BT_BOUNDS = 0, BT_L1 = 1, BT_L2 = 2, BT_CARD = 3, BT_DIST = 4 };
+enum JobKind : int32_t { JOB_L1 = 0, JOB_TOPK = 1 };
+// How a selection job resolved: run the radix select, or the set keeps
+// everything (inside the ball / k >= M), or nothing (tau = 0 / k = 0).
+enum JobMode : int32_t { JM_SELECT = 0, JM_ALL = 1, JM_NONE = 2 };
+
+// Per-block binary64 accumulators (one iteration).
+enum Acc : int32_t {
+  A_WNORM = 0,   // ||w||_2^2 (l2 set) or ||w||_1 (l1 set)
+  A_FEAS_D2,     // ||s - P(s)||^2 for bounds sets
+  A_S2,          // ||s||^2
+  A_S1,          // ||s||_1
+  A_HV, A_HH, A_VHVH,   // adapt-rho-gamma: dh.dvh, dh.dh, dvh.dvh
+  A_GV, A_GG, A_VV,     // adapt-rho-gamma: dg.dv, dg.dg, dv.dv
+  A_M1, A_M2,    // ||A m||_1, ||A m||_2^2 (relative radii)
+  kNAcc
+};
+
+struct Tile {
+  int32_t inst;   // instance
+  int32_t item;   // segment (set pass), block (final pass) or job (select)
+  int64_t start;  // first row / grid point
+  int32_t len;    // rows in this tile (<= kTile)
+  int32_t seq;    // tile number inside its item (tie ranks)
+};
+
+struct SegDev {
+  int32_t kind;   // SegKind
+  int32_t block;  // owning block (-1 for the x-history ring)
+  int64_t row0;   // first row of the segment inside its block
+  int64_t len;    // rows
+};
+
+struct BlockDev {
+  int32_t op, type;      // sip_op, BlkType
+  int64_t M;             // rows of A_i
+  int64_t yoff;          // offset into y, v and the adapt copies
+  int64_t woff;          // offset into the w scratch (l1/l2/card), -1 otherwise
+  int64_t soff;          // offset into the s scratch (l1/card feasibility), -1
+  double lo, hi;         // bounds
+  double sigma_abs, sigma_rel, k_frac;
+  int64_t k_abs;
+  int32_t job_w, job_s;  // selection jobs (global index) or -1
+  int32_t seg0, nseg;
+};
+
+struct JobDev {
+  int32_t inst, block, kind, feas;  // feas: selection on s = A x (Eq. feas_stop)
+  int64_t M;
+  int64_t data_off;   // into w or s scratch
+  int64_t hist_off;   // into the histogram arrays (kBins per job)
+  int64_t tie_off;    // into the tie-count array (one per tile)
+  int32_t ntiles;
+};
+
+struct JobScal {
+  int32_t active, mode, pass, tie_needed;
+  uint32_t counter;
+  int32_t pad;
+  uint64_t prefix;    // fixed high key bits so far; final key after the last pass
+  double c_above, s1_above, s2_above;  // entries with key above the current bin
+  double tau;         // l1 radius
+  int64_t k;          // cardinality
+  double theta;       // l1 soft threshold
+  int64_t need;       // card: ties to keep at the final key
+  int64_t cK;         // card: entries equal to the final key
+  double kval;        // card: |value| of the final key
+};
+
+struct InstDev {
+  int32_t nz, nx, ny, ndim;
+  double ihz, ihx, ihy;      // 1/h per axis
+  int64_t N;
+  int32_t nb, p, alg1, nseg, njob, job0;
+  int32_t nt_n, nt_set, nt_fin;
+  int32_t hist;              // evol_hist
+  // options
+  int32_t max_iter, cg_iters, cg_max, check_every, stop, adapt, adapt_every;
+  double eps_feas, eps_evol, rho0, gamma0, eps_corr, rho_ratio_max, gamma_max;
+  const double *rho_sched, *gamma_sched;  // device copies, may be null
+  double *trace;             // device trace rows, may be null
+  int32_t trace_w;
+  int32_t pad;
+  // device arrays, element type = the plan's dtype
+  const void *m;
+  void *x, *r, *p0, *p1, *q, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;
+  BlockDev blk[kMaxBlocks];
+  SegDev seg[kMaxSegs];
+};
+
+struct InstScal {
+  int32_t k;            // iteration in progress (1-based)
+  int32_t done;         // stopping rule held (or a non-finite model); kernels no-op
+  int32_t iters, stop_reason;
+  int32_t cg_active, cg_steps, cg_total, pbuf;
+  int32_t have_k0, nonfinite;
+  uint32_t cnt_n, cnt_set, cnt_norm;
+  int32_t pad;
+  double rr, rr0, bnorm2, alpha, beta;
+  double acc_n[2];
+  double rho[kMaxBlocks], gamma[kMaxBlocks], irho[kMaxBlocks], inv1p[kMaxBlocks];
+  double l2scale[kMaxBlocks];
+  double c0, cz, cx, cy;
+  double sigma[kMaxBlocks];
+  int64_t kcard[kMaxBlocks];
+  double r_feas[kMaxSets];
+  double r_evol;
+  double acc[kMaxBlocks][kNAcc];
+  double acc_ring[kMaxHist + 1];
+};
+
+// Type traits for the radix keys of |value|.
+template <typename T> struct KeyOf;
+template <> struct KeyOf<float> {
+  using K = uint32_t;
+  static constexpr int kBits = 31;  // sign bit of |v| is zero
+  static __device__ __forceinline__ K key(float v) { return __float_as_uint(fabsf(v)); }
+  static __device__ __forceinline__ double val(K k) { return (double)__uint_as_float((uint32_t)k); }
+};
+template <> struct KeyOf<double> {
+  using K = uint64_t;
+  static constexpr int kBits = 63;
+  static __device__ __forceinline__ K key(double v) { return (K)__double_as_longlong(fabs(v)); }
+  static __device__ __forceinline__ double val(K k) { return __longlong_as_double((long long)k); }
+};
+
+template <typename T> constexpr int num_passes() { return (KeyOf<T>::kBits + kDigitBits - 1) / kDigitBits; }
+
+}  // namespace sip

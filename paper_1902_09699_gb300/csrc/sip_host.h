@@ -1,0 +1,119 @@
+// Host-side plan / handle structures of libsip.so (internal).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sip.h"
+#include "sip_dev.cuh"
+
+namespace sip {
+
+extern thread_local std::string g_err;
+sip_status fail(sip_status s, const char *fmt, ...);
+
+struct GridDesc {
+  int ndim;
+  int64_t n[3];
+  double h[3];
+  int64_t N() const { return n[0] * n[1] * n[2]; }
+};
+
+struct InstLayout {
+  GridDesc g;
+  sip_options opts;
+  InstDev dev;
+  int64_t Mtot = 0, Mw = 0, Ms = 0;
+  std::vector<JobDev> jobs;
+};
+
+// kernel categories of the per-kernel timer
+enum KernelCat { KT_RHS = 0, KT_CG_DIR, KT_CG_UPD, KT_SETPASS, KT_SELECT, KT_TIES, KT_FINAL, KT_TAIL, KT_COUNT };
+
+// CUDA-event timing of every launch, by kernel category (opt-in; used to
+// report per-kernel device time without a profiler).
+struct KernelTimer {
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> cat;   // category of each (begin, end) pair
+  size_t used = 0;        // events used
+  cudaEvent_t open_ev = nullptr;
+  double ms[KT_COUNT] = {};
+  int64_t launches[KT_COUNT] = {};
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int c, cudaStream_t st) {
+    cudaEventRecord(next(), st);
+    cat.push_back(c);
+  }
+  void end(int, cudaStream_t st) { cudaEventRecord(next(), st); }
+  // call after the stream has been synchronised
+  void collect() {
+    for (size_t i = 0; i < cat.size(); ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]);
+      ms[cat[i]] += t;
+      launches[cat[i]] += 1;
+    }
+    cat.clear();
+    used = 0;
+  }
+  void reset() {
+    for (int c = 0; c < KT_COUNT; ++c) {
+      ms[c] = 0.0;
+      launches[c] = 0;
+    }
+  }
+  ~KernelTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct Plan {
+  int dtype = SIP_F32;
+  int ninst = 0;
+  void *arena = nullptr;
+  int64_t arena_bytes = 0;
+  int64_t warm_end = 0, state_end = 0, hist_begin = 0, hist_end = 0;
+  bool m_own = false;
+  InstDev *d_insts = nullptr;
+  InstScal *d_scal = nullptr;
+  JobDev *d_jobs = nullptr;
+  JobScal *d_jscal = nullptr;
+  uint32_t *d_hcnt = nullptr;
+  double *d_hs1 = nullptr, *d_hs2 = nullptr;
+  uint32_t *d_ties = nullptr;
+  Tile *d_tn = nullptr, *d_tset = nullptr, *d_tsel = nullptr, *d_tfin = nullptr;
+  int nt_n = 0, nt_set = 0, nt_sel = 0, nt_fin = 0, njobs = 0;
+  bool any_card = false, any_fin = false, any_stop = false;
+  int cg_launch = 0, max_iter = 0, check_every = 1;
+  std::vector<InstDev> h_insts;
+  std::vector<InstLayout> layouts;
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  void release();
+};
+
+GridDesc grid_desc(const sip_grid &g);
+std::vector<int> op_parts(const GridDesc &g, int op);
+int64_t part_rows(const GridDesc &g, int kind);
+int64_t op_rows(const GridDesc &g, int op);
+void part_dims(const GridDesc &g, int kind, int64_t d[3], int &stag);
+sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const sip_options *opts);
+InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const sip_options &o);
+double layout_bytes_per_iter(const InstLayout &L, int dtype);
+sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m);
+sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm);
+sip_status plan_set_m(Plan &P, int inst, const void *m, cudaStream_t st);
+sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,
+                          KernelTimer *tm);
+
+}  // namespace sip

@@ -1,0 +1,44 @@
+// Host-side launchers of the device kernels (internal to libsip.so).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sip_dev.cuh"
+
+namespace sip {
+
+struct Launch {
+  int dtype;  // SIP_F64 / SIP_F32
+  cudaStream_t stream;
+};
+
+// iteration kernels (kernels.cu)
+cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, int ninst);
+cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_cg_dir(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_cg_upd(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                           JobScal *jscal, const JobDev *jobs);
+cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                          const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, int pass);
+int select_passes(int dtype);
+cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                        const JobDev *jobs, JobScal *jscal, uint32_t *ties);
+cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                         const JobDev *jobs, const JobScal *jscal, const uint32_t *ties);
+cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst);
+
+// single-step operators on one grid (kernels.cu): `in` describes the grid and
+// the segments of one operator; `sc` carries the stencil coefficients.
+cudaError_t launch_apply_op(const Launch &L, const InstDev *in, const void *x, void *s, int64_t rows);
+cudaError_t launch_apply_op_t(const Launch &L, const InstDev *in, const void *s, void *x, int64_t n);
+cudaError_t launch_system_apply(const Launch &L, const InstDev *in, const InstScal *sc, const void *x, void *out,
+                                int64_t n);
+
+// multilevel transfer (kernels_ml.cu); dims are (nz, nx, ny) of the arrays
+cudaError_t launch_restrict(const Launch &L, const int64_t fine[3], const int64_t coarse[3], const void *mf, void *mc);
+cudaError_t launch_prolong(const Launch &L, const int64_t cdims[3], const int64_t fdims[3], int stagger_axis,
+                           const void *uc, void *uf);
+
+}  // namespace sip

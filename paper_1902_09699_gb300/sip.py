@@ -1,0 +1,355 @@
+"""Thin ctypes binding of the C ABI in include/sip.h (libsip.so).
+
+Argument marshalling only: every step of a projection runs in the library's
+CUDA kernels.  Device memory and streams come from PyTorch tensors.  If the
+library has not been built this module raises on first use; there is no
+fallback path.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsip.so")
+
+OPS = {"I": 0, "DZ": 1, "DX": 2, "DY": 3, "TV": 4}
+SET_TYPES = {"bounds": 0, "l1": 1, "l2": 2, "card": 3}
+F64, F32 = 0, 1
+FORMS = {"alg1": 0, "direct": 1}
+STATUS = {0: "SIP_OK", 1: "SIP_ERR_INVALID_ARG", 2: "SIP_ERR_OOM", 3: "SIP_ERR_CUDA", 4: "SIP_ERR_TIMEOUT",
+          5: "SIP_ERR_NONFINITE", 6: "SIP_ERR_BUDGET", 7: "SIP_ERR_INTERNAL"}
+MAX_SETS = 16
+
+c_int, c_i64, c_dbl, c_vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("ndim", c_int), ("n", c_i64 * 3), ("h", c_dbl * 3)]
+
+
+class Set(ctypes.Structure):
+    _fields_ = [("op", c_int), ("type", c_int), ("lo", c_dbl), ("hi", c_dbl), ("sigma", c_dbl),
+                ("sigma_rel", c_dbl), ("k", c_i64), ("k_frac", c_dbl)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("max_iter", c_int), ("cg_iters", c_int), ("cg_max", c_int), ("eps_feas", c_dbl),
+                ("eps_evol", c_dbl), ("check_every", c_int), ("evol_hist", c_int), ("stop", c_int),
+                ("adapt", c_int), ("adapt_every", c_int), ("rho0", c_dbl), ("gamma0", c_dbl),
+                ("eps_corr", c_dbl), ("rho_ratio_max", c_dbl), ("gamma_max", c_dbl), ("form", c_int),
+                ("dtype", c_int), ("levels", c_int), ("coarse_iter", c_int),
+                ("rho_schedule", ctypes.POINTER(c_dbl)), ("gamma_schedule", ctypes.POINTER(c_dbl)),
+                ("trace", ctypes.POINTER(c_dbl))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("cg_steps_total", c_int), ("stop_reason", c_int), ("nblocks", c_int),
+                ("r_evol", c_dbl), ("r_feas", c_dbl * MAX_SETS), ("rho", c_dbl * (MAX_SETS + 1)),
+                ("gamma", c_dbl * (MAX_SETS + 1)), ("sigma", c_dbl * MAX_SETS), ("k", c_i64 * MAX_SETS),
+                ("ms", ctypes.c_float)]
+
+
+# every function declared in include/sip.h: name -> (restype, argtypes)
+SIGNATURES = {
+    "sip_options_default": (None, [ctypes.POINTER(Options)]),
+    "sip_create": (c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Set), c_int, ctypes.POINTER(Options),
+                           ctypes.POINTER(c_vp)]),
+    "sip_project": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Info)]),
+    "sip_destroy": (c_int, [c_vp]),
+    "sip_last_error": (ctypes.c_char_p, [c_vp]),
+    "sip_device_bytes": (c_i64, [c_vp]),
+    "sip_bytes_per_iter": (c_dbl, [c_vp]),
+    "sip_set_timing": (c_int, [c_vp, c_int]),
+    "sip_kernel_times": (c_int, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]),
+    "sip_kernel_name": (ctypes.c_char_p, [c_int]),
+    "sip_apply_op": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_vp, c_vp, c_vp]),
+    "sip_apply_op_t": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_vp, c_vp, c_vp]),
+    "sip_op_rows": (c_i64, [ctypes.POINTER(Grid), c_int]),
+    "sip_system_apply": (c_int, [ctypes.POINTER(Grid), ctypes.POINTER(c_int), ctypes.POINTER(c_dbl), c_int, c_dbl,
+                                 c_int, c_vp, c_vp, c_vp]),
+    "sip_project_set": (c_int, [ctypes.POINTER(Set), c_int, c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(c_dbl)]),
+    "sip_op_norm": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_int, c_vp, c_vp, ctypes.POINTER(c_dbl)]),
+    "sip_restrict": (c_int, [ctypes.POINTER(Grid), c_int, c_vp, c_vp, c_vp]),
+    "sip_prolong": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_vp, c_vp, c_vp]),
+}
+
+_lib = None
+
+
+class SipError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def lib():
+    """Load libsip.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsip.so is not built (run paper_1902_09699_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = lib().sip_last_error(handle)
+        raise SipError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- marshalling
+def make_grid(grid):
+    n = tuple(int(v) for v in grid["n"])
+    h = tuple(float(v) for v in grid.get("h", (1.0,) * len(n)))
+    g = Grid()
+    g.ndim = len(n)
+    for a in range(3):
+        g.n[a] = n[a] if a < len(n) else 1
+        g.h[a] = h[a] if a < len(h) else 1.0
+    return g
+
+
+def make_set(s):
+    c = Set()
+    c.op = OPS[s["op"]]
+    c.type = SET_TYPES[s["type"]]
+    c.lo = float(s.get("lo", -math.inf))
+    c.hi = float(s.get("hi", math.inf))
+    c.sigma = float(s.get("sigma", 0.0))
+    c.sigma_rel = float(s.get("sigma_rel", 0.0))
+    c.k = int(s.get("k", 0))
+    c.k_frac = float(s.get("k_frac", 0.0))
+    return c
+
+
+def make_sets(sets):
+    arr = (Set * len(sets))()
+    for i, s in enumerate(sets):
+        arr[i] = make_set(s)
+    return arr
+
+
+def default_options():
+    o = Options()
+    lib().sip_options_default(ctypes.byref(o))
+    return o
+
+
+def _dtype_code(dtype):
+    import torch
+    if dtype in ("f64", torch.float64, F64):
+        return F64
+    if dtype in ("f32", torch.float32, F32):
+        return F32
+    raise ValueError("dtype must be f32 or f64")
+
+
+def _torch_dtype(code):
+    import torch
+    return torch.float64 if code == F64 else torch.float32
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_vp(stream.cuda_stream)
+
+
+def _ptr(t):
+    return c_vp(t.data_ptr())
+
+
+def _dev(t, code):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t))
+    return t.to(device="cuda", dtype=_torch_dtype(code)).contiguous()
+
+
+# ---------------------------------------------------------------- projector
+class Projector:
+    """One sip_handle: a grid, a list of (A_i, C_i) and options.
+
+    ``opts`` keys follow sip_options (max_iter, cg_iters, adapt, rho0, gamma0,
+    form="alg1"|"direct", levels, ...).  ``rho_schedule`` / ``gamma_schedule``
+    (arrays [max_iter, nblocks]) replay rho / gamma; ``trace=True`` records
+    the per-iteration trace.
+    """
+
+    def __init__(self, grid, sets, dtype="f32", rho_schedule=None, gamma_schedule=None, trace=False, **opts):
+        L = lib()
+        self.grid_dict = dict(grid)
+        self.sets = [dict(s) for s in sets]
+        self.code = _dtype_code(dtype)
+        self.N = int(np.prod(grid["n"]))
+        o = default_options()
+        for k, v in opts.items():
+            if k == "form":
+                v = FORMS[v] if isinstance(v, str) else int(v)
+            if not hasattr(o, k):
+                raise KeyError("unknown option %r" % (k,))
+            setattr(o, k, v)
+        o.dtype = self.code
+        self.nblocks = len(sets) + (1 if o.form == FORMS["alg1"] else 0)
+        self._keep = []
+        if rho_schedule is not None:
+            rs = np.ascontiguousarray(rho_schedule, dtype=np.float64)
+            assert rs.shape == (o.max_iter, self.nblocks), rs.shape
+            self._keep.append(rs)
+            o.rho_schedule = rs.ctypes.data_as(ctypes.POINTER(c_dbl))
+        if gamma_schedule is not None:
+            gs = np.ascontiguousarray(gamma_schedule, dtype=np.float64)
+            assert gs.shape == (o.max_iter, self.nblocks), gs.shape
+            self._keep.append(gs)
+            o.gamma_schedule = gs.ctypes.data_as(ctypes.POINTER(c_dbl))
+        self.trace = None
+        if trace:
+            self.trace_w = 2 * self.nblocks + 2 + len(sets)
+            self.trace = np.zeros((o.max_iter, self.trace_w))
+            o.trace = self.trace.ctypes.data_as(ctypes.POINTER(c_dbl))
+        self.opts = o
+        self._grid = make_grid(grid)
+        self._sets = make_sets(sets)
+        h = c_vp()
+        _check(L.sip_create(ctypes.byref(self._grid), self._sets, len(sets), ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def torch_dtype(self):
+        return _torch_dtype(self.code)
+
+    def project(self, m, x=None, stream=None, info=True):
+        """x = P(m) for a CUDA tensor m (flat, z fastest).  Returns (x, info)
+        where info is a dict (or None when info=False: no synchronisation)."""
+        import torch
+        m = _dev(m, self.code)
+        if m.numel() != self.N:
+            raise ValueError("m has %d entries, grid has %d" % (m.numel(), self.N))
+        if x is None:
+            x = torch.empty(self.N, dtype=self.torch_dtype, device=m.device)
+        inf = Info() if info else None
+        _check(lib().sip_project(self.handle, _ptr(m), _ptr(x), _stream_ptr(stream),
+                                 ctypes.byref(inf) if info else None), self.handle)
+        if not info:
+            return x, None
+        p = len(self.sets)
+        d = dict(iters=inf.iters, cg_steps=inf.cg_steps_total, stop_reason=inf.stop_reason,
+                 r_evol=inf.r_evol, r_feas=list(inf.r_feas[:p]), rho=list(inf.rho[:self.nblocks]),
+                 gamma=list(inf.gamma[:self.nblocks]), sigma=list(inf.sigma[:p]), k=list(inf.k[:p]),
+                 ms=float(inf.ms))
+        return x, d
+
+    def device_bytes(self):
+        return int(lib().sip_device_bytes(self.handle))
+
+    def bytes_per_iter(self):
+        return float(lib().sip_bytes_per_iter(self.handle))
+
+    def set_timing(self, on):
+        _check(lib().sip_set_timing(self.handle, 1 if on else 0), self.handle)
+
+    def kernel_times(self):
+        n = 8
+        ms = (c_dbl * n)()
+        la = (c_i64 * n)()
+        by = (c_dbl * n)()
+        _check(lib().sip_kernel_times(self.handle, ms, la, by), self.handle)
+        return {lib().sip_kernel_name(i).decode(): dict(ms=ms[i], launches=la[i], bytes_per_launch=by[i])
+                for i in range(n)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sip_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- single steps
+def op_rows(grid, op):
+    return int(lib().sip_op_rows(ctypes.byref(make_grid(grid)), OPS[op]))
+
+
+def apply_op(grid, op, x, stream=None):
+    import torch
+    code = _dtype_code(x.dtype)
+    g = make_grid(grid)
+    s = torch.empty(op_rows(grid, op), dtype=x.dtype, device=x.device)
+    _check(lib().sip_apply_op(ctypes.byref(g), OPS[op], code, _ptr(x), _ptr(s), _stream_ptr(stream)))
+    return s
+
+
+def apply_op_t(grid, op, s, stream=None):
+    import torch
+    code = _dtype_code(s.dtype)
+    g = make_grid(grid)
+    x = torch.empty(int(np.prod(grid["n"])), dtype=s.dtype, device=s.device)
+    _check(lib().sip_apply_op_t(ctypes.byref(g), OPS[op], code, _ptr(s), _ptr(x), _stream_ptr(stream)))
+    return x
+
+
+def system_apply(grid, ops, rhos, c_identity, x, stream=None):
+    import torch
+    code = _dtype_code(x.dtype)
+    g = make_grid(grid)
+    oa = (c_int * len(ops))(*[OPS[o] for o in ops])
+    ra = (c_dbl * len(rhos))(*[float(r) for r in rhos])
+    out = torch.empty_like(x)
+    _check(lib().sip_system_apply(ctypes.byref(g), oa, ra, len(ops), float(c_identity), code, _ptr(x), _ptr(out),
+                                  _stream_ptr(stream)))
+    return out
+
+
+def project_set(set_spec, w, stream=None):
+    """y = P_C(w) with the loop's kernels; returns (y, scalar)."""
+    import torch
+    code = _dtype_code(w.dtype)
+    s = make_set(dict(set_spec, op="I"))
+    y = torch.empty_like(w)
+    sc = c_dbl(0.0)
+    _check(lib().sip_project_set(ctypes.byref(s), code, _ptr(w), w.numel(), _ptr(y), _stream_ptr(stream),
+                                 ctypes.byref(sc)))
+    return y, sc.value
+
+
+def op_norm(grid, op, set_type, m, stream=None):
+    code = _dtype_code(m.dtype)
+    out = c_dbl(0.0)
+    _check(lib().sip_op_norm(ctypes.byref(make_grid(grid)), OPS[op], SET_TYPES[set_type], code, _ptr(m),
+                             _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def coarse_grid(grid):
+    n = tuple((int(v) + 1) // 2 for v in grid["n"])
+    h = tuple(2.0 * float(v) for v in grid.get("h", (1.0,) * len(n)))
+    return {"n": n, "h": h}
+
+
+def restrict(grid, m, stream=None):
+    import torch
+    code = _dtype_code(m.dtype)
+    mc = torch.empty(int(np.prod(coarse_grid(grid)["n"])), dtype=m.dtype, device=m.device)
+    _check(lib().sip_restrict(ctypes.byref(make_grid(grid)), code, _ptr(m), _ptr(mc), _stream_ptr(stream)))
+    return mc
+
+
+def prolong(grid, op, uc, stream=None):
+    import torch
+    code = _dtype_code(uc.dtype)
+    uf = torch.empty(op_rows(grid, op), dtype=uc.dtype, device=uc.device)
+    _check(lib().sip_prolong(ctypes.byref(make_grid(grid)), OPS[op], code, _ptr(uc), _ptr(uf), _stream_ptr(stream)))
+    return uf

@@ -1,0 +1,104 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/sip.h declares, the ctypes structs match the C layout, and
+host-side argument validation rejects bad input before any device work."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sip.h")
+
+
+@pytest.fixture(scope="module")
+def sip():
+    from paper_1902_09699_gb300 import build, sip as S
+    if not os.path.exists(S.LIB_PATH):
+        build.build()
+    S.lib()
+    return S
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sip_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_functions_exported_and_bound(sip):
+    names = declared_functions()
+    assert len(names) >= 15
+    L = sip.lib()
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in sip.SIGNATURES, "binding misses " + n
+    assert set(sip.SIGNATURES) == set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", sip.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (sip_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_struct_layouts_match_c(sip, tmp_path):
+    prog = tmp_path / "sizes.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sip.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sip_grid), sizeof(sip_set),'
+                    ' sizeof(sip_options), sizeof(sip_info), offsetof(sip_options, rho0),'
+                    ' offsetof(sip_options, trace), offsetof(sip_info, ms)); return 0;}\n')
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(sip.Grid), ctypes.sizeof(sip.Set), ctypes.sizeof(sip.Options), ctypes.sizeof(sip.Info),
+            sip.Options.rho0.offset, sip.Options.trace.offset, sip.Info.ms.offset]
+    assert got == want
+
+
+def test_defaults_follow_the_paper(sip):
+    o = sip.default_options()
+    assert (o.eps_feas, o.eps_evol, o.check_every, o.evol_hist) == (1e-3, 1e-2, 5, 5)
+    assert (o.eps_corr, o.adapt_every, o.cg_iters) == (0.3, 2, 5)
+
+
+def test_op_rows(sip):
+    g = {"n": (5, 4), "h": (1.0, 1.0)}
+    assert sip.op_rows(g, "I") == 20
+    assert sip.op_rows(g, "DZ") == 16
+    assert sip.op_rows(g, "DX") == 15
+    assert sip.op_rows(g, "TV") == 31
+    g3 = {"n": (4, 3, 5)}
+    assert sip.op_rows(g3, "DY") == 48
+    assert sip.op_rows(g3, "TV") == 3 * 3 * 5 + 4 * 2 * 5 + 48
+    assert sip.op_rows(g, "DY") == -1             # 2D grid has no y axis
+
+
+@pytest.mark.parametrize("bad", [
+    dict(grid={"n": (0, 4)}),
+    dict(grid={"n": (4, 4), "h": (0.0, 1.0)}),
+    dict(sets=[{"op": "I", "type": "bounds", "lo": 3.0, "hi": 2.0}]),
+    dict(sets=[{"op": "TV", "type": "l1", "sigma": -1.0}]),
+    dict(sets=[{"op": "DZ", "type": "card", "k": -2}]),
+    dict(sets=[{"op": "DY", "type": "bounds", "lo": 0.0, "hi": 1.0}]),
+    dict(grid={"n": (1, 8)}, sets=[{"op": "DZ", "type": "bounds", "lo": 0.0, "hi": 1.0}]),
+    dict(opts=dict(max_iter=0)),
+    dict(opts=dict(evol_hist=9)),
+    dict(opts=dict(gamma0=2.0)),
+    dict(sets=[{"op": "I", "type": "bounds", "lo": 0.0, "hi": 1.0}] * 17),
+])
+def test_invalid_arguments_rejected_on_host(sip, bad):
+    grid = bad.get("grid", {"n": (8, 8)})
+    sets = bad.get("sets", [{"op": "I", "type": "bounds", "lo": 0.0, "hi": 1.0}])
+    with pytest.raises(sip.SipError) as e:
+        sip.Projector(grid, sets, dtype="f64", **bad.get("opts", {}))
+    assert e.value.status == 1
+    assert str(e.value)
+
+
+def test_null_arguments(sip):
+    L = sip.lib()
+    h = ctypes.c_void_p()
+    assert L.sip_create(None, None, 0, None, ctypes.byref(h)) == 1
+    assert L.sip_project(None, None, None, None, None) == 1
+    assert L.sip_destroy(None) == 0
+    assert L.sip_last_error(None)

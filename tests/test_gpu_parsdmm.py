@@ -1,0 +1,218 @@
+"""Loop parity: the CUDA PARSDMM loop against the FP64 oracle on the same
+seeded inputs, under a fixed iteration count and a deterministic rho
+schedule, through the C ABI.
+
+Bars: ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-10 in FP64 and <= 1e-4 in
+FP32 (FP32 runs replay the oracle's rho/gamma schedule so binary32 rounding
+cannot flip an adapt-rho-gamma branch).  The FP64 GPU loop also runs its own
+adapt-rho-gamma, whose rho trajectory must match the oracle's to 1e-9.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import operators as O                 # noqa: E402
+from oracle import parsdmm as P                   # noqa: E402
+from paper_1902_09699_gb300 import sip            # noqa: E402
+from paper_1902_09699_gb300 import workloads as W  # noqa: E402
+
+TD = {"f64": torch.float64, "f32": torch.float32}
+BAR = {"f64": 1e-10, "f32": 1e-4}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_gpu(m, grid, sets, dt, opts, rho_schedule=None, gamma_schedule=None, trace=False):
+    pr = sip.Projector(grid, sets, dtype=dt, rho_schedule=rho_schedule, gamma_schedule=gamma_schedule,
+                       trace=trace, **opts)
+    x, info = pr.project(torch.as_tensor(m, dtype=TD[dt], device="cuda"))
+    out = x.double().cpu().numpy(), info, (pr.trace.copy() if trace else None)
+    pr.close()
+    return out
+
+
+def oracle_run(m, grid, sets, opts, **kw):
+    o = P.options(**opts)
+    return P.parsdmm(m, grid, sets, o, **kw)
+
+
+def schedules(res):
+    rs = np.array([t["rho"] for t in res["trace"]])
+    gs = np.array([t["gamma"] for t in res["trace"]])
+    return rs, gs
+
+
+def m_as(m, dt):
+    return torch.as_tensor(m, dtype=TD[dt]).double().numpy()
+
+
+# ---------------------------------------------------------------- 64 x 64 FP64
+def test_small_2d_fp64_fixed_rho():
+    c = W.small_2d()
+    ref = oracle_run(c["m"], c["grid"], c["sets"], c["opts"])
+    x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", c["opts"])
+    assert info["iters"] == 200
+    assert rel(x, ref["x"]) <= 1e-10
+    for a, b in zip(info["r_feas"], ref["r_feas"]):
+        assert a == pytest.approx(b, rel=1e-8, abs=1e-14)
+    assert info["r_evol"] == pytest.approx(ref["r_evol"], rel=1e-8)
+    assert info["cg_steps"] == ref["cg_steps"]
+
+
+def test_small_2d_fp32():
+    c = W.small_2d()
+    m32 = m_as(c["m"], "f32")
+    ref = oracle_run(m32, c["grid"], c["sets"], c["opts"])
+    x, info, _ = run_gpu(m32, c["grid"], c["sets"], "f32", c["opts"])
+    assert rel(x, ref["x"]) <= 1e-4
+
+
+# ---------------------------------------------------------------- config-2 set list, reduced grid
+def layered_small(n=(96, 128)):
+    c = W.layered_2d(n=n, seed=77)
+    c["opts"] = dict(c["opts"], max_iter=60)
+    return c
+
+
+def test_layered_fp64_own_adapt_matches_oracle():
+    c = layered_small()
+    ref = oracle_run(c["m"], c["grid"], c["sets"], c["opts"])
+    x, info, tr = run_gpu(c["m"], c["grid"], c["sets"], "f64", c["opts"], trace=True)
+    rs, _ = schedules(ref)
+    nb = len(c["sets"]) + 1
+    assert np.ptp(rs) > 0, "rho must move in this case"
+    assert np.allclose(tr[:, :nb], rs, rtol=1e-9, atol=0)
+    assert rel(x, ref["x"]) <= 1e-10
+    assert info["k"][3] == math.floor(0.02 * 96 * 128)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_layered_replayed_schedule(dt):
+    c = layered_small()
+    m = m_as(c["m"], dt)
+    ref = oracle_run(m, c["grid"], c["sets"], c["opts"])
+    rs, gs = schedules(ref)
+    x, info, _ = run_gpu(m, c["grid"], c["sets"], dt, c["opts"], rho_schedule=rs, gamma_schedule=gs)
+    assert rel(x, ref["x"]) <= BAR[dt]
+
+
+def test_adapt_rho_and_gamma_full_algorithm():
+    c = layered_small((40, 56))
+    opts = dict(c["opts"], adapt=2, max_iter=40)
+    ref = oracle_run(c["m"], c["grid"], c["sets"], opts)
+    x, info, tr = run_gpu(c["m"], c["grid"], c["sets"], "f64", opts, trace=True)
+    rs, gs = schedules(ref)
+    nb = len(c["sets"]) + 1
+    assert np.allclose(tr[:, :nb], rs, rtol=1e-9)
+    assert np.allclose(tr[:, nb:2 * nb], gs, rtol=1e-9)
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+def test_direct_form():
+    c = layered_small((48, 40))
+    opts = dict(c["opts"], form="direct", max_iter=50)
+    ref = oracle_run(c["m"], c["grid"], c["sets"], opts)
+    x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", opts)
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+# ---------------------------------------------------------------- 3D and multilevel
+def grf3(n=(20, 16, 12)):
+    c = W.grf_3d(n=n, seed=33)
+    c["opts"] = dict(c["opts"], max_iter=40)
+    return c
+
+
+def test_3d_fp64():
+    c = grf3()
+    ref = oracle_run(c["m"], c["grid"], c["sets"], c["opts"])
+    x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", c["opts"])
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("n", [(24, 16, 12), (33, 20)])
+def test_two_level_fp64(n):
+    c = W.grf_3d(n=n, seed=5) if len(n) == 3 else W.small_2d(n=n, seed=5)
+    opts = dict(c["opts"], max_iter=30, adapt=1, gamma0=1.5)
+    ref = P.ml_parsdmm(c["m"], c["grid"], c["sets"], P.options(**opts), levels=2, coarse_iter=20)
+    x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", dict(opts, levels=2, coarse_iter=20))
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+# ---------------------------------------------------------------- stopping, edge cases, errors
+def test_stopping_rule_iteration_count():
+    c = W.small_2d(n=(32, 24), seed=9)
+    opts = dict(max_iter=2000, adapt=1, gamma0=1.5, stop=1)
+    sets = [c["sets"][0], c["sets"][2]]
+    ref = oracle_run(c["m"], c["grid"], sets, opts)
+    x, info, _ = run_gpu(c["m"], c["grid"], sets, "f64", opts)
+    assert ref["stop_reason"] == 1
+    assert info["stop_reason"] == 1 and info["iters"] == ref["iters"]
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("grid,sets", [
+    ({"n": (2, 2)}, [{"op": "TV", "type": "l1", "sigma": 0.1}, {"op": "I", "type": "bounds", "lo": 0.0, "hi": 1.0}]),
+    ({"n": (1, 9)}, [{"op": "DX", "type": "card", "k": 2}]),
+    ({"n": (5, 1)}, [{"op": "DZ", "type": "l2", "sigma": 0.3}]),
+    ({"n": (3, 2, 2)}, [{"op": "TV", "type": "l1", "sigma_rel": 0.2}, {"op": "DY", "type": "bounds", "lo": 0.0, "hi": 9.0}]),
+    ({"n": (1031, 3)}, [{"op": "DZ", "type": "card", "k_frac": 0.1}, {"op": "I", "type": "l1", "sigma_rel": 0.5}]),
+])
+def test_degenerate_and_ragged_grids(grid, sets):
+    g = np.random.default_rng(1)
+    m = g.standard_normal(int(np.prod(grid["n"])))
+    opts = dict(max_iter=25, adapt=1, gamma0=1.5)
+    ref = oracle_run(m, grid, sets, opts)
+    x, info, _ = run_gpu(m, grid, sets, "f64", opts)
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+def test_repeat_calls_on_one_handle():
+    c = layered_small((32, 48))
+    pr = sip.Projector(c["grid"], c["sets"], dtype="f64", **c["opts"])
+    m = torch.as_tensor(c["m"], device="cuda")
+    x1, _ = pr.project(m)
+    x2, _ = pr.project(m)
+    m2 = m.flip(0).contiguous()
+    x3, _ = pr.project(m2)
+    x4, _ = pr.project(m)
+    a, b, d = x1.cpu().numpy(), x2.cpu().numpy(), x4.cpu().numpy()
+    assert rel(b, a) <= 1e-12 and rel(d, a) <= 1e-12
+    ref = oracle_run(c["m"][::-1].copy(), c["grid"], c["sets"], c["opts"])
+    assert rel(x3.cpu().numpy(), ref["x"]) <= 1e-10
+    pr.close()
+
+
+def test_nonfinite_model_rejected():
+    c = W.small_2d(n=(16, 16))
+    m = c["m"].copy()
+    m[37] = np.nan
+    pr = sip.Projector(c["grid"], c["sets"], dtype="f64", max_iter=10)
+    with pytest.raises(sip.SipError) as e:
+        pr.project(torch.as_tensor(m, device="cuda"))
+    assert e.value.status == 5
+    x, info = pr.project(torch.as_tensor(c["m"], device="cuda"))   # handle still usable
+    assert info["iters"] == 10
+    pr.close()
+
+
+# ---------------------------------------------------------------- full size 512 x 1024
+def test_full_size_layered_first_iterations():
+    """The 512 x 1024 five-set workload in the bench launch configuration:
+    a few iterations compared whole against the oracle."""
+    c = W.layered_2d()
+    opts = dict(c["opts"], max_iter=6)
+    ref = oracle_run(c["m"], c["grid"], c["sets"], opts)
+    x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", opts)
+    assert rel(x, ref["x"]) <= 1e-10
+    m32 = m_as(c["m"], "f32")
+    ref32 = oracle_run(m32, c["grid"], c["sets"], opts)
+    rs, gs = schedules(ref32)
+    x, info, _ = run_gpu(m32, c["grid"], c["sets"], "f32", opts, rho_schedule=rs, gamma_schedule=gs)
+    assert rel(x, ref32["x"]) <= 1e-4
