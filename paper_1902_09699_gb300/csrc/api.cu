@@ -174,6 +174,13 @@ sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const 
   return check_opts(*opts);
 }
 
+void set_fastdiv(InstDev &d) {
+  d.fz = make_fastdiv((uint32_t)d.nz);
+  d.fx = make_fastdiv((uint32_t)d.nx);
+  d.fzm = make_fastdiv((uint32_t)(d.nz > 1 ? d.nz - 1 : 1));
+  d.fxm = make_fastdiv((uint32_t)(d.nx > 1 ? d.nx - 1 : 1));
+}
+
 // ----------------------------------------------------------------------------
 // instance layout (host description; device pointers filled at placement)
 // ----------------------------------------------------------------------------
@@ -187,9 +194,13 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
   d.nx = (int32_t)g.n[1];
   d.ny = (int32_t)g.n[2];
   d.ndim = g.ndim;
+  set_fastdiv(d);
   d.ihz = 1.0 / g.h[0];
   d.ihx = 1.0 / g.h[1];
   d.ihy = 1.0 / g.h[2];
+  d.ihzf = (float)d.ihz;
+  d.ihxf = (float)d.ihx;
+  d.ihyf = (float)d.ihy;
   d.N = g.N();
   d.p = nsets;
   d.alg1 = o.form == SIP_FORM_ALG1 ? 1 : 0;
@@ -310,17 +321,40 @@ double layout_bytes_per_iter(const InstLayout &L, int dtype) {
 // ----------------------------------------------------------------------------
 // plan: one or more instances placed in one device arena
 // ----------------------------------------------------------------------------
-static void push_tiles(std::vector<Tile> &v, int inst, int item, int64_t n) {
+// One work item per CTA: `chunk` rows (a multiple of kTile) of one item.
+static void push_tiles(std::vector<Tile> &v, int inst, int item, int64_t n, int64_t chunk) {
   int seq = 0;
-  for (int64_t s = 0; s < n; s += kTile, ++seq) {
+  for (int64_t s = 0; s < n; s += chunk, ++seq) {
     Tile t;
     t.inst = inst;
     t.item = item;
     t.start = s;
-    t.len = (int32_t)(n - s < kTile ? n - s : kTile);
+    t.len = (int32_t)(n - s < chunk ? n - s : chunk);
     t.seq = seq;
     v.push_back(t);
   }
+}
+
+// Rows per work item for a launch that covers `total` rows: `slots` CTAs
+// (SMs x resident CTAs per SM, so the launch runs in one wave), a multiple
+// of the CTA width, at most kMaxChunk.
+static int64_t chunk_for(int64_t total, int64_t slots) {
+  constexpr int64_t kMaxChunk = 64 * kTile;
+  if (slots < 1) slots = 1;
+  int64_t c = (total + slots - 1) / slots;
+  c = (c + kThreads - 1) / kThreads * kThreads;
+  if (c < kThreads) c = kThreads;
+  if (c > kMaxChunk) c = kMaxChunk;
+  return c;
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  return n > 0 ? n : 152;
 }
 
 void Plan::release() {
@@ -342,6 +376,23 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.max_iter = 0;
   P.check_every = 1 << 30;
   P.any_stop = false;
+  // rows covered by each launch kind over all instances -> work-item size
+  int64_t tot_n = 0, tot_set = 0, tot_fin = 0, tot_sel = 0;
+  for (auto &L : insts) {
+    tot_n += L.dev.N;
+    for (int s = 0; s < L.dev.nseg; ++s) tot_set += L.dev.seg[s].len;
+    for (int b = 0; b < L.dev.nb; ++b) {
+      const int t = L.dev.blk[b].type;
+      if (t == BT_L1 || t == BT_L2 || t == BT_CARD) tot_fin += L.dev.blk[b].M;
+    }
+    for (auto &j : L.jobs) tot_sel += j.M;
+  }
+  if (cudaError_t e = kernels_setup()) return fail(SIP_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e));
+  const int64_t sms = sm_count();
+  const int64_t ch_n = chunk_for(tot_n, sms * launch_occupancy(dtype, 0));
+  const int64_t ch_set = chunk_for(tot_set, sms * launch_occupancy(dtype, 1));
+  const int64_t ch_sel = chunk_for(tot_sel, sms * launch_occupancy(dtype, 2));
+  const int64_t ch_fin = chunk_for(tot_fin, sms * launch_occupancy(dtype, 3));
   for (int i = 0; i < P.ninst; ++i) {
     InstLayout &L = insts[i];
     InstDev &d = L.dev;
@@ -354,26 +405,29 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     for (auto &j : L.jobs) {
       j.inst = i;
       j.hist_off = (int64_t)(njobs++) * kBins;
+      // select passes walk the job in ch_sel items; tie counts follow the
+      // final pass's ch_fin items of the job's block
+      j.ntiles = (int32_t)((j.M + ch_sel - 1) / ch_sel);
       j.tie_off = ntie;
-      ntie += j.ntiles;
+      ntie += (j.M + ch_fin - 1) / ch_fin;
     }
     const size_t b0 = tn.size();
-    push_tiles(tn, i, 0, d.N);
+    push_tiles(tn, i, 0, d.N, ch_n);
     d.nt_n = (int32_t)(tn.size() - b0);
     const size_t b1 = tset.size();
-    for (int s = 0; s < d.nseg; ++s) push_tiles(tset, i, s, d.seg[s].len);
+    for (int s = 0; s < d.nseg; ++s) push_tiles(tset, i, s, d.seg[s].len, ch_set);
     d.nt_set = (int32_t)(tset.size() - b1);
     const size_t b2 = tfin.size();
     for (int b = 0; b < d.nb; ++b) {
       const int t = d.blk[b].type;
       if (t == BT_L1 || t == BT_L2 || t == BT_CARD) {
-        push_tiles(tfin, i, b, d.blk[b].M);
+        push_tiles(tfin, i, b, d.blk[b].M, ch_fin);
         P.any_fin = true;
       }
       if (t == BT_CARD) P.any_card = true;
     }
     d.nt_fin = (int32_t)(tfin.size() - b2);
-    for (int j = 0; j < (int)L.jobs.size(); ++j) push_tiles(tsel, i, d.job0 + j, L.jobs[j].M);
+    for (int j = 0; j < (int)L.jobs.size(); ++j) push_tiles(tsel, i, d.job0 + j, L.jobs[j].M, ch_sel);
     const int cgl = L.opts.cg_iters > 0 ? L.opts.cg_iters : L.opts.cg_max;
     if (cgl > P.cg_launch) P.cg_launch = cgl;
     if (L.opts.max_iter > P.max_iter) P.max_iter = L.opts.max_iter;
@@ -437,6 +491,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const int64_t o_hcnt = take((int64_t)njobs * kBins * 4);
   const int64_t o_hs1 = take((int64_t)njobs * kBins * 8);
   const int64_t o_hs2 = take((int64_t)njobs * kBins * 8);
+  const int64_t o_hs3 = take((int64_t)njobs * kBins * 8);
   P.hist_end = off;
   const int64_t o_ties = take(ntie * 4);
   const int64_t o_tn = take((int64_t)tn.size() * sizeof(Tile));
@@ -487,6 +542,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.d_hcnt = (uint32_t *)at(o_hcnt);
   P.d_hs1 = (double *)at(o_hs1);
   P.d_hs2 = (double *)at(o_hs2);
+  P.d_hs3 = (double *)at(o_hs3);
   P.d_ties = (uint32_t *)at(o_ties);
   P.d_tn = (Tile *)at(o_tn);
   P.d_tset = (Tile *)at(o_tset);
@@ -532,7 +588,7 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, KernelTimer *tm) {
     for (int pass = 0; pass < np; ++pass) {
       T0(KT_SELECT);
       CK(launch_select(L, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
-                       pass));
+                       P.d_hs3, pass));
       T1(KT_SELECT);
     }
   }

@@ -59,9 +59,13 @@ InstDev op_inst(const GridDesc &g, int op) {
   d.nx = (int32_t)g.n[1];
   d.ny = (int32_t)g.n[2];
   d.ndim = g.ndim;
+  set_fastdiv(d);
   d.ihz = 1.0 / g.h[0];
   d.ihx = 1.0 / g.h[1];
   d.ihy = 1.0 / g.h[2];
+  d.ihzf = (float)d.ihz;
+  d.ihxf = (float)d.ihx;
+  d.ihyf = (float)d.ihy;
   d.N = g.N();
   int64_t row0 = 0;
   for (int kind : op_parts(g, op)) {
@@ -398,6 +402,10 @@ sip_status sip_system_apply(const sip_grid *grid, const int *ops, const double *
   sc.cz = cz / (g.h[0] * g.h[0]);
   sc.cx = cx / (g.h[1] * g.h[1]);
   sc.cy = cy / (g.h[2] * g.h[2]);
+  sc.cf[0] = (float)sc.c0;
+  sc.cf[1] = (float)sc.cz;
+  sc.cf[2] = (float)sc.cx;
+  sc.cf[3] = (float)sc.cy;
   DevCopy<InstDev> d;
   DevCopy<InstScal> ds;
   CKH(d.make(op_inst(g, SIP_OP_I)));
@@ -449,7 +457,7 @@ sip_status sip_project_set(const sip_set *set, int dtype, const void *w_dev, int
   if (P.nt_sel)
     for (int pass = 0; pass < select_passes(dtype); ++pass)
       CKH(launch_select(Ln, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
-                        pass));
+                        P.d_hs3, pass));
   if (P.any_card) CKH(launch_ties(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
   if (P.nt_fin) CKH(launch_final(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
   CKH(cudaMemcpyAsync(y_dev, d.y, (size_t)n * esz(dtype), cudaMemcpyDeviceToDevice, cs));

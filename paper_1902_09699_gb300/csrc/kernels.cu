@@ -16,8 +16,17 @@
 //   k_final      l1 / l2 / card prox from the stored w_i and the dual update
 //   k_tail       per instance: r_feas, r_evol, stopping rule, Algorithm
 //                adapt-rho-gamma, new stencil coefficients of C, k += 1
-// All scalars live on the device; reductions are binary64 and finish in the
-// last CTA to arrive ("last tile"), so no launch depends on a host sync.
+// All scalars live on the device; reductions are binary64 across threads and
+// finish in the last CTA to arrive ("last tile"), so no launch waits on the
+// host.
+//
+// Work decomposition: every launch walks a list of work items; one CTA owns
+// one item (a contiguous run of grid points / rows of one instance, segment,
+// block or selection job) and walks it in steps of PT rows per thread
+// (PerThread<T>).  Inside a step every thread first issues all of its
+// global loads and only then computes, so the memory system sees many
+// independent requests per thread.  Per-CTA partial sums are merged with one
+// set of binary64 atomics per CTA.
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -71,56 +80,134 @@ __device__ __forceinline__ bool arrive_last(uint32_t *counter, uint32_t n) {
   return false;
 }
 
+// Per-thread partial sums: binary32 for binary32 storage (a thread adds at
+// most the rows of one work item), binary64 otherwise; every sum across
+// threads and CTAs is binary64.
+template <typename T> struct AccOf { using type = double; };
+template <> struct AccOf<float> { using type = float; };
+
+// Rows per thread per step: 4 in binary32, 2 in binary64 (register budget).
+template <typename T> struct PerThread { static constexpr int value = 2; };
+template <> struct PerThread<float> { static constexpr int value = 4; };
+#define SIP_STEP_CONSTANTS                               \
+  constexpr int PT = PerThread<T>::value;                \
+  constexpr int SUB = kThreads * PT;                     \
+  static_assert(kTile % SUB == 0, "step must divide kTile")
+
 __device__ __forceinline__ bool adapt_iter(const InstDev &in, int k) {
   return in.adapt != 0 && in.rho_sched == nullptr &&
          (k % in.adapt_every) == (1 % in.adapt_every);
 }
 __device__ __forceinline__ bool check_iter(const InstDev &in, int k) { return (k % in.check_every) == 0; }
 
-// s = A x for one row of a segment (Eq. FD_mat): forward differences scaled
-// by 1/h, no boundary rows.  g receives the grid index of the row's base
-// sample.
-template <typename T>
-__device__ __forceinline__ T seg_forward(const InstDev &in, int kind, const T *__restrict__ x,
-                                         int64_t row, int64_t &g) {
-  switch (kind) {
-    case SEG_DZ: {
-      const uint32_t r = (uint32_t)row, d = (uint32_t)(in.nz - 1);
-      const uint32_t t = r / d;             // ix + nx*iy
-      g = (int64_t)r + t;                   // iz + nz*t
-      return (x[g + 1] - x[g]) * (T)in.ihz;
-    }
-    case SEG_DX: {
-      const uint32_t r = (uint32_t)row, nz = (uint32_t)in.nz;
-      const uint32_t t = r / nz;            // ix + (nx-1)*iy
-      const uint32_t iy = t / (uint32_t)(in.nx - 1);
-      g = (int64_t)r + (int64_t)nz * iy;
-      return (x[g + nz] - x[g]) * (T)in.ihx;
-    }
-    case SEG_DY: {
-      g = row;
-      return (x[g + (int64_t)in.nz * in.nx] - x[g]) * (T)in.ihy;
-    }
-    default:
-      g = row;
-      return x[row];
+// Per-iteration scalars in the storage type.  The binary64 values are
+// authoritative; binary32 kernels read the binary32 copies the tails write
+// next to them, so no hot loop converts between precisions.
+enum BlkField : int { BF_RHO = 0, BF_IRHO, BF_GAMMA, BF_OMG, BF_INV1P, BF_L2SCALE };
+template <typename T> struct SV;
+template <> struct SV<double> {
+  static __device__ __forceinline__ double c(const InstScal &s, int i) {
+    return i == 0 ? s.c0 : i == 1 ? s.cz : i == 2 ? s.cx : s.cy;
   }
+  static __device__ __forceinline__ double alpha(const InstScal &s) { return s.alpha; }
+  static __device__ __forceinline__ double beta(const InstScal &s) { return s.beta; }
+  static __device__ __forceinline__ double blk(const InstScal &s, int b, int f) {
+    switch (f) {
+      case BF_RHO: return s.rho[b];
+      case BF_IRHO: return s.irho[b];
+      case BF_GAMMA: return s.gamma[b];
+      case BF_OMG: return 1.0 - s.gamma[b];
+      case BF_INV1P: return s.inv1p[b];
+      default: return s.l2scale[b];
+    }
+  }
+  static __device__ __forceinline__ double ih(const InstDev &in, int axis) {
+    return axis == 0 ? in.ihz : axis == 1 ? in.ihx : in.ihy;
+  }
+  static __device__ __forceinline__ double theta(const JobScal &j) { return j.theta; }
+};
+template <> struct SV<float> {
+  static __device__ __forceinline__ float c(const InstScal &s, int i) { return s.cf[i]; }
+  static __device__ __forceinline__ float alpha(const InstScal &s) { return s.alphaf; }
+  static __device__ __forceinline__ float beta(const InstScal &s) { return s.betaf; }
+  static __device__ __forceinline__ float blk(const InstScal &s, int b, int f) { return s.bf[b][f]; }
+  static __device__ __forceinline__ float ih(const InstDev &in, int axis) {
+    return axis == 0 ? in.ihzf : axis == 1 ? in.ihxf : in.ihyf;
+  }
+  static __device__ __forceinline__ float theta(const JobScal &j) { return j.thetaf; }
+};
+
+// binary32 copies of the block scalars after rho / gamma / l2 scale changed
+__device__ __forceinline__ void store_block_f32(InstScal &sc, int b) {
+  sc.bf[b][BF_RHO] = (float)sc.rho[b];
+  sc.bf[b][BF_IRHO] = (float)sc.irho[b];
+  sc.bf[b][BF_GAMMA] = (float)sc.gamma[b];
+  sc.bf[b][BF_OMG] = (float)(1.0 - sc.gamma[b]);
+  sc.bf[b][BF_INV1P] = (float)sc.inv1p[b];
+  sc.bf[b][BF_L2SCALE] = (float)sc.l2scale[b];
+}
+__device__ __forceinline__ void store_coef_f32(InstScal &sc) {
+  sc.cf[0] = (float)sc.c0;
+  sc.cf[1] = (float)sc.cz;
+  sc.cf[2] = (float)sc.cx;
+  sc.cf[3] = (float)sc.cy;
 }
 
+// Grid position of a linear index g (z fastest).
 struct GridPos {
   int32_t iz, ix, iy;
   int64_t t;  // ix + nx*iy
 };
 __device__ __forceinline__ GridPos grid_pos(const InstDev &in, int64_t g) {
   GridPos p;
-  const uint32_t gg = (uint32_t)g, nz = (uint32_t)in.nz;
-  const uint32_t t = gg / nz;
-  p.iz = (int32_t)(gg - t * nz);
+  const uint32_t gg = (uint32_t)g;
+  const uint32_t t = fdiv(gg, in.fz);
+  p.iz = (int32_t)(gg - t * (uint32_t)in.nz);
   p.t = t;
-  const uint32_t iy = t / (uint32_t)in.nx;
+  const uint32_t iy = fdiv(t, in.fx);
   p.iy = (int32_t)iy;
   p.ix = (int32_t)(t - iy * (uint32_t)in.nx);
   return p;
+}
+
+// Grid index of the base sample of a row of a difference segment and the
+// offset of its partner sample (Eq. FD_mat: row = (x[g + off] - x[g]) / h).
+__device__ __forceinline__ int64_t seg_base(const InstDev &in, int kind, int64_t row, int64_t &off) {
+  switch (kind) {
+    case SEG_DZ: {
+      const uint32_t t = fdiv((uint32_t)row, in.fzm);  // ix + nx*iy
+      off = 1;
+      return row + t;
+    }
+    case SEG_DX: {
+      const uint32_t t = fdiv((uint32_t)row, in.fz);   // ix + (nx-1)*iy
+      const uint32_t iy = fdiv(t, in.fxm);
+      off = in.nz;
+      return row + (int64_t)in.nz * iy;
+    }
+    case SEG_DY:
+      off = (int64_t)in.nz * in.nx;
+      return row;
+    default:
+      off = 0;
+      return row;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T seg_ih(const InstDev &in, int kind) {
+  return kind == SEG_DZ ? SV<T>::ih(in, 0) : kind == SEG_DX ? SV<T>::ih(in, 1) : kind == SEG_DY ? SV<T>::ih(in, 2) : T(1);
+}
+
+// s = A x for one row of a segment (used by the single-step entry points and
+// the norm kernel; the loop kernels inline the same arithmetic).
+template <typename T>
+__device__ __forceinline__ T seg_forward(const InstDev &in, int kind, const T *__restrict__ x, int64_t row,
+                                         int64_t &g) {
+  int64_t off;
+  g = seg_base(in, kind, row, off);
+  if (kind == SEG_I || kind == SEG_RING) return x[g];
+  return (x[g + off] - x[g]) * seg_ih<T>(in, kind);
 }
 
 // (A^T u)[g] for one segment, where u(row) is supplied by a functor over the
@@ -132,49 +219,83 @@ __device__ __forceinline__ T seg_adjoint(const InstDev &in, int kind, const Grid
       const int64_t r = g - p.t;  // iz + (nz-1)*t
       T a = p.iz >= 1 ? u(r - 1) : T(0);
       T b = p.iz <= in.nz - 2 ? u(r) : T(0);
-      return (a - b) * (T)in.ihz;
+      return (a - b) * SV<T>::ih(in, 0);
     }
     case SEG_DX: {
       const int64_t r = g - (int64_t)in.nz * p.iy;  // iz + nz*(ix + (nx-1)*iy)
       T a = p.ix >= 1 ? u(r - in.nz) : T(0);
       T b = p.ix <= in.nx - 2 ? u(r) : T(0);
-      return (a - b) * (T)in.ihx;
+      return (a - b) * SV<T>::ih(in, 1);
     }
     case SEG_DY: {
       const int64_t s = (int64_t)in.nz * in.nx;
       T a = p.iy >= 1 ? u(g - s) : T(0);
       T b = p.iy <= in.ny - 2 ? u(g) : T(0);
-      return (a - b) * (T)in.ihy;
+      return (a - b) * SV<T>::ih(in, 2);
     }
     default:
       return u(g);
   }
 }
 
-// (C v)[g] with C = c0 I + cz D_z^T D_z + cx D_x^T D_x + cy D_y^T D_y
-// (Eq. sys_mat); D^T D along an axis is the Neumann second difference.
+// Coefficients of C = c0 I + cz D_z^T D_z + cx D_x^T D_x + cy D_y^T D_y
+// (Eq. sys_mat) in the storage type; D^T D along an axis is the Neumann
+// second difference.
+template <typename T>
+struct CSys {
+  T c0, cz, cx, cy;
+  __device__ __forceinline__ void load(const InstScal &sc) {
+    c0 = SV<T>::c(sc, 0);
+    cz = SV<T>::c(sc, 1);
+    cx = SV<T>::c(sc, 2);
+    cy = SV<T>::c(sc, 3);
+  }
+};
+
+// Values of a vector v (v(i) = functor) at the 7-point stencil of g; the
+// neighbours that fall outside the grid are not read.
+template <typename T>
+struct Nbr {
+  T c, zm, zp, xm, xp, ym, yp;
+};
+template <typename T, typename V>
+__device__ __forceinline__ void load_nbr(const InstDev &in, const GridPos &p, int64_t g, V v, Nbr<T> &o) {
+  const int64_t sxy = (int64_t)in.nz * in.nx;
+  o.c = v(g);
+  o.zm = p.iz > 0 ? v(g - 1) : o.c;
+  o.zp = p.iz < in.nz - 1 ? v(g + 1) : o.c;
+  o.xm = p.ix > 0 ? v(g - in.nz) : o.c;
+  o.xp = p.ix < in.nx - 1 ? v(g + in.nz) : o.c;
+  o.ym = p.iy > 0 ? v(g - sxy) : o.c;
+  o.yp = p.iy < in.ny - 1 ? v(g + sxy) : o.c;
+}
+// A missing neighbour was loaded as the centre value, so its difference is 0:
+// exactly the Neumann (no boundary row) second difference of Eq. FD_mat.
+template <typename T>
+__device__ __forceinline__ T apply_c(const CSys<T> &C, const Nbr<T> &n) {
+  const T lz = (n.c - n.zm) + (n.c - n.zp);
+  const T lx = (n.c - n.xm) + (n.c - n.xp);
+  const T ly = (n.c - n.ym) + (n.c - n.yp);
+  return C.c0 * n.c + C.cz * lz + C.cx * lx + C.cy * ly;
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ T csys(const InstDev &in, const InstScal &sc, const GridPos &p, int64_t g, V v) {
-  const T c = v(g);
-  T lz = T(0), lx = T(0), ly = T(0);
-  if (p.iz > 0) lz += c - v(g - 1);
-  if (p.iz < in.nz - 1) lz += c - v(g + 1);
-  if (p.ix > 0) lx += c - v(g - in.nz);
-  if (p.ix < in.nx - 1) lx += c - v(g + in.nz);
-  if (in.ny > 1) {
-    const int64_t s = (int64_t)in.nz * in.nx;
-    if (p.iy > 0) ly += c - v(g - s);
-    if (p.iy < in.ny - 1) ly += c - v(g + s);
-  }
-  return (T)sc.c0 * c + (T)sc.cz * lz + (T)sc.cx * lx + (T)sc.cy * ly;
+  CSys<T> C;
+  C.load(sc);
+  Nbr<T> n;
+  load_nbr<T>(in, p, g, v, n);
+  return apply_c(C, n);
 }
 
 // --------------------------------------------------------------------------
 // x-update right-hand side and warm residual
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                   InstScal *__restrict__ scal) {
+  SIP_STEP_CONSTANTS;
+  using A = typename AccOf<T>::type;
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
@@ -184,27 +305,52 @@ __global__ void __launch_bounds__(kThreads) k_rhs(const Tile *__restrict__ tiles
   const T *__restrict__ v = (const T *)in.v;
   const T *__restrict__ m = (const T *)in.m;
   T *__restrict__ r = (T *)in.r;
-  double acc[2] = {0.0, 0.0};
+  CSys<T> C;
+  C.load(sc);
+  __shared__ T srho[kMaxBlocks];
+  if (threadIdx.x < in.nb) srho[threadIdx.x] = SV<T>::blk(sc, threadIdx.x, BF_RHO);
+  __syncthreads();
+  const int alg1 = in.alg1, nseg = in.nseg;
+  const int64_t end = tl.start + tl.len;
+  A a0 = A(0), a1 = A(0);
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    int64_t g[PT];
+    GridPos pos[PT];
+    T b[PT];
+    Nbr<T> xn[PT];
 #pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t g = tl.start + threadIdx.x + (int64_t)e * kThreads;
-    if (g >= tl.start + tl.len) break;
-    const GridPos p = grid_pos(in, g);
-    T b = in.alg1 ? T(0) : m[g];
-    for (int sgi = 0; sgi < in.nseg; ++sgi) {
+    for (int e = 0; e < PT; ++e) {
+      g[e] = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g[e] < end) {
+        pos[e] = grid_pos(in, g[e]);
+        b[e] = alg1 ? T(0) : m[g[e]];
+        load_nbr<T>(in, pos[e], g[e], [&](int64_t i) { return x[i]; }, xn[e]);
+      }
+    }
+    for (int sgi = 0; sgi < nseg; ++sgi) {
       const SegDev &sg = in.seg[sgi];
       if (sg.kind == SEG_RING) continue;
       const int blk = sg.block;
-      const T rho = (T)sc.rho[blk];
-      const int64_t base = in.blk[blk].yoff + sg.row0;
-      b += seg_adjoint<T>(in, sg.kind, p, g, [&](int64_t row) { return rho * y[base + row] + v[base + row]; });
+      const T rho = srho[blk];
+      const int64_t bs = in.blk[blk].yoff + sg.row0;
+      const T *__restrict__ ys = y + bs;
+      const T *__restrict__ vs = v + bs;
+#pragma unroll
+      for (int e = 0; e < PT; ++e)
+        if (g[e] < end)
+          b[e] += seg_adjoint<T>(in, sg.kind, pos[e], g[e], [&](int64_t row) { return rho * ys[row] + vs[row]; });
     }
-    const T cx = csys<T>(in, sc, p, g, [&](int64_t i) { return x[i]; });
-    const T rv = b - cx;
-    r[g] = rv;
-    acc[0] += (double)b * (double)b;
-    acc[1] += (double)rv * (double)rv;
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      if (g[e] < end) {
+        const T rv = b[e] - apply_c(C, xn[e]);
+        r[g[e]] = rv;
+        a0 += (A)b[e] * (A)b[e];
+        a1 += (A)rv * (A)rv;
+      }
+    }
   }
+  double acc[2] = {(double)a0, (double)a1};
   block_sum<2>(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -221,6 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(const Tile *__restrict__ tiles
     sc.rr = rr;
     sc.rr0 = rr;
     sc.beta = 0.0;
+    sc.betaf = 0.f;
     sc.cg_steps = 0;
     const int limit = in.cg_iters > 0 ? in.cg_iters : in.cg_max;
     sc.cg_active = (limit > 0 && rr > 0.0) ? 1 : 0;
@@ -231,36 +378,56 @@ __global__ void __launch_bounds__(kThreads) k_rhs(const Tile *__restrict__ tiles
 // CG: direction + matrix-vector product
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cg_dir(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kThreads, 3) k_cg_dir(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                      InstScal *__restrict__ scal) {
+  SIP_STEP_CONSTANTS;
+  using A = typename AccOf<T>::type;
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done || !sc.cg_active) return;
   const T *__restrict__ r = (const T *)in.r;
-  const T *__restrict__ pold = (const T *)(sc.pbuf ? in.p1 : in.p0);
-  T *__restrict__ pnew = (T *)(sc.pbuf ? in.p0 : in.p1);
+  const int pb = sc.pbuf;
+  const T *__restrict__ pold = (const T *)(pb ? in.p1 : in.p0);
+  T *__restrict__ pnew = (T *)(pb ? in.p0 : in.p1);
   T *__restrict__ q = (T *)in.q;
-  const bool first = sc.cg_steps == 0;
-  const T beta = (T)sc.beta;
-  double acc[1] = {0.0};
+  // beta = 0 on the first step: p = r (the old direction, finite, drops out)
+  const T beta = sc.cg_steps == 0 ? T(0) : SV<T>::beta(sc);
+  CSys<T> C;
+  C.load(sc);
+  const int64_t end = tl.start + tl.len;
+  A a0 = A(0);
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    int64_t g[PT];
+    Nbr<T> rn[PT], pn[PT];
 #pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t g = tl.start + threadIdx.x + (int64_t)e * kThreads;
-    if (g >= tl.start + tl.len) break;
-    const GridPos p = grid_pos(in, g);
-    T pg, qg;
-    if (first) {
-      pg = r[g];
-      qg = csys<T>(in, sc, p, g, [&](int64_t i) { return r[i]; });
-    } else {
-      pg = r[g] + beta * pold[g];
-      qg = csys<T>(in, sc, p, g, [&](int64_t i) { return r[i] + beta * pold[i]; });
+    for (int e = 0; e < PT; ++e) {
+      g[e] = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g[e] < end) {
+        const GridPos p = grid_pos(in, g[e]);
+        load_nbr<T>(in, p, g[e], [&](int64_t i) { return r[i]; }, rn[e]);
+        load_nbr<T>(in, p, g[e], [&](int64_t i) { return pold[i]; }, pn[e]);
+      }
     }
-    pnew[g] = pg;
-    q[g] = qg;
-    acc[0] += (double)pg * (double)qg;
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      if (g[e] < end) {
+        Nbr<T> d;
+        d.c = rn[e].c + beta * pn[e].c;
+        d.zm = rn[e].zm + beta * pn[e].zm;
+        d.zp = rn[e].zp + beta * pn[e].zp;
+        d.xm = rn[e].xm + beta * pn[e].xm;
+        d.xp = rn[e].xp + beta * pn[e].xp;
+        d.ym = rn[e].ym + beta * pn[e].ym;
+        d.yp = rn[e].yp + beta * pn[e].yp;
+        const T qg = apply_c(C, d);
+        pnew[g[e]] = d.c;
+        q[g[e]] = qg;
+        a0 += (A)d.c * (A)qg;
+      }
+    }
   }
+  double acc[1] = {(double)a0};
   block_sum<1>(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -273,6 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(const Tile *__restrict__ ti
     sc.acc_n[0] = 0.0;
     if (pq > 0.0) {
       sc.alpha = sc.rr / pq;
+      sc.alphaf = (float)sc.alpha;
     } else {
       sc.cg_active = 0;  // p^T C p <= 0: stop CG
     }
@@ -280,8 +448,10 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(const Tile *__restrict__ ti
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cg_upd(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kThreads, 4) k_cg_upd(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                      InstScal *__restrict__ scal) {
+  SIP_STEP_CONSTANTS;
+  using A = typename AccOf<T>::type;
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
@@ -290,17 +460,33 @@ __global__ void __launch_bounds__(kThreads) k_cg_upd(const Tile *__restrict__ ti
   const T *__restrict__ q = (const T *)in.q;
   T *__restrict__ x = (T *)in.x;
   T *__restrict__ r = (T *)in.r;
-  const T alpha = (T)sc.alpha;
-  double acc[1] = {0.0};
+  const T alpha = SV<T>::alpha(sc);
+  const int64_t end = tl.start + tl.len;
+  A a0 = A(0);
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    T pv[PT], qv[PT], xv[PT], rv[PT];
 #pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t g = tl.start + threadIdx.x + (int64_t)e * kThreads;
-    if (g >= tl.start + tl.len) break;
-    x[g] = x[g] + alpha * p[g];
-    const T rv = r[g] - alpha * q[g];
-    r[g] = rv;
-    acc[0] += (double)rv * (double)rv;
+    for (int e = 0; e < PT; ++e) {
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) {
+        pv[e] = p[g];
+        qv[e] = q[g];
+        xv[e] = x[g];
+        rv[e] = r[g];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) {
+        x[g] = xv[e] + alpha * pv[e];
+        const T rn = rv[e] - alpha * qv[e];
+        r[g] = rn;
+        a0 += (A)rn * (A)rn;
+      }
+    }
   }
+  double acc[1] = {(double)a0};
   block_sum<1>(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -312,6 +498,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_upd(const Tile *__restrict__ ti
     const double rr = ldv(&sc.acc_n[0]);
     sc.acc_n[0] = 0.0;
     sc.beta = rr / sc.rr;
+    sc.betaf = (float)sc.beta;
     sc.rr = rr;
     sc.cg_steps += 1;
     sc.cg_total += 1;
@@ -332,12 +519,202 @@ __global__ void __launch_bounds__(kThreads) k_cg_upd(const Tile *__restrict__ ti
 // adapt-rho-gamma; Eqs. feas_stop, obj_stop)
 // --------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ T clip(T w, double lo, double hi) {
-  return fmin(fmax(w, (T)lo), (T)hi);
+__device__ void setpass_ring(const Tile &tl, const InstDev &in, InstScal &sc, int k, bool chk) {
+  SIP_STEP_CONSTANTS;
+  using A = typename AccOf<T>::type;
+  // x^k against the stored x^{k-1} .. x^{k-s} (Eq. obj_stop), then store x^k.
+  const T *__restrict__ x = (const T *)in.x;
+  T *__restrict__ ring = (T *)in.ring;
+  const int H = in.hist;
+  const int jmax = k < H ? k : H;
+  const int64_t N = in.N;
+  const int64_t wslot = (int64_t)(k % H) * N;
+  const int64_t end = tl.start + tl.len;
+  A acc[kMaxHist + 1];
+#pragma unroll
+  for (int j = 0; j <= kMaxHist; ++j) acc[j] = A(0);
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    T xv[PT];
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) xv[e] = x[g];
+    }
+    if (chk) {
+#pragma unroll
+      for (int j = 1; j <= kMaxHist; ++j) {
+        if (j <= jmax) {
+          const int64_t so = (int64_t)((k - j) % H) * N;
+          T hv[PT];
+#pragma unroll
+          for (int e = 0; e < PT; ++e) {
+            const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+            if (g < end) hv[e] = ring[so + g];
+          }
+#pragma unroll
+          for (int e = 0; e < PT; ++e) {
+            const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+            if (g < end) {
+              const A d = (A)xv[e] - (A)hv[e];
+              acc[j] += d * d;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) {
+        if (chk) acc[0] += (A)xv[e] * (A)xv[e];
+        ring[wslot + g] = xv[e];
+      }
+    }
+  }
+  if (chk) {
+    double dacc[kMaxHist + 1];
+#pragma unroll
+    for (int j = 0; j <= kMaxHist; ++j) dacc[j] = (double)acc[j];
+    block_sum<kMaxHist + 1>(dacc);
+    if (threadIdx.x == 0)
+      for (int j = 0; j <= jmax; ++j) atomicAdd(&sc.acc_ring[j], dacc[j]);
+  }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, const SegDev &sg, int k, bool ad,
+                              bool ad_dots, bool chk) {
+  SIP_STEP_CONSTANTS;
+  using A = typename AccOf<T>::type;
+  const int b = sg.block;
+  const BlockDev &bd = in.blk[b];
+  const T rho = SV<T>::blk(sc, b, BF_RHO), irho = SV<T>::blk(sc, b, BF_IRHO);
+  const T gam = SV<T>::blk(sc, b, BF_GAMMA), one_m_gam = SV<T>::blk(sc, b, BF_OMG);
+  const T inv1p = SV<T>::blk(sc, b, BF_INV1P);
+  const T lo = (T)bd.lo, hi = (T)bd.hi;
+  const T ih = seg_ih<T>(in, sg.kind);
+  const int kind = sg.kind;
+  const int type = bd.type;
+  const bool pointwise = type == BT_BOUNDS || type == BT_DIST;
+  const T *__restrict__ x = (const T *)in.x;
+  T *__restrict__ y = (T *)in.y + bd.yoff + sg.row0;
+  T *__restrict__ v = (T *)in.v + bd.yoff + sg.row0;
+  T *__restrict__ wbuf = (T *)in.w + bd.woff + sg.row0;
+  T *__restrict__ sbuf = (T *)in.s + bd.soff + sg.row0;
+  T *__restrict__ k0s = (T *)in.k0s + bd.yoff + sg.row0;
+  T *__restrict__ k0vh = (T *)in.k0vh + bd.yoff + sg.row0;
+  T *__restrict__ k0y = (T *)in.k0y + bd.yoff + sg.row0;
+  T *__restrict__ k0v = (T *)in.k0v + bd.yoff + sg.row0;
+  const T *__restrict__ m = (const T *)in.m;
+  const int64_t end = tl.start + tl.len;
+  // partials: 0..5 adapt dots, 6 feasD2, 7 s2, 8 s1, 9 wnorm
+  A acc[10];
+#pragma unroll
+  for (int j = 0; j < 10; ++j) acc[j] = A(0);
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    T x0[PT], x1[PT], y0[PT], v0[PT], mg[PT];
+    T ks[PT], kvh[PT], ky[PT], kv[PT];
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+      if (row < end) {
+        int64_t off;
+        const int64_t g = seg_base(in, kind, row, off);
+        x0[e] = x[g];
+        x1[e] = x[g + off];
+        y0[e] = y[row];
+        v0[e] = v[row];
+        if (type == BT_DIST) mg[e] = m[g];
+        if (ad_dots) {
+          ks[e] = k0s[row];
+          kvh[e] = k0vh[row];
+          if (pointwise) {
+            ky[e] = k0y[row];
+            kv[e] = k0v[row];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+      if (row >= end) continue;
+      const T s = kind == SEG_I ? x0[e] : (x1[e] - x0[e]) * ih;
+      const T xbar = gam * s + one_m_gam * y0[e];
+      const T w = xbar - v0[e] * irho;
+      if (ad) {
+        // vhat^{k+1} = v^k + rho (y^k - s^{k+1}); dh = s - s^{k0}; dvh = vhat - vhat^{k0}
+        const T vh = v0[e] + rho * (y0[e] - s);
+        if (ad_dots) {
+          const A dh = (A)s - (A)ks[e];
+          const A dvh = (A)vh - (A)kvh[e];
+          acc[0] += dh * dvh;
+          acc[1] += dh * dh;
+          acc[2] += dvh * dvh;
+        }
+        k0s[row] = s;
+        k0vh[row] = vh;
+      }
+      if (pointwise) {
+        const T yn = type == BT_BOUNDS ? fmin(fmax(w, lo), hi) : (mg[e] + rho * w) * inv1p;  // Eq. prox_sq_dist
+        const T vn = v0[e] + rho * (yn - xbar);
+        y[row] = yn;
+        v[row] = vn;
+        if (ad) {
+          if (ad_dots) {
+            const A dg = (A)ky[e] - (A)yn;
+            const A dv = (A)vn - (A)kv[e];
+            acc[3] += dg * dv;
+            acc[4] += dg * dg;
+            acc[5] += dv * dv;
+          }
+          k0y[row] = yn;
+          k0v[row] = vn;
+        }
+        if (chk && type == BT_BOUNDS) {
+          const A d = (A)s - (A)fmin(fmax(s, lo), hi);
+          acc[6] += d * d;
+          acc[7] += (A)s * (A)s;
+        }
+      } else {
+        wbuf[row] = w;
+        if (type == BT_L2) acc[9] += (A)w * (A)w;
+        if (type == BT_L1) acc[9] += fabs((A)w);
+        if (chk) {
+          acc[7] += (A)s * (A)s;
+          if (type == BT_L1) acc[8] += fabs((A)s);
+          if (type != BT_L2) sbuf[row] = s;
+        }
+      }
+    }
+  }
+  double dacc[10];
+#pragma unroll
+  for (int j = 0; j < 10; ++j) dacc[j] = (double)acc[j];
+  block_sum<10>(dacc);
+  if (threadIdx.x == 0) {
+    double *a = sc.acc[b];
+    if (ad_dots) {
+      atomicAdd(&a[A_HV], dacc[0]);
+      atomicAdd(&a[A_HH], dacc[1]);
+      atomicAdd(&a[A_VHVH], dacc[2]);
+      if (pointwise) {
+        atomicAdd(&a[A_GV], dacc[3]);
+        atomicAdd(&a[A_GG], dacc[4]);
+        atomicAdd(&a[A_VV], dacc[5]);
+      }
+    }
+    if (chk) {
+      if (type == BT_BOUNDS) atomicAdd(&a[A_FEAS_D2], dacc[6]);
+      if (type != BT_DIST) atomicAdd(&a[A_S2], dacc[7]);
+      if (type == BT_L1) atomicAdd(&a[A_S1], dacc[8]);
+    }
+    if (type == BT_L1 || type == BT_L2) atomicAdd(&a[A_WNORM], dacc[9]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                       InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
                                                       const JobDev *__restrict__ jobs) {
   const Tile tl = tiles[blockIdx.x];
@@ -349,180 +726,57 @@ __global__ void __launch_bounds__(kThreads) k_setpass(const Tile *__restrict__ t
   const bool ad_dots = ad && sc.have_k0;
   const bool chk = check_iter(in, k);
   const SegDev sg = in.seg[tl.item];
-  const T *__restrict__ x = (const T *)in.x;
-  // acc layout: 0..5 adapt dots, 6 feasD2 / ring, 7 s2, 8 s1, 9 wnorm
-  double acc[kMaxHist + 2];
-#pragma unroll
-  for (int i = 0; i < kMaxHist + 2; ++i) acc[i] = 0.0;
-
-  if (sg.kind == SEG_RING) {
-    // x^k against the stored x^{k-1} .. x^{k-s} (Eq. obj_stop), then store x^k.
-    T *__restrict__ ring = (T *)in.ring;
-    const int H = in.hist;
-    const int jmax = k < H ? k : H;
-#pragma unroll
-    for (int e = 0; e < kPerThread; ++e) {
-      const int64_t g = tl.start + threadIdx.x + (int64_t)e * kThreads;
-      if (g >= tl.start + tl.len) break;
-      const T xv = x[g];
-      if (chk) {
-        acc[0] += (double)xv * (double)xv;
-        for (int j = 1; j <= jmax; ++j) {
-          const int slot = (k - j) % H;
-          const double d = (double)xv - (double)ring[(int64_t)slot * in.N + g];
-          acc[j] += d * d;
-        }
-      }
-      ring[(int64_t)(k % H) * in.N + g] = xv;
-    }
-    if (chk) {
-      block_sum<kMaxHist + 1>(*reinterpret_cast<double(*)[kMaxHist + 1]>(acc));
-      if (threadIdx.x == 0)
-        for (int j = 0; j <= jmax; ++j) atomicAdd(&sc.acc_ring[j], acc[j]);
-    }
-  } else {
-    const int b = sg.block;
-    const BlockDev &bd = in.blk[b];
-    const T rho = (T)sc.rho[b], irho = (T)sc.irho[b], gam = (T)sc.gamma[b];
-    const T one_m_gam = (T)(1.0 - sc.gamma[b]);
-    T *__restrict__ y = (T *)in.y;
-    T *__restrict__ v = (T *)in.v;
-    T *__restrict__ wbuf = (T *)in.w;
-    T *__restrict__ sbuf = (T *)in.s;
-    T *__restrict__ k0s = (T *)in.k0s;
-    T *__restrict__ k0vh = (T *)in.k0vh;
-    T *__restrict__ k0y = (T *)in.k0y;
-    T *__restrict__ k0v = (T *)in.k0v;
-    const T *__restrict__ m = (const T *)in.m;
-    const int type = bd.type;
-#pragma unroll
-    for (int e = 0; e < kPerThread; ++e) {
-      const int64_t row = tl.start + threadIdx.x + (int64_t)e * kThreads;
-      if (row >= tl.start + tl.len) break;
-      int64_t g;
-      const T s = seg_forward<T>(in, sg.kind, x, row, g);
-      const int64_t rb = sg.row0 + row;  // row inside the block
-      const int64_t yi = bd.yoff + rb;
-      const T y0 = y[yi], v0 = v[yi];
-      const T xbar = gam * s + one_m_gam * y0;
-      const T w = xbar - v0 * irho;
-      if (ad) {
-        // vhat^{k+1} = v^k + rho (y^k - s^{k+1}); dh = s - s^{k0}; dvh = vhat - vhat^{k0}
-        const T vh = v0 + rho * (y0 - s);
-        if (ad_dots) {
-          const double dh = (double)s - (double)k0s[yi];
-          const double dvh = (double)vh - (double)k0vh[yi];
-          acc[0] += dh * dvh;
-          acc[1] += dh * dh;
-          acc[2] += dvh * dvh;
-        }
-        k0s[yi] = s;
-        k0vh[yi] = vh;
-      }
-      if (type == BT_BOUNDS || type == BT_DIST) {
-        T yn;
-        if (type == BT_BOUNDS) {
-          yn = clip<T>(w, bd.lo, bd.hi);
-        } else {  // Eq. prox_sq_dist
-          yn = (m[g] + rho * w) * (T)sc.inv1p[b];
-        }
-        const T vn = v0 + rho * (yn - xbar);
-        y[yi] = yn;
-        v[yi] = vn;
-        if (ad) {
-          if (ad_dots) {
-            const double dg = -((double)yn - (double)k0y[yi]);
-            const double dv = (double)vn - (double)k0v[yi];
-            acc[3] += dg * dv;
-            acc[4] += dg * dg;
-            acc[5] += dv * dv;
-          }
-          k0y[yi] = yn;
-          k0v[yi] = vn;
-        }
-        if (chk && type == BT_BOUNDS) {
-          const double d = (double)s - (double)clip<T>(s, bd.lo, bd.hi);
-          acc[6] += d * d;
-          acc[7] += (double)s * (double)s;
-        }
-      } else {
-        wbuf[bd.woff + rb] = w;
-        if (type == BT_L2) acc[9] += (double)w * (double)w;
-        if (type == BT_L1) acc[9] += fabs((double)w);
-        if (chk) {
-          acc[7] += (double)s * (double)s;
-          if (type == BT_L1) acc[8] += fabs((double)s);
-          if (type != BT_L2) sbuf[bd.soff + rb] = s;
-        }
-      }
-    }
-    block_sum<10>(*reinterpret_cast<double(*)[10]>(acc));
-    if (threadIdx.x == 0) {
-      double *a = sc.acc[b];
-      if (ad_dots) {
-        atomicAdd(&a[A_HV], acc[0]);
-        atomicAdd(&a[A_HH], acc[1]);
-        atomicAdd(&a[A_VHVH], acc[2]);
-        if (type == BT_BOUNDS || type == BT_DIST) {
-          atomicAdd(&a[A_GV], acc[3]);
-          atomicAdd(&a[A_GG], acc[4]);
-          atomicAdd(&a[A_VV], acc[5]);
-        }
-      }
-      if (chk) {
-        atomicAdd(&a[A_FEAS_D2], acc[6]);
-        atomicAdd(&a[A_S2], acc[7]);
-        atomicAdd(&a[A_S1], acc[8]);
-      }
-      if (type == BT_L1 || type == BT_L2) atomicAdd(&a[A_WNORM], acc[9]);
-    }
-  }
+  if (sg.kind == SEG_RING)
+    setpass_ring<T>(tl, in, sc, k, chk);
+  else
+    setpass_block<T>(tl, in, sc, sg, k, ad, ad_dots, chk);
 
   // The last CTA of the instance resolves the l2 scales and arms the
-  // selection jobs of this iteration.
+  // selection jobs of this iteration, one block per lane of warp 0.
   __shared__ bool last;
   if (threadIdx.x == 0) last = arrive_last(&sc.cnt_set, (uint32_t)in.nt_set);
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
-  for (int b = 0; b < in.nb; ++b) {
-    const BlockDev &bd = in.blk[b];
-    const double *a = sc.acc[b];
-    if (bd.type == BT_L2) {
-      const double nrm = sqrt(ldv(&a[A_WNORM]));
-      const double sg2 = sc.sigma[b];
-      sc.l2scale[b] = nrm > sg2 ? sg2 / nrm : 1.0;
+  if (!last || threadIdx.x >= 32) return;
+  const int b = threadIdx.x;
+  if (b >= in.nb) return;
+  const BlockDev &bd = in.blk[b];
+  const double *a = sc.acc[b];
+  if (bd.type == BT_L2) {
+    const double nrm = sqrt(ldv(&a[A_WNORM]));
+    const double sg2 = sc.sigma[b];
+    sc.l2scale[b] = nrm > sg2 ? sg2 / nrm : 1.0;
+    sc.bf[b][BF_L2SCALE] = (float)sc.l2scale[b];
+  }
+  if (bd.job_w >= 0) {
+    JobScal &js = jscal[bd.job_w];
+    js.active = 1;
+    js.pass = 0;
+    js.prefix = 0;
+    js.c_above = js.s1_above = js.s2_above = 0.0;
+    js.tie_needed = 0;
+    if (bd.type == BT_L1) {
+      js.tau = sc.sigma[b];
+      js.theta = 0.0;
+      js.mode = js.tau == 0.0 ? JM_NONE : (ldv(&a[A_WNORM]) <= js.tau ? JM_ALL : JM_SELECT);
+    } else {
+      js.k = sc.kcard[b];
+      js.mode = js.k == 0 ? JM_NONE : (js.k >= bd.M ? JM_ALL : JM_SELECT);
     }
-    if (bd.job_w >= 0) {
-      JobScal &js = jscal[bd.job_w];
-      js.active = 1;
-      js.pass = 0;
-      js.prefix = 0;
-      js.c_above = js.s1_above = js.s2_above = 0.0;
-      js.tie_needed = 0;
-      if (bd.type == BT_L1) {
-        js.tau = sc.sigma[b];
-        js.theta = 0.0;
-        js.mode = js.tau == 0.0 ? JM_NONE : (ldv(&a[A_WNORM]) <= js.tau ? JM_ALL : JM_SELECT);
-      } else {
-        js.k = sc.kcard[b];
-        js.mode = js.k == 0 ? JM_NONE : (js.k >= bd.M ? JM_ALL : JM_SELECT);
-      }
-    }
-    if (bd.job_s >= 0) {
-      JobScal &js = jscal[bd.job_s];
-      js.active = chk ? 1 : 0;
-      js.pass = 0;
-      js.prefix = 0;
-      js.c_above = js.s1_above = js.s2_above = 0.0;
-      js.tie_needed = 0;
-      if (bd.type == BT_L1) {
-        js.tau = sc.sigma[b];
-        js.theta = 0.0;
-        js.mode = js.tau == 0.0 ? JM_NONE : (ldv(&a[A_S1]) <= js.tau ? JM_ALL : JM_SELECT);
-      } else {
-        js.k = sc.kcard[b];
-        js.mode = js.k == 0 ? JM_NONE : (js.k >= bd.M ? JM_ALL : JM_SELECT);
-      }
+  }
+  if (bd.job_s >= 0) {
+    JobScal &js = jscal[bd.job_s];
+    js.active = chk ? 1 : 0;
+    js.pass = 0;
+    js.prefix = 0;
+    js.c_above = js.s1_above = js.s2_above = 0.0;
+    js.tie_needed = 0;
+    if (bd.type == BT_L1) {
+      js.tau = sc.sigma[b];
+      js.theta = 0.0;
+      js.mode = js.tau == 0.0 ? JM_NONE : (ldv(&a[A_S1]) <= js.tau ? JM_ALL : JM_SELECT);
+    } else {
+      js.k = sc.kcard[b];
+      js.mode = js.k == 0 ? JM_NONE : (js.k >= bd.M ? JM_ALL : JM_SELECT);
     }
   }
   (void)jobs;
@@ -536,14 +790,71 @@ __global__ void __launch_bounds__(kThreads) k_setpass(const Tile *__restrict__ t
 //   l1:  largest bin d with g(lo_d) >= tau, g(t) = sum_{|w|>t} (|w| - t):
 //        the soft threshold theta lies at or above lo_d (Duchi et al.).
 //   top-k: largest bin d with count(keys >= lo_d) >= k.
+// Bin counts are exact integers; bin sums of |w| (l1) and of w^2 (the
+// feasibility measure of the l1 and card sets) are binary64.
 // --------------------------------------------------------------------------
+// Bin accumulators.  binary32 data: every value in a bin shares one exponent
+// E (the first digit holds all exponent bits), so |w| = sig * 2^(E' - 150)
+// with an integer significand sig < 2^24 (E' = max(E, 1)); the bin sums of
+// sig and of sig^2 (split at bit 22) are then exact 64-bit integer sums,
+// formed with warp integer reductions and integer atomics.  binary64 data:
+// binary64 bin sums.
+template <typename T> struct BinAcc;
+template <> struct BinAcc<float> {
+  using S = unsigned long long;
+  static constexpr size_t kSmem = kBins * (sizeof(uint32_t) + 3 * sizeof(S));
+};
+template <> struct BinAcc<double> {
+  using S = double;
+  static constexpr size_t kSmem = kBins * (sizeof(uint32_t) + 2 * sizeof(S));
+};
+
+__device__ __forceinline__ double pow2(int k) {  // 2^k, -1022 <= k <= 1023
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// inclusive suffix sum over the CTA's threads (thread t gets sum_{t' >= t})
+__device__ __forceinline__ double cta_suffix(double x, double *wsum) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double v = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o < 32) x += v;
+  }
+  if (lane == 0) wsum[wid] = x;
+  __syncthreads();
+  double above = 0.0;
+  for (int w = wid + 1; w < kThreads / 32; ++w) above += wsum[w];
+  __syncthreads();
+  return x + above;
+}
+
+__device__ __forceinline__ unsigned long long cta_suffix_u64(unsigned long long x, unsigned long long *wsum) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o < 32) x += v;
+  }
+  if (lane == 0) wsum[wid] = x;
+  __syncthreads();
+  unsigned long long above = 0;
+  for (int w = wid + 1; w < kThreads / 32; ++w) above += wsum[w];
+  __syncthreads();
+  return x + above;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_select(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                     InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
-                                                     JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
-                                                     double *__restrict__ hs1, double *__restrict__ hs2, int pass) {
+__global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                        InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
+                                                        JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
+                                                        double *__restrict__ hs1, double *__restrict__ hs2,
+                                                        double *__restrict__ hs3, int pass) {
+  SIP_STEP_CONSTANTS;
   using KT = KeyOf<T>;
   using K = typename KT::K;
+  using S = typename BinAcc<T>::S;
+  constexpr bool kInt = sizeof(T) == 4;
   const Tile tl = tiles[blockIdx.x];
   const JobDev jd = jobs[tl.item];
   const InstDev &in = insts[jd.inst];
@@ -553,65 +864,95 @@ __global__ void __launch_bounds__(kThreads) k_select(const Tile *__restrict__ ti
 
   extern __shared__ unsigned char smem_raw[];
   uint32_t *cnt = (uint32_t *)smem_raw;
-  double *s1 = (double *)(smem_raw + kBins * sizeof(uint32_t));
-  double *s2 = s1 + kBins;
+  S *s1 = (S *)(smem_raw + kBins * sizeof(uint32_t));
+  S *s2 = s1 + kBins;  // binary64: sum of squares; binary32: high part of sig^2
+  S *s3 = s2 + kBins;  // binary32 only: low 22 bits of sig^2
   const bool need1 = jd.kind == JOB_L1;
   const bool need2 = jd.feas != 0;
-  for (int i = threadIdx.x; i < kBins; i += kThreads) {
+  const int hi = KT::kBits - pass * kDigitBits;
+  const int lo = hi - kDigitBits > 0 ? hi - kDigitBits : 0;
+  const int nbins = 1 << (hi - lo);
+  for (int i = threadIdx.x; i < nbins; i += kThreads) {
     cnt[i] = 0;
-    s1[i] = 0.0;
-    s2[i] = 0.0;
+    if (need1) s1[i] = S(0);
+    if (need2) {
+      s2[i] = S(0);
+      if (kInt) s3[i] = S(0);
+    }
   }
   __syncthreads();
 
-  const int hi = KT::kBits - pass * kDigitBits;
-  const int lo = hi - kDigitBits > 0 ? hi - kDigitBits : 0;
-  const K mask = (K)((1u << (hi - lo)) - 1u);
+  const K mask = (K)(nbins - 1);
   const K pre = (K)js.prefix;
+  const bool all = hi >= KT::kBits;
   const T *__restrict__ data = (const T *)(jd.feas ? in.s : in.w) + jd.data_off;
   const int lane = threadIdx.x & 31;
+  const int64_t end = tl.start + tl.len;
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    T val[PT];
 #pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t row = tl.start + threadIdx.x + (int64_t)e * kThreads;
-    const bool valid = row < tl.start + tl.len;
-    int bin = -1;
-    double a = 0.0;
-    if (valid) {
-      const T val = data[row];
-      const K key = KT::key(val);
-      if (hi >= KT::kBits || (key >> hi) == (pre >> hi)) {
-        bin = (int)((key >> lo) & mask);
-        a = fabs((double)val);
-      }
+    for (int e = 0; e < PT; ++e) {
+      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+      val[e] = row < end ? data[row] : T(0);
     }
-    // warp-aggregated histogram update: one shared atomic per distinct bin
-    unsigned pending = __ballot_sync(0xffffffffu, bin >= 0);
-    while (pending) {
-      const int leader = __ffs(pending) - 1;
-      const int lb = __shfl_sync(0xffffffffu, bin, leader);
-      const unsigned grp = __ballot_sync(0xffffffffu, bin == lb);
-      const bool mine = bin == lb;
-      double v1 = (mine && need1) ? a : 0.0;
-      double v2 = (mine && need2) ? a * a : 0.0;
-      if (need1) v1 = warp_sum(v1);
-      if (need2) v2 = warp_sum(v2);
-      if (lane == leader) {
-        atomicAdd(&cnt[lb], (uint32_t)__popc(grp));
-        if (need1) atomicAdd(&s1[lb], v1);
-        if (need2) atomicAdd(&s2[lb], v2);
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+      int bin = -1;
+      K key = 0;
+      if (row < end) {
+        key = KT::key(val[e]);
+        if (all || (key >> hi) == (pre >> hi)) bin = (int)((key >> lo) & mask);
       }
-      pending &= ~grp;
+      if constexpr (kInt) {
+        // exact integer significand and its square split at bit 22; one
+        // shared-memory integer atomic per entry and accumulator (no FP64)
+        if (bin >= 0) {
+          const uint32_t ex = (uint32_t)key >> 23, man = (uint32_t)key & 0x7fffffu;
+          const uint32_t sig = ex ? (man | 0x800000u) : man;
+          atomicAdd(&cnt[bin], 1u);
+          if (need1) atomicAdd((unsigned long long *)&s1[bin], (unsigned long long)sig);
+          if (need2) {
+            const uint64_t sq = (uint64_t)sig * sig;
+            atomicAdd((unsigned long long *)&s2[bin], (unsigned long long)(sq >> 22));
+            atomicAdd((unsigned long long *)&s3[bin], (unsigned long long)(sq & 0x3fffffu));
+          }
+        }
+      } else {
+        unsigned pending = __ballot_sync(0xffffffffu, bin >= 0);
+        const double a = bin >= 0 ? fabs((double)val[e]) : 0.0;
+        while (pending) {
+          const int leader = __ffs(pending) - 1;
+          const int lb = __shfl_sync(0xffffffffu, bin, leader);
+          const unsigned grp = __ballot_sync(0xffffffffu, bin == lb);
+          const bool mine = bin == lb;
+          double v1 = 0.0, v2 = 0.0;
+          if (need1) v1 = warp_sum(mine ? a : 0.0);
+          if (need2) v2 = warp_sum(mine ? a * a : 0.0);
+          if (lane == leader) {
+            atomicAdd(&cnt[lb], (uint32_t)__popc(grp));
+            if (need1) atomicAdd((double *)&s1[lb], v1);
+            if (need2) atomicAdd((double *)&s2[lb], v2);
+          }
+          pending &= ~grp;
+        }
+      }
     }
   }
   __syncthreads();
   uint32_t *gc = hcnt + jd.hist_off;
-  double *g1 = hs1 + jd.hist_off;
-  double *g2 = hs2 + jd.hist_off;
-  for (int i = threadIdx.x; i < kBins; i += kThreads) {
-    if (cnt[i]) {
-      atomicAdd(&gc[i], cnt[i]);
+  S *g1 = (S *)(hs1 + jd.hist_off);
+  S *g2 = (S *)(hs2 + jd.hist_off);
+  S *g3 = (S *)(hs3 + jd.hist_off);
+  for (int i = threadIdx.x; i < nbins; i += kThreads) {
+    const uint32_t c = cnt[i];
+    if (c) {
+      atomicAdd(&gc[i], c);
       if (need1) atomicAdd(&g1[i], s1[i]);
-      if (need2) atomicAdd(&g2[i], s2[i]);
+      if (need2) {
+        atomicAdd(&g2[i], s2[i]);
+        if (kInt) atomicAdd(&g3[i], s3[i]);
+      }
     }
   }
   __shared__ bool last;
@@ -621,55 +962,48 @@ __global__ void __launch_bounds__(kThreads) k_select(const Tile *__restrict__ ti
   if (!last) return;
 
   // ---- last CTA: choose the bin -------------------------------------------
-  constexpr int kPer = kBins / kThreads;  // bins per thread
-  const int nb = 1 << (hi - lo);
-  // thread t owns bins [t*kPer, t*kPer + kPer)
-  uint32_t c[kPer];
-  double a1[kPer], a2[kPer];
+  constexpr int kPer = kBins / kThreads;  // bins per thread; thread t owns [t*kPer, t*kPer + kPer)
+  double c[kPer], a1[kPer], a2[kPer];
   double tc = 0.0, t1 = 0.0, t2 = 0.0;
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const int bi = threadIdx.x * kPer + j;
-    c[j] = bi < nb ? *(volatile uint32_t *)&gc[bi] : 0u;
-    a1[j] = (bi < nb && need1) ? ldv(&g1[bi]) : 0.0;
-    a2[j] = (bi < nb && need2) ? ldv(&g2[bi]) : 0.0;
-    tc += (double)c[j];
+    c[j] = a1[j] = a2[j] = 0.0;
+    if (bi < nbins) {
+      c[j] = (double)__ldcg(&gc[bi]);
+      if constexpr (kInt) {
+        const int ex = (int)(((uint32_t)(pre | ((K)bi << lo))) >> 23);
+        const int e2 = (ex > 0 ? ex : 1) - 150;
+        if (need1) a1[j] = (double)__ldcg((const unsigned long long *)&g1[bi]) * pow2(e2);
+        if (need2)
+          a2[j] = ((double)__ldcg((const unsigned long long *)&g2[bi]) * 4194304.0 +
+                   (double)__ldcg((const unsigned long long *)&g3[bi])) * pow2(2 * e2);
+      } else {
+        if (need1) a1[j] = __ldcg((const double *)&g1[bi]);
+        if (need2) a2[j] = __ldcg((const double *)&g2[bi]);
+      }
+    }
+    tc += c[j];
     t1 += a1[j];
     t2 += a2[j];
   }
-  // exclusive suffix sums over threads (bins above this thread's range)
-  __shared__ double suf[3][kThreads];
-  suf[0][threadIdx.x] = tc;
-  suf[1][threadIdx.x] = t1;
-  suf[2][threadIdx.x] = t2;
-  __syncthreads();
-  // Hillis-Steele inclusive suffix scan
-  for (int off = 1; off < kThreads; off <<= 1) {
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-    if (threadIdx.x + off < kThreads) {
-      v0 = suf[0][threadIdx.x + off];
-      v1 = suf[1][threadIdx.x + off];
-      v2 = suf[2][threadIdx.x + off];
-    }
-    __syncthreads();
-    suf[0][threadIdx.x] += v0;
-    suf[1][threadIdx.x] += v1;
-    suf[2][threadIdx.x] += v2;
-    __syncthreads();
-  }
-  double ac = js.c_above + suf[0][threadIdx.x] - tc;  // entries above my bins
-  double as1 = js.s1_above + suf[1][threadIdx.x] - t1;
-  double as2 = js.s2_above + suf[2][threadIdx.x] - t2;
+  __shared__ double wsum[kThreads / 32];
+  __shared__ unsigned long long wsumi[kThreads / 32];
+  // exclusive suffix sums: entries in bins above this thread's range
+  const unsigned long long tci = (unsigned long long)tc;
+  double ac = js.c_above + (double)(cta_suffix_u64(tci, wsumi) - tci);
+  double as1 = js.s1_above, as2 = js.s2_above;
+  if (need1) as1 += cta_suffix(t1, wsum) - t1;
+  if (need2) as2 += cta_suffix(t2, wsum) - t2;
   int best = -1;
   double bc = 0, b1 = 0, b2 = 0;  // "above" sums for the chosen bin
   for (int j = kPer - 1; j >= 0; --j) {
     const int bi = threadIdx.x * kPer + j;
-    if (bi < nb) {
-      const double cge = ac + (double)c[j];
+    if (bi < nbins) {
+      const double cge = ac + c[j];
       bool ok;
       if (jd.kind == JOB_L1) {
-        const K lokey = pre | ((K)bi << lo);
-        const double lov = KT::val(lokey);
+        const double lov = KT::val(pre | ((K)bi << lo));
         ok = (as1 + a1[j]) - cge * lov >= js.tau;
       } else {
         ok = cge >= (double)js.k;
@@ -682,11 +1016,10 @@ __global__ void __launch_bounds__(kThreads) k_select(const Tile *__restrict__ ti
         break;
       }
     }
-    ac += (double)c[j];
+    ac += c[j];
     as1 += a1[j];
     as2 += a2[j];
   }
-  // highest satisfying bin over the CTA
   __shared__ int sbest;
   if (threadIdx.x == 0) sbest = -1;
   __syncthreads();
@@ -702,6 +1035,7 @@ __global__ void __launch_bounds__(kThreads) k_select(const Tile *__restrict__ ti
     if (lo == 0) {  // final digit: the breakpoint key is exact
       if (jd.kind == JOB_L1) {
         js.theta = (b1 - js.tau) / bc;
+        js.thetaf = (float)js.theta;
       } else {
         js.need = js.k - (int64_t)bc;
         js.cK = (int64_t)c[j];
@@ -712,18 +1046,22 @@ __global__ void __launch_bounds__(kThreads) k_select(const Tile *__restrict__ ti
     js.pass = pass + 1;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kBins; i += kThreads) {
+  for (int i = threadIdx.x; i < nbins; i += kThreads) {
     gc[i] = 0;
-    g1[i] = 0.0;
-    g2[i] = 0.0;
+    if (need1) g1[i] = S(0);
+    if (need2) {
+      g2[i] = S(0);
+      if (kInt) g3[i] = S(0);
+    }
   }
 }
 
-// Tie counts per final-pass tile for card sets whose k-th value is tied.
+// Tie counts per final-pass work item for card sets whose k-th value is tied.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ties(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kThreads, 4) k_ties(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                    InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                    JobScal *__restrict__ jscal, uint32_t *__restrict__ ties) {
+  SIP_STEP_CONSTANTS;
   using KT = KeyOf<T>;
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
@@ -734,11 +1072,14 @@ __global__ void __launch_bounds__(kThreads) k_ties(const Tile *__restrict__ tile
   if (js.mode != JM_SELECT || !js.tie_needed) return;
   const typename KT::K K = (typename KT::K)js.prefix;
   const T *__restrict__ w = (const T *)in.w + bd.woff;
+  const int64_t end = tl.start + tl.len;
   int n = 0;
+  for (int64_t base = tl.start; base < end; base += SUB) {
 #pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t row = tl.start + threadIdx.x + (int64_t)e * kThreads;
-    if (row < tl.start + tl.len && KT::key(w[row]) == K) ++n;
+    for (int e = 0; e < PT; ++e) {
+      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+      if (row < end && KT::key(w[row]) == K) ++n;
+    }
   }
   __shared__ int tot;
   if (threadIdx.x == 0) tot = 0;
@@ -753,12 +1094,14 @@ __global__ void __launch_bounds__(kThreads) k_ties(const Tile *__restrict__ tile
 // v = v + rho (y - xbar) = rho (y - w), since w = xbar - v / rho.
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_final(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                     InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                     const JobScal *__restrict__ jscal,
                                                     const uint32_t *__restrict__ ties) {
+  SIP_STEP_CONSTANTS;
   using KT = KeyOf<T>;
   using K = typename KT::K;
+  using A = typename AccOf<T>::type;
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
@@ -768,25 +1111,25 @@ __global__ void __launch_bounds__(kThreads) k_final(const Tile *__restrict__ til
   const int k = sc.k;
   const bool ad = adapt_iter(in, k);
   const bool ad_dots = ad && sc.have_k0;
-  const T rho = (T)sc.rho[b];
+  const T rho = SV<T>::blk(sc, b, BF_RHO);
   const T *__restrict__ w = (const T *)in.w + bd.woff;
   T *__restrict__ y = (T *)in.y + bd.yoff;
   T *__restrict__ v = (T *)in.v + bd.yoff;
   T *__restrict__ k0y = (T *)in.k0y + bd.yoff;
   T *__restrict__ k0v = (T *)in.k0v + bd.yoff;
   int mode = JM_ALL;
-  double theta = 0.0;
+  T theta = T(0);
   K K0 = 0;
   bool tie = false;
   int64_t need = 0, before = 0;
   if (bd.type != BT_L2) {
     const JobScal &js = jscal[bd.job_w];
     mode = js.mode;
-    theta = js.theta;
+    theta = SV<T>::theta(js);
     K0 = (K)js.prefix;
     tie = bd.type == BT_CARD && mode == JM_SELECT && js.tie_needed;
     need = js.need;
-    if (tie) {  // ties in earlier tiles of this block
+    if (tie) {  // ties in earlier work items of this block
       const uint32_t *tc = ties + jobs[bd.job_w].tie_off;
       for (int i = threadIdx.x; i < tl.seq; i += kThreads) before += tc[i];
       __shared__ unsigned long long sb;
@@ -797,71 +1140,90 @@ __global__ void __launch_bounds__(kThreads) k_final(const Tile *__restrict__ til
       before = (int64_t)sb;
     }
   }
-  const T scale = (T)sc.l2scale[b];
-  const T th = (T)theta;
-  double acc[3] = {0.0, 0.0, 0.0};
+  const T scale = SV<T>::blk(sc, b, BF_L2SCALE);
+  const T th = theta;
+  const int type = bd.type;
+  A acc[3] = {A(0), A(0), A(0)};
   __shared__ int wcount[kThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t end = tl.start + tl.len;
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    T wv[PT], ky[PT], kv[PT];
 #pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t row = tl.start + threadIdx.x + (int64_t)e * kThreads;
-    const bool valid = row < tl.start + tl.len;
-    const T wv = valid ? w[row] : T(0);
-    T yn = T(0);
-    if (bd.type == BT_L2) {
-      yn = wv * scale;
-    } else if (mode == JM_ALL) {
-      yn = wv;
-    } else if (mode == JM_NONE) {
-      yn = T(0);
-    } else if (bd.type == BT_L1) {
-      const T a = fabs(wv) - th;
-      yn = a > T(0) ? copysign(a, wv) : T(0);
-    } else {
-      // card: keep keys above the k-th key; at the k-th key keep all ties
-      // unless the tie rule must choose (ranked below)
-      const K key = KT::key(wv);
-      yn = (key > K0 || (key == K0 && !tie)) ? wv : T(0);
-    }
-    if (tie) {
-      // all threads take part in the ranked scan of this round
-      const K key = KT::key(wv);
-      const bool f = valid && key == K0;
-      const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (lane == 0) wcount[wid] = __popc(bal);
-      __syncthreads();
-      int pre = 0;
-      for (int i = 0; i < wid; ++i) pre += wcount[i];
-      int total = 0;
-      for (int i = 0; i < kThreads / 32; ++i) total += wcount[i];
-      const int rank = (int)before + pre + __popc(bal & ((1u << lane) - 1u));
-      if (f) yn = rank < need ? wv : T(0);
-      before += total;
-      __syncthreads();
-    }
-    if (valid) {
-      const T vn = rho * (yn - wv);
-      y[row] = yn;
-      v[row] = vn;
-      if (ad) {
+    for (int e = 0; e < PT; ++e) {
+      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+      if (row < end) {
+        wv[e] = w[row];
         if (ad_dots) {
-          const double dg = -((double)yn - (double)k0y[row]);
-          const double dv = (double)vn - (double)k0v[row];
-          acc[0] += dg * dv;
-          acc[1] += dg * dg;
-          acc[2] += dv * dv;
+          ky[e] = k0y[row];
+          kv[e] = k0v[row];
         }
-        k0y[row] = yn;
-        k0v[row] = vn;
+      } else {
+        wv[e] = T(0);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+      const bool valid = row < end;
+      T yn;
+      if (type == BT_L2) {
+        yn = wv[e] * scale;
+      } else if (mode == JM_ALL) {
+        yn = wv[e];
+      } else if (mode == JM_NONE) {
+        yn = T(0);
+      } else if (type == BT_L1) {
+        const T a = fabs(wv[e]) - th;
+        yn = a > T(0) ? copysign(a, wv[e]) : T(0);
+      } else {
+        // card: keep keys above the k-th key; at the k-th key keep all ties
+        // unless the tie rule must choose (ranked below)
+        const K key = KT::key(wv[e]);
+        yn = (key > K0 || (key == K0 && !tie)) ? wv[e] : T(0);
+      }
+      if (tie) {
+        // rank among tied entries in row order: rows are ordered by
+        // (step, e, thread), so scan this round's flags over the CTA
+        const bool f = valid && KT::key(wv[e]) == K0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcount[wid] = __popc(bal);
+        __syncthreads();
+        int pre = 0, total = 0;
+        for (int i = 0; i < kThreads / 32; ++i) {
+          if (i < wid) pre += wcount[i];
+          total += wcount[i];
+        }
+        const int64_t rank = before + pre + __popc(bal & ((1u << lane) - 1u));
+        if (f) yn = rank < need ? wv[e] : T(0);
+        before += total;
+        __syncthreads();
+      }
+      if (valid) {
+        const T vn = rho * (yn - wv[e]);
+        y[row] = yn;
+        v[row] = vn;
+        if (ad) {
+          if (ad_dots) {
+            const A dg = (A)ky[e] - (A)yn;
+            const A dv = (A)vn - (A)kv[e];
+            acc[0] += dg * dv;
+            acc[1] += dg * dg;
+            acc[2] += dv * dv;
+          }
+          k0y[row] = yn;
+          k0v[row] = vn;
+        }
       }
     }
   }
   if (ad_dots) {
-    block_sum<3>(acc);
+    double dacc[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+    block_sum<3>(dacc);
     if (threadIdx.x == 0) {
-      atomicAdd(&sc.acc[b][A_GV], acc[0]);
-      atomicAdd(&sc.acc[b][A_GG], acc[1]);
-      atomicAdd(&sc.acc[b][A_VV], acc[2]);
+      atomicAdd(&sc.acc[b][A_GV], dacc[0]);
+      atomicAdd(&sc.acc[b][A_GG], dacc[1]);
+      atomicAdd(&sc.acc[b][A_VV], dacc[2]);
     }
   }
 }
@@ -887,6 +1249,8 @@ __device__ void set_coefficients(const InstDev &in, InstScal &sc) {
   sc.cz = cz * in.ihz * in.ihz;
   sc.cx = cx * in.ihx * in.ihx;
   sc.cy = cy * in.ihy * in.ihy;
+  store_coef_f32(sc);
+  for (int b = 0; b < in.nb; ++b) store_block_f32(sc, b);
 }
 
 __device__ __forceinline__ double corr(double ab, double aa, double bb) {
@@ -898,126 +1262,166 @@ __device__ __forceinline__ double spectral(double ab, double aa, double bb) {
   return 2.0 * mg > sd ? mg : sd - 0.5 * mg;
 }
 
-__global__ void k_tail(const InstDev *__restrict__ insts, InstScal *__restrict__ scal,
-                       const JobScal *__restrict__ jscal, int ninst) {
+__global__ void __launch_bounds__(32) k_tail(const InstDev *__restrict__ insts, InstScal *__restrict__ scal,
+                                              const JobScal *__restrict__ jscal, int ninst) {
   const int i = blockIdx.x;
   if (i >= ninst) return;
   const InstDev &in = insts[i];
   InstScal &sc = scal[i];
   if (sc.done) return;
-  if (threadIdx.x == 0) {
-    const int k = sc.k;
-    const bool chk = check_iter(in, k);
-    const bool ad = adapt_iter(in, k);
-    double *tr = in.trace ? in.trace + (int64_t)(k - 1) * in.trace_w : nullptr;
-    if (tr) {
-      for (int b = 0; b < in.nb; ++b) {
-        tr[b] = sc.rho[b];
-        tr[in.nb + b] = sc.gamma[b];
-      }
-      tr[2 * in.nb] = sc.cg_steps;
-      tr[2 * in.nb + 1] = __longlong_as_double(0x7ff8000000000000LL);
-      for (int b = 0; b < in.p; ++b) tr[2 * in.nb + 2 + b] = __longlong_as_double(0x7ff8000000000000LL);
+  const unsigned FULL = 0xffffffffu;
+  const int b = threadIdx.x;  // one lane per block
+  const int nb = in.nb, p = in.p;
+  const int k = sc.k;
+  const bool chk = check_iter(in, k);
+  const bool ad = adapt_iter(in, k);
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  double *tr = in.trace ? in.trace + (int64_t)(k - 1) * in.trace_w : nullptr;
+  double rho_b = b < nb ? sc.rho[b] : 1.0;
+  double gam_b = b < nb ? sc.gamma[b] : 1.0;
+  const bool have_k0 = sc.have_k0 != 0;
+  if (tr) {
+    if (b < nb) {
+      tr[b] = rho_b;
+      tr[nb + b] = gam_b;
     }
-    sc.iters = k;
-    if (chk) {
-      bool feas_ok = true;
-      for (int b = 0; b < in.p; ++b) {
-        const BlockDev &bd = in.blk[b];
-        const double *a = sc.acc[b];
-        const double s2 = a[A_S2];
-        double d = 0.0;
-        if (bd.type == BT_BOUNDS) {
-          d = sqrt(a[A_FEAS_D2]);
-        } else if (bd.type == BT_L2) {
-          d = fmax(0.0, sqrt(s2) - sc.sigma[b]);
+    if (b == 0) {
+      tr[2 * nb] = sc.cg_steps;
+      tr[2 * nb + 1] = nan;
+    }
+    if (b < p) tr[2 * nb + 2 + b] = nan;
+  }
+  bool stop = false;
+  if (chk) {
+    // r_feas_i (Eq. feas_stop), one set per lane
+    bool ok = true;
+    if (b < p) {
+      const BlockDev &bd = in.blk[b];
+      const double *a = sc.acc[b];
+      const double s2 = a[A_S2];
+      double d = 0.0;
+      if (bd.type == BT_BOUNDS) {
+        d = sqrt(a[A_FEAS_D2]);
+      } else if (bd.type == BT_L2) {
+        d = fmax(0.0, sqrt(s2) - sc.sigma[b]);  // ||s - P(s)|| = ||s|| - sigma outside the ball
+      } else {
+        const JobScal &js = jscal[bd.job_s];
+        if (js.mode == JM_ALL) {
+          d = 0.0;
+        } else if (js.mode == JM_NONE) {
+          d = sqrt(s2);
+        } else if (bd.type == BT_L1) {
+          // s - P(s) = sign(s) min(|s|, theta)
+          d = sqrt(fmax(js.c_above * js.theta * js.theta + (s2 - js.s2_above), 0.0));
         } else {
-          const JobScal &js = jscal[bd.job_s];
-          if (js.mode == JM_ALL) {
-            d = 0.0;
-          } else if (js.mode == JM_NONE) {
-            d = sqrt(s2);
-          } else if (bd.type == BT_L1) {
-            // s - P(s) = sign(s) min(|s|, theta)
-            const double d2 = js.c_above * js.theta * js.theta + (s2 - js.s2_above);
-            d = sqrt(fmax(d2, 0.0));
-          } else {
-            // card: ||s - P(s)||^2 = ||s||^2 - (squares of the k kept entries)
-            const double d2 = s2 - js.s2_above - (double)js.need * js.kval * js.kval;
-            d = sqrt(fmax(d2, 0.0));
-          }
+          // ||s - P(s)||^2 = ||s||^2 - (squares of the k kept entries)
+          d = sqrt(fmax(s2 - js.s2_above - (double)js.need * js.kval * js.kval, 0.0));
         }
-        const double r = s2 > 0.0 ? d / sqrt(s2) : d;
-        sc.r_feas[b] = r;
-        if (!(r < in.eps_feas)) feas_ok = false;
-        if (tr) tr[2 * in.nb + 2 + b] = r;
       }
-      const int jmax = k < in.hist ? k : in.hist;
-      double mx = 0.0;
-      for (int j = 1; j <= jmax; ++j) mx = fmax(mx, sc.acc_ring[j]);
-      const double xn = sqrt(sc.acc_ring[0]);
-      sc.r_evol = xn > 0.0 ? sqrt(mx) / xn : sqrt(mx);
-      if (tr) tr[2 * in.nb + 1] = sc.r_evol;
-      if ((in.stop == 1 && feas_ok && sc.r_evol < in.eps_evol) || (in.stop == 2 && feas_ok)) {
-        sc.done = 1;
-        sc.stop_reason = 1;
+      const double r = s2 > 0.0 ? d / sqrt(s2) : d;
+      sc.r_feas[b] = r;
+      ok = r < in.eps_feas;
+      if (tr) tr[2 * nb + 2 + b] = r;
+    }
+    const bool all_ok = __all_sync(FULL, ok);
+    // r_evol (Eq. obj_stop): max over the stored history
+    const int jmax = k < in.hist ? k : in.hist;
+    double dmax = (b >= 1 && b <= jmax) ? sc.acc_ring[b] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, o));
+    const double xn = sqrt(sc.acc_ring[0]);
+    const double r_evol = xn > 0.0 ? sqrt(dmax) / xn : sqrt(dmax);
+    if (b == 0) {
+      sc.r_evol = r_evol;
+      if (tr) tr[2 * nb + 1] = r_evol;
+    }
+    stop = (in.stop == 1 && all_ok && r_evol < in.eps_evol) || (in.stop == 2 && all_ok);
+  }
+  if (b == 0) sc.iters = k;
+  if (stop) {
+    if (b == 0) {
+      sc.done = 1;
+      sc.stop_reason = 1;
+    }
+  } else {
+    if (ad) {
+      // Algorithm adapt-rho-gamma, one block per lane; the first call only
+      // stores the k0 quantities (done by the set and final passes).
+      if (have_k0 && b < nb) {
+        const double *a = sc.acc[b];
+        const double ac = corr(a[A_HV], a[A_HH], a[A_VHVH]);
+        const double bc = corr(a[A_GV], a[A_GG], a[A_VV]);
+        const bool aok = ac > in.eps_corr, bok = bc > in.eps_corr;
+        const double ah = aok ? spectral(a[A_HV], a[A_HH], a[A_VHVH]) : 0.0;
+        const double bh = bok ? spectral(a[A_GV], a[A_GG], a[A_VV]) : 0.0;
+        double r, g;
+        if (aok && bok) {
+          r = sqrt(ah * bh);
+          g = 1.0 + 2.0 * r / (ah + bh);
+        } else if (aok) {
+          r = ah;
+          g = 1.9;
+        } else if (bok) {
+          r = bh;
+          g = 1.1;
+        } else {
+          r = rho_b;
+          g = 1.5;
+        }
+        if (in.adapt == 1) g = gam_b;
+        rho_b = r;
+        gam_b = fmin(g, in.gamma_max);
+      }
+      if (have_k0) {
+        // safeguard: rho_i within a factor R of rho_{p+1} (direct form: of 1)
+        const double ref = in.alg1 ? __shfl_sync(FULL, rho_b, p) : 1.0;
+        const double R = in.rho_ratio_max;
+        if (b < p) rho_b = fmin(fmax(rho_b, ref / R), ref * R);
       }
     }
-    if (!sc.done) {
-      if (ad) {
-        if (sc.have_k0) {
-          double nr[kMaxBlocks], ng[kMaxBlocks];
-          for (int b = 0; b < in.nb; ++b) {
-            const double *a = sc.acc[b];
-            const double ac = corr(a[A_HV], a[A_HH], a[A_VHVH]);
-            const double bc = corr(a[A_GV], a[A_GG], a[A_VV]);
-            const bool aok = ac > in.eps_corr, bok = bc > in.eps_corr;
-            const double ah = aok ? spectral(a[A_HV], a[A_HH], a[A_VHVH]) : 0.0;
-            const double bh = bok ? spectral(a[A_GV], a[A_GG], a[A_VV]) : 0.0;
-            double r, g;
-            if (aok && bok) {
-              r = sqrt(ah * bh);
-              g = 1.0 + 2.0 * r / (ah + bh);
-            } else if (aok) {
-              r = ah;
-              g = 1.9;
-            } else if (bok) {
-              r = bh;
-              g = 1.1;
-            } else {
-              r = sc.rho[b];
-              g = 1.5;
-            }
-            if (in.adapt == 1) g = sc.gamma[b];
-            nr[b] = r;
-            ng[b] = fmin(g, in.gamma_max);
-          }
-          const double ref = in.alg1 ? nr[in.p] : 1.0;
-          const double R = in.rho_ratio_max;
-          for (int b = 0; b < in.p; ++b) nr[b] = fmin(fmax(nr[b], ref / R), ref * R);
-          for (int b = 0; b < in.nb; ++b) {
-            sc.rho[b] = nr[b];
-            sc.gamma[b] = ng[b];
-          }
-        }
-        sc.have_k0 = 1;
+    if (in.rho_sched && k < in.max_iter && b < nb) {
+      rho_b = in.rho_sched[(int64_t)k * nb + b];
+      if (in.gamma_sched) gam_b = in.gamma_sched[(int64_t)k * nb + b];
+    }
+    // stencil coefficients of C (Eq. sys_mat), summed over the lanes
+    double c0 = 0.0, cz = 0.0, cx = 0.0, cy = 0.0;
+    if (b < nb) {
+      sc.rho[b] = rho_b;
+      sc.gamma[b] = gam_b;
+      sc.irho[b] = 1.0 / rho_b;
+      sc.inv1p[b] = 1.0 / (1.0 + rho_b);
+      store_block_f32(sc, b);
+      switch (in.blk[b].op) {
+        case SIP_OP_I: c0 = rho_b; break;
+        case SIP_OP_DZ: cz = rho_b; break;
+        case SIP_OP_DX: cx = rho_b; break;
+        case SIP_OP_DY: cy = rho_b; break;
+        default: cz = rho_b; cx = rho_b; if (in.ndim == 3) cy = rho_b; break;
       }
-      if (in.rho_sched && k < in.max_iter) {
-        for (int b = 0; b < in.nb; ++b) {
-          sc.rho[b] = in.rho_sched[(int64_t)k * in.nb + b];
-          if (in.gamma_sched) sc.gamma[b] = in.gamma_sched[(int64_t)k * in.nb + b];
-        }
-      }
-      set_coefficients(in, sc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c0 += __shfl_xor_sync(FULL, c0, o);
+      cz += __shfl_xor_sync(FULL, cz, o);
+      cx += __shfl_xor_sync(FULL, cx, o);
+      cy += __shfl_xor_sync(FULL, cy, o);
+    }
+    if (b == 0) {
+      sc.c0 = (in.alg1 ? 0.0 : 1.0) + c0;
+      sc.cz = cz * in.ihz * in.ihz;
+      sc.cx = cx * in.ihx * in.ihx;
+      sc.cy = cy * in.ihy * in.ihy;
+      store_coef_f32(sc);
+      if (ad) sc.have_k0 = 1;
       sc.k = k + 1;
       if (k >= in.max_iter) sc.done = 1;
     }
   }
-  __syncthreads();
+  __syncwarp();
   // clear the per-iteration accumulators
   double *acc = &sc.acc[0][0];
-  for (int j = threadIdx.x; j < kMaxBlocks * kNAcc; j += blockDim.x) acc[j] = 0.0;
-  for (int j = threadIdx.x; j <= kMaxHist; j += blockDim.x) sc.acc_ring[j] = 0.0;
+  for (int j = b; j < kMaxBlocks * kNAcc; j += 32) acc[j] = 0.0;
+  if (b <= kMaxHist) sc.acc_ring[b] = 0.0;
 }
 
 }  // namespace sip
@@ -1072,10 +1476,7 @@ __global__ void __launch_bounds__(kThreads) k_norms(const Tile *__restrict__ til
   const SegDev sg = in.seg[tl.item];
   const T *__restrict__ m = (const T *)in.m;
   double acc[2] = {0.0, 0.0};
-#pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t row = tl.start + threadIdx.x + (int64_t)e * kThreads;
-    if (row >= tl.start + tl.len) break;
+  for (int64_t row = tl.start + threadIdx.x; row < tl.start + tl.len; row += kThreads) {
     if (sg.kind == SEG_RING) {
       if (!isfinite((double)m[row])) acc[0] += 1.0;
     } else {
@@ -1201,14 +1602,60 @@ cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const Ins
   SIP_DISPATCH(L, k_setpass, nt, kThreads, 0, tiles, insts, scal, jscal, jobs);
   return cudaGetLastError();
 }
-static constexpr size_t kSelectSmem = kBins * (sizeof(uint32_t) + 2 * sizeof(double));
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                          const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, int pass) {
-  // 40 KB of dynamic shared memory: below the 48 KB default, no opt-in needed
-  static_assert(kSelectSmem <= 48 * 1024, "select histogram exceeds the default shared-memory limit");
-  SIP_DISPATCH(L, k_select, nt, kThreads, kSelectSmem, tiles, insts, scal, jobs, jscal, hcnt, hs1, hs2, pass);
+                          const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
+                          int pass) {
+  if (L.dtype == SIP_F64)
+    k_select<double><<<nt, kThreads, BinAcc<double>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1,
+                                                                       hs2, hs3, pass);
+  else
+    k_select<float><<<nt, kThreads, BinAcc<float>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1, hs2,
+                                                                     hs3, pass);
   return cudaGetLastError();
 }
+cudaError_t kernels_setup() {
+  // the binary32 select histogram needs 56 KB of shared memory: opt in once
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_select<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)BinAcc<float>::kSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_select<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
+  if (e != cudaSuccess) return e;
+  done = true;
+  return cudaSuccess;
+}
+
+// CTAs per SM of the kernels that share one work-item list.
+int launch_occupancy(int dtype, int kind) {
+  int n = 0, best = 1 << 30;
+  auto occ = [&](const void *f, size_t smem) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem) == cudaSuccess && n > 0 && n < best)
+      best = n;
+  };
+  const bool d = dtype == SIP_F64;
+  switch (kind) {
+    case 0:  // grid-point items: rhs, CG
+      occ(d ? (const void *)k_rhs<double> : (const void *)k_rhs<float>, 0);
+      occ(d ? (const void *)k_cg_dir<double> : (const void *)k_cg_dir<float>, 0);
+      occ(d ? (const void *)k_cg_upd<double> : (const void *)k_cg_upd<float>, 0);
+      break;
+    case 1:  // segment items: set pass
+      occ(d ? (const void *)k_setpass<double> : (const void *)k_setpass<float>, 0);
+      break;
+    case 2:  // selection items
+      occ(d ? (const void *)k_select<double> : (const void *)k_select<float>,
+          d ? BinAcc<double>::kSmem : BinAcc<float>::kSmem);
+      break;
+    default:  // final-pass items
+      occ(d ? (const void *)k_final<double> : (const void *)k_final<float>, 0);
+      occ(d ? (const void *)k_ties<double> : (const void *)k_ties<float>, 0);
+      break;
+  }
+  cudaGetLastError();
+  return best == (1 << 30) ? 1 : best;
+}
+
 int select_passes(int dtype) { return dtype == SIP_F64 ? num_passes<double>() : num_passes<float>(); }
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                         const JobDev *jobs, JobScal *jscal, uint32_t *ties) {

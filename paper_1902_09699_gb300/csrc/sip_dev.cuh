@@ -51,11 +51,41 @@ enum Acc : int32_t {
   kNAcc
 };
 
+// Division by a fixed divisor d >= 1 for 0 <= n < 2^31 by a multiply-high
+// and a shift (Granlund and Montgomery's round-up method):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (mulhi(n, m) + n) >> l.
+struct FastDiv {
+  uint32_t d, m, s;
+};
+
+#ifdef __CUDACC__
+__host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+#ifdef __CUDA_ARCH__
+  const uint32_t t = __umulhi(n, f.m);
+#else
+  const uint32_t t = (uint32_t)(((uint64_t)n * f.m) >> 32);
+#endif
+  return (uint32_t)(((uint64_t)t + n) >> f.s);
+}
+#endif
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  if (d == 0) d = 1;
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  f.d = d;
+  f.m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+  f.s = l;
+  return f;
+}
+
 struct Tile {
   int32_t inst;   // instance
   int32_t item;   // segment (set pass), block (final pass) or job (select)
   int64_t start;  // first row / grid point
-  int32_t len;    // rows in this tile (<= kTile)
+  int32_t len;    // rows in this work item (a CTA walks it kTile rows at a time)
   int32_t seq;    // tile number inside its item (tie ranks)
 };
 
@@ -100,11 +130,16 @@ struct JobScal {
   int64_t need;       // card: ties to keep at the final key
   int64_t cK;         // card: entries equal to the final key
   double kval;        // card: |value| of the final key
+  float thetaf;       // theta in binary32
+  int32_t pad2;
 };
 
 struct InstDev {
   int32_t nz, nx, ny, ndim;
+  FastDiv fz, fx, fzm, fxm;  // division by n_z, n_x, n_z - 1, n_x - 1
   double ihz, ihx, ihy;      // 1/h per axis
+  float ihzf, ihxf, ihyf;    // the same in binary32
+  int32_t pad0;
   int64_t N;
   int32_t nb, p, alg1, nseg, njob, job0;
   int32_t nt_n, nt_set, nt_fin;
@@ -136,6 +171,12 @@ struct InstScal {
   double rho[kMaxBlocks], gamma[kMaxBlocks], irho[kMaxBlocks], inv1p[kMaxBlocks];
   double l2scale[kMaxBlocks];
   double c0, cz, cx, cy;
+  // binary32 copies written next to the binary64 values, so binary32
+  // kernels convert nothing: c0, cz, cx, cy, alpha, beta and per block
+  // rho, 1/rho, gamma, 1-gamma, 1/(1+rho), l2 scale
+  float cf[4];
+  float alphaf, betaf;
+  float bf[kMaxBlocks][6];
   double sigma[kMaxBlocks];
   int64_t kcard[kMaxBlocks];
   double r_feas[kMaxSets];

@@ -89,7 +89,7 @@ struct Plan {
   JobDev *d_jobs = nullptr;
   JobScal *d_jscal = nullptr;
   uint32_t *d_hcnt = nullptr;
-  double *d_hs1 = nullptr, *d_hs2 = nullptr;
+  double *d_hs1 = nullptr, *d_hs2 = nullptr, *d_hs3 = nullptr;
   uint32_t *d_ties = nullptr;
   Tile *d_tn = nullptr, *d_tset = nullptr, *d_tsel = nullptr, *d_tfin = nullptr;
   int nt_n = 0, nt_set = 0, nt_sel = 0, nt_fin = 0, njobs = 0;
@@ -108,6 +108,7 @@ int64_t part_rows(const GridDesc &g, int kind);
 int64_t op_rows(const GridDesc &g, int op);
 void part_dims(const GridDesc &g, int kind, int64_t d[3], int &stag);
 sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const sip_options *opts);
+void set_fastdiv(InstDev &d);
 InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const sip_options &o);
 double layout_bytes_per_iter(const InstLayout &L, int dtype);
 sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m);

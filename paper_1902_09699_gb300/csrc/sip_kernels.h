@@ -21,7 +21,13 @@ cudaError_t launch_cg_upd(const Launch &L, const Tile *tiles, int nt, const Inst
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            JobScal *jscal, const JobDev *jobs);
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                          const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, int pass);
+                          const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
+                          int pass);
+// one-time kernel attribute set-up (call outside stream capture)
+cudaError_t kernels_setup();
+// CTAs per SM for the kernels of a work-item list: 0 grid points, 1 set
+// segments, 2 selection jobs, 3 final-pass blocks
+int launch_occupancy(int dtype, int kind);
 int select_passes(int dtype);
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                         const JobDev *jobs, JobScal *jscal, uint32_t *ties);

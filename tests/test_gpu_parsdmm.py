@@ -165,11 +165,15 @@ def test_stopping_rule_iteration_count():
     ({"n": (1031, 3)}, [{"op": "DZ", "type": "card", "k_frac": 0.1}, {"op": "I", "type": "l1", "sigma_rel": 0.5}]),
 ])
 def test_degenerate_and_ragged_grids(grid, sets):
+    # On grids this small adapt-rho-gamma's correlation tests sit on exact
+    # ties (the oracle itself moves by 1e-3 under a 1e-15 perturbation of m
+    # on the 2 x 2 case), so the rho / gamma schedule is replayed.
     g = np.random.default_rng(1)
     m = g.standard_normal(int(np.prod(grid["n"])))
     opts = dict(max_iter=25, adapt=1, gamma0=1.5)
     ref = oracle_run(m, grid, sets, opts)
-    x, info, _ = run_gpu(m, grid, sets, "f64", opts)
+    rs, gs = schedules(ref)
+    x, info, _ = run_gpu(m, grid, sets, "f64", opts, rho_schedule=rs, gamma_schedule=gs)
     assert rel(x, ref["x"]) <= 1e-10
 
 
