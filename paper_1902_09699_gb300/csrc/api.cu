@@ -301,7 +301,7 @@ double layout_bytes_per_iter(const InstLayout &L, int dtype) {
   const int ncg = L.opts.cg_iters > 0 ? L.opts.cg_iters : 5;
   const int rsel = select_passes(dtype);
   double words = 2 * Mp + 2 * N + (d.alg1 ? 0 : N);  // rhs: y, v, x read; r write (+ m)
-  words += ncg * 10.0 * N;                            // CG: p, q, x, r traffic per step
+  words += 3.0 * N + ncg * 10.0 * N;                  // CG: w0 = C r0; per step p, x, r, w, s
   words += 4 * Mp + N + (d.alg1 ? N : 0);             // set pass: x, y, v read, y, v write (+ m)
   double feas = 0.0;
   for (int b = 0; b < d.nb; ++b) {
@@ -448,7 +448,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     return o;
   };
   struct Offs {
-    int64_t x, y, v, r, p0, p1, q, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace;
+    int64_t x, y, v, cr[2], cw[2], cs[2], cp, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace;
   };
   std::vector<Offs> offs(P.ninst);
   // warm state (x, y, v) of all instances first, then the rest of the state,
@@ -463,10 +463,12 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     const InstLayout &L = insts[i];
     const int64_t N = L.dev.N;
     const bool ad = L.opts.adapt != 0;
-    offs[i].r = take(N * W);
-    offs[i].p0 = take(N * W);
-    offs[i].p1 = take(N * W);
-    offs[i].q = take(N * W);
+    for (int j = 0; j < 2; ++j) {
+      offs[i].cr[j] = take(N * W);
+      offs[i].cw[j] = take(N * W);
+      offs[i].cs[j] = take(N * W);
+    }
+    offs[i].cp = take(N * W);
     offs[i].ring = take((int64_t)L.dev.hist * N * W);
     offs[i].w = take(L.Mw * W);
     offs[i].s = take(L.Ms * W);
@@ -515,10 +517,12 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     d.x = at(o.x);
     d.y = at(o.y);
     d.v = at(o.v);
-    d.r = at(o.r);
-    d.p0 = at(o.p0);
-    d.p1 = at(o.p1);
-    d.q = at(o.q);
+    for (int j = 0; j < 2; ++j) {
+      d.cr[j] = at(o.cr[j]);
+      d.cw[j] = at(o.cw[j]);
+      d.cs[j] = at(o.cs[j]);
+    }
+    d.cp = at(o.cp);
     d.ring = at(o.ring);
     d.w = at(o.w);
     d.s = at(o.s);
@@ -572,13 +576,13 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, KernelTimer *tm) {
   T0(KT_RHS);
   CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
   T1(KT_RHS);
+  T0(KT_CG_W0);
+  CK(launch_cg_w0(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));  // w_0 = C r_0
+  T1(KT_CG_W0);
   for (int j = 0; j < P.cg_launch; ++j) {
-    T0(KT_CG_DIR);
-    CK(launch_cg_dir(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
-    T1(KT_CG_DIR);
-    T0(KT_CG_UPD);
-    CK(launch_cg_upd(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
-    T1(KT_CG_UPD);
+    T0(KT_CG_STEP);
+    CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));  // one CG step
+    T1(KT_CG_STEP);
   }
   T0(KT_SETPASS);
   CK(launch_setpass(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs));

@@ -302,7 +302,7 @@ sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev, void *stre
 // ----------------------------------------------------------------------------
 // per-kernel timing
 // ----------------------------------------------------------------------------
-static const char *kKernelNames[KT_COUNT] = {"rhs", "cg_dir", "cg_upd", "setpass", "select", "ties", "final", "tail"};
+static const char *kKernelNames[KT_COUNT] = {"rhs", "cg_w0", "cg_step", "setpass", "select", "ties", "final", "tail"};
 
 const char *sip_kernel_name(int i) { return (i >= 0 && i < KT_COUNT) ? kKernelNames[i] : ""; }
 
@@ -328,8 +328,8 @@ sip_status sip_kernel_times(const sip_handle *h, double *ms, int64_t *launches, 
   const double ad = (h->opts.adapt && !h->opts.rho_schedule) ? 1.0 / h->opts.adapt_every : 0.0;
   double bytes[KT_COUNT] = {};
   bytes[KT_RHS] = W * (2 * Mp + 2 * N + (d.alg1 ? 0 : N));
-  bytes[KT_CG_DIR] = W * 4 * N;
-  bytes[KT_CG_UPD] = W * 6 * N;
+  bytes[KT_CG_W0] = W * 2 * N;   // read r, write w = C r
+  bytes[KT_CG_STEP] = W * 10 * N;  // read x, p, r, w, s; write x, p, r, w, s
   bytes[KT_SETPASS] = W * (N + 2 * Mp + 2 * Mpw + Mms + (d.alg1 ? N : 0) + 2 * N + ad * (4 * Mp + 2 * Mpw));
   bytes[KT_SELECT] = W * Msel;
   bytes[KT_TIES] = 0.0;

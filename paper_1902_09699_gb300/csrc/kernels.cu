@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ ti
   const T *__restrict__ y = (const T *)in.y;
   const T *__restrict__ v = (const T *)in.v;
   const T *__restrict__ m = (const T *)in.m;
-  T *__restrict__ r = (T *)in.r;
+  T *__restrict__ r = (T *)in.cr[sc.rbuf];
   CSys<T> C;
   C.load(sc);
   __shared__ T srho[kMaxBlocks];
@@ -375,55 +375,49 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ ti
 }
 
 // --------------------------------------------------------------------------
-// CG: direction + matrix-vector product
+// Conjugate gradient on C x = b from the warm start x (Sec. "Solving the
+// linear system and automatic parameter selection"), in the Chronopoulos-Gear
+// arrangement of the CG recurrences: with w = C r and s = C p kept as
+// vectors, both inner products of a step (gamma = r.r, delta = w.r) come
+// from one reduction, so a step is one launch:
+//   p_i = r_i + beta_i p_{i-1};      s_i = w_i + beta_i s_{i-1}
+//   x_{i+1} = x_i + alpha_i p_i;     r_{i+1} = r_i - alpha_i s_i
+//   w_{i+1} = C r_{i+1};  gamma_{i+1} = r_{i+1}.r_{i+1};  delta_{i+1} = w_{i+1}.r_{i+1}
+//   beta_{i+1} = gamma_{i+1} / gamma_i
+//   alpha_{i+1} = gamma_{i+1} / (delta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i)
+// In exact arithmetic these are the iterates of textbook CG; the
+// denominator of alpha equals p^T C p, so "p^T C p <= 0" stops as in CG.
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_cg_dir(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                     InstScal *__restrict__ scal) {
+__global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                       InstScal *__restrict__ scal) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done || !sc.cg_active) return;
-  const T *__restrict__ r = (const T *)in.r;
-  const int pb = sc.pbuf;
-  const T *__restrict__ pold = (const T *)(pb ? in.p1 : in.p0);
-  T *__restrict__ pnew = (T *)(pb ? in.p0 : in.p1);
-  T *__restrict__ q = (T *)in.q;
-  // beta = 0 on the first step: p = r (the old direction, finite, drops out)
-  const T beta = sc.cg_steps == 0 ? T(0) : SV<T>::beta(sc);
+  const int rb = sc.rbuf;
+  const T *__restrict__ r = (const T *)in.cr[rb];
+  T *__restrict__ w = (T *)in.cw[rb];
   CSys<T> C;
   C.load(sc);
   const int64_t end = tl.start + tl.len;
   A a0 = A(0);
   for (int64_t base = tl.start; base < end; base += SUB) {
-    int64_t g[PT];
-    Nbr<T> rn[PT], pn[PT];
+    Nbr<T> rn[PT];
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
-      g[e] = base + threadIdx.x + (int64_t)e * kThreads;
-      if (g[e] < end) {
-        const GridPos p = grid_pos(in, g[e]);
-        load_nbr<T>(in, p, g[e], [&](int64_t i) { return r[i]; }, rn[e]);
-        load_nbr<T>(in, p, g[e], [&](int64_t i) { return pold[i]; }, pn[e]);
-      }
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) load_nbr<T>(in, grid_pos(in, g), g, [&](int64_t i) { return r[i]; }, rn[e]);
     }
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
-      if (g[e] < end) {
-        Nbr<T> d;
-        d.c = rn[e].c + beta * pn[e].c;
-        d.zm = rn[e].zm + beta * pn[e].zm;
-        d.zp = rn[e].zp + beta * pn[e].zp;
-        d.xm = rn[e].xm + beta * pn[e].xm;
-        d.xp = rn[e].xp + beta * pn[e].xp;
-        d.ym = rn[e].ym + beta * pn[e].ym;
-        d.yp = rn[e].yp + beta * pn[e].yp;
-        const T qg = apply_c(C, d);
-        pnew[g[e]] = d.c;
-        q[g[e]] = qg;
-        a0 += (A)d.c * (A)qg;
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) {
+        const T wg = apply_c(C, rn[e]);
+        w[g] = wg;
+        a0 += (A)wg * (A)rn[e].c;
       }
     }
   }
@@ -436,80 +430,122 @@ __global__ void __launch_bounds__(kThreads, 3) k_cg_dir(const Tile *__restrict__
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
-    const double pq = ldv(&sc.acc_n[0]);
+    const double delta = ldv(&sc.acc_n[0]);
     sc.acc_n[0] = 0.0;
-    if (pq > 0.0) {
-      sc.alpha = sc.rr / pq;
+    if (delta > 0.0) {  // delta_0 = r_0^T C r_0 = p_0^T C p_0
+      sc.alpha = sc.rr / delta;
       sc.alphaf = (float)sc.alpha;
+      sc.beta = 0.0;
+      sc.betaf = 0.f;
     } else {
-      sc.cg_active = 0;  // p^T C p <= 0: stop CG
+      sc.cg_active = 0;
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) k_cg_upd(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                     InstScal *__restrict__ scal) {
-  SIP_STEP_CONSTANTS;
+__global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
+                                                         const InstDev *__restrict__ insts,
+                                                         InstScal *__restrict__ scal) {
   using A = typename AccOf<T>::type;
+  constexpr int PT = sizeof(T) == 4 ? 2 : 1;  // 3 stencils per row: keep the register budget
+  constexpr int SUB = kThreads * PT;
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done || !sc.cg_active) return;
-  const T *__restrict__ p = (const T *)(sc.pbuf ? in.p0 : in.p1);
-  const T *__restrict__ q = (const T *)in.q;
+  const int c = sc.rbuf, n = c ^ 1;
+  const T *__restrict__ r = (const T *)in.cr[c];
+  const T *__restrict__ w = (const T *)in.cw[c];
+  const T *__restrict__ sp = (const T *)in.cs[c];  // s_{i-1}
+  T *__restrict__ rn_ = (T *)in.cr[n];
+  T *__restrict__ wn_ = (T *)in.cw[n];
+  T *__restrict__ sn_ = (T *)in.cs[n];             // s_i
+  T *__restrict__ p = (T *)in.cp;
   T *__restrict__ x = (T *)in.x;
-  T *__restrict__ r = (T *)in.r;
-  const T alpha = SV<T>::alpha(sc);
+  const T alpha = SV<T>::alpha(sc), beta = SV<T>::beta(sc);
+  CSys<T> C;
+  C.load(sc);
   const int64_t end = tl.start + tl.len;
-  A a0 = A(0);
+  A ag = A(0), ad = A(0);
   for (int64_t base = tl.start; base < end; base += SUB) {
-    T pv[PT], qv[PT], xv[PT], rv[PT];
+    Nbr<T> rr[PT], ww[PT], ss[PT];
+    T pv[PT], xv[PT];
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
       const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
       if (g < end) {
+        const GridPos ps = grid_pos(in, g);
+        load_nbr<T>(in, ps, g, [&](int64_t i) { return r[i]; }, rr[e]);
+        load_nbr<T>(in, ps, g, [&](int64_t i) { return w[i]; }, ww[e]);
+        load_nbr<T>(in, ps, g, [&](int64_t i) { return sp[i]; }, ss[e]);
         pv[e] = p[g];
-        qv[e] = q[g];
         xv[e] = x[g];
-        rv[e] = r[g];
       }
     }
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
       const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
       if (g < end) {
-        x[g] = xv[e] + alpha * pv[e];
-        const T rn = rv[e] - alpha * qv[e];
-        r[g] = rn;
-        a0 += (A)rn * (A)rn;
+        // s_i and r_{i+1} at the stencil points (a missing neighbour repeats
+        // the centre, so its difference stays zero)
+        Nbr<T> rnew;
+        const T s_c = ww[e].c + beta * ss[e].c;
+        rnew.c = rr[e].c - alpha * s_c;
+#define SIP_CG_AT(f) rnew.f = rr[e].f - alpha * (ww[e].f + beta * ss[e].f);
+        SIP_CG_AT(zm)
+        SIP_CG_AT(zp)
+        SIP_CG_AT(xm)
+        SIP_CG_AT(xp)
+        SIP_CG_AT(ym)
+        SIP_CG_AT(yp)
+#undef SIP_CG_AT
+        const T pi = rr[e].c + beta * pv[e];
+        p[g] = pi;
+        x[g] = xv[e] + alpha * pi;
+        sn_[g] = s_c;
+        rn_[g] = rnew.c;
+        const T wnew = apply_c(C, rnew);
+        wn_[g] = wnew;
+        ag += (A)rnew.c * (A)rnew.c;
+        ad += (A)wnew * (A)rnew.c;
       }
     }
   }
-  double acc[1] = {(double)a0};
-  block_sum<1>(acc);
+  double acc[2] = {(double)ag, (double)ad};
+  block_sum<2>(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
     atomicAdd(&sc.acc_n[0], acc[0]);
+    atomicAdd(&sc.acc_n[1], acc[1]);
     last = arrive_last(&sc.cnt_n, (uint32_t)in.nt_n);
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
-    const double rr = ldv(&sc.acc_n[0]);
+    const double g1 = ldv(&sc.acc_n[0]), d1 = ldv(&sc.acc_n[1]);
     sc.acc_n[0] = 0.0;
-    sc.beta = rr / sc.rr;
-    sc.betaf = (float)sc.beta;
-    sc.rr = rr;
+    sc.acc_n[1] = 0.0;
     sc.cg_steps += 1;
     sc.cg_total += 1;
-    sc.pbuf ^= 1;
+    sc.rbuf = n;
     bool more;
     if (in.cg_iters > 0) {
       more = sc.cg_steps < in.cg_iters;
     } else {  // Eq. cg_stop: ||r_j|| < 0.1 ||r_0||
-      more = sc.cg_steps < in.cg_max && !(sqrt(rr) < 0.1 * sqrt(sc.rr0));
+      more = sc.cg_steps < in.cg_max && !(sqrt(g1) < 0.1 * sqrt(sc.rr0));
     }
-    sc.cg_active = (more && rr > 0.0) ? 1 : 0;
+    const double b1 = g1 / sc.rr;
+    const double den = d1 - b1 * g1 / sc.alpha;  // = p_{i+1}^T C p_{i+1}
+    if (more && g1 > 0.0 && den > 0.0) {
+      sc.beta = b1;
+      sc.betaf = (float)b1;
+      sc.alpha = g1 / den;
+      sc.alphaf = (float)sc.alpha;
+    } else {
+      more = false;
+    }
+    sc.rr = g1;
+    sc.cg_active = more ? 1 : 0;
   }
 }
 
@@ -688,28 +724,36 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
       }
     }
   }
-  double dacc[10];
-#pragma unroll
-  for (int j = 0; j < 10; ++j) dacc[j] = (double)acc[j];
-  block_sum<10>(dacc);
-  if (threadIdx.x == 0) {
-    double *a = sc.acc[b];
-    if (ad_dots) {
-      atomicAdd(&a[A_HV], dacc[0]);
-      atomicAdd(&a[A_HH], dacc[1]);
-      atomicAdd(&a[A_VHVH], dacc[2]);
+  // binary64 CTA sums of only the quantities this iteration uses (cross-thread
+  // binary64 work is costly on this part)
+  double *a = sc.acc[b];
+  if (ad_dots) {
+    double d6[6] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3], (double)acc[4], (double)acc[5]};
+    block_sum<6>(d6);
+    if (threadIdx.x == 0) {
+      atomicAdd(&a[A_HV], d6[0]);
+      atomicAdd(&a[A_HH], d6[1]);
+      atomicAdd(&a[A_VHVH], d6[2]);
       if (pointwise) {
-        atomicAdd(&a[A_GV], dacc[3]);
-        atomicAdd(&a[A_GG], dacc[4]);
-        atomicAdd(&a[A_VV], dacc[5]);
+        atomicAdd(&a[A_GV], d6[3]);
+        atomicAdd(&a[A_GG], d6[4]);
+        atomicAdd(&a[A_VV], d6[5]);
       }
     }
-    if (chk) {
-      if (type == BT_BOUNDS) atomicAdd(&a[A_FEAS_D2], dacc[6]);
-      if (type != BT_DIST) atomicAdd(&a[A_S2], dacc[7]);
-      if (type == BT_L1) atomicAdd(&a[A_S1], dacc[8]);
+  }
+  if (chk && type != BT_DIST) {
+    double d3[3] = {(double)acc[6], (double)acc[7], (double)acc[8]};
+    block_sum<3>(d3);
+    if (threadIdx.x == 0) {
+      if (type == BT_BOUNDS) atomicAdd(&a[A_FEAS_D2], d3[0]);
+      atomicAdd(&a[A_S2], d3[1]);
+      if (type == BT_L1) atomicAdd(&a[A_S1], d3[2]);
     }
-    if (type == BT_L1 || type == BT_L2) atomicAdd(&a[A_WNORM], dacc[9]);
+  }
+  if (type == BT_L1 || type == BT_L2) {
+    double d1[1] = {(double)acc[9]};
+    block_sum<1>(d1);
+    if (threadIdx.x == 0) atomicAdd(&a[A_WNORM], d1[0]);
   }
 }
 
@@ -1262,93 +1306,59 @@ __device__ __forceinline__ double spectral(double ab, double aa, double bb) {
   return 2.0 * mg > sd ? mg : sd - 0.5 * mg;
 }
 
-__global__ void __launch_bounds__(32) k_tail(const InstDev *__restrict__ insts, InstScal *__restrict__ scal,
-                                              const JobScal *__restrict__ jscal, int ninst) {
+constexpr int kTailWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restrict__ insts,
+                                                          InstScal *__restrict__ scal,
+                                                          const JobScal *__restrict__ jscal, int ninst) {
   const int i = blockIdx.x;
   if (i >= ninst) return;
   const InstDev &in = insts[i];
   InstScal &sc = scal[i];
   if (sc.done) return;
   const unsigned FULL = 0xffffffffu;
-  const int b = threadIdx.x;  // one lane per block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nb = in.nb, p = in.p;
   const int k = sc.k;
   const bool chk = check_iter(in, k);
   const bool ad = adapt_iter(in, k);
-  const double nan = __longlong_as_double(0x7ff8000000000000LL);
-  double *tr = in.trace ? in.trace + (int64_t)(k - 1) * in.trace_w : nullptr;
-  double rho_b = b < nb ? sc.rho[b] : 1.0;
-  double gam_b = b < nb ? sc.gamma[b] : 1.0;
   const bool have_k0 = sc.have_k0 != 0;
-  if (tr) {
-    if (b < nb) {
-      tr[b] = rho_b;
-      tr[nb + b] = gam_b;
-    }
-    if (b == 0) {
-      tr[2 * nb] = sc.cg_steps;
-      tr[2 * nb + 1] = nan;
-    }
-    if (b < p) tr[2 * nb + 2 + b] = nan;
-  }
-  bool stop = false;
-  if (chk) {
-    // r_feas_i (Eq. feas_stop), one set per lane
-    bool ok = true;
-    if (b < p) {
+  __shared__ double s_rho[kMaxBlocks], s_gam[kMaxBlocks], s_feas[kMaxBlocks];
+
+  // ---- phase 1: per block, lane 0 of warp b % kTailWarps (binary64 chains
+  // of different blocks run on different SM sub-partitions)
+  if (lane == 0) {
+    for (int b = wid; b < nb; b += kTailWarps) {
+      double rho_b = sc.rho[b], gam_b = sc.gamma[b];
       const BlockDev &bd = in.blk[b];
       const double *a = sc.acc[b];
-      const double s2 = a[A_S2];
-      double d = 0.0;
-      if (bd.type == BT_BOUNDS) {
-        d = sqrt(a[A_FEAS_D2]);
-      } else if (bd.type == BT_L2) {
-        d = fmax(0.0, sqrt(s2) - sc.sigma[b]);  // ||s - P(s)|| = ||s|| - sigma outside the ball
-      } else {
-        const JobScal &js = jscal[bd.job_s];
-        if (js.mode == JM_ALL) {
-          d = 0.0;
-        } else if (js.mode == JM_NONE) {
-          d = sqrt(s2);
-        } else if (bd.type == BT_L1) {
-          // s - P(s) = sign(s) min(|s|, theta)
-          d = sqrt(fmax(js.c_above * js.theta * js.theta + (s2 - js.s2_above), 0.0));
+      if (chk && b < p) {
+        // r_feas_i (Eq. feas_stop)
+        const double s2 = a[A_S2];
+        double d = 0.0;
+        if (bd.type == BT_BOUNDS) {
+          d = sqrt(a[A_FEAS_D2]);
+        } else if (bd.type == BT_L2) {
+          d = fmax(0.0, sqrt(s2) - sc.sigma[b]);  // ||s - P(s)|| = ||s|| - sigma outside the ball
         } else {
-          // ||s - P(s)||^2 = ||s||^2 - (squares of the k kept entries)
-          d = sqrt(fmax(s2 - js.s2_above - (double)js.need * js.kval * js.kval, 0.0));
+          const JobScal &js = jscal[bd.job_s];
+          if (js.mode == JM_ALL) {
+            d = 0.0;
+          } else if (js.mode == JM_NONE) {
+            d = sqrt(s2);
+          } else if (bd.type == BT_L1) {
+            // s - P(s) = sign(s) min(|s|, theta)
+            d = sqrt(fmax(js.c_above * js.theta * js.theta + (s2 - js.s2_above), 0.0));
+          } else {
+            // ||s - P(s)||^2 = ||s||^2 - (squares of the k kept entries)
+            d = sqrt(fmax(s2 - js.s2_above - (double)js.need * js.kval * js.kval, 0.0));
+          }
         }
+        s_feas[b] = s2 > 0.0 ? d / sqrt(s2) : d;
       }
-      const double r = s2 > 0.0 ? d / sqrt(s2) : d;
-      sc.r_feas[b] = r;
-      ok = r < in.eps_feas;
-      if (tr) tr[2 * nb + 2 + b] = r;
-    }
-    const bool all_ok = __all_sync(FULL, ok);
-    // r_evol (Eq. obj_stop): max over the stored history
-    const int jmax = k < in.hist ? k : in.hist;
-    double dmax = (b >= 1 && b <= jmax) ? sc.acc_ring[b] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, o));
-    const double xn = sqrt(sc.acc_ring[0]);
-    const double r_evol = xn > 0.0 ? sqrt(dmax) / xn : sqrt(dmax);
-    if (b == 0) {
-      sc.r_evol = r_evol;
-      if (tr) tr[2 * nb + 1] = r_evol;
-    }
-    stop = (in.stop == 1 && all_ok && r_evol < in.eps_evol) || (in.stop == 2 && all_ok);
-  }
-  if (b == 0) sc.iters = k;
-  if (stop) {
-    if (b == 0) {
-      sc.done = 1;
-      sc.stop_reason = 1;
-    }
-  } else {
-    if (ad) {
-      // Algorithm adapt-rho-gamma, one block per lane; the first call only
-      // stores the k0 quantities (done by the set and final passes).
-      if (have_k0 && b < nb) {
-        const double *a = sc.acc[b];
+      if (ad && have_k0) {
+        // Algorithm adapt-rho-gamma; the first call only stores the k0
+        // quantities (done by the set and final passes)
         const double ac = corr(a[A_HV], a[A_HH], a[A_VHVH]);
         const double bc = corr(a[A_GV], a[A_GG], a[A_VV]);
         const bool aok = ac > in.eps_corr, bok = bc > in.eps_corr;
@@ -1372,12 +1382,62 @@ __global__ void __launch_bounds__(32) k_tail(const InstDev *__restrict__ insts, 
         rho_b = r;
         gam_b = fmin(g, in.gamma_max);
       }
-      if (have_k0) {
-        // safeguard: rho_i within a factor R of rho_{p+1} (direct form: of 1)
-        const double ref = in.alg1 ? __shfl_sync(FULL, rho_b, p) : 1.0;
-        const double R = in.rho_ratio_max;
-        if (b < p) rho_b = fmin(fmax(rho_b, ref / R), ref * R);
-      }
+      s_rho[b] = rho_b;
+      s_gam[b] = gam_b;
+    }
+  }
+  __syncthreads();
+  if (wid != 0) return;
+
+  // ---- phase 2: warp 0, one lane per block
+  const int b = lane;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  double *tr = in.trace ? in.trace + (int64_t)(k - 1) * in.trace_w : nullptr;
+  if (tr) {
+    if (b < nb) {
+      tr[b] = sc.rho[b];
+      tr[nb + b] = sc.gamma[b];
+    }
+    if (b == 0) {
+      tr[2 * nb] = sc.cg_steps;
+      tr[2 * nb + 1] = nan;
+    }
+    if (b < p) tr[2 * nb + 2 + b] = chk ? s_feas[b] : nan;
+  }
+  bool stop = false;
+  if (chk) {
+    bool ok = true;
+    if (b < p) {
+      sc.r_feas[b] = s_feas[b];
+      ok = s_feas[b] < in.eps_feas;
+    }
+    const bool all_ok = __all_sync(FULL, ok);
+    // r_evol (Eq. obj_stop): max over the stored history
+    const int jmax = k < in.hist ? k : in.hist;
+    double dmax = (b >= 1 && b <= jmax) ? sc.acc_ring[b] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, o));
+    const double xn = sqrt(sc.acc_ring[0]);
+    const double r_evol = xn > 0.0 ? sqrt(dmax) / xn : sqrt(dmax);
+    if (b == 0) {
+      sc.r_evol = r_evol;
+      if (tr) tr[2 * nb + 1] = r_evol;
+    }
+    stop = (in.stop == 1 && all_ok && r_evol < in.eps_evol) || (in.stop == 2 && all_ok);
+  }
+  if (b == 0) sc.iters = k;
+  if (stop) {
+    if (b == 0) {
+      sc.done = 1;
+      sc.stop_reason = 1;
+    }
+  } else {
+    double rho_b = b < nb ? s_rho[b] : 1.0, gam_b = b < nb ? s_gam[b] : 1.0;
+    if (ad && have_k0) {
+      // safeguard: rho_i within a factor R of rho_{p+1} (direct form: of 1)
+      const double ref = in.alg1 ? __shfl_sync(FULL, rho_b, p) : 1.0;
+      const double R = in.rho_ratio_max;
+      if (b < p) rho_b = fmin(fmax(rho_b, ref / R), ref * R);
     }
     if (in.rho_sched && k < in.max_iter && b < nb) {
       rho_b = in.rho_sched[(int64_t)k * nb + b];
@@ -1447,7 +1507,7 @@ __global__ void k_init(const InstDev *__restrict__ insts, InstScal *__restrict__
   sc.cg_active = 0;
   sc.cg_steps = 0;
   sc.cg_total = 0;
-  sc.pbuf = 0;
+  sc.rbuf = 0;
   sc.have_k0 = 0;
   sc.nonfinite = 0;
   sc.cnt_n = sc.cnt_set = sc.cnt_norm = 0;
@@ -1589,12 +1649,12 @@ cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev
   SIP_DISPATCH(L, k_rhs, nt, kThreads, 0, tiles, insts, scal);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_dir(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_cg_dir, nt, kThreads, 0, tiles, insts, scal);
+cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
+  SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_upd(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_cg_upd, nt, kThreads, 0, tiles, insts, scal);
+cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
+  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal);
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
@@ -1637,8 +1697,8 @@ int launch_occupancy(int dtype, int kind) {
   switch (kind) {
     case 0:  // grid-point items: rhs, CG
       occ(d ? (const void *)k_rhs<double> : (const void *)k_rhs<float>, 0);
-      occ(d ? (const void *)k_cg_dir<double> : (const void *)k_cg_dir<float>, 0);
-      occ(d ? (const void *)k_cg_upd<double> : (const void *)k_cg_upd<float>, 0);
+      occ(d ? (const void *)k_cg_w0<double> : (const void *)k_cg_w0<float>, 0);
+      occ(d ? (const void *)k_cg_step<double> : (const void *)k_cg_step<float>, 0);
       break;
     case 1:  // segment items: set pass
       occ(d ? (const void *)k_setpass<double> : (const void *)k_setpass<float>, 0);
@@ -1668,7 +1728,7 @@ cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstD
   return cudaGetLastError();
 }
 cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst) {
-  k_tail<<<ninst, 32, 0, L.stream>>>(insts, scal, jscal, ninst);
+  k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst);
   return cudaGetLastError();
 }
 cudaError_t launch_apply_op(const Launch &L, const InstDev *in, const void *x, void *s, int64_t rows) {

@@ -153,7 +153,11 @@ struct InstDev {
   int32_t pad;
   // device arrays, element type = the plan's dtype
   const void *m;
-  void *x, *r, *p0, *p1, *q, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;
+  void *x, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;
+  // conjugate-gradient vectors: residual r, w = C r and s = C p are double
+  // buffered (read at stencil neighbours while the next values are written);
+  // the direction p is updated in place
+  void *cr[2], *cw[2], *cs[2], *cp;
   BlockDev blk[kMaxBlocks];
   SegDev seg[kMaxSegs];
 };
@@ -162,11 +166,11 @@ struct InstScal {
   int32_t k;            // iteration in progress (1-based)
   int32_t done;         // stopping rule held (or a non-finite model); kernels no-op
   int32_t iters, stop_reason;
-  int32_t cg_active, cg_steps, cg_total, pbuf;
+  int32_t cg_active, cg_steps, cg_total, rbuf;
   int32_t have_k0, nonfinite;
   uint32_t cnt_n, cnt_set, cnt_norm;
   int32_t pad;
-  double rr, rr0, bnorm2, alpha, beta;
+  double rr, rr0, bnorm2, alpha, beta;  // rr = r.r (gamma of the CG recurrence)
   double acc_n[2];
   double rho[kMaxBlocks], gamma[kMaxBlocks], irho[kMaxBlocks], inv1p[kMaxBlocks];
   double l2scale[kMaxBlocks];

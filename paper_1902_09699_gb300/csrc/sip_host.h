@@ -31,7 +31,7 @@ struct InstLayout {
 };
 
 // kernel categories of the per-kernel timer
-enum KernelCat { KT_RHS = 0, KT_CG_DIR, KT_CG_UPD, KT_SETPASS, KT_SELECT, KT_TIES, KT_FINAL, KT_TAIL, KT_COUNT };
+enum KernelCat { KT_RHS = 0, KT_CG_W0, KT_CG_STEP, KT_SETPASS, KT_SELECT, KT_TIES, KT_FINAL, KT_TAIL, KT_COUNT };
 
 // CUDA-event timing of every launch, by kernel category (opt-in; used to
 // report per-kernel device time without a profiler).

@@ -16,8 +16,8 @@ struct Launch {
 cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, int ninst);
 cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
-cudaError_t launch_cg_dir(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
-cudaError_t launch_cg_upd(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            JobScal *jscal, const JobDev *jobs);
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
