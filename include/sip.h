@@ -242,6 +242,36 @@ sip_status sip_restrict(const sip_grid *fine, int dtype, const void *m_dev,
 sip_status sip_prolong(const sip_grid *fine, int op, int dtype,
                        const void *uc_dev, void *uf_dev, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free l1-ball projection.  The paper has no counterpart: this
+ * is a deployment variant of sip_project_set with SIP_SET_L1.
+ *
+ * Same result as sip_project_set(l1 set with sigma = tau) on n device
+ * elements w_dev -> y_dev, but the call allocates no memory: no cudaMalloc,
+ * cudaFree or allocating library routine (host memory is touched only to
+ * format an error message on failure).  It
+ * is meant for callers that cannot allocate while they run: code that works
+ * inside a fixed memory pool or budget a raw device allocation would bypass,
+ * and latency-sensitive loops in which an allocation or free could
+ * synchronise the device.  Its scratch (work list, selection state, radix
+ * histograms; 89 KB) is one fixed array compiled into the library,
+ * held on every GPU that loads the library until the process exits.
+ *
+ * n must be in [1, SIP_NOALLOC_MAX_N]; larger n returns
+ * SIP_ERR_INVALID_ARG.  tau >= 0.  The first call on each device looks up
+ * the array's device address (once, with that device current) and may set
+ * a kernel attribute; make that first call before any stream capture.
+ * Every call on a device shares the array: calls whose device work could
+ * overlap (several streams or host threads on one device) race and must be
+ * serialised by the caller.  Stream-ordered on `stream`; synchronises only
+ * when theta_out (host, may be NULL; receives the threshold, 0 when w is
+ * already inside the ball or tau = 0) is requested.
+ * ------------------------------------------------------------------- */
+#define SIP_NOALLOC_MAX_N (INT64_C(1) << 24)
+sip_status sip_project_l1_noalloc(int dtype, const void *w_dev, int64_t n,
+                                  double tau, void *y_dev, void *stream,
+                                  double *theta_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,7 +73,9 @@ SIGNATURES = {
     "sip_op_norm": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_int, c_vp, c_vp, ctypes.POINTER(c_dbl)]),
     "sip_restrict": (c_int, [ctypes.POINTER(Grid), c_int, c_vp, c_vp, c_vp]),
     "sip_prolong": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_vp, c_vp, c_vp]),
+    "sip_project_l1_noalloc": (c_int, [c_int, c_vp, c_i64, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl)]),
 }
+NOALLOC_MAX_N = 1 << 24
 
 _lib = None
 
@@ -323,6 +325,20 @@ def project_set(set_spec, w, stream=None):
     _check(lib().sip_project_set(ctypes.byref(s), code, _ptr(w), w.numel(), _ptr(y), _stream_ptr(stream),
                                  ctypes.byref(sc)))
     return y, sc.value
+
+
+def project_l1_noalloc(w, tau, y=None, stream=None):
+    """l1-ball projection through the allocation-free entry point; the
+    output tensor y may be passed in (nothing is allocated by the library
+    either way).  Returns (y, theta)."""
+    import torch
+    code = _dtype_code(w.dtype)
+    if y is None:
+        y = torch.empty_like(w)
+    th = c_dbl(0.0)
+    _check(lib().sip_project_l1_noalloc(code, _ptr(w), w.numel(), float(tau), _ptr(y), _stream_ptr(stream),
+                                        ctypes.byref(th)))
+    return y, th.value
 
 
 def op_norm(grid, op, set_type, m, stream=None):
