@@ -158,7 +158,7 @@ def run_ours(args):
 
     c = workload()
     its = c["opts"]["max_iter"]
-    pr = sip.Projector(c["grid"], c["sets"], dtype=args.dtype, **c["opts"])
+    pr = sip.Projector(c["grid"], c["sets"], dtype=args.dtype, exec=args.exec, **c["opts"])
     tdt = torch.float32 if args.dtype == "f32" else torch.float64
     # independent replicas: each rank projects its own models (seeded per rank)
     from paper_1902_09699_gb300 import workloads as W
@@ -198,7 +198,7 @@ def run_ours(args):
 
     # ---- accuracy of this form against the FP64 GPU loop (projections/s at 1e-4)
     x32, _ = pr.project(models[0], None)
-    pr64 = sip.Projector(c["grid"], c["sets"], dtype="f64", **c["opts"])
+    pr64 = sip.Projector(c["grid"], c["sets"], dtype="f64", exec=args.exec, **c["opts"])
     x64, _ = pr64.project(models[0].double())
     rel_err = float((x32.double() - x64).norm() / x64.norm())
     # plain FP64 GPU loop throughput (one step, same workload)
@@ -252,7 +252,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": config_dict(c, {"parallelism": "replicas" if world > 1 else "single"}),
+            "config": config_dict(c, {"parallelism": "replicas" if world > 1 else "single", "exec": args.exec}),
             "projections_per_s": value / its,
             "projections_per_s_at_1e-4": (value / its) if rel_err <= 1e-4 else 0.0,
             "rel_err_vs_f64_gpu": rel_err,
@@ -287,6 +287,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--cpu-iters", type=int, default=30)
+    ap.add_argument("--exec", default="auto", choices=["auto", "graph", "persistent"],
+                    help="iteration execution: persistent cooperative kernel or per-phase kernels in a CUDA graph")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -125,7 +125,17 @@ typedef struct {
      * used, the CG steps, r_evol and r_feas_i (NaN when not a check
      * iteration). */
     double *trace;
+    /* Execution of the iterations: SIP_EXEC_AUTO (currently the graph path),
+     * SIP_EXEC_GRAPH (one kernel per phase, replayed from a CUDA graph) or
+     * SIP_EXEC_PERSISTENT (one cooperative kernel for all iterations, grid
+     * barriers between phases).  Results are the same up to rounding order
+     * of the binary64 atomics. */
+    int exec;
 } sip_options;
+
+#define SIP_EXEC_AUTO 0
+#define SIP_EXEC_GRAPH 1
+#define SIP_EXEC_PERSISTENT 2
 
 typedef struct {
     int iters;          /* iterations run (finest level) */

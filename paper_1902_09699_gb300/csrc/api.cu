@@ -159,6 +159,7 @@ static sip_status check_opts(const sip_options &o) {
   if (o.levels == 2 && (o.rho_schedule || o.gamma_schedule || o.trace))
     return fail(SIP_ERR_INVALID_ARG, "schedules and traces are single-level only");
   if (o.gamma_schedule && !o.rho_schedule) return fail(SIP_ERR_INVALID_ARG, "gamma_schedule needs rho_schedule");
+  if (o.exec < SIP_EXEC_AUTO || o.exec > SIP_EXEC_PERSISTENT) return fail(SIP_ERR_INVALID_ARG, "unknown exec mode");
   return SIP_OK;
 }
 
@@ -434,6 +435,15 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     if (L.opts.check_every < P.check_every) P.check_every = L.opts.check_every;
     if (L.opts.stop) P.any_stop = true;
   }
+  // persistent execution needs every work list to fit the cooperative grid
+  // in one pass per phase; otherwise (or on request) the graph path runs
+  P.exec = insts.empty() ? SIP_EXEC_GRAPH : insts[0].opts.exec;
+  P.fused_grid = fused_grid(dtype);
+  // AUTO takes the graph path: measured on the 512 x 1024 five-set workload,
+  // the persistent kernel (all phases in one register allocation, 2 CTAs
+  // per SM) runs at half its speed
+  if (P.exec == SIP_EXEC_AUTO) P.exec = SIP_EXEC_GRAPH;
+  if (P.exec == SIP_EXEC_PERSISTENT && P.fused_grid <= 0) P.exec = SIP_EXEC_GRAPH;
   P.nt_n = (int)tn.size();
   P.nt_set = (int)tset.size();
   P.nt_sel = (int)tsel.size();
@@ -485,6 +495,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     offs[i].sched_g = L.opts.gamma_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
     offs[i].trace = L.opts.trace ? take((int64_t)L.opts.max_iter * (2 * L.dev.nb + 2 + L.dev.p) * 8) : -1;
   }
+  const int64_t o_ctrl = take(8 * sizeof(uint32_t));  // grid barrier words + finished count
   const int64_t o_insts = take((int64_t)P.ninst * sizeof(InstDev));
   const int64_t o_scal = take((int64_t)P.ninst * sizeof(InstScal));
   const int64_t o_jobs = take((int64_t)njobs * sizeof(JobDev));
@@ -539,6 +550,12 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     P.layouts[i] = insts[i];
   }
   P.m_own = own_m;
+  P.d_ctrl = (uint32_t *)at(o_ctrl);
+  for (int i = 0; i < P.ninst; ++i) {
+    P.h_insts[i].ndone = P.d_ctrl + 4;
+    insts[i].dev.ndone = P.d_ctrl + 4;
+    P.layouts[i].dev.ndone = P.d_ctrl + 4;
+  }
   P.d_insts = (InstDev *)at(o_insts);
   P.d_scal = (InstScal *)at(o_scal);
   P.d_jobs = (JobDev *)at(o_jobs);
@@ -639,8 +656,39 @@ static sip_status build_graph(Plan &P, cudaStream_t cap, int iters) {
 }
 
 // Run `iters` iterations (kernels no-op once an instance is done).
+static sip_status run_persistent(Plan &P, cudaStream_t st, int iters) {
+  FusedLaunch F;
+  F.tn = P.d_tn;
+  F.tset = P.d_tset;
+  F.tsel = P.d_tsel;
+  F.tfin = P.d_tfin;
+  F.nt_n = P.nt_n;
+  F.nt_set = P.nt_set;
+  F.nt_sel = P.nt_sel;
+  F.nt_fin = P.nt_fin;
+  F.insts = P.d_insts;
+  F.scal = P.d_scal;
+  F.jobs = P.d_jobs;
+  F.jscal = P.d_jscal;
+  F.hcnt = P.d_hcnt;
+  F.hs1 = P.d_hs1;
+  F.hs2 = P.d_hs2;
+  F.hs3 = P.d_hs3;
+  F.ties = P.d_ties;
+  F.bar = P.d_ctrl;
+  F.ndone = P.d_ctrl + 4;
+  F.ninst = P.ninst;
+  F.cg_launch = P.cg_launch;
+  F.any_card = P.any_card ? 1 : 0;
+  F.any_fin = P.any_fin ? 1 : 0;
+  F.iters = iters;
+  CK(launch_fused(Launch{P.dtype, st}, F, P.fused_grid));
+  return SIP_OK;
+}
+
 sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,
                           KernelTimer *tm) {
+  if (!tm && P.exec == SIP_EXEC_PERSISTENT) return run_persistent(P, st, iters);
   if (tm) {
     for (int i = 0; i < iters; ++i) {
       sip_status s = enqueue_iteration(P, st, tm);
@@ -677,6 +725,7 @@ sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm) {
     CK(cudaMemsetAsync(base, 0, (size_t)P.state_end, st));
   }
   CK(cudaMemsetAsync(base + P.hist_begin, 0, (size_t)(P.hist_end - P.hist_begin), st));
+  CK(cudaMemsetAsync(P.d_ctrl, 0, 8 * sizeof(uint32_t), st));
   CK(launch_init(L, P.d_insts, P.d_scal, P.ninst));
   CK(launch_norms(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal));
   return SIP_OK;

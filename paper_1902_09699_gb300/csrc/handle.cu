@@ -265,6 +265,9 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
   if (!sync) return SIP_OK;
   CKH(cudaStreamSynchronize(st));
   if (tm) tm->collect();
+  uint32_t ctrl[8];
+  CKH(cudaMemcpy(ctrl, F.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
+  if (ctrl[2] != 0) return fail(SIP_ERR_TIMEOUT, "a grid barrier of the persistent kernel timed out");
   InstScal sc;
   CKH(cudaMemcpy(&sc, F.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
   if (o.trace) CKH(cudaMemcpy(o.trace, df.trace, (size_t)o.max_iter * df.trace_w * 8, cudaMemcpyDeviceToHost));

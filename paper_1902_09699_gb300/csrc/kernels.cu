@@ -292,11 +292,10 @@ __device__ __forceinline__ T csys(const InstDev &in, const InstScal &sc, const G
 // x-update right-hand side and warm residual
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restrict__ insts,
                                                   InstScal *__restrict__ scal) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
-  const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done) return;
@@ -374,6 +373,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ ti
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                  InstScal *__restrict__ scal) {
+  body_rhs<T>(tiles[blockIdx.x], insts, scal);
+}
+
 // --------------------------------------------------------------------------
 // Conjugate gradient on C x = b from the warm start x (Sec. "Solving the
 // linear system and automatic parameter selection"), in the Chronopoulos-Gear
@@ -389,11 +394,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ ti
 // denominator of alpha equals p^T C p, so "p^T C p <= 0" stops as in CG.
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__restrict__ insts,
                                                        InstScal *__restrict__ scal) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
-  const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done || !sc.cg_active) return;
@@ -444,13 +448,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
+__global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                       InstScal *__restrict__ scal) {
+  body_cg_w0<T>(tiles[blockIdx.x], insts, scal);
+}
+
+template <typename T>
+__device__ __forceinline__ void body_cg_step(const Tile &tl,
                                                          const InstDev *__restrict__ insts,
                                                          InstScal *__restrict__ scal) {
   using A = typename AccOf<T>::type;
   constexpr int PT = sizeof(T) == 4 ? 2 : 1;  // 3 stencils per row: keep the register budget
   constexpr int SUB = kThreads * PT;
-  const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done || !sc.cg_active) return;
@@ -547,6 +556,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict_
     sc.rr = g1;
     sc.cg_active = more ? 1 : 0;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
+                                                         const InstDev *__restrict__ insts,
+                                                         InstScal *__restrict__ scal) {
+  body_cg_step<T>(tiles[blockIdx.x], insts, scal);
 }
 
 // --------------------------------------------------------------------------
@@ -758,10 +774,9 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__restrict__ insts,
                                                       InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
                                                       const JobDev *__restrict__ jobs) {
-  const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done) return;
@@ -824,6 +839,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict_
     }
   }
   (void)jobs;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                      InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
+                                                      const JobDev *__restrict__ jobs) {
+  body_setpass<T>(tiles[blockIdx.x], insts, scal, jscal, jobs);
 }
 
 // --------------------------------------------------------------------------
@@ -889,7 +911,7 @@ __device__ __forceinline__ unsigned long long cta_suffix_u64(unsigned long long 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__restrict__ insts,
                                                         InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                         JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
                                                         double *__restrict__ hs1, double *__restrict__ hs2,
@@ -899,7 +921,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__
   using K = typename KT::K;
   using S = typename BinAcc<T>::S;
   constexpr bool kInt = sizeof(T) == 4;
-  const Tile tl = tiles[blockIdx.x];
   const JobDev jd = jobs[tl.item];
   const InstDev &in = insts[jd.inst];
   InstScal &sc = scal[jd.inst];
@@ -1100,14 +1121,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                        InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
+                                                        JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
+                                                        double *__restrict__ hs1, double *__restrict__ hs2,
+                                                        double *__restrict__ hs3, int pass) {
+  body_select<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, hcnt, hs1, hs2, hs3, pass);
+}
+
 // Tie counts per final-pass work item for card sets whose k-th value is tied.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) k_ties(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__device__ __forceinline__ void body_ties(const Tile &tl, const InstDev *__restrict__ insts,
                                                    InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                    JobScal *__restrict__ jscal, uint32_t *__restrict__ ties) {
   SIP_STEP_CONSTANTS;
   using KT = KeyOf<T>;
-  const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   const BlockDev &bd = in.blk[tl.item];
@@ -1133,12 +1162,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_ties(const Tile *__restrict__ t
   if (threadIdx.x == 0) ties[jobs[bd.job_w].tie_off + tl.seq] = (uint32_t)tot;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 4) k_ties(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                   InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
+                                                   JobScal *__restrict__ jscal, uint32_t *__restrict__ ties) {
+  body_ties<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, ties);
+}
+
 // --------------------------------------------------------------------------
 // Final pass: l1 / l2 / card prox from the stored w and the dual update
 // v = v + rho (y - xbar) = rho (y - w), since w = xbar - v / rho.
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__restrict__ insts,
                                                     InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                     const JobScal *__restrict__ jscal,
                                                     const uint32_t *__restrict__ ties) {
@@ -1146,7 +1182,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ 
   using KT = KeyOf<T>;
   using K = typename KT::K;
   using A = typename AccOf<T>::type;
-  const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (sc.done) return;
@@ -1272,6 +1307,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                    InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
+                                                    const JobScal *__restrict__ jscal,
+                                                    const uint32_t *__restrict__ ties) {
+  body_final<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, ties);
+}
+
 // --------------------------------------------------------------------------
 // Per-instance tail: stopping quantities, Algorithm adapt-rho-gamma, C.
 // --------------------------------------------------------------------------
@@ -1308,11 +1351,8 @@ __device__ __forceinline__ double spectral(double ab, double aa, double bb) {
 
 constexpr int kTailWarps = 8;
 
-__global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restrict__ insts,
-                                                          InstScal *__restrict__ scal,
-                                                          const JobScal *__restrict__ jscal, int ninst) {
-  const int i = blockIdx.x;
-  if (i >= ninst) return;
+__device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ insts, InstScal *__restrict__ scal,
+                                          const JobScal *__restrict__ jscal) {
   const InstDev &in = insts[i];
   InstScal &sc = scal[i];
   if (sc.done) return;
@@ -1430,6 +1470,7 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restr
     if (b == 0) {
       sc.done = 1;
       sc.stop_reason = 1;
+      atomicAdd(in.ndone, 1u);
     }
   } else {
     double rho_b = b < nb ? s_rho[b] : 1.0, gam_b = b < nb ? s_gam[b] : 1.0;
@@ -1474,7 +1515,10 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restr
       store_coef_f32(sc);
       if (ad) sc.have_k0 = 1;
       sc.k = k + 1;
-      if (k >= in.max_iter) sc.done = 1;
+      if (k >= in.max_iter) {
+        sc.done = 1;
+        atomicAdd(in.ndone, 1u);
+      }
     }
   }
   __syncwarp();
@@ -1482,6 +1526,107 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restr
   double *acc = &sc.acc[0][0];
   for (int j = b; j < kMaxBlocks * kNAcc; j += 32) acc[j] = 0.0;
   if (b <= kMaxHist) sc.acc_ring[b] = 0.0;
+}
+
+__global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restrict__ insts,
+                                                          InstScal *__restrict__ scal,
+                                                          const JobScal *__restrict__ jscal, int ninst) {
+  if ((int)blockIdx.x < ninst) body_tail(blockIdx.x, insts, scal, jscal);
+}
+
+// --------------------------------------------------------------------------
+// Persistent form: every phase of the iteration in one cooperative launch.
+// Kernel boundaries become grid barriers; the work items and the phase
+// bodies are the ones of the separate kernels above.
+// --------------------------------------------------------------------------
+// Barrier words: [0] arrivals, [1] generation, [2] error, [3] unused.
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier with a bounded wait.  A CTA that waits longer than
+// kBarrierSpins polls (seconds) records SIP_ERR_TIMEOUT in bar[2] and every
+// CTA returns false, so the kernel ends instead of hanging.
+constexpr long long kBarrierSpins = 1ll << 26;
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const uint32_t g = ld_acquire(&bar[1]);
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      long long spins = 0;
+      while (ld_acquire(&bar[1]) == g) {
+        if (ld_acquire(&bar[2]) != 0 || ++spins > kBarrierSpins) {
+          atomicExch(&bar[2], (uint32_t)SIP_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (ld_acquire(&bar[2]) != 0) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct FusedArgs {
+  const Tile *tn, *tset, *tsel, *tfin;
+  int nt_n, nt_set, nt_sel, nt_fin;
+  const InstDev *insts;
+  InstScal *scal;
+  const JobDev *jobs;
+  JobScal *jscal;
+  uint32_t *hcnt;
+  double *hs1, *hs2, *hs3;
+  uint32_t *ties;
+  uint32_t *bar;
+  const uint32_t *ndone;
+  int ninst, npass, cg_launch, any_card, any_fin, iters;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
+  for (int it = 0; it < A.iters; ++it) {
+    for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_rhs<T>(A.tn[i], A.insts, A.scal);
+    if (!grid_barrier(A.bar)) return;
+    for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_cg_w0<T>(A.tn[i], A.insts, A.scal);
+    if (!grid_barrier(A.bar)) return;
+    for (int j = 0; j < A.cg_launch; ++j) {
+      for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_cg_step<T>(A.tn[i], A.insts, A.scal);
+      if (!grid_barrier(A.bar)) return;
+    }
+    for (int i = blockIdx.x; i < A.nt_set; i += gridDim.x) body_setpass<T>(A.tset[i], A.insts, A.scal, A.jscal, A.jobs);
+    if (!grid_barrier(A.bar)) return;
+    if (A.nt_sel) {
+      for (int pass = 0; pass < A.npass; ++pass) {
+        for (int i = blockIdx.x; i < A.nt_sel; i += gridDim.x)
+          body_select<T>(A.tsel[i], A.insts, A.scal, A.jobs, A.jscal, A.hcnt, A.hs1, A.hs2, A.hs3, pass);
+        if (!grid_barrier(A.bar)) return;
+      }
+    }
+    if (A.any_card) {
+      for (int i = blockIdx.x; i < A.nt_fin; i += gridDim.x) body_ties<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
+      if (!grid_barrier(A.bar)) return;
+    }
+    if (A.any_fin) {
+      for (int i = blockIdx.x; i < A.nt_fin; i += gridDim.x) body_final<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
+      if (!grid_barrier(A.bar)) return;
+    }
+    for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) body_tail(i, A.insts, A.scal, A.jscal);
+    if (!grid_barrier(A.bar)) return;
+    if (ld_acquire(A.ndone) >= (uint32_t)A.ninst) return;  // every instance stopped
+  }
 }
 
 }  // namespace sip
@@ -1572,6 +1717,7 @@ __global__ void __launch_bounds__(kThreads) k_norms(const Tile *__restrict__ til
   if (*(volatile int *)&sc.nonfinite) {
     sc.done = 1;
     sc.stop_reason = -1;
+    atomicAdd(in.ndone, 1u);
   }
 }
 
@@ -1682,6 +1828,10 @@ cudaError_t kernels_setup() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_select<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<float>::kSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
+  if (e != cudaSuccess) return e;
   done = true;
   return cudaSuccess;
 }
@@ -1714,6 +1864,52 @@ int launch_occupancy(int dtype, int kind) {
   }
   cudaGetLastError();
   return best == (1 << 30) ? 1 : best;
+}
+
+cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
+  FusedArgs A;
+  A.tn = F.tn;
+  A.tset = F.tset;
+  A.tsel = F.tsel;
+  A.tfin = F.tfin;
+  A.nt_n = F.nt_n;
+  A.nt_set = F.nt_set;
+  A.nt_sel = F.nt_sel;
+  A.nt_fin = F.nt_fin;
+  A.insts = F.insts;
+  A.scal = F.scal;
+  A.jobs = F.jobs;
+  A.jscal = F.jscal;
+  A.hcnt = F.hcnt;
+  A.hs1 = F.hs1;
+  A.hs2 = F.hs2;
+  A.hs3 = F.hs3;
+  A.ties = F.ties;
+  A.bar = F.bar;
+  A.ndone = F.ndone;
+  A.ninst = F.ninst;
+  A.npass = select_passes(L.dtype);
+  A.cg_launch = F.cg_launch;
+  A.any_card = F.any_card;
+  A.any_fin = F.any_fin;
+  A.iters = F.iters;
+  void *args[] = {&A};
+  const bool d = L.dtype == SIP_F64;
+  const size_t smem = d ? BinAcc<double>::kSmem : BinAcc<float>::kSmem;
+  return cudaLaunchCooperativeKernel(d ? (const void *)k_fused<double> : (const void *)k_fused<float>, grid, kThreads,
+                                     args, smem, L.stream);
+}
+
+// CTAs of the persistent kernel that are resident at once (its cooperative grid).
+int fused_grid(int dtype) {
+  int dev = 0, sms = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const bool d = dtype == SIP_F64;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d ? (const void *)k_fused<double> : (const void *)k_fused<float>,
+                                                kThreads, d ? BinAcc<double>::kSmem : BinAcc<float>::kSmem);
+  cudaGetLastError();
+  return sms * n;
 }
 
 int select_passes(int dtype) { return dtype == SIP_F64 ? num_passes<double>() : num_passes<float>(); }

@@ -149,6 +149,7 @@ struct InstDev {
   double eps_feas, eps_evol, rho0, gamma0, eps_corr, rho_ratio_max, gamma_max;
   const double *rho_sched, *gamma_sched;  // device copies, may be null
   double *trace;             // device trace rows, may be null
+  uint32_t *ndone;           // plan-wide count of finished instances
   int32_t trace_w;
   int32_t pad;
   // device arrays, element type = the plan's dtype

@@ -99,6 +99,9 @@ struct Plan {
   std::vector<InstLayout> layouts;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
+  uint32_t *d_ctrl = nullptr;  // grid-barrier words [0..3], finished-instance count [4]
+  int exec = SIP_EXEC_GRAPH;
+  int fused_grid = 0;
   void release();
 };
 

@@ -29,6 +29,24 @@ cudaError_t kernels_setup();
 // segments, 2 selection jobs, 3 final-pass blocks
 int launch_occupancy(int dtype, int kind);
 int select_passes(int dtype);
+
+// persistent cooperative form of the iteration (kernels.cu)
+struct FusedLaunch {
+  const Tile *tn, *tset, *tsel, *tfin;
+  int nt_n, nt_set, nt_sel, nt_fin;
+  const InstDev *insts;
+  InstScal *scal;
+  const JobDev *jobs;
+  JobScal *jscal;
+  uint32_t *hcnt;
+  double *hs1, *hs2, *hs3;
+  uint32_t *ties;
+  uint32_t *bar;          // 4 words: arrivals, generation, error, unused
+  const uint32_t *ndone;  // finished instances
+  int ninst, cg_launch, any_card, any_fin, iters;
+};
+cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid);
+int fused_grid(int dtype);
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                         const JobDev *jobs, JobScal *jscal, uint32_t *ties);
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,

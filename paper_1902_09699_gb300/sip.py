@@ -18,6 +18,7 @@ OPS = {"I": 0, "DZ": 1, "DX": 2, "DY": 3, "TV": 4}
 SET_TYPES = {"bounds": 0, "l1": 1, "l2": 2, "card": 3}
 F64, F32 = 0, 1
 FORMS = {"alg1": 0, "direct": 1}
+EXEC = {"auto": 0, "graph": 1, "persistent": 2}
 STATUS = {0: "SIP_OK", 1: "SIP_ERR_INVALID_ARG", 2: "SIP_ERR_OOM", 3: "SIP_ERR_CUDA", 4: "SIP_ERR_TIMEOUT",
           5: "SIP_ERR_NONFINITE", 6: "SIP_ERR_BUDGET", 7: "SIP_ERR_INTERNAL"}
 MAX_SETS = 16
@@ -41,7 +42,7 @@ class Options(ctypes.Structure):
                 ("eps_corr", c_dbl), ("rho_ratio_max", c_dbl), ("gamma_max", c_dbl), ("form", c_int),
                 ("dtype", c_int), ("levels", c_int), ("coarse_iter", c_int),
                 ("rho_schedule", ctypes.POINTER(c_dbl)), ("gamma_schedule", ctypes.POINTER(c_dbl)),
-                ("trace", ctypes.POINTER(c_dbl))]
+                ("trace", ctypes.POINTER(c_dbl)), ("exec", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -197,6 +198,8 @@ class Projector:
         for k, v in opts.items():
             if k == "form":
                 v = FORMS[v] if isinstance(v, str) else int(v)
+            if k == "exec":
+                v = EXEC[v] if isinstance(v, str) else int(v)
             if not hasattr(o, k):
                 raise KeyError("unknown option %r" % (k,))
             setattr(o, k, v)

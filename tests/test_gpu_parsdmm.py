@@ -102,6 +102,24 @@ def test_layered_replayed_schedule(dt):
     assert rel(x, ref["x"]) <= BAR[dt]
 
 
+@pytest.mark.parametrize("mode", ["graph", "persistent"])
+def test_execution_modes_agree_with_oracle(mode):
+    # both ways of running the iterations: one kernel per phase replayed from
+    # a CUDA graph, and one cooperative kernel with grid barriers
+    c = layered_small((72, 100))
+    ref = oracle_run(c["m"], c["grid"], c["sets"], c["opts"])
+    x, info, tr = run_gpu(c["m"], c["grid"], c["sets"], "f64", dict(c["opts"], exec=mode), trace=True)
+    rs, _ = schedules(ref)
+    nb = len(c["sets"]) + 1
+    assert np.allclose(tr[:, :nb], rs, rtol=1e-9, atol=0)
+    assert rel(x, ref["x"]) <= 1e-10
+    c2 = W.small_2d(n=(40, 36), seed=3)
+    opts = dict(max_iter=2000, adapt=1, gamma0=1.5, stop=1, exec=mode)
+    ref2 = oracle_run(c2["m"], c2["grid"], c2["sets"][::2], {k: v for k, v in opts.items() if k != "exec"})
+    x2, info2, _ = run_gpu(c2["m"], c2["grid"], c2["sets"][::2], "f64", opts)
+    assert info2["iters"] == ref2["iters"] and rel(x2, ref2["x"]) <= 1e-10
+
+
 def test_adapt_rho_and_gamma_full_algorithm():
     c = layered_small((40, 56))
     opts = dict(c["opts"], adapt=2, max_iter=40)
