@@ -183,6 +183,31 @@ sip_status sip_destroy(sip_handle *h);
 
 const char *sip_last_error(const sip_handle *h);
 
+/* ---------------------------------------------------------------------
+ * Batched projections: `count` independent problems, each with its own
+ * grid and set list, run together.  Every launch of an iteration covers the
+ * work items of all instances (a ragged launch: instances of any size share
+ * the launch; reductions, selections and the adapt-rho-gamma tail stay per
+ * instance), so launch and synchronisation costs are paid once per batch
+ * instead of once per problem.  Each instance follows exactly the iteration
+ * of a single sip_project with the same options (Algorithm PARSDMM); the
+ * results equal the one-at-a-time results up to the rounding order of the
+ * binary64 atomics.
+ *
+ * sets holds the sets of instance 0, then of instance 1, ...; nsets[i] of
+ * them for instance i.  opts applies to every instance (single level, no
+ * schedules or traces).  Models and results are packed: instance i's N_i
+ * elements start at element sip_batch_offset(h, i); sip_batch_offset(h,
+ * count) is the total.  infos (host, may be NULL) receives count entries;
+ * passing it synchronises the stream.  sip_project on a batched handle
+ * returns SIP_ERR_INVALID_ARG. */
+sip_status sip_batch_create(int count, const sip_grid *grids, const sip_set *sets,
+                            const int *nsets, const sip_options *opts,
+                            sip_handle **out);
+sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev,
+                             void *stream, sip_info *infos);
+int64_t sip_batch_offset(const sip_handle *h, int i);
+
 /* Bytes of device memory the handle holds. */
 int64_t sip_device_bytes(const sip_handle *h);
 

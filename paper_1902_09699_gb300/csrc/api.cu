@@ -365,7 +365,7 @@ void Plan::release() {
   arena = nullptr;
 }
 
-sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m) {
+sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed) {
   P.dtype = dtype;
   P.ninst = (int)insts.size();
   const size_t W = esize(dtype);
@@ -463,8 +463,13 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   std::vector<Offs> offs(P.ninst);
   // warm state (x, y, v) of all instances first, then the rest of the state,
   // then everything else: memsets stay contiguous
+  // batched plans keep every instance's x (and m) back to back, so one copy
+  // moves all outputs (inputs); instance i starts at element P.pack_off[i]
+  P.pack_off.assign(P.ninst + 1, 0);
+  for (int i = 0; i < P.ninst; ++i) P.pack_off[i + 1] = P.pack_off[i] + insts[i].dev.N;
+  const int64_t o_xpack = packed ? take(P.pack_off[P.ninst] * W) : -1;
   for (int i = 0; i < P.ninst; ++i) {
-    offs[i].x = take(insts[i].dev.N * W);
+    offs[i].x = packed ? o_xpack + P.pack_off[i] * W : take(insts[i].dev.N * W);
     offs[i].y = take(insts[i].Mtot * W);
     offs[i].v = take(insts[i].Mtot * W);
   }
@@ -488,9 +493,10 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     offs[i].k0v = ad ? take(L.Mtot * W) : -1;
   }
   P.state_end = off;
+  const int64_t o_mpack = (own_m && packed) ? take(P.pack_off[P.ninst] * W) : -1;
   for (int i = 0; i < P.ninst; ++i) {
     const InstLayout &L = insts[i];
-    offs[i].m = own_m ? take(L.dev.N * W) : -1;
+    offs[i].m = own_m ? (packed ? o_mpack + P.pack_off[i] * W : take(L.dev.N * W)) : -1;
     offs[i].sched_r = L.opts.rho_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
     offs[i].sched_g = L.opts.gamma_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
     offs[i].trace = L.opts.trace ? take((int64_t)L.opts.max_iter * (2 * L.dev.nb + 2 + L.dev.p) * 8) : -1;
@@ -550,6 +556,9 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     P.layouts[i] = insts[i];
   }
   P.m_own = own_m;
+  P.packed = packed;
+  P.x_pack = packed ? at(o_xpack) : nullptr;
+  P.m_pack = (own_m && packed) ? at(o_mpack) : nullptr;
   P.d_ctrl = (uint32_t *)at(o_ctrl);
   for (int i = 0; i < P.ninst; ++i) {
     P.h_insts[i].ndone = P.d_ctrl + 4;
@@ -704,10 +713,10 @@ sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters,
     CK(cudaGraphLaunch(P.graph, st));
     done_iters += chunk;
     if (poll && done_iters < iters) {
-      // all instances done?  (one flag per instance; single-instance plans)
-      CK(cudaMemcpyAsync(pinned_flag, &P.d_scal[0].done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      // every instance done?  (the tails count finished instances)
+      CK(cudaMemcpyAsync(pinned_flag, P.d_ctrl + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      if (*pinned_flag) break;
+      if (*pinned_flag >= P.ninst) break;
     }
   }
   return SIP_OK;

@@ -16,6 +16,7 @@ using namespace sip;
 struct sip_handle {
   Plan lev[2];      // lev[0]: finest grid; lev[1]: coarse grid (two-level ML)
   int levels = 1;
+  int batch = 0;    // > 0: a batched handle of `batch` instances (packed buffers)
   sip_options opts;
   sip_grid grid;
   std::vector<sip_set> sets;
@@ -198,7 +199,9 @@ int64_t sip_device_bytes(const sip_handle *h) {
 
 double sip_bytes_per_iter(const sip_handle *h) {
   if (!h || h->lev[0].layouts.empty()) return 0.0;
-  return layout_bytes_per_iter(h->lev[0].layouts[0], h->opts.dtype);
+  double b = 0.0;
+  for (const auto &L : h->lev[0].layouts) b += layout_bytes_per_iter(L, h->opts.dtype);
+  return b;
 }
 
 static sip_status prolong_state(Plan &C, Plan &F, cudaStream_t st) {
@@ -297,6 +300,7 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
 
 sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev, void *stream, sip_info *info) {
   if (!h) return fail(SIP_ERR_INVALID_ARG, "handle is NULL");
+  if (h->batch) return keep(h, fail(SIP_ERR_INVALID_ARG, "batched handle: use sip_batch_project"));
   if (!m_dev || !x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "m_dev / x_dev is NULL"));
   h->err.clear();
   return keep(h, project_impl(h, m_dev, x_dev, (cudaStream_t)stream, info));
@@ -512,6 +516,105 @@ sip_status sip_op_norm(const sip_grid *grid, int op, int type, int dtype, const 
   CKH(cudaMemcpy(&sc, P.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
   *out = sc.sigma[0];
   return SIP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// batched (ragged) projections
+// ----------------------------------------------------------------------------
+sip_status sip_batch_create(int count, const sip_grid *grids, const sip_set *sets, const int *nsets,
+                            const sip_options *opts, sip_handle **out) {
+  if (!out) return fail(SIP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1) return fail(SIP_ERR_INVALID_ARG, "count must be >= 1");
+  if (!grids || !sets || !nsets || !opts) return fail(SIP_ERR_INVALID_ARG, "NULL argument");
+  if (opts->levels != 1) return fail(SIP_ERR_INVALID_ARG, "batched projections are single-level");
+  if (opts->rho_schedule || opts->gamma_schedule || opts->trace)
+    return fail(SIP_ERR_INVALID_ARG, "schedules and traces are per-handle, not batched");
+  std::vector<InstLayout> L;
+  L.reserve(count);
+  int64_t so = 0;
+  for (int i = 0; i < count; ++i) {
+    sip_status st = validate(&grids[i], sets + so, nsets[i], opts);
+    if (st) return fail(st, "instance %d: %s", i, g_err.c_str());
+    L.push_back(make_layout(grid_desc(grids[i]), sets + so, nsets[i], *opts));
+    so += nsets[i];
+  }
+  sip_handle *h = new (std::nothrow) sip_handle();
+  if (!h) return fail(SIP_ERR_OOM, "host allocation failed");
+  h->opts = *opts;
+  h->grid = grids[0];
+  h->batch = count;
+  sip_status st = plan_build(h->lev[0], L, opts->dtype, true, true);
+  if (st) {
+    sip_destroy(h);
+    return st;
+  }
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&h->pinned, sizeof(int32_t)) != cudaSuccess || cudaEventCreate(&h->ev0) != cudaSuccess ||
+      cudaEventCreate(&h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    sip_destroy(h);
+    return fail(SIP_ERR_CUDA, "stream/event set-up failed");
+  }
+  *out = h;
+  return SIP_OK;
+}
+
+int64_t sip_batch_offset(const sip_handle *h, int i) {
+  if (!h || !h->batch || i < 0 || i > h->batch) return -1;
+  return h->lev[0].pack_off[i];
+}
+
+sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void *stream, sip_info *infos) {
+  if (!h || !h->batch) return fail(SIP_ERR_INVALID_ARG, "not a batched handle");
+  if (!m_dev || !x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "m_dev / x_dev is NULL"));
+  h->err.clear();
+  Plan &P = h->lev[0];
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)P.pack_off[P.ninst] * esz(P.dtype);
+  KernelTimer *tm = h->timing ? &h->timer : nullptr;
+  auto run = [&]() -> sip_status {
+    CKH(cudaEventRecord(h->ev0, st));
+    CKH(cudaMemcpyAsync(P.m_pack, m_dev, bytes, cudaMemcpyDeviceToDevice, st));
+    sip_status s = plan_prepare(P, st, false);
+    if (!s) s = run_iterations(P, st, h->cap, P.max_iter, h->opts.stop != 0, h->pinned, tm);
+    if (s) return s;
+    CKH(cudaMemcpyAsync(x_dev, P.x_pack, bytes, cudaMemcpyDeviceToDevice, st));
+    CKH(cudaEventRecord(h->ev1, st));
+    if (!infos && !tm) return SIP_OK;
+    CKH(cudaStreamSynchronize(st));
+    if (tm) tm->collect();
+    if (!infos) return SIP_OK;
+    std::vector<InstScal> sc(P.ninst);
+    CKH(cudaMemcpy(sc.data(), P.d_scal, P.ninst * sizeof(InstScal), cudaMemcpyDeviceToHost));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    bool nonfinite = false;
+    for (int i = 0; i < P.ninst; ++i) {
+      const InstDev &d = P.h_insts[i];
+      sip_info &f = infos[i];
+      memset(&f, 0, sizeof f);
+      f.iters = sc[i].iters;
+      f.cg_steps_total = sc[i].cg_total;
+      f.stop_reason = sc[i].stop_reason;
+      f.nblocks = d.nb;
+      f.r_evol = sc[i].r_evol;
+      for (int b = 0; b < d.p; ++b) {
+        f.r_feas[b] = sc[i].r_feas[b];
+        f.sigma[b] = sc[i].sigma[b];
+        f.k[b] = sc[i].kcard[b];
+      }
+      for (int b = 0; b < d.nb; ++b) {
+        f.rho[b] = sc[i].rho[b];
+        f.gamma[b] = sc[i].gamma[b];
+      }
+      f.ms = ms;
+      if (sc[i].stop_reason < 0) nonfinite = true;
+    }
+    if (nonfinite) return fail(SIP_ERR_NONFINITE, "a model holds NaN or Inf");
+    return SIP_OK;
+  };
+  return keep(h, run());
 }
 
 sip_status sip_restrict(const sip_grid *fine, int dtype, const void *m_dev, void *mc_dev, void *stream) {

@@ -100,6 +100,9 @@ struct Plan {
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
   uint32_t *d_ctrl = nullptr;  // grid-barrier words [0..3], finished-instance count [4]
+  bool packed = false;         // batched plan: x (and m) of all instances back to back
+  std::vector<int64_t> pack_off;
+  void *x_pack = nullptr, *m_pack = nullptr;
   int exec = SIP_EXEC_GRAPH;
   int fused_grid = 0;
   void release();
@@ -114,7 +117,7 @@ sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const 
 void set_fastdiv(InstDev &d);
 InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const sip_options &o);
 double layout_bytes_per_iter(const InstLayout &L, int dtype);
-sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m);
+sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed = false);
 sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm);
 sip_status plan_set_m(Plan &P, int inst, const void *m, cudaStream_t st);
 sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,

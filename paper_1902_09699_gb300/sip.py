@@ -75,6 +75,10 @@ SIGNATURES = {
     "sip_restrict": (c_int, [ctypes.POINTER(Grid), c_int, c_vp, c_vp, c_vp]),
     "sip_prolong": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_vp, c_vp, c_vp]),
     "sip_project_l1_noalloc": (c_int, [c_int, c_vp, c_i64, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl)]),
+    "sip_batch_create": (c_int, [c_int, ctypes.POINTER(Grid), ctypes.POINTER(Set), ctypes.POINTER(c_int),
+                                 ctypes.POINTER(Options), ctypes.POINTER(c_vp)]),
+    "sip_batch_project": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Info)]),
+    "sip_batch_offset": (c_i64, [c_vp, c_int]),
 }
 NOALLOC_MAX_N = 1 << 24
 
@@ -270,6 +274,84 @@ class Projector:
         _check(lib().sip_kernel_times(self.handle, ms, la, by), self.handle)
         return {lib().sip_kernel_name(i).decode(): dict(ms=ms[i], launches=la[i], bytes_per_launch=by[i])
                 for i in range(n)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sip_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _info_dict(inf, nsets, nblocks):
+    return dict(iters=inf.iters, cg_steps=inf.cg_steps_total, stop_reason=inf.stop_reason, r_evol=inf.r_evol,
+                r_feas=list(inf.r_feas[:nsets]), rho=list(inf.rho[:nblocks]), gamma=list(inf.gamma[:nblocks]),
+                sigma=list(inf.sigma[:nsets]), k=list(inf.k[:nsets]), ms=float(inf.ms))
+
+
+class BatchProjector:
+    """A batched handle: ``instances`` is a list of (grid, sets); options as
+    for Projector.  project() takes the packed models (or a list of
+    per-instance tensors) and returns the per-instance results."""
+
+    def __init__(self, instances, dtype="f32", **opts):
+        L = lib()
+        self.code = _dtype_code(dtype)
+        o = default_options()
+        for k, v in opts.items():
+            if k == "form":
+                v = FORMS[v] if isinstance(v, str) else int(v)
+            if k == "exec":
+                v = EXEC[v] if isinstance(v, str) else int(v)
+            setattr(o, k, v)
+        o.dtype = self.code
+        self.opts = o
+        self.count = len(instances)
+        self.grids = (Grid * self.count)(*[make_grid(g) for g, _ in instances])
+        all_sets = [s for _, ss in instances for s in ss]
+        self.sets = make_sets(all_sets)
+        self.nsets = (c_int * self.count)(*[len(ss) for _, ss in instances])
+        self.nblocks = [len(ss) + (1 if o.form == FORMS["alg1"] else 0) for _, ss in instances]
+        h = c_vp()
+        _check(L.sip_batch_create(self.count, self.grids, self.sets, self.nsets, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+        self.offsets = [int(L.sip_batch_offset(h, i)) for i in range(self.count + 1)]
+
+    @property
+    def torch_dtype(self):
+        return _torch_dtype(self.code)
+
+    def pack(self, models):
+        import torch
+        return torch.cat([_dev(m, self.code).reshape(-1) for m in models])
+
+    def project(self, m, x=None, stream=None, info=True):
+        import torch
+        if isinstance(m, (list, tuple)):
+            m = self.pack(m)
+        m = _dev(m, self.code)
+        total = self.offsets[-1]
+        if m.numel() != total:
+            raise ValueError("packed models hold %d elements, the batch needs %d" % (m.numel(), total))
+        if x is None:
+            x = torch.empty(total, dtype=self.torch_dtype, device=m.device)
+        infos = (Info * self.count)() if info else None
+        _check(lib().sip_batch_project(self.handle, _ptr(m), _ptr(x), _stream_ptr(stream), infos), self.handle)
+        xs = [x[self.offsets[i]:self.offsets[i + 1]] for i in range(self.count)]
+        if not info:
+            return xs, None
+        nsets = list(self.nsets)
+        return xs, [_info_dict(infos[i], nsets[i], self.nblocks[i]) for i in range(self.count)]
+
+    def set_timing(self, on):
+        _check(lib().sip_set_timing(self.handle, 1 if on else 0), self.handle)
+
+    def bytes_per_iter(self):
+        return float(lib().sip_bytes_per_iter(self.handle))
 
     def close(self):
         if getattr(self, "handle", None):

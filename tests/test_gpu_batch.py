@@ -1,0 +1,100 @@
+"""Batched (ragged) projections: many instances of different grids and set
+lists in one handle, every launch covering all of them.
+
+Each instance must follow exactly the iteration a single projection runs:
+against the FP64 oracle (fixed rho: 1e-10), against one-at-a-time runs of
+the library (adaptive rho; equal up to the rounding order of the binary64
+atomics: 1e-10 in FP64, 1e-5 in FP32) and with per-instance stopping.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import parsdmm as P                   # noqa: E402
+from paper_1902_09699_gb300 import sip            # noqa: E402
+from paper_1902_09699_gb300 import workloads as W  # noqa: E402
+
+TD = {"f64": torch.float64, "f32": torch.float32}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def mixed_instances():
+    """Heterogeneous instances: 2D and 3D, ragged sizes, all set types."""
+    g = np.random.default_rng(12)
+    out = []
+    out.append(({"n": (40, 33)}, W.small_2d()["sets"]))
+    out.append(({"n": (17, 64)}, W.layered_2d()["sets"]))
+    out.append(({"n": (9, 8, 7)}, W.grf_3d()["sets"]))
+    out.append(({"n": (130, 3)}, [{"op": "DZ", "type": "card", "k_frac": 0.05},
+                                  {"op": "I", "type": "l2", "sigma_rel": 0.6}]))
+    out.append(({"n": (25, 25)}, [{"op": "TV", "type": "l1", "sigma_rel": 0.2}]))
+    models = [3.0 + g.standard_normal(int(np.prod(gr["n"]))) for gr, _ in out]
+    return out, models
+
+
+def test_batch_matches_oracle_fixed_rho():
+    inst, models = mixed_instances()
+    opts = dict(max_iter=40, adapt=0, rho0=1.0, gamma0=1.5)
+    bp = sip.BatchProjector(inst, dtype="f64", **opts)
+    xs, infos = bp.project(models)
+    for i, ((grid, sets), m) in enumerate(zip(inst, models)):
+        ref = P.parsdmm(m, grid, sets, P.options(**opts))
+        assert rel(xs[i].cpu().numpy(), ref["x"]) <= 1e-10, i
+        assert infos[i]["iters"] == 40
+    bp.close()
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_batch_equals_one_at_a_time(dt, tol):
+    """Each result alone and in the mix is the same."""
+    inst, models = mixed_instances()
+    opts = dict(max_iter=60, adapt=1, gamma0=1.5)
+    bp = sip.BatchProjector(inst, dtype=dt, **opts)
+    xs, _ = bp.project(models)
+    for i, ((grid, sets), m) in enumerate(zip(inst, models)):
+        pr = sip.Projector(grid, sets, dtype=dt, **opts)
+        x1, _ = pr.project(torch.as_tensor(m, dtype=TD[dt], device="cuda"))
+        pr.close()
+        assert rel(xs[i].double().cpu().numpy(), x1.double().cpu().numpy()) <= tol, i
+    bp.close()
+
+
+def test_batch_per_instance_stopping():
+    inst, models = mixed_instances()
+    sel = [(g, [s for s in sets if s["type"] in ("bounds", "l2")] or [{"op": "I", "type": "bounds", "lo": 2.5,
+                                                                           "hi": 3.5}]) for g, sets in inst]
+    opts = dict(max_iter=1500, adapt=1, gamma0=1.5, stop=1)
+    bp = sip.BatchProjector(sel, dtype="f64", **opts)
+    xs, infos = bp.project(models)
+    for i, ((grid, sets), m) in enumerate(zip(sel, models)):
+        ref = P.parsdmm(m, grid, sets, P.options(**opts))
+        assert infos[i]["stop_reason"] == ref["stop_reason"], i
+        assert infos[i]["iters"] == ref["iters"], i
+        assert rel(xs[i].cpu().numpy(), ref["x"]) <= 1e-9, i
+    bp.close()
+
+
+def test_batch_ragged_workload_shapes():
+    """A slice of the 512-instance ragged workload (sizes 32..512, 2-5 sets)
+    in FP32: every instance runs its iterations and stays finite."""
+    rb = W.ragged_batch(count=12, seed=77)
+    inst = [(it["grid"], it["sets"]) for it in rb["instances"]]
+    bp = sip.BatchProjector(inst, dtype="f32", **dict(rb["opts"], max_iter=30))
+    xs, infos = bp.project([it["m"] for it in rb["instances"]])
+    for i, x in enumerate(xs):
+        assert infos[i]["iters"] == 30
+        assert torch.isfinite(x).all()
+    bp.close()
+
+
+def test_batch_rejects_bad_instance():
+    with pytest.raises(sip.SipError) as e:
+        sip.BatchProjector([({"n": (8, 8)}, [{"op": "I", "type": "bounds", "lo": 1.0, "hi": 0.0}])], dtype="f64")
+    assert e.value.status == 1
