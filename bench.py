@@ -405,6 +405,49 @@ def run_grf3d(args):
     return 0
 
 
+def run_serving(args):
+    """Serving: requests from a Poisson stream (2D 64^2-1024^2 and 3D
+    64^3-192^3, 2-6 sets of the small_2d types, FP32 with FP64 reductions,
+    stop at feasibility 1e-3 or 500 iterations) submitted at their arrival
+    times to the continuous-batching server under a 120 GB budget; latency
+    is arrival to delivery."""
+    import numpy as np
+
+    from paper_1902_09699_gb300 import sip
+    from paper_1902_09699_gb300 import workloads as W
+    trace = W.request_stream(rate=args.rate, seconds=60.0, max_requests=args.requests)
+    models = [W.request_model(r) for _, r in trace]
+    srv = sip.Server(dtype="f32", budget_bytes=120 << 30, max_batch=64, max_cohorts=8, max_wait_ms=2.0,
+                     max_iter=500, stop=2, adapt=1, gamma0=1.5, exec=args.exec)
+    t0 = time.perf_counter()
+    ids = []
+    for (t_arr, r), m in zip(trace, models):
+        dt = t_arr - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(r["grid"], r["sets"], m))
+    lat, its = [], []
+    for i in ids:
+        x, info, l = srv.wait(i)
+        lat.append(l)
+        its.append(info["iters"])
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    offered = len(trace) / max(trace[-1][0], 1e-9)
+    out = {"metric": METRIC, "value": len(trace) / wall, "unit": "projections/s", "n_gpus": 1,
+           "steps": 1, "warmup": 0, "ms_per_step": wall * 1000.0, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "serving-poisson", "requests": len(trace), "offered_rate_per_s": offered,
+                      "budget_gb": 120, "max_batch": 64, "max_cohorts": 8, "exec": args.exec},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(np.max(lat))},
+           "iterations": {"mean": float(np.mean(its)), "max": int(np.max(its))},
+           "hbm_peak_gb": st["hbm_peak"] / 2 ** 30, "failed": st["failed"]}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,11 +458,13 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=30)
     ap.add_argument("--exec", default="auto", choices=["auto", "graph", "persistent"],
                     help="iteration execution: persistent cooperative kernel or per-phase kernels in a CUDA graph")
-    ap.add_argument("--workload", default="layered", choices=["layered", "ragged", "grf3d"],
+    ap.add_argument("--workload", default="layered", choices=["layered", "ragged", "grf3d", "serving"],
                     help="layered: 512 x 1024 five-set 2D model (default line); ragged: 512-instance batch; "
                          "grf3d: 256 x 256 x 128 two-level")
     ap.add_argument("--count", type=int, default=512, help="ragged: instances")
     ap.add_argument("--sample", type=int, default=16, help="ragged: instances timed one at a time in FP64")
+    ap.add_argument("--requests", type=int, default=64, help="serving: requests taken from the Poisson stream")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -427,6 +472,8 @@ def main():
         return run_ragged(args)
     if args.workload == "grf3d":
         return run_grf3d(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

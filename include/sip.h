@@ -208,6 +208,58 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev,
                              void *stream, sip_info *infos);
 int64_t sip_batch_offset(const sip_handle *h, int i);
 
+/* ---------------------------------------------------------------------
+ * Projection server (continuous batching).  Requests may be submitted
+ * from any thread at any time; a worker thread admits queued requests as
+ * cohorts when the HBM budget has room for a cohort's whole state (sized
+ * before allocation, so the budget is never exceeded), runs every cohort as
+ * a batched plan on its own stream (cohorts admitted at different times
+ * overlap on the device), keeps each request's x, y_i, v_i, rho_i and CG
+ * state resident until its own stopping rule holds, then delivers it and
+ * records its latency (submission to delivery, queueing included).
+ * ------------------------------------------------------------------- */
+typedef struct {
+    sip_options opts;      /* per-request options (single level; dtype of the
+                              models and results; default: stop = 2, i.e.
+                              feasibility 1e-3, or max_iter = 500) */
+    int64_t budget_bytes;  /* device memory the server may hold (default 120 GiB) */
+    int max_batch;         /* requests per cohort (default 64) */
+    int max_cohorts;       /* cohorts running at once (default 8) */
+    double max_wait_ms;    /* a cohort forms once the oldest request waited
+                              this long, even if smaller than max_batch */
+    int64_t max_points;    /* grid points per cohort (default 2^24); a cohort
+                              takes requests within a factor 4 of the size
+                              of the oldest queued request */
+} sip_server_config;
+
+typedef struct {
+    int64_t completed, failed, queued;
+    int running_cohorts;
+    int64_t hbm_in_use, hbm_peak;  /* bytes of cohort state */
+    double p50_ms, p99_ms;         /* latency of completed requests */
+    double projections_per_s;      /* completed / (last completion - first submission) */
+} sip_server_stats;
+
+typedef struct sip_server sip_server;
+
+void sip_server_config_default(sip_server_config *cfg);
+sip_status sip_server_create(const sip_server_config *cfg, sip_server **out);
+/* Queue a projection of the host model m_host (N elements of opts.dtype);
+ * the result is written to x_host (N elements) before the request is
+ * reported done.  The model is copied; x_host must stay valid until
+ * sip_server_wait returns for this request.  A request that does not fit
+ * the budget even alone fails with SIP_ERR_BUDGET. */
+sip_status sip_server_submit(sip_server *srv, const sip_grid *grid,
+                             const sip_set *sets, int nsets,
+                             const void *m_host, void *x_host, int64_t *req_id);
+/* Block until the request is done (timeout_ms < 0: no limit); returns its
+ * status, info and latency, and forgets the request. */
+sip_status sip_server_wait(sip_server *srv, int64_t req_id, double timeout_ms,
+                           sip_info *info, double *latency_ms);
+sip_status sip_server_query_stats(sip_server *srv, sip_server_stats *out);
+/* Finishes every queued and running request, then stops the worker. */
+sip_status sip_server_destroy(sip_server *srv);
+
 /* Bytes of device memory the handle holds. */
 int64_t sip_device_bytes(const sip_handle *h);
 

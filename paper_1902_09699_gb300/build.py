@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsip.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["kernels.cu", "kernels_ml.cu", "api.cu", "handle.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "kernels_ml.cu", "api.cu", "handle.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

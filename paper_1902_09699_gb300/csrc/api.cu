@@ -365,7 +365,7 @@ void Plan::release() {
   arena = nullptr;
 }
 
-sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed) {
+sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed, bool dry) {
   P.dtype = dtype;
   P.ninst = (int)insts.size();
   const size_t W = esize(dtype);
@@ -518,6 +518,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const int64_t o_tsel = take((int64_t)tsel.size() * sizeof(Tile));
   const int64_t o_tfin = take((int64_t)tfin.size() * sizeof(Tile));
   P.arena_bytes = off;
+  if (dry) return SIP_OK;  // size only (admission control)
 
   if (cudaMalloc(&P.arena, (size_t)off) != cudaSuccess) {
     cudaGetLastError();
@@ -590,6 +591,13 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   if (!tsel.empty()) CK(cudaMemcpy(P.d_tsel, tsel.data(), tsel.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   if (!tfin.empty()) CK(cudaMemcpy(P.d_tfin, tfin.data(), tfin.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   return SIP_OK;
+}
+
+int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed) {
+  Plan P;
+  std::vector<InstLayout> copy = insts;
+  if (plan_build(P, copy, dtype, own_m, packed, true) != SIP_OK) return -1;
+  return P.arena_bytes;
 }
 
 // ----------------------------------------------------------------------------

@@ -117,7 +117,10 @@ sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const 
 void set_fastdiv(InstDev &d);
 InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const sip_options &o);
 double layout_bytes_per_iter(const InstLayout &L, int dtype);
-sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed = false);
+sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed = false,
+                      bool dry = false);
+// device bytes plan_build would allocate for these instances (no allocation)
+int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed);
 sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm);
 sip_status plan_set_m(Plan &P, int inst, const void *m, cudaStream_t st);
 sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,

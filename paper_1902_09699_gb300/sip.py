@@ -52,6 +52,17 @@ class Info(ctypes.Structure):
                 ("ms", ctypes.c_float)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("opts", Options), ("budget_bytes", c_i64), ("max_batch", c_int), ("max_cohorts", c_int),
+                ("max_wait_ms", c_dbl), ("max_points", c_i64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", c_i64), ("failed", c_i64), ("queued", c_i64), ("running_cohorts", c_int),
+                ("hbm_in_use", c_i64), ("hbm_peak", c_i64), ("p50_ms", c_dbl), ("p99_ms", c_dbl),
+                ("projections_per_s", c_dbl)]
+
+
 # every function declared in include/sip.h: name -> (restype, argtypes)
 SIGNATURES = {
     "sip_options_default": (None, [ctypes.POINTER(Options)]),
@@ -79,6 +90,13 @@ SIGNATURES = {
                                  ctypes.POINTER(Options), ctypes.POINTER(c_vp)]),
     "sip_batch_project": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Info)]),
     "sip_batch_offset": (c_i64, [c_vp, c_int]),
+    "sip_server_config_default": (None, [ctypes.POINTER(ServerConfig)]),
+    "sip_server_create": (c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(c_vp)]),
+    "sip_server_submit": (c_int, [c_vp, ctypes.POINTER(Grid), ctypes.POINTER(Set), c_int, c_vp, c_vp,
+                                  ctypes.POINTER(c_i64)]),
+    "sip_server_wait": (c_int, [c_vp, c_i64, c_dbl, ctypes.POINTER(Info), ctypes.POINTER(c_dbl)]),
+    "sip_server_query_stats": (c_int, [c_vp, ctypes.POINTER(ServerStats)]),
+    "sip_server_destroy": (c_int, [c_vp]),
 }
 NOALLOC_MAX_N = 1 << 24
 
@@ -356,6 +374,70 @@ class BatchProjector:
     def close(self):
         if getattr(self, "handle", None):
             lib().sip_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A projection server (continuous batching; see sip_server_* in
+    include/sip.h).  Models and results are host numpy arrays of the server's
+    dtype."""
+
+    def __init__(self, dtype="f32", budget_bytes=120 << 30, max_batch=64, max_cohorts=8, max_wait_ms=2.0, **opts):
+        L = lib()
+        cfg = ServerConfig()
+        L.sip_server_config_default(ctypes.byref(cfg))
+        self.code = _dtype_code(dtype)
+        self.np_dtype = np.float64 if self.code == F64 else np.float32
+        for k, v in opts.items():
+            if k == "form":
+                v = FORMS[v] if isinstance(v, str) else int(v)
+            if k == "exec":
+                v = EXEC[v] if isinstance(v, str) else int(v)
+            setattr(cfg.opts, k, v)
+        cfg.opts.dtype = self.code
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.max_batch = int(max_batch)
+        cfg.max_cohorts = int(max_cohorts)
+        cfg.max_wait_ms = float(max_wait_ms)
+        h = c_vp()
+        _check(L.sip_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self.pending = {}
+
+    def submit(self, grid, sets, m):
+        m = np.ascontiguousarray(np.asarray(m, dtype=self.np_dtype).reshape(-1))
+        x = np.empty_like(m)
+        g = make_grid(grid)
+        ss = make_sets(sets)
+        rid = c_i64(0)
+        _check(lib().sip_server_submit(self.handle, ctypes.byref(g), ss, len(sets), m.ctypes.data_as(c_vp),
+                                       x.ctypes.data_as(c_vp), ctypes.byref(rid)))
+        self.pending[rid.value] = (x, len(sets), len(sets) + 1)
+        return rid.value
+
+    def wait(self, rid, timeout_ms=-1.0):
+        inf = Info()
+        lat = c_dbl(0.0)
+        x, ns, nb = self.pending[rid]
+        st = lib().sip_server_wait(self.handle, rid, float(timeout_ms), ctypes.byref(inf), ctypes.byref(lat))
+        del self.pending[rid]
+        _check(st)
+        return x, _info_dict(inf, ns, nb), lat.value
+
+    def stats(self):
+        out = ServerStats()
+        _check(lib().sip_server_query_stats(self.handle, ctypes.byref(out)))
+        return {k: getattr(out, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sip_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
