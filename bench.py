@@ -33,6 +33,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def captured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1902_09699_gb300", "csrc", "kernels.cu"), "rb").read()
+        sha = hashlib.sha1(src).hexdigest()
+        for line in open(os.path.join(ROOT, "profiles", "traffic_per_launch.txt")):
+            parts = line.split()
+            if len(parts) == 3 and not line.startswith("#") and parts[0] == kernel and parts[2] == sha:
+                return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
 def workload():
     from paper_1902_09699_gb300 import workloads as W
     return W.layered_2d()
@@ -260,7 +276,7 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "bytes_per_iter": bpi, "pct_hbm_peak": pct_hbm, "hbm_peak_gbs": peak,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "frac": achieved / peak, "traffic": captured_traffic(dom), "peak_source": peak_src,
                          "kernel_ms_per_launch": avg_s * 1000.0},
             "kernel_breakdown_ms_per_step": {k: v["ms"] for k, v in kt.items()},
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": models[0].numel() * models[0].element_size(),
