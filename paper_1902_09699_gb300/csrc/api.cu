@@ -245,13 +245,14 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
     yoff += bd.M;
     bd.woff = bd.soff = -1;
     bd.job_w = bd.job_s = -1;
+    // w / s scratch regions start on 16-byte boundaries (vector loads)
     if (bd.type == BT_L1 || bd.type == BT_L2 || bd.type == BT_CARD) {
       bd.woff = woff;
-      woff += bd.M;
+      woff += (bd.M + 3) / 4 * 4;
     }
     if (bd.type == BT_L1 || bd.type == BT_CARD) {
       bd.soff = soff;
-      soff += bd.M;
+      soff += (bd.M + 3) / 4 * 4;
     }
     bd.seg0 = nseg;
     int64_t row0 = 0;
@@ -340,7 +341,6 @@ static void push_tiles(std::vector<Tile> &v, int inst, int item, int64_t n, int6
 // (SMs x resident CTAs per SM, so the launch runs in one wave), a multiple
 // of the CTA width, at most kMaxChunk.
 static int64_t chunk_for(int64_t total, int64_t slots) {
-  constexpr int64_t kMaxChunk = 64 * kTile;
   if (slots < 1) slots = 1;
   int64_t c = (total + slots - 1) / slots;
   c = (c + kThreads - 1) / kThreads * kThreads;
@@ -458,7 +458,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     return o;
   };
   struct Offs {
-    int64_t x, y, v, cr[2], cw[2], cs[2], cp, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace;
+    int64_t x, y, v, cr[2], cw[2], cs[2], cp, cgp, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace;
   };
   std::vector<Offs> offs(P.ninst);
   // warm state (x, y, v) of all instances first, then the rest of the state,
@@ -484,6 +484,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       offs[i].cs[j] = take(N * W);
     }
     offs[i].cp = take(N * W);
+    offs[i].cgp = take((int64_t)3 * 2 * L.dev.nt_n * W);  // accumulator type = storage type
     offs[i].ring = take((int64_t)L.dev.hist * N * W);
     offs[i].w = take(L.Mw * W);
     offs[i].s = take(L.Ms * W);
@@ -541,6 +542,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       d.cs[j] = at(o.cs[j]);
     }
     d.cp = at(o.cp);
+    d.cgp = at(o.cgp);
     d.ring = at(o.ring);
     d.w = at(o.w);
     d.s = at(o.s);
@@ -615,7 +617,7 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, KernelTimer *tm) {
   T1(KT_CG_W0);
   for (int j = 0; j < P.cg_launch; ++j) {
     T0(KT_CG_STEP);
-    CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));  // one CG step
+    CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j));  // one CG step
     T1(KT_CG_STEP);
   }
   T0(KT_SETPASS);
@@ -641,7 +643,7 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, KernelTimer *tm) {
     T1(KT_FINAL);
   }
   T0(KT_TAIL);
-  CK(launch_tail(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst));
+  CK(launch_tail(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst, P.cg_launch));
   T1(KT_TAIL);
   return SIP_OK;
 }

@@ -41,31 +41,136 @@ namespace sip {
 // --------------------------------------------------------------------------
 __device__ __forceinline__ double ldv(const double *p) { return *(const volatile double *)p; }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename A>
+__device__ __forceinline__ A warp_sum(A v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Sums NQ values over the CTA; thread 0 gets the totals.
-template <int NQ>
-__device__ __forceinline__ void block_sum(double (&v)[NQ]) {
-  __shared__ double sm[NQ][kThreads / 32];
+// Sums NQ values over the CTA in their own type; thread 0 gets the totals.
+// (Binary64 arithmetic issues at a small fraction of the binary32 rate on
+// this part, so binary32 data is summed in binary32 within a CTA.)
+template <int NQ, typename A>
+__device__ __forceinline__ void block_sum(A (&v)[NQ]) {
+  __shared__ A sm[NQ][kThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double t = warp_sum(v[q]);
+    A t = warp_sum(v[q]);
     if (lane == 0) sm[q][wid] = t;
   }
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      double t = lane < kThreads / 32 ? sm[q][lane] : 0.0;
+      A t = lane < kThreads / 32 ? sm[q][lane] : A(0);
       v[q] = warp_sum(t);
     }
   }
   __syncthreads();
+}
+
+// Exact sum of two binary32 numbers as an unevaluated pair s + e (Knuth's
+// TwoSum: s = fl(a + b), e = a + b - s exactly, for any order of a, b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// Totals of NQ per-tile partial arrays p[q][0..nt), formed by all threads of
+// the CTA in a fixed order (thread-strided sums, a butterfly in each warp
+// whose two partners add the same operands, then the warps in order), so
+// every CTA that reads the same partials gets the same bits.  Binary32
+// partials are added in double-binary32 arithmetic (hi + lo, the rounding
+// error of each addition kept by TwoSum), binary64 partials in binary64.
+// Thread 0 gets the totals (binary32 partials: in binary32, or as hi + lo in
+// binary64); the call contains __syncthreads.
+constexpr int kGatherBatch = 2;  // loads in flight per thread and quantity
+
+__device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2) {
+  float sum, err;
+  two_sum(hi, h2, sum, err);
+  hi = sum;
+  lo = (lo + l2) + err;
+}
+
+template <int NQ, typename O>
+__device__ __forceinline__ void cta_gather(const float *const (&p)[NQ], int nt, O (&out)[NQ]) {
+  constexpr int NW = kThreads / 32;
+  __shared__ float sh[NQ][NW], sl[NQ][NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float hi[NQ], lo[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) hi[q] = lo[q] = 0.f;
+  for (int i0 = 0; i0 < nt; i0 += kThreads * kGatherBatch) {
+    float v[NQ][kGatherBatch];
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) {
+      const int i = i0 + u * kThreads + threadIdx.x;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q][u] = i < nt ? __ldcg(p[q] + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) df_add(hi[q], lo[q], v[q][u], 0.f);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      df_add(hi[q], lo[q], __shfl_xor_sync(0xffffffffu, hi[q], o), __shfl_xor_sync(0xffffffffu, lo[q], o));
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      sh[q][wid] = hi[q];
+      sl[q][wid] = lo[q];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      float H = sh[q][0], L = sl[q][0];
+      for (int w = 1; w < NW; ++w) df_add(H, L, sh[q][w], sl[q][w]);
+      out[q] = sizeof(O) == 4 ? (O)(H + L) : (O)H + (O)L;
+    }
+}
+template <int NQ>
+__device__ __forceinline__ void cta_gather(const double *const (&p)[NQ], int nt, double (&out)[NQ]) {
+  constexpr int NW = kThreads / 32;
+  __shared__ double sh[NQ][NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double t[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) t[q] = 0.0;
+  for (int i0 = 0; i0 < nt; i0 += kThreads * kGatherBatch) {
+    double v[NQ][kGatherBatch];
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) {
+      const int i = i0 + u * kThreads + threadIdx.x;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q][u] = i < nt ? __ldcg(p[q] + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) t[q] += v[q][u];
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double w = warp_sum(t[q]);
+    if (lane == 0) sh[q][wid] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double tot = sh[q][0];
+      for (int w = 1; w < NW; ++w) tot += sh[q][w];
+      out[q] = tot;
+    }
 }
 
 // Called by thread 0 after its atomics: true in the last CTA of a group.
@@ -80,9 +185,9 @@ __device__ __forceinline__ bool arrive_last(uint32_t *counter, uint32_t n) {
   return false;
 }
 
-// Per-thread partial sums: binary32 for binary32 storage (a thread adds at
-// most the rows of one work item), binary64 otherwise; every sum across
-// threads and CTAs is binary64.
+// Partial sums within a CTA: binary32 for binary32 storage, binary64
+// otherwise; sums across CTAs are binary64 (or double-binary32, see
+// cta_gather).
 template <typename T> struct AccOf { using type = double; };
 template <> struct AccOf<float> { using type = float; };
 
@@ -109,8 +214,6 @@ template <> struct SV<double> {
   static __device__ __forceinline__ double c(const InstScal &s, int i) {
     return i == 0 ? s.c0 : i == 1 ? s.cz : i == 2 ? s.cx : s.cy;
   }
-  static __device__ __forceinline__ double alpha(const InstScal &s) { return s.alpha; }
-  static __device__ __forceinline__ double beta(const InstScal &s) { return s.beta; }
   static __device__ __forceinline__ double blk(const InstScal &s, int b, int f) {
     switch (f) {
       case BF_RHO: return s.rho[b];
@@ -128,8 +231,6 @@ template <> struct SV<double> {
 };
 template <> struct SV<float> {
   static __device__ __forceinline__ float c(const InstScal &s, int i) { return s.cf[i]; }
-  static __device__ __forceinline__ float alpha(const InstScal &s) { return s.alphaf; }
-  static __device__ __forceinline__ float beta(const InstScal &s) { return s.betaf; }
   static __device__ __forceinline__ float blk(const InstScal &s, int b, int f) { return s.bf[b][f]; }
   static __device__ __forceinline__ float ih(const InstDev &in, int axis) {
     return axis == 0 ? in.ihzf : axis == 1 ? in.ihxf : in.ihyf;
@@ -291,27 +392,98 @@ __device__ __forceinline__ T csys(const InstDev &in, const InstScal &sc, const G
 // --------------------------------------------------------------------------
 // x-update right-hand side and warm residual
 // --------------------------------------------------------------------------
+// Partial sums of the grid-point launches: slot 0 holds r_0.r_0 of the
+// right-hand side launch; the CG launch of phase ph (1 = w_0, 2, 3, ... = the
+// steps) writes slot 1 + (ph & 1) and reads the slot of phase ph - 1.
+template <typename A>
+__device__ __forceinline__ A *cg_part(const InstDev &in, int slot, int q) {
+  return (A *)in.cgp + (int64_t)(slot * 2 + q) * in.nt_n;
+}
+
+// Rows of a segment that meet at grid point g in (A^T u)[g] (Eq. FD_mat):
+// (A^T u)[g] = (u[ra] if va) - (u[rb] if vb), times 1/h for a difference.
+struct AdjRows {
+  int64_t ra, rb;
+  bool va, vb;
+};
+__device__ __forceinline__ AdjRows adj_rows(const InstDev &in, int kind, const GridPos &p, int64_t g) {
+  AdjRows a;
+  switch (kind) {
+    case SEG_DZ: {
+      const int64_t r = g - p.t;  // iz + (nz-1)*t
+      a.ra = r - 1;
+      a.rb = r;
+      a.va = p.iz >= 1;
+      a.vb = p.iz <= in.nz - 2;
+      break;
+    }
+    case SEG_DX: {
+      const int64_t r = g - (int64_t)in.nz * p.iy;  // iz + nz*(ix + (nx-1)*iy)
+      a.ra = r - in.nz;
+      a.rb = r;
+      a.va = p.ix >= 1;
+      a.vb = p.ix <= in.nx - 2;
+      break;
+    }
+    case SEG_DY: {
+      a.ra = g - (int64_t)in.nz * in.nx;
+      a.rb = g;
+      a.va = p.iy >= 1;
+      a.vb = p.iy <= in.ny - 2;
+      break;
+    }
+    default:
+      a.ra = g;
+      a.rb = g;
+      a.va = true;
+      a.vb = false;
+      break;
+  }
+  return a;
+}
+
 template <typename T>
 __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restrict__ insts,
                                                   InstScal *__restrict__ scal) {
-  SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
+  // points per thread per round, segments whose rows are loaded together
+  // (the adds wait on the loads: batching the segments overlaps their
+  // round trips)
+  constexpr int PT = 2;
+  constexpr int SB = sizeof(T) == 4 ? 4 : 2;
+  constexpr int SUB = kThreads * PT;
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
-  if (sc.done) return;
+  const int done = sc.done;
   const T *__restrict__ x = (const T *)in.x;
   const T *__restrict__ y = (const T *)in.y;
   const T *__restrict__ v = (const T *)in.v;
   const T *__restrict__ m = (const T *)in.m;
-  T *__restrict__ r = (T *)in.cr[sc.rbuf];
+  T *__restrict__ r = (T *)in.cr[0];
   CSys<T> C;
   C.load(sc);
-  __shared__ T srho[kMaxBlocks];
+  __shared__ T srho[kMaxBlocks], sih[kMaxSegs];
+  __shared__ int64_t sbase[kMaxSegs];
+  __shared__ int skind[kMaxSegs];
+  const int nseg = in.nseg;
   if (threadIdx.x < in.nb) srho[threadIdx.x] = SV<T>::blk(sc, threadIdx.x, BF_RHO);
+  if (threadIdx.x < nseg) {
+    const SegDev &sg = in.seg[threadIdx.x];
+    skind[threadIdx.x] = sg.kind;
+    if (sg.kind != SEG_RING) {
+      sbase[threadIdx.x] = in.blk[sg.block].yoff + sg.row0;
+      sih[threadIdx.x] = seg_ih<T>(in, sg.kind);
+    }
+  }
   __syncthreads();
-  const int alg1 = in.alg1, nseg = in.nseg;
+  if (done) return;
+  // rho of a segment's block, by segment
+  __shared__ T srs[kMaxSegs];
+  if (threadIdx.x < nseg && skind[threadIdx.x] != SEG_RING) srs[threadIdx.x] = srho[in.seg[threadIdx.x].block];
+  __syncthreads();
+  const int alg1 = in.alg1;
   const int64_t end = tl.start + tl.len;
-  A a0 = A(0), a1 = A(0);
+  A a1 = A(0);
   for (int64_t base = tl.start; base < end; base += SUB) {
     int64_t g[PT];
     GridPos pos[PT];
@@ -320,57 +492,60 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
       g[e] = base + threadIdx.x + (int64_t)e * kThreads;
+      b[e] = T(0);
       if (g[e] < end) {
         pos[e] = grid_pos(in, g[e]);
-        b[e] = alg1 ? T(0) : m[g[e]];
+        if (!alg1) b[e] = m[g[e]];
         load_nbr<T>(in, pos[e], g[e], [&](int64_t i) { return x[i]; }, xn[e]);
       }
     }
-    for (int sgi = 0; sgi < nseg; ++sgi) {
-      const SegDev &sg = in.seg[sgi];
-      if (sg.kind == SEG_RING) continue;
-      const int blk = sg.block;
-      const T rho = srho[blk];
-      const int64_t bs = in.blk[blk].yoff + sg.row0;
-      const T *__restrict__ ys = y + bs;
-      const T *__restrict__ vs = v + bs;
+    for (int s0 = 0; s0 < nseg; s0 += SB) {
+      T ya[SB][PT], va[SB][PT], yb[SB][PT], vb[SB][PT];
 #pragma unroll
-      for (int e = 0; e < PT; ++e)
-        if (g[e] < end)
-          b[e] += seg_adjoint<T>(in, sg.kind, pos[e], g[e], [&](int64_t row) { return rho * ys[row] + vs[row]; });
+      for (int j = 0; j < SB; ++j) {
+        const int sgi = s0 + j;
+        const bool live = sgi < nseg && skind[sgi] != SEG_RING;
+        const int kind = live ? skind[sgi] : SEG_I;
+        const int64_t bs = live ? sbase[sgi] : 0;
+#pragma unroll
+        for (int e = 0; e < PT; ++e) {
+          ya[j][e] = va[j][e] = yb[j][e] = vb[j][e] = T(0);
+          if (live && g[e] < end) {
+            const AdjRows ar = adj_rows(in, kind, pos[e], g[e]);
+            if (ar.va) {
+              ya[j][e] = y[bs + ar.ra];
+              va[j][e] = v[bs + ar.ra];
+            }
+            if (ar.vb) {
+              yb[j][e] = y[bs + ar.rb];
+              vb[j][e] = v[bs + ar.rb];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < SB; ++j) {
+        const int sgi = s0 + j;
+        if (sgi < nseg && skind[sgi] != SEG_RING) {
+          const T rho = srs[sgi], ih = sih[sgi];
+#pragma unroll
+          for (int e = 0; e < PT; ++e)
+            b[e] += ((rho * ya[j][e] + va[j][e]) - (rho * yb[j][e] + vb[j][e])) * ih;
+        }
+      }
     }
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
       if (g[e] < end) {
         const T rv = b[e] - apply_c(C, xn[e]);
         r[g[e]] = rv;
-        a0 += (A)b[e] * (A)b[e];
         a1 += (A)rv * (A)rv;
       }
     }
   }
-  double acc[2] = {(double)a0, (double)a1};
-  block_sum<2>(acc);
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    atomicAdd(&sc.acc_n[0], acc[0]);
-    atomicAdd(&sc.acc_n[1], acc[1]);
-    last = arrive_last(&sc.cnt_n, (uint32_t)in.nt_n);
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    const double bn = ldv(&sc.acc_n[0]), rr = ldv(&sc.acc_n[1]);
-    sc.acc_n[0] = 0.0;
-    sc.acc_n[1] = 0.0;
-    sc.bnorm2 = bn;
-    sc.rr = rr;
-    sc.rr0 = rr;
-    sc.beta = 0.0;
-    sc.betaf = 0.f;
-    sc.cg_steps = 0;
-    const int limit = in.cg_iters > 0 ? in.cg_iters : in.cg_max;
-    sc.cg_active = (limit > 0 && rr > 0.0) ? 1 : 0;
-  }
+  A acc[1] = {a1};
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) cg_part<A>(in, 0, 0)[tl.seq] = acc[0];
 }
 
 template <typename T>
@@ -392,6 +567,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ ti
 //   alpha_{i+1} = gamma_{i+1} / (delta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i)
 // In exact arithmetic these are the iterates of textbook CG; the
 // denominator of alpha equals p^T C p, so "p^T C p <= 0" stops as in CG.
+// No launch finalises its own sums: each CTA of the next launch adds the
+// per-tile partials (the same bits in every CTA) and derives alpha, beta.
+// The r, w, s buffers alternate with the launch: the right-hand side and
+// w_0 use buffer 0, the step launch of phase ph reads buffer ph & 1 and
+// writes the other one.
 // --------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__restrict__ insts,
@@ -400,10 +580,9 @@ __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__rest
   using A = typename AccOf<T>::type;
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
-  if (sc.done || !sc.cg_active) return;
-  const int rb = sc.rbuf;
-  const T *__restrict__ r = (const T *)in.cr[rb];
-  T *__restrict__ w = (T *)in.cw[rb];
+  const int done = sc.done;
+  const T *__restrict__ r = (const T *)in.cr[0];
+  T *__restrict__ w = (T *)in.cw[0];
   CSys<T> C;
   C.load(sc);
   const int64_t end = tl.start + tl.len;
@@ -415,6 +594,7 @@ __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__rest
       const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
       if (g < end) load_nbr<T>(in, grid_pos(in, g), g, [&](int64_t i) { return r[i]; }, rn[e]);
     }
+    if (done) return;
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
       const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
@@ -425,26 +605,9 @@ __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__rest
       }
     }
   }
-  double acc[1] = {(double)a0};
+  A acc[1] = {a0};
   block_sum<1>(acc);
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    atomicAdd(&sc.acc_n[0], acc[0]);
-    last = arrive_last(&sc.cnt_n, (uint32_t)in.nt_n);
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    const double delta = ldv(&sc.acc_n[0]);
-    sc.acc_n[0] = 0.0;
-    if (delta > 0.0) {  // delta_0 = r_0^T C r_0 = p_0^T C p_0
-      sc.alpha = sc.rr / delta;
-      sc.alphaf = (float)sc.alpha;
-      sc.beta = 0.0;
-      sc.betaf = 0.f;
-    } else {
-      sc.cg_active = 0;
-    }
-  }
+  if (threadIdx.x == 0) cg_part<A>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0 = p_0^T C p_0
 }
 
 template <typename T>
@@ -453,17 +616,106 @@ __global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ 
   body_cg_w0<T>(tiles[blockIdx.x], insts, scal);
 }
 
+// CG state fields in the storage precision (binary32 kernels do their
+// scalar work in binary32: binary64 issues at a small fraction of the rate).
+template <typename T> struct CgOf;
+template <> struct CgOf<double> {
+  static __device__ __forceinline__ double &alpha(CgState &s) { return s.alpha; }
+  static __device__ __forceinline__ double &rr(CgState &s) { return s.rr; }
+  static __device__ __forceinline__ double &rr0(CgState &s) { return s.rr0; }
+};
+template <> struct CgOf<float> {
+  static __device__ __forceinline__ float &alpha(CgState &s) { return s.alphaf; }
+  static __device__ __forceinline__ float &rr(CgState &s) { return s.rrf; }
+  static __device__ __forceinline__ float &rr0(CgState &s) { return s.rr0f; }
+};
+
+// alpha, beta and "take a step" for the step launch of phase ph >= 2: all
+// threads add the partial sums, thread 0 updates the CG state (the same
+// values in every CTA) and the instance's first tile stores it for the next
+// launch.  Results in s_ab, s_go after the closing __syncthreads.
+template <typename T>
+__device__ __forceinline__ void cg_scalars(const Tile &tl, const InstDev &in, InstScal &sc, int ph, T *s_ab,
+                                           int *s_go) {
+  using A = typename AccOf<T>::type;
+  using G = CgOf<T>;
+  const int nt = in.nt_n;
+  const int done = *(volatile const int *)&sc.done;
+  T t[2] = {T(0), T(0)};
+  CgState *pv = &sc.cg[(ph - 1) & 1];
+  int prev_active = 1;
+  if (ph == 2) {
+    // r_0.r_0 from the right-hand side launch, delta_0 from the w_0 launch
+    const A *const p[2] = {cg_part<A>(in, 0, 0), cg_part<A>(in, 2, 0)};
+    if (!done) cta_gather<2>(p, nt, t);
+  } else {
+    prev_active = __ldcg(&pv->active);
+    const int slot = 1 + ((ph - 1) & 1);
+    const A *const p[2] = {cg_part<A>(in, slot, 0), cg_part<A>(in, slot, 1)};
+    if (!done && prev_active) cta_gather<2>(p, nt, t);
+  }
+  if (threadIdx.x == 0) {
+    CgState st;
+    T beta = T(0);
+    if (ph == 2) {
+      const T rr0 = t[0], delta = t[1];
+      const int limit = in.cg_iters > 0 ? in.cg_iters : in.cg_max;
+      st.active = (limit > 0 && rr0 > T(0) && delta > T(0)) ? 1 : 0;
+      G::alpha(st) = st.active ? rr0 / delta : T(0);
+      G::rr(st) = rr0;
+      G::rr0(st) = rr0;
+      st.steps = 0;
+    } else {
+      G::alpha(st) = __ldcg(&G::alpha(*pv));
+      G::rr(st) = __ldcg(&G::rr(*pv));
+      G::rr0(st) = __ldcg(&G::rr0(*pv));
+      st.steps = __ldcg(&pv->steps);
+      st.active = prev_active;
+      if (st.active) {
+        const T g1 = t[0], d1 = t[1];
+        st.steps += 1;
+        bool more;
+        if (in.cg_iters > 0) {
+          more = st.steps < in.cg_iters;
+        } else {  // Eq. cg_stop: ||r_j|| < 0.1 ||r_0||
+          more = st.steps < in.cg_max && !(sqrt(g1) < T(0.1) * sqrt(G::rr0(st)));
+        }
+        const T b1 = g1 / G::rr(st);
+        const T den = d1 - b1 * g1 / G::alpha(st);  // = p_{i+1}^T C p_{i+1}
+        if (more && g1 > T(0) && den > T(0)) {
+          beta = b1;
+          G::alpha(st) = g1 / den;
+        } else {
+          st.active = 0;
+        }
+        G::rr(st) = g1;
+      }
+    }
+    s_ab[0] = G::alpha(st);
+    s_ab[1] = beta;
+    *s_go = (st.active && !done) ? 1 : 0;
+    if (tl.seq == 0 && !done) {
+      pv = &sc.cg[ph & 1];
+      G::alpha(*pv) = G::alpha(st);
+      G::rr(*pv) = G::rr(st);
+      G::rr0(*pv) = G::rr0(st);
+      pv->active = st.active;
+      pv->steps = st.steps;
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ __forceinline__ void body_cg_step(const Tile &tl,
                                                          const InstDev *__restrict__ insts,
-                                                         InstScal *__restrict__ scal) {
+                                                         InstScal *__restrict__ scal, int ph) {
   using A = typename AccOf<T>::type;
   constexpr int PT = sizeof(T) == 4 ? 2 : 1;  // 3 stencils per row: keep the register budget
   constexpr int SUB = kThreads * PT;
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
-  if (sc.done || !sc.cg_active) return;
-  const int c = sc.rbuf, n = c ^ 1;
+  const int c = ph & 1, n = c ^ 1;
   const T *__restrict__ r = (const T *)in.cr[c];
   const T *__restrict__ w = (const T *)in.cw[c];
   const T *__restrict__ sp = (const T *)in.cs[c];  // s_{i-1}
@@ -472,7 +724,9 @@ __device__ __forceinline__ void body_cg_step(const Tile &tl,
   T *__restrict__ sn_ = (T *)in.cs[n];             // s_i
   T *__restrict__ p = (T *)in.cp;
   T *__restrict__ x = (T *)in.x;
-  const T alpha = SV<T>::alpha(sc), beta = SV<T>::beta(sc);
+  __shared__ T s_ab[2];
+  __shared__ int s_go;
+  T alpha = T(0), beta = T(0);
   CSys<T> C;
   C.load(sc);
   const int64_t end = tl.start + tl.len;
@@ -491,6 +745,13 @@ __device__ __forceinline__ void body_cg_step(const Tile &tl,
         pv[e] = p[g];
         xv[e] = x[g];
       }
+    }
+    if (base == tl.start) {
+      // the previous launch's sums, while this CTA's first loads are in flight
+      cg_scalars<T>(tl, in, sc, ph, s_ab, &s_go);
+      if (!s_go) return;
+      alpha = s_ab[0];
+      beta = s_ab[1];
     }
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
@@ -521,48 +782,20 @@ __device__ __forceinline__ void body_cg_step(const Tile &tl,
       }
     }
   }
-  double acc[2] = {(double)ag, (double)ad};
+  A acc[2] = {ag, ad};
   block_sum<2>(acc);
-  __shared__ bool last;
   if (threadIdx.x == 0) {
-    atomicAdd(&sc.acc_n[0], acc[0]);
-    atomicAdd(&sc.acc_n[1], acc[1]);
-    last = arrive_last(&sc.cnt_n, (uint32_t)in.nt_n);
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    const double g1 = ldv(&sc.acc_n[0]), d1 = ldv(&sc.acc_n[1]);
-    sc.acc_n[0] = 0.0;
-    sc.acc_n[1] = 0.0;
-    sc.cg_steps += 1;
-    sc.cg_total += 1;
-    sc.rbuf = n;
-    bool more;
-    if (in.cg_iters > 0) {
-      more = sc.cg_steps < in.cg_iters;
-    } else {  // Eq. cg_stop: ||r_j|| < 0.1 ||r_0||
-      more = sc.cg_steps < in.cg_max && !(sqrt(g1) < 0.1 * sqrt(sc.rr0));
-    }
-    const double b1 = g1 / sc.rr;
-    const double den = d1 - b1 * g1 / sc.alpha;  // = p_{i+1}^T C p_{i+1}
-    if (more && g1 > 0.0 && den > 0.0) {
-      sc.beta = b1;
-      sc.betaf = (float)b1;
-      sc.alpha = g1 / den;
-      sc.alphaf = (float)sc.alpha;
-    } else {
-      more = false;
-    }
-    sc.rr = g1;
-    sc.cg_active = more ? 1 : 0;
+    const int slot = 1 + (ph & 1);
+    cg_part<A>(in, slot, 0)[tl.seq] = acc[0];
+    cg_part<A>(in, slot, 1)[tl.seq] = acc[1];
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
                                                          const InstDev *__restrict__ insts,
-                                                         InstScal *__restrict__ scal) {
-  body_cg_step<T>(tiles[blockIdx.x], insts, scal);
+                                                         InstScal *__restrict__ scal, int ph) {
+  body_cg_step<T>(tiles[blockIdx.x], insts, scal, ph);
 }
 
 // --------------------------------------------------------------------------
@@ -624,12 +857,9 @@ __device__ void setpass_ring(const Tile &tl, const InstDev &in, InstScal &sc, in
     }
   }
   if (chk) {
-    double dacc[kMaxHist + 1];
-#pragma unroll
-    for (int j = 0; j <= kMaxHist; ++j) dacc[j] = (double)acc[j];
-    block_sum<kMaxHist + 1>(dacc);
+    block_sum<kMaxHist + 1>(acc);
     if (threadIdx.x == 0)
-      for (int j = 0; j <= jmax; ++j) atomicAdd(&sc.acc_ring[j], dacc[j]);
+      for (int j = 0; j <= jmax; ++j) atomicAdd(&sc.acc_ring[j], (double)acc[j]);
   }
 }
 
@@ -740,36 +970,36 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
       }
     }
   }
-  // binary64 CTA sums of only the quantities this iteration uses (cross-thread
-  // binary64 work is costly on this part)
+  // CTA sums (in the accumulator type) of only the quantities this
+  // iteration uses; binary64 across CTAs
   double *a = sc.acc[b];
   if (ad_dots) {
-    double d6[6] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3], (double)acc[4], (double)acc[5]};
+    A d6[6] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5]};
     block_sum<6>(d6);
     if (threadIdx.x == 0) {
-      atomicAdd(&a[A_HV], d6[0]);
-      atomicAdd(&a[A_HH], d6[1]);
-      atomicAdd(&a[A_VHVH], d6[2]);
+      atomicAdd(&a[A_HV], (double)d6[0]);
+      atomicAdd(&a[A_HH], (double)d6[1]);
+      atomicAdd(&a[A_VHVH], (double)d6[2]);
       if (pointwise) {
-        atomicAdd(&a[A_GV], d6[3]);
-        atomicAdd(&a[A_GG], d6[4]);
-        atomicAdd(&a[A_VV], d6[5]);
+        atomicAdd(&a[A_GV], (double)d6[3]);
+        atomicAdd(&a[A_GG], (double)d6[4]);
+        atomicAdd(&a[A_VV], (double)d6[5]);
       }
     }
   }
   if (chk && type != BT_DIST) {
-    double d3[3] = {(double)acc[6], (double)acc[7], (double)acc[8]};
+    A d3[3] = {acc[6], acc[7], acc[8]};
     block_sum<3>(d3);
     if (threadIdx.x == 0) {
-      if (type == BT_BOUNDS) atomicAdd(&a[A_FEAS_D2], d3[0]);
-      atomicAdd(&a[A_S2], d3[1]);
-      if (type == BT_L1) atomicAdd(&a[A_S1], d3[2]);
+      if (type == BT_BOUNDS) atomicAdd(&a[A_FEAS_D2], (double)d3[0]);
+      atomicAdd(&a[A_S2], (double)d3[1]);
+      if (type == BT_L1) atomicAdd(&a[A_S1], (double)d3[2]);
     }
   }
   if (type == BT_L1 || type == BT_L2) {
-    double d1[1] = {(double)acc[9]};
+    A d1[1] = {acc[9]};
     block_sum<1>(d1);
-    if (threadIdx.x == 0) atomicAdd(&a[A_WNORM], d1[0]);
+    if (threadIdx.x == 0) atomicAdd(&a[A_WNORM], (double)d1[0]);
   }
 }
 
@@ -811,6 +1041,7 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
     js.active = 1;
     js.pass = 0;
     js.prefix = 0;
+    js.n_above = 0;
     js.c_above = js.s1_above = js.s2_above = 0.0;
     js.tie_needed = 0;
     if (bd.type == BT_L1) {
@@ -827,6 +1058,7 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
     js.active = chk ? 1 : 0;
     js.pass = 0;
     js.prefix = 0;
+    js.n_above = 0;
     js.c_above = js.s1_above = js.s2_above = 0.0;
     js.tie_needed = 0;
     if (bd.type == BT_L1) {
@@ -861,14 +1093,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict_
 // --------------------------------------------------------------------------
 // Bin accumulators.  binary32 data: every value in a bin shares one exponent
 // E (the first digit holds all exponent bits), so |w| = sig * 2^(E' - 150)
-// with an integer significand sig < 2^24 (E' = max(E, 1)); the bin sums of
-// sig and of sig^2 (split at bit 22) are then exact 64-bit integer sums,
-// formed with warp integer reductions and integer atomics.  binary64 data:
-// binary64 bin sums.
+// with an integer significand sig < 2^24 (E' = max(E, 1)); a CTA adds sig
+// and sig^2 in 12-bit chunks (2 and 4 of them) with 32-bit shared-memory
+// atomics, exact while a work item has at most kMaxChunk rows
+// (kMaxChunk * 4095 < 2^32), and folds them into 64-bit global bin sums of
+// sig and of sig^2 (the latter as hi * 2^22 + lo).  (64-bit shared-memory
+// additions would retry under the contention of the few hot bins.)
+// binary64 data: binary64 bin sums.
+static_assert((uint64_t)kMaxChunk * 4095u < (1ull << 32), "12-bit chunk sums must fit 32 bits");
 template <typename T> struct BinAcc;
 template <> struct BinAcc<float> {
   using S = unsigned long long;
-  static constexpr size_t kSmem = kBins * (sizeof(uint32_t) + 3 * sizeof(S));
+  static constexpr size_t kSmem = kBins * 7 * sizeof(uint32_t);  // count, 2 + 4 chunk sums
 };
 template <> struct BinAcc<double> {
   using S = double;
@@ -910,124 +1146,136 @@ __device__ __forceinline__ unsigned long long cta_suffix_u64(unsigned long long 
   return x + above;
 }
 
+// ---- bin choice by the last CTA of a pass ---------------------------------
+// Thread t owns bins [t*kPer, t*kPer + kPer); bins are visited from the top.
+//   l1:    largest bin d with g(lo_d) >= tau, g(t) = sum_{|w| >= t} (|w| - t)
+//   top-k: largest bin d with count(keys >= lo_d) >= k
+// The winner records the entries above the chosen bin (count, sum of |w|,
+// sum of w^2) and the new prefix; after the last digit, theta (l1) or the
+// k-th key and its tie count (top-k).
+constexpr int kPer = kBins / kThreads;
+
+// binary32 keys: integer arithmetic.  A thread's bins share one exponent
+// (pass 0: exponent field = thread index; later passes: the prefix's), so
+// its bin sums of sig are exact integers in units of 2^e.  Across threads
+// pass 0 adds binary64 values (different exponents), later passes integers.
+// The l1 test  S_j - cge_j * sig_lo_j >= R  compares an exact integer with
+// R = ceil((tau - sums above, binary64) / 2^e).
+__device__ __noinline__ void select_choose_int(const JobDev &jd, JobScal &js, const uint32_t *gc,
+                                               const unsigned long long *g1, const unsigned long long *g2,
+                                               const unsigned long long *g3, int pass, uint32_t pre, int lo,
+                                               int nbins, bool need1, bool need2) {
+  using U = unsigned long long;
+  __shared__ U wsumi[kThreads / 32];
+  __shared__ double wsum[kThreads / 32];
+  __shared__ int sbest;
+  if (threadIdx.x == 0) sbest = -1;
+  const bool l1 = jd.kind == JOB_L1;
+  U cb[kPer], s1b[kPer], h2b[kPer], l2b[kPer];
+  U tc = 0, t1 = 0, th = 0, tl2 = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int bi = threadIdx.x * kPer + j;
+    const bool ok = bi < nbins;
+    cb[j] = ok ? (U)__ldcg(&gc[bi]) : 0ull;
+    s1b[j] = (ok && need1) ? __ldcg(&g1[bi]) : 0ull;
+    h2b[j] = (ok && need2) ? __ldcg(&g2[bi]) : 0ull;
+    l2b[j] = (ok && need2) ? __ldcg(&g3[bi]) : 0ull;
+    tc += cb[j];
+    t1 += s1b[j];
+    th += h2b[j];
+    tl2 += l2b[j];
+  }
+  // entries strictly above this thread's bins
+  U ac = js.n_above + (cta_suffix_u64(tc, wsumi) - tc);
+  const int ef = pass == 0 ? (int)threadIdx.x : (int)(pre >> 23);  // exponent field of this thread's bins
+  const int e2 = (ef > 0 ? ef : 1) - 150;                          // |w| = sig * 2^e2
+  double as1 = js.s1_above, as2 = js.s2_above;  // binary64 sums above (pass 0: incl. higher threads)
+  U cs1 = 0, ch2 = 0, cl2 = 0;                  // integer sums above, this pass (later passes: incl. higher threads)
+  if (pass == 0) {
+    if (need1) {
+      const double v = (double)t1 * pow2(e2);
+      as1 += cta_suffix(v, wsum) - v;
+    }
+    if (need2) {
+      const double v = ((double)th * 4194304.0 + (double)tl2) * pow2(2 * e2);
+      as2 += cta_suffix(v, wsum) - v;
+    }
+  } else {
+    if (need1) cs1 = cta_suffix_u64(t1, wsumi) - t1;
+    if (need2) {
+      ch2 = cta_suffix_u64(th, wsumi) - th;
+      cl2 = cta_suffix_u64(tl2, wsumi) - tl2;
+    }
+  }
+  long long R = 0;
+  if (l1) {
+    const double r = (js.tau - as1) * pow2(-e2);
+    R = r <= -4.0e18 ? -(1ll << 62) : (r >= 4.0e18 ? (1ll << 62) : (long long)ceil(r));
+  }
+  int best = -1, bj = 0;
+  U bc = 0, bs1 = 0, bh2 = 0, bl2 = 0;
+  for (int j = kPer - 1; j >= 0; --j) {
+    const int bi = threadIdx.x * kPer + j;
+    if (bi >= nbins) continue;
+    const U cge = ac + cb[j];
+    bool ok;
+    if (l1) {
+      const uint32_t klo = pre | ((uint32_t)bi << lo);
+      const uint32_t exl = klo >> 23, manl = klo & 0x7fffffu;
+      const U siglo = exl ? (manl | 0x800000u) : manl;
+      ok = (long long)(cs1 + s1b[j]) - (long long)(cge * siglo) >= R;
+    } else {
+      ok = cge >= (U)js.k;
+    }
+    if (ok) {  // bins below also satisfy; keep the highest
+      best = bi;
+      bj = j;
+      bc = ac;
+      bs1 = cs1;
+      bh2 = ch2;
+      bl2 = cl2;
+      break;
+    }
+    ac = cge;
+    cs1 += s1b[j];
+    ch2 += h2b[j];
+    cl2 += l2b[j];
+  }
+  __syncthreads();
+  if (best >= 0) atomicMax(&sbest, best);
+  __syncthreads();
+  if (best >= 0 && best == sbest) {
+    const uint32_t np = pre | ((uint32_t)best << lo);
+    const double s1a = as1 + (double)bs1 * pow2(e2);
+    js.n_above = bc;
+    js.c_above = (double)bc;
+    js.s1_above = s1a;
+    js.s2_above = as2 + ((double)bh2 * 4194304.0 + (double)bl2) * pow2(2 * e2);
+    js.prefix = (uint64_t)np;
+    if (lo == 0) {  // final digit: the breakpoint key is exact
+      if (l1) {
+        js.theta = (s1a - js.tau) / (double)bc;
+        js.thetaf = (float)js.theta;
+      } else {
+        js.need = js.k - (int64_t)bc;
+        js.cK = (int64_t)cb[bj];
+        js.kval = (double)__uint_as_float(np);
+        js.tie_needed = (js.need < js.cK && np != 0) ? 1 : 0;
+      }
+    }
+    js.pass = pass + 1;
+  }
+}
+
+// binary64 keys: binary64 bin sums.
 template <typename T>
-__device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__restrict__ insts,
-                                                        InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
-                                                        JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
-                                                        double *__restrict__ hs1, double *__restrict__ hs2,
-                                                        double *__restrict__ hs3, int pass) {
-  SIP_STEP_CONSTANTS;
+__device__ __noinline__ void select_choose_f64(const JobDev &jd, JobScal &js, const uint32_t *gc, const double *g1,
+                                               const double *g2, int pass, uint64_t pre_, int lo, int nbins,
+                                               bool need1, bool need2) {
   using KT = KeyOf<T>;
   using K = typename KT::K;
-  using S = typename BinAcc<T>::S;
-  constexpr bool kInt = sizeof(T) == 4;
-  const JobDev jd = jobs[tl.item];
-  const InstDev &in = insts[jd.inst];
-  InstScal &sc = scal[jd.inst];
-  JobScal &js = jscal[tl.item];
-  if (sc.done || !js.active || js.mode != JM_SELECT || js.pass != pass) return;
-
-  extern __shared__ unsigned char smem_raw[];
-  uint32_t *cnt = (uint32_t *)smem_raw;
-  S *s1 = (S *)(smem_raw + kBins * sizeof(uint32_t));
-  S *s2 = s1 + kBins;  // binary64: sum of squares; binary32: high part of sig^2
-  S *s3 = s2 + kBins;  // binary32 only: low 22 bits of sig^2
-  const bool need1 = jd.kind == JOB_L1;
-  const bool need2 = jd.feas != 0;
-  const int hi = KT::kBits - pass * kDigitBits;
-  const int lo = hi - kDigitBits > 0 ? hi - kDigitBits : 0;
-  const int nbins = 1 << (hi - lo);
-  for (int i = threadIdx.x; i < nbins; i += kThreads) {
-    cnt[i] = 0;
-    if (need1) s1[i] = S(0);
-    if (need2) {
-      s2[i] = S(0);
-      if (kInt) s3[i] = S(0);
-    }
-  }
-  __syncthreads();
-
-  const K mask = (K)(nbins - 1);
-  const K pre = (K)js.prefix;
-  const bool all = hi >= KT::kBits;
-  const T *__restrict__ data = (const T *)(jd.feas ? in.s : in.w) + jd.data_off;
-  const int lane = threadIdx.x & 31;
-  const int64_t end = tl.start + tl.len;
-  for (int64_t base = tl.start; base < end; base += SUB) {
-    T val[PT];
-#pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
-      val[e] = row < end ? data[row] : T(0);
-    }
-#pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
-      int bin = -1;
-      K key = 0;
-      if (row < end) {
-        key = KT::key(val[e]);
-        if (all || (key >> hi) == (pre >> hi)) bin = (int)((key >> lo) & mask);
-      }
-      if constexpr (kInt) {
-        // exact integer significand and its square split at bit 22; one
-        // shared-memory integer atomic per entry and accumulator (no FP64)
-        if (bin >= 0) {
-          const uint32_t ex = (uint32_t)key >> 23, man = (uint32_t)key & 0x7fffffu;
-          const uint32_t sig = ex ? (man | 0x800000u) : man;
-          atomicAdd(&cnt[bin], 1u);
-          if (need1) atomicAdd((unsigned long long *)&s1[bin], (unsigned long long)sig);
-          if (need2) {
-            const uint64_t sq = (uint64_t)sig * sig;
-            atomicAdd((unsigned long long *)&s2[bin], (unsigned long long)(sq >> 22));
-            atomicAdd((unsigned long long *)&s3[bin], (unsigned long long)(sq & 0x3fffffu));
-          }
-        }
-      } else {
-        unsigned pending = __ballot_sync(0xffffffffu, bin >= 0);
-        const double a = bin >= 0 ? fabs((double)val[e]) : 0.0;
-        while (pending) {
-          const int leader = __ffs(pending) - 1;
-          const int lb = __shfl_sync(0xffffffffu, bin, leader);
-          const unsigned grp = __ballot_sync(0xffffffffu, bin == lb);
-          const bool mine = bin == lb;
-          double v1 = 0.0, v2 = 0.0;
-          if (need1) v1 = warp_sum(mine ? a : 0.0);
-          if (need2) v2 = warp_sum(mine ? a * a : 0.0);
-          if (lane == leader) {
-            atomicAdd(&cnt[lb], (uint32_t)__popc(grp));
-            if (need1) atomicAdd((double *)&s1[lb], v1);
-            if (need2) atomicAdd((double *)&s2[lb], v2);
-          }
-          pending &= ~grp;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  uint32_t *gc = hcnt + jd.hist_off;
-  S *g1 = (S *)(hs1 + jd.hist_off);
-  S *g2 = (S *)(hs2 + jd.hist_off);
-  S *g3 = (S *)(hs3 + jd.hist_off);
-  for (int i = threadIdx.x; i < nbins; i += kThreads) {
-    const uint32_t c = cnt[i];
-    if (c) {
-      atomicAdd(&gc[i], c);
-      if (need1) atomicAdd(&g1[i], s1[i]);
-      if (need2) {
-        atomicAdd(&g2[i], s2[i]);
-        if (kInt) atomicAdd(&g3[i], s3[i]);
-      }
-    }
-  }
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) last = arrive_last(&js.counter, (uint32_t)jd.ntiles);
-  __syncthreads();
-  if (!last) return;
-
-  // ---- last CTA: choose the bin -------------------------------------------
-  constexpr int kPer = kBins / kThreads;  // bins per thread; thread t owns [t*kPer, t*kPer + kPer)
+  const K pre = (K)pre_;
   double c[kPer], a1[kPer], a2[kPer];
   double tc = 0.0, t1 = 0.0, t2 = 0.0;
 #pragma unroll
@@ -1036,17 +1284,8 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
     c[j] = a1[j] = a2[j] = 0.0;
     if (bi < nbins) {
       c[j] = (double)__ldcg(&gc[bi]);
-      if constexpr (kInt) {
-        const int ex = (int)(((uint32_t)(pre | ((K)bi << lo))) >> 23);
-        const int e2 = (ex > 0 ? ex : 1) - 150;
-        if (need1) a1[j] = (double)__ldcg((const unsigned long long *)&g1[bi]) * pow2(e2);
-        if (need2)
-          a2[j] = ((double)__ldcg((const unsigned long long *)&g2[bi]) * 4194304.0 +
-                   (double)__ldcg((const unsigned long long *)&g3[bi])) * pow2(2 * e2);
-      } else {
-        if (need1) a1[j] = __ldcg((const double *)&g1[bi]);
-        if (need2) a2[j] = __ldcg((const double *)&g2[bi]);
-      }
+      if (need1) a1[j] = __ldcg(&g1[bi]);
+      if (need2) a2[j] = __ldcg(&g2[bi]);
     }
     tc += c[j];
     t1 += a1[j];
@@ -1093,6 +1332,7 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
   if (best >= 0 && best == sbest) {
     const int j = best - threadIdx.x * kPer;
     js.c_above = bc;
+    js.n_above = (unsigned long long)bc;
     js.s1_above = b1;
     js.s2_above = b2;
     const K np = pre | ((K)best << lo);
@@ -1109,6 +1349,185 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
       }
     }
     js.pass = pass + 1;
+  }
+}
+
+// Vector type of a 16-byte load, and its components by (unrolled) index.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+__device__ __forceinline__ float vat(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vat(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4 &v, int c, float a) {
+  if (c == 0) v.x = a; else if (c == 1) v.y = a; else if (c == 2) v.z = a; else v.w = a;
+}
+__device__ __forceinline__ void vset(double2 &v, int c, double a) {
+  if (c == 0) v.x = a; else v.y = a;
+}
+
+template <typename T>
+__device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__restrict__ insts,
+                                                        InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
+                                                        JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
+                                                        double *__restrict__ hs1, double *__restrict__ hs2,
+                                                        double *__restrict__ hs3, int pass) {
+  using KT = KeyOf<T>;
+  using K = typename KT::K;
+  using S = typename BinAcc<T>::S;
+  using V = typename Vec16<T>::type;
+  constexpr bool kInt = sizeof(T) == 4;
+  constexpr int VW = (int)(sizeof(V) / sizeof(T));  // values per vector load
+  constexpr int VPT = 4;                            // vector loads per thread and round
+  const JobDev jd = jobs[tl.item];
+  const InstDev &in = insts[jd.inst];
+  InstScal &sc = scal[jd.inst];
+  JobScal &js = jscal[tl.item];
+  if (sc.done || !js.active || js.mode != JM_SELECT || js.pass != pass) return;
+
+  extern __shared__ unsigned char smem_raw[];
+  uint32_t *cnt = (uint32_t *)smem_raw;
+  // binary32: 12-bit chunk sums u[0..1] of sig, u[2..5] of sig^2
+  uint32_t *u = cnt + kBins;
+  // binary64: sums of |w| and of w^2
+  S *s1 = (S *)(smem_raw + kBins * sizeof(uint32_t));
+  S *s2 = s1 + kBins;
+  const bool need1 = jd.kind == JOB_L1;
+  const bool need2 = jd.feas != 0;
+  const int hi = KT::kBits - pass * kDigitBits;
+  const int lo = hi - kDigitBits > 0 ? hi - kDigitBits : 0;
+  const int nbins = 1 << (hi - lo);
+  for (int i = threadIdx.x; i < nbins; i += kThreads) {
+    cnt[i] = 0;
+    if constexpr (kInt) {
+      if (need1) u[i] = u[kBins + i] = 0;
+      if (need2)
+#pragma unroll
+        for (int c = 2; c < 6; ++c) u[c * kBins + i] = 0;
+    } else {
+      if (need1) s1[i] = S(0);
+      if (need2) s2[i] = S(0);
+    }
+  }
+  __syncthreads();
+
+  const K mask = (K)(nbins - 1);
+  const K pre = (K)js.prefix;
+  const bool all = hi >= KT::kBits;
+  const T *__restrict__ data = (const T *)(jd.feas ? in.s : in.w) + jd.data_off;
+  const int lane = threadIdx.x & 31;
+  const int64_t end = tl.start + tl.len;
+  // one entry into this CTA's histogram (called by all lanes of a warp)
+  auto add = [&](T val, bool valid) {
+    int bin = -1;
+    K key = 0;
+    if (valid) {
+      key = KT::key(val);
+      if (all || (key >> hi) == (pre >> hi)) bin = (int)((key >> lo) & mask);
+    }
+    if constexpr (kInt) {
+      // exact integer significand and its square in 12-bit chunks
+      if (bin >= 0) {
+        const uint32_t ex = (uint32_t)key >> 23, man = (uint32_t)key & 0x7fffffu;
+        const uint32_t sig = ex ? (man | 0x800000u) : man;
+        atomicAdd(&cnt[bin], 1u);
+        if (need1) {
+          atomicAdd(&u[bin], sig & 0xfffu);
+          atomicAdd(&u[kBins + bin], sig >> 12);
+        }
+        if (need2) {
+          const uint64_t sq = (uint64_t)sig * sig;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) atomicAdd(&u[(2 + c) * kBins + bin], (uint32_t)(sq >> (12 * c)) & 0xfffu);
+        }
+      }
+    } else {
+      unsigned pending = __ballot_sync(0xffffffffu, bin >= 0);
+      const double a = bin >= 0 ? fabs((double)val) : 0.0;
+      while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int lb = __shfl_sync(0xffffffffu, bin, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, bin == lb);
+        const bool mine = bin == lb;
+        double v1 = 0.0, v2 = 0.0;
+        if (need1) v1 = warp_sum(mine ? a : 0.0);
+        if (need2) v2 = warp_sum(mine ? a * a : 0.0);
+        if (lane == leader) {
+          atomicAdd(&cnt[lb], (uint32_t)__popc(grp));
+          if (need1) atomicAdd((double *)&s1[lb], v1);
+          if (need2) atomicAdd((double *)&s2[lb], v2);
+        }
+        pending &= ~grp;
+      }
+    }
+  };
+  if (((uintptr_t)(data + tl.start) & (sizeof(V) - 1)) == 0) {
+    // 16-byte loads (a vector that reaches past the work item is read one
+    // value at a time)
+    for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * VW * VPT) {
+      V v[VPT];
+#pragma unroll
+      for (int e = 0; e < VPT; ++e) {
+        const int64_t i0 = base + (int64_t)(threadIdx.x + e * kThreads) * VW;
+        if (i0 + VW <= end) {
+          v[e] = *(const V *)(data + i0);
+        } else {
+#pragma unroll
+          for (int c = 0; c < VW; ++c) vset(v[e], c, i0 + c < end ? data[i0 + c] : T(0));
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < VPT; ++e) {
+        const int64_t i0 = base + (int64_t)(threadIdx.x + e * kThreads) * VW;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) add(vat(v[e], c), i0 + c < end);
+      }
+    }
+  } else {
+    constexpr int PT = 4;
+    for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * PT) {
+      T val[PT];
+#pragma unroll
+      for (int e = 0; e < PT; ++e) {
+        const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+        val[e] = row < end ? data[row] : T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < PT; ++e) add(val[e], base + threadIdx.x + (int64_t)e * kThreads < end);
+    }
+  }
+  __syncthreads();
+  uint32_t *gc = hcnt + jd.hist_off;
+  S *g1 = (S *)(hs1 + jd.hist_off);
+  S *g2 = (S *)(hs2 + jd.hist_off);
+  S *g3 = (S *)(hs3 + jd.hist_off);
+  for (int i = threadIdx.x; i < nbins; i += kThreads) {
+    const uint32_t c = cnt[i];
+    if (c) {
+      atomicAdd(&gc[i], c);
+      if constexpr (kInt) {
+        if (need1) atomicAdd(&g1[i], (S)u[i] + ((S)u[kBins + i] << 12));
+        if (need2) {
+          // sum of sig^2 = lo24 + Q2 2^24 + Q3 2^36 = hi * 2^22 + (lo24 mod 2^22)
+          const S lo24 = (S)u[2 * kBins + i] + ((S)u[3 * kBins + i] << 12);
+          atomicAdd(&g2[i], (lo24 >> 22) + ((S)u[4 * kBins + i] << 2) + ((S)u[5 * kBins + i] << 14));
+          atomicAdd(&g3[i], lo24 & 0x3fffffull);
+        }
+      } else {
+        if (need1) atomicAdd(&g1[i], s1[i]);
+        if (need2) atomicAdd(&g2[i], s2[i]);
+      }
+    }
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = arrive_last(&js.counter, (uint32_t)jd.ntiles);
+  __syncthreads();
+  if (!last) return;
+
+  if constexpr (kInt) {
+    select_choose_int(jd, js, gc, (const S *)g1, (const S *)g2, (const S *)g3, pass, pre, lo, nbins, need1, need2);
+  } else {
+    select_choose_f64<T>(jd, js, gc, g1, g2, pass, pre, lo, nbins, need1, need2);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nbins; i += kThreads) {
@@ -1297,12 +1716,11 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
     }
   }
   if (ad_dots) {
-    double dacc[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-    block_sum<3>(dacc);
+    block_sum<3>(acc);
     if (threadIdx.x == 0) {
-      atomicAdd(&sc.acc[b][A_GV], dacc[0]);
-      atomicAdd(&sc.acc[b][A_GG], dacc[1]);
-      atomicAdd(&sc.acc[b][A_VV], dacc[2]);
+      atomicAdd(&sc.acc[b][A_GV], (double)acc[0]);
+      atomicAdd(&sc.acc[b][A_GG], (double)acc[1]);
+      atomicAdd(&sc.acc[b][A_VV], (double)acc[2]);
     }
   }
 }
@@ -1352,7 +1770,7 @@ __device__ __forceinline__ double spectral(double ab, double aa, double bb) {
 constexpr int kTailWarps = 8;
 
 __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ insts, InstScal *__restrict__ scal,
-                                          const JobScal *__restrict__ jscal) {
+                                          const JobScal *__restrict__ jscal, int cg_launch) {
   const InstDev &in = insts[i];
   InstScal &sc = scal[i];
   if (sc.done) return;
@@ -1431,6 +1849,16 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
 
   // ---- phase 2: warp 0, one lane per block
   const int b = lane;
+  // CG steps of this iteration: the state the last step launch stored
+  int cg_steps = 0;
+  if (cg_launch > 0) {
+    const CgState &st = sc.cg[(cg_launch + 1) & 1];
+    cg_steps = st.steps + st.active;
+  }
+  if (b == 0) {
+    sc.cg_steps = cg_steps;
+    sc.cg_total += cg_steps;
+  }
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   double *tr = in.trace ? in.trace + (int64_t)(k - 1) * in.trace_w : nullptr;
   if (tr) {
@@ -1439,7 +1867,7 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
       tr[nb + b] = sc.gamma[b];
     }
     if (b == 0) {
-      tr[2 * nb] = sc.cg_steps;
+      tr[2 * nb] = cg_steps;
       tr[2 * nb + 1] = nan;
     }
     if (b < p) tr[2 * nb + 2 + b] = chk ? s_feas[b] : nan;
@@ -1530,8 +1958,9 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
 
 __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restrict__ insts,
                                                           InstScal *__restrict__ scal,
-                                                          const JobScal *__restrict__ jscal, int ninst) {
-  if ((int)blockIdx.x < ninst) body_tail(blockIdx.x, insts, scal, jscal);
+                                                          const JobScal *__restrict__ jscal, int ninst,
+                                                          int cg_launch) {
+  if ((int)blockIdx.x < ninst) body_tail(blockIdx.x, insts, scal, jscal, cg_launch);
 }
 
 // --------------------------------------------------------------------------
@@ -1603,7 +2032,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
     for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_cg_w0<T>(A.tn[i], A.insts, A.scal);
     if (!grid_barrier(A.bar)) return;
     for (int j = 0; j < A.cg_launch; ++j) {
-      for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_cg_step<T>(A.tn[i], A.insts, A.scal);
+      for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_cg_step<T>(A.tn[i], A.insts, A.scal, 2 + j);
       if (!grid_barrier(A.bar)) return;
     }
     for (int i = blockIdx.x; i < A.nt_set; i += gridDim.x) body_setpass<T>(A.tset[i], A.insts, A.scal, A.jscal, A.jobs);
@@ -1623,7 +2052,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
       for (int i = blockIdx.x; i < A.nt_fin; i += gridDim.x) body_final<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
       if (!grid_barrier(A.bar)) return;
     }
-    for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) body_tail(i, A.insts, A.scal, A.jscal);
+    for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) body_tail(i, A.insts, A.scal, A.jscal, A.cg_launch);
     if (!grid_barrier(A.bar)) return;
     if (ld_acquire(A.ndone) >= (uint32_t)A.ninst) return;  // every instance stopped
   }
@@ -1649,15 +2078,12 @@ __global__ void k_init(const InstDev *__restrict__ insts, InstScal *__restrict__
   sc.done = 0;
   sc.iters = 0;
   sc.stop_reason = 0;
-  sc.cg_active = 0;
   sc.cg_steps = 0;
   sc.cg_total = 0;
-  sc.rbuf = 0;
   sc.have_k0 = 0;
   sc.nonfinite = 0;
-  sc.cnt_n = sc.cnt_set = sc.cnt_norm = 0;
-  sc.rr = sc.rr0 = sc.bnorm2 = sc.alpha = sc.beta = 0.0;
-  sc.acc_n[0] = sc.acc_n[1] = 0.0;
+  sc.cnt_set = sc.cnt_norm = 0;
+  for (int j = 0; j < 2; ++j) sc.cg[j] = CgState{0.0, 0.0, 0.0, 0.f, 0.f, 0.f, 0, 0};
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   for (int b = 0; b < kMaxSets; ++b) sc.r_feas[b] = nan;
   sc.r_evol = nan;
@@ -1799,8 +2225,8 @@ cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstD
   SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal);
+cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph) {
+  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph);
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
@@ -1923,8 +2349,9 @@ cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstD
   SIP_DISPATCH(L, k_final, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties);
   return cudaGetLastError();
 }
-cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst) {
-  k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst);
+cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst,
+                        int cg_launch) {
+  k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst, cg_launch);
   return cudaGetLastError();
 }
 cudaError_t launch_apply_op(const Launch &L, const InstDev *in, const void *x, void *s, int64_t rows) {

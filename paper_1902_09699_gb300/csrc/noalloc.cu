@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) k_na_l1norm(const T *__restrict__ w, int6
   js.active = 1;
   js.pass = 0;
   js.prefix = 0;
+  js.n_above = 0;
   js.c_above = js.s1_above = js.s2_above = 0.0;
   js.tie_needed = 0;
   js.counter = 0;

@@ -29,6 +29,7 @@ constexpr int kMaxHist = 8;          // s of Eq. obj_stop, upper limit
 constexpr int kThreads = 256;        // threads per CTA for the streaming kernels
 constexpr int kPerThread = 4;
 constexpr int kTile = kThreads * kPerThread;
+constexpr int64_t kMaxChunk = 64 * kTile;  // rows of one work item, at most
 constexpr int kDigitBits = 11;       // radix digit of the selection passes
 constexpr int kBins = 1 << kDigitBits;
 
@@ -123,7 +124,8 @@ struct JobScal {
   uint32_t counter;
   int32_t pad;
   uint64_t prefix;    // fixed high key bits so far; final key after the last pass
-  double c_above, s1_above, s2_above;  // entries with key above the current bin
+  uint64_t n_above;   // entries with key above the current bin (count)
+  double c_above, s1_above, s2_above;  // the same count; sums of |w| and w^2 over them
   double tau;         // l1 radius
   int64_t k;          // cardinality
   double theta;       // l1 soft threshold
@@ -159,28 +161,40 @@ struct InstDev {
   // buffered (read at stencil neighbours while the next values are written);
   // the direction p is updated in place
   void *cr[2], *cw[2], *cs[2], *cp;
+  // per-tile partial sums of the grid-point launches, in the accumulator
+  // type (binary32 for binary32 storage): 3 slots x 2 quantities x nt_n,
+  // slot 0 r.r of the right-hand side launch, slots 1 and 2 alternate
+  // between the CG launches
+  void *cgp;
   BlockDev blk[kMaxBlocks];
   SegDev seg[kMaxSegs];
+};
+
+// Conjugate-gradient state between step launches.  Every CTA of a step
+// launch derives it from the previous launch's partial sums and the previous
+// state; the instance's first tile stores it in slot (phase & 1) while the
+// launch reads slot ((phase - 1) & 1).
+struct CgState {
+  double alpha, rr, rr0;  // step length; r.r; r_0.r_0 (binary64 storage)
+  float alphaf, rrf, rr0f;  // the same for binary32 storage
+  int32_t active, steps;  // this launch takes a step; steps taken before it
 };
 
 struct InstScal {
   int32_t k;            // iteration in progress (1-based)
   int32_t done;         // stopping rule held (or a non-finite model); kernels no-op
   int32_t iters, stop_reason;
-  int32_t cg_active, cg_steps, cg_total, rbuf;
+  int32_t cg_steps, cg_total;  // CG steps of the last iteration; of the run
   int32_t have_k0, nonfinite;
-  uint32_t cnt_n, cnt_set, cnt_norm;
-  int32_t pad;
-  double rr, rr0, bnorm2, alpha, beta;  // rr = r.r (gamma of the CG recurrence)
-  double acc_n[2];
+  uint32_t cnt_set, cnt_norm;
+  CgState cg[2];
   double rho[kMaxBlocks], gamma[kMaxBlocks], irho[kMaxBlocks], inv1p[kMaxBlocks];
   double l2scale[kMaxBlocks];
   double c0, cz, cx, cy;
   // binary32 copies written next to the binary64 values, so binary32
-  // kernels convert nothing: c0, cz, cx, cy, alpha, beta and per block
+  // kernels convert nothing: c0, cz, cx, cy and per block
   // rho, 1/rho, gamma, 1-gamma, 1/(1+rho), l2 scale
   float cf[4];
-  float alphaf, betaf;
   float bf[kMaxBlocks][6];
   double sigma[kMaxBlocks];
   int64_t kcard[kMaxBlocks];

@@ -17,7 +17,8 @@ cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, i
 cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
-cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+// ph: 2 for the first step launch of an iteration, then 3, 4, ...
+cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph);
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            JobScal *jscal, const JobDev *jobs);
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
@@ -51,7 +52,9 @@ cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDe
                         const JobDev *jobs, JobScal *jscal, uint32_t *ties);
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                          const JobDev *jobs, const JobScal *jscal, const uint32_t *ties);
-cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst);
+// cg_launch: step launches per iteration
+cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst,
+                        int cg_launch);
 
 // single-step operators on one grid (kernels.cu): `in` describes the grid and
 // the segments of one operator; `sc` carries the stencil coefficients.
