@@ -361,6 +361,11 @@ static int sm_count() {
 void Plan::release() {
   if (graph) cudaGraphExecDestroy(graph);
   graph = nullptr;
+  if (tgraph) cudaGraphExecDestroy(tgraph);
+  tgraph = nullptr;
+  for (auto e : tev) cudaEventDestroy(e);
+  tev.clear();
+  tcat.clear();
   if (arena) cudaFree(arena);
   arena = nullptr;
 }
@@ -605,10 +610,23 @@ int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, 
 // ----------------------------------------------------------------------------
 // launch sequencing
 // ----------------------------------------------------------------------------
-static sip_status enqueue_iteration(Plan &P, cudaStream_t st, KernelTimer *tm) {
+// marks: record an event pair (the plan's timing events) around every launch
+static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   const Launch L{P.dtype, st};
-  auto T0 = [&](int c) { if (tm) tm->begin(c, st); };
-  auto T1 = [&](int c) { if (tm) tm->end(c, st); };
+  cudaError_t me = cudaSuccess;
+  auto mark = [&](int c) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      me = cudaErrorMemoryAllocation;
+      return;
+    }
+    P.tev.push_back(e);
+    if (c >= 0) P.tcat.push_back(c);
+    // an external record: a real event record node when captured
+    if (cudaError_t r = cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)) me = r;
+  };
+  auto T0 = [&](int c) { if (marks) mark(c); };
+  auto T1 = [&](int) { if (marks) mark(-1); };
   T0(KT_RHS);
   CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
   T1(KT_RHS);
@@ -645,6 +663,27 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, KernelTimer *tm) {
   T0(KT_TAIL);
   CK(launch_tail(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst, P.cg_launch));
   T1(KT_TAIL);
+  if (me != cudaSuccess) return fail(SIP_ERR_CUDA, "timing events: %s", cudaGetErrorString(me));
+  return SIP_OK;
+}
+
+static sip_status capture(Plan &P, cudaStream_t cap, int iters, bool marks, cudaGraphExec_t *out) {
+  CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  sip_status st = SIP_OK;
+  for (int i = 0; i < iters && st == SIP_OK; ++i) st = enqueue_iteration(P, cap, marks);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap, &g);
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(SIP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return fail(SIP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
   return SIP_OK;
 }
 
@@ -654,24 +693,21 @@ static sip_status build_graph(Plan &P, cudaStream_t cap, int iters) {
     cudaGraphExecDestroy(P.graph);
     P.graph = nullptr;
   }
-  CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-  sip_status st = SIP_OK;
-  for (int i = 0; i < iters && st == SIP_OK; ++i) st = enqueue_iteration(P, cap, nullptr);
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(cap, &g);
-  if (st) {
-    if (g) cudaGraphDestroy(g);
-    return st;
-  }
-  if (e != cudaSuccess) return fail(SIP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&P.graph, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    P.graph = nullptr;
-    return fail(SIP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-  }
-  P.graph_iters = iters;
-  return SIP_OK;
+  sip_status s = capture(P, cap, iters, false, &P.graph);
+  if (!s) P.graph_iters = iters;
+  return s;
+}
+
+static sip_status build_timing_graph(Plan &P, cudaStream_t cap, int iters) {
+  if (P.tgraph && P.tgraph_iters == iters) return SIP_OK;
+  if (P.tgraph) cudaGraphExecDestroy(P.tgraph);
+  P.tgraph = nullptr;
+  for (auto e : P.tev) cudaEventDestroy(e);
+  P.tev.clear();
+  P.tcat.clear();
+  sip_status s = capture(P, cap, iters, true, &P.tgraph);
+  if (!s) P.tgraph_iters = iters;
+  return s;
 }
 
 // Run `iters` iterations (kernels no-op once an instance is done).
@@ -708,14 +744,29 @@ static sip_status run_persistent(Plan &P, cudaStream_t st, int iters) {
 sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,
                           KernelTimer *tm) {
   if (!tm && P.exec == SIP_EXEC_PERSISTENT) return run_persistent(P, st, iters);
+  const int chunk = poll ? P.check_every : (iters < 10 ? iters : 10);
   if (tm) {
-    for (int i = 0; i < iters; ++i) {
-      sip_status s = enqueue_iteration(P, st, tm);
-      if (s) return s;
+    // per-kernel device time: the graph with event pairs, read after each replay
+    sip_status s = build_timing_graph(P, cap, chunk);
+    if (s) return s;
+    for (int done_iters = 0; done_iters < iters;) {
+      CK(cudaGraphLaunch(P.tgraph, st));
+      done_iters += chunk;
+      CK(cudaStreamSynchronize(st));
+      for (size_t i = 0; i < P.tcat.size(); ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, P.tev[2 * i], P.tev[2 * i + 1]));
+        tm->ms[P.tcat[i]] += t;
+        tm->launches[P.tcat[i]] += 1;
+      }
+      if (poll && done_iters < iters) {
+        CK(cudaMemcpyAsync(pinned_flag, P.d_ctrl + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*pinned_flag >= P.ninst) break;
+      }
     }
     return SIP_OK;
   }
-  const int chunk = poll ? P.check_every : (iters < 10 ? iters : 10);
   sip_status s = build_graph(P, cap, chunk);
   if (s) return s;
   int done_iters = 0;

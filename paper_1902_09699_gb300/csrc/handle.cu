@@ -267,7 +267,6 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
   const bool sync = info || o.trace || tm;
   if (!sync) return SIP_OK;
   CKH(cudaStreamSynchronize(st));
-  if (tm) tm->collect();
   uint32_t ctrl[8];
   CKH(cudaMemcpy(ctrl, F.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
   if (ctrl[2] != 0) return fail(SIP_ERR_TIMEOUT, "a grid barrier of the persistent kernel timed out");
@@ -583,8 +582,7 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void
     CKH(cudaEventRecord(h->ev1, st));
     if (!infos && !tm) return SIP_OK;
     CKH(cudaStreamSynchronize(st));
-    if (tm) tm->collect();
-    if (!infos) return SIP_OK;
+      if (!infos) return SIP_OK;
     std::vector<InstScal> sc(P.ninst);
     CKH(cudaMemcpy(sc.data(), P.d_scal, P.ninst * sizeof(InstScal), cudaMemcpyDeviceToHost));
     float ms = 0.f;

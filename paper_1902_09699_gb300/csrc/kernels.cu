@@ -1960,7 +1960,16 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restr
                                                           InstScal *__restrict__ scal,
                                                           const JobScal *__restrict__ jscal, int ninst,
                                                           int cg_launch) {
-  if ((int)blockIdx.x < ninst) body_tail(blockIdx.x, insts, scal, jscal, cg_launch);
+  if ((int)blockIdx.x >= ninst) return;
+  // the tail's scattered descriptor reads (blocks, operators, options) from
+  // a shared-memory copy
+  __shared__ InstDev s_in;
+  static_assert(sizeof(InstDev) % 8 == 0, "InstDev copies in 8-byte words");
+  const uint2 *src = reinterpret_cast<const uint2 *>(&insts[blockIdx.x]);
+  uint2 *dst = reinterpret_cast<uint2 *>(&s_in);
+  for (int i = threadIdx.x; i < (int)(sizeof(InstDev) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  body_tail(0, &s_in, scal + blockIdx.x, jscal, cg_launch);
 }
 
 // --------------------------------------------------------------------------

@@ -33,47 +33,17 @@ struct InstLayout {
 // kernel categories of the per-kernel timer
 enum KernelCat { KT_RHS = 0, KT_CG_W0, KT_CG_STEP, KT_SETPASS, KT_SELECT, KT_TIES, KT_FINAL, KT_TAIL, KT_COUNT };
 
-// CUDA-event timing of every launch, by kernel category (opt-in; used to
-// report per-kernel device time without a profiler).
+// Per-kernel device time by category (opt-in): the iterations run as a CUDA
+// graph with an event pair around every launch (event record nodes); the
+// pairs' elapsed times are added up after each replay.
 struct KernelTimer {
-  std::vector<cudaEvent_t> pool;
-  std::vector<int> cat;   // category of each (begin, end) pair
-  size_t used = 0;        // events used
-  cudaEvent_t open_ev = nullptr;
   double ms[KT_COUNT] = {};
   int64_t launches[KT_COUNT] = {};
-  cudaEvent_t next() {
-    if (used == pool.size()) {
-      cudaEvent_t e;
-      cudaEventCreate(&e);
-      pool.push_back(e);
-    }
-    return pool[used++];
-  }
-  void begin(int c, cudaStream_t st) {
-    cudaEventRecord(next(), st);
-    cat.push_back(c);
-  }
-  void end(int, cudaStream_t st) { cudaEventRecord(next(), st); }
-  // call after the stream has been synchronised
-  void collect() {
-    for (size_t i = 0; i < cat.size(); ++i) {
-      float t = 0.f;
-      cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]);
-      ms[cat[i]] += t;
-      launches[cat[i]] += 1;
-    }
-    cat.clear();
-    used = 0;
-  }
   void reset() {
     for (int c = 0; c < KT_COUNT; ++c) {
       ms[c] = 0.0;
       launches[c] = 0;
     }
-  }
-  ~KernelTimer() {
-    for (auto e : pool) cudaEventDestroy(e);
   }
 };
 
@@ -99,6 +69,11 @@ struct Plan {
   std::vector<InstLayout> layouts;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
+  // timing graph: the same iterations with an event pair around every launch
+  cudaGraphExec_t tgraph = nullptr;
+  int tgraph_iters = 0;
+  std::vector<cudaEvent_t> tev;  // begin, end of launch i at 2i, 2i + 1
+  std::vector<int> tcat;         // kernel category of launch i
   uint32_t *d_ctrl = nullptr;  // grid-barrier words [0..3], finished-instance count [4]
   bool packed = false;         // batched plan: x (and m) of all instances back to back
   std::vector<int64_t> pack_off;
