@@ -246,7 +246,8 @@ def run_ours(args):
     e2e_ms = t0.elapsed_time(t1) / e2e_steps
     e2e_value = world * its / (e2e_ms / 1000.0)
 
-    # ---- per-kernel device time (CUDA events around every launch, no graph)
+    # ---- per-kernel device time: the iteration graph with every launch stamping
+    # its first CTA start and last CTA end (global timer), read after each replay
     pr.set_timing(True)
     flush.fill_(2.0)
     pr.project(models[1], x, info=True)

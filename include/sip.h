@@ -268,12 +268,13 @@ int64_t sip_device_bytes(const sip_handle *h);
  * uses), finest level. */
 double sip_bytes_per_iter(const sip_handle *h);
 
-/* Per-kernel device timing.  With timing on, sip_project launches every
- * kernel directly (no CUDA graph) between CUDA events on the caller's stream
- * and sip_project synchronises; sip_kernel_times returns, per kernel
- * category (see sip_kernel_name, 0..SIP_KERNEL_CATEGORIES-1), the summed
- * device milliseconds, the launch count since timing was switched on, and
- * the algorithmic bytes one launch moves (the roofline numerator). */
+/* Per-kernel device timing.  With timing on, sip_project runs the
+ * iterations as a CUDA graph in which every launch records the global timer
+ * at its first CTA's start and its last CTA's end, and synchronises after
+ * each replay to read them; sip_kernel_times returns, per kernel category
+ * (see sip_kernel_name, 0..SIP_KERNEL_CATEGORIES-1), the summed device
+ * milliseconds, the launch count since timing was switched on, and the
+ * algorithmic bytes one launch moves (the roofline numerator). */
 #define SIP_KERNEL_CATEGORIES 8
 sip_status sip_set_timing(sip_handle *h, int on);
 sip_status sip_kernel_times(const sip_handle *h, double *ms, int64_t *launches,

@@ -363,8 +363,8 @@ void Plan::release() {
   graph = nullptr;
   if (tgraph) cudaGraphExecDestroy(tgraph);
   tgraph = nullptr;
-  for (auto e : tev) cudaEventDestroy(e);
-  tev.clear();
+  if (d_ts) cudaFree(d_ts);
+  d_ts = nullptr;
   tcat.clear();
   if (arena) cudaFree(arena);
   arena = nullptr;
@@ -610,23 +610,20 @@ int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, 
 // ----------------------------------------------------------------------------
 // launch sequencing
 // ----------------------------------------------------------------------------
-// marks: record an event pair (the plan's timing events) around every launch
+// Launches of one iteration.
+static int launches_per_iter(const Plan &P) {
+  return 3 + P.cg_launch + (P.nt_sel ? select_passes(P.dtype) : 0) + (P.any_card ? 1 : 0) + (P.nt_fin ? 1 : 0) + 1;
+}
+
+// marks: every launch stamps its own slot pair of P.d_ts (timing graph)
 static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
-  const Launch L{P.dtype, st};
-  cudaError_t me = cudaSuccess;
-  auto mark = [&](int c) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) {
-      me = cudaErrorMemoryAllocation;
-      return;
-    }
-    P.tev.push_back(e);
-    if (c >= 0) P.tcat.push_back(c);
-    // an external record: a real event record node when captured
-    if (cudaError_t r = cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)) me = r;
+  Launch L{P.dtype, st};
+  auto T0 = [&](int c) {
+    if (!marks) return;
+    L.ts = P.d_ts + 2 * P.tcat.size();
+    P.tcat.push_back(c);
   };
-  auto T0 = [&](int c) { if (marks) mark(c); };
-  auto T1 = [&](int) { if (marks) mark(-1); };
+  auto T1 = [&](int) {};
   T0(KT_RHS);
   CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
   T1(KT_RHS);
@@ -663,7 +660,6 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   T0(KT_TAIL);
   CK(launch_tail(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst, P.cg_launch));
   T1(KT_TAIL);
-  if (me != cudaSuccess) return fail(SIP_ERR_CUDA, "timing events: %s", cudaGetErrorString(me));
   return SIP_OK;
 }
 
@@ -702,10 +698,17 @@ static sip_status build_timing_graph(Plan &P, cudaStream_t cap, int iters) {
   if (P.tgraph && P.tgraph_iters == iters) return SIP_OK;
   if (P.tgraph) cudaGraphExecDestroy(P.tgraph);
   P.tgraph = nullptr;
-  for (auto e : P.tev) cudaEventDestroy(e);
-  P.tev.clear();
+  if (P.d_ts) cudaFree(P.d_ts);
+  P.d_ts = nullptr;
   P.tcat.clear();
+  const size_t words = 2 * (size_t)launches_per_iter(P) * iters;
+  if (cudaMalloc(&P.d_ts, words * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    P.d_ts = nullptr;
+    return fail(SIP_ERR_OOM, "timing stamps: device allocation failed");
+  }
   sip_status s = capture(P, cap, iters, true, &P.tgraph);
+  if (!s && 2 * P.tcat.size() > words) return fail(SIP_ERR_INTERNAL, "timing stamps: launch count");
   if (!s) P.tgraph_iters = iters;
   return s;
 }
@@ -746,17 +749,19 @@ sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters,
   if (!tm && P.exec == SIP_EXEC_PERSISTENT) return run_persistent(P, st, iters);
   const int chunk = poll ? P.check_every : (iters < 10 ? iters : 10);
   if (tm) {
-    // per-kernel device time: the graph with event pairs, read after each replay
+    // per-kernel device time: the stamping graph, its stamps read after each replay
     sip_status s = build_timing_graph(P, cap, chunk);
     if (s) return s;
+    std::vector<unsigned long long> ts(2 * P.tcat.size());
     for (int done_iters = 0; done_iters < iters;) {
+      CK(cudaMemsetAsync(P.d_ts, 0xff, ts.size() * sizeof(unsigned long long), st));
       CK(cudaGraphLaunch(P.tgraph, st));
       done_iters += chunk;
+      CK(cudaMemcpyAsync(ts.data(), P.d_ts, ts.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (size_t i = 0; i < P.tcat.size(); ++i) {
-        float t = 0.f;
-        CK(cudaEventElapsedTime(&t, P.tev[2 * i], P.tev[2 * i + 1]));
-        tm->ms[P.tcat[i]] += t;
+        const unsigned long long t0 = ts[2 * i], t1 = ~ts[2 * i + 1];
+        tm->ms[P.tcat[i]] += t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
         tm->launches[P.tcat[i]] += 1;
       }
       if (poll && done_iters < iters) {

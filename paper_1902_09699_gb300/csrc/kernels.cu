@@ -389,6 +389,26 @@ __device__ __forceinline__ T csys(const InstDev &in, const InstScal &sc, const G
   return apply_c(C, n);
 }
 
+
+// Launch-time stamps of the timing runs: thread 0 of every CTA folds the
+// global nanosecond timer at its start into ts[0] (minimum) and the
+// complement of the timer at its end into ts[1] (minimum, i.e. the latest
+// end); both slots start at all ones, and the launch took ~ts[1] - ts[0].
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+struct Stamp {
+  unsigned long long *ts;
+  __device__ __forceinline__ explicit Stamp(unsigned long long *p) : ts(p) {
+    if (ts && threadIdx.x == 0) atomicMin(&ts[0], gtimer());
+  }
+  __device__ __forceinline__ ~Stamp() {
+    if (ts && threadIdx.x == 0) atomicMin(&ts[1], ~gtimer());
+  }
+};
+
 // --------------------------------------------------------------------------
 // x-update right-hand side and warm residual
 // --------------------------------------------------------------------------
@@ -550,7 +570,8 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                  InstScal *__restrict__ scal) {
+                                                  InstScal *__restrict__ scal, unsigned long long *ts) {
+  const Stamp stamp(ts);
   body_rhs<T>(tiles[blockIdx.x], insts, scal);
 }
 
@@ -612,7 +633,8 @@ __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__rest
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                       InstScal *__restrict__ scal) {
+                                                       InstScal *__restrict__ scal, unsigned long long *ts) {
+  const Stamp stamp(ts);
   body_cg_w0<T>(tiles[blockIdx.x], insts, scal);
 }
 
@@ -794,7 +816,8 @@ __device__ __forceinline__ void body_cg_step(const Tile &tl,
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
                                                          const InstDev *__restrict__ insts,
-                                                         InstScal *__restrict__ scal, int ph) {
+                                                         InstScal *__restrict__ scal, int ph, unsigned long long *ts) {
+  const Stamp stamp(ts);
   body_cg_step<T>(tiles[blockIdx.x], insts, scal, ph);
 }
 
@@ -1076,7 +1099,8 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                       InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
-                                                      const JobDev *__restrict__ jobs) {
+                                                      const JobDev *__restrict__ jobs, unsigned long long *ts) {
+  const Stamp stamp(ts);
   body_setpass<T>(tiles[blockIdx.x], insts, scal, jscal, jobs);
 }
 
@@ -1545,7 +1569,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__
                                                         InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                         JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
                                                         double *__restrict__ hs1, double *__restrict__ hs2,
-                                                        double *__restrict__ hs3, int pass) {
+                                                        double *__restrict__ hs3, int pass, unsigned long long *ts) {
+  const Stamp stamp(ts);
   body_select<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, hcnt, hs1, hs2, hs3, pass);
 }
 
@@ -1584,7 +1609,8 @@ __device__ __forceinline__ void body_ties(const Tile &tl, const InstDev *__restr
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) k_ties(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                    InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
-                                                   JobScal *__restrict__ jscal, uint32_t *__restrict__ ties) {
+                                                   JobScal *__restrict__ jscal, uint32_t *__restrict__ ties, unsigned long long *ts) {
+  const Stamp stamp(ts);
   body_ties<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, ties);
 }
 
@@ -1729,7 +1755,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                     InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                     const JobScal *__restrict__ jscal,
-                                                    const uint32_t *__restrict__ ties) {
+                                                    const uint32_t *__restrict__ ties, unsigned long long *ts) {
+  const Stamp stamp(ts);
   body_final<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, ties);
 }
 
@@ -1959,7 +1986,8 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
 __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restrict__ insts,
                                                           InstScal *__restrict__ scal,
                                                           const JobScal *__restrict__ jscal, int ninst,
-                                                          int cg_launch) {
+                                                          int cg_launch, unsigned long long *ts) {
+  const Stamp stamp(ts);
   if ((int)blockIdx.x >= ninst) return;
   // the tail's scattered descriptor reads (blocks, operators, options) from
   // a shared-memory copy
@@ -2227,20 +2255,20 @@ cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstD
   return cudaGetLastError();
 }
 cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_rhs, nt, kThreads, 0, tiles, insts, scal);
+  SIP_DISPATCH(L, k_rhs, nt, kThreads, 0, tiles, insts, scal, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal);
+  SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph) {
-  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph);
+  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            JobScal *jscal, const JobDev *jobs) {
-  SIP_DISPATCH(L, k_setpass, nt, kThreads, 0, tiles, insts, scal, jscal, jobs);
+  SIP_DISPATCH(L, k_setpass, nt, kThreads, 0, tiles, insts, scal, jscal, jobs, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
@@ -2248,10 +2276,10 @@ cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const Inst
                           int pass) {
   if (L.dtype == SIP_F64)
     k_select<double><<<nt, kThreads, BinAcc<double>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1,
-                                                                       hs2, hs3, pass);
+                                                                       hs2, hs3, pass, L.ts);
   else
     k_select<float><<<nt, kThreads, BinAcc<float>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1, hs2,
-                                                                     hs3, pass);
+                                                                     hs3, pass, L.ts);
   return cudaGetLastError();
 }
 cudaError_t kernels_setup() {
@@ -2350,17 +2378,17 @@ int fused_grid(int dtype) {
 int select_passes(int dtype) { return dtype == SIP_F64 ? num_passes<double>() : num_passes<float>(); }
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                         const JobDev *jobs, JobScal *jscal, uint32_t *ties) {
-  SIP_DISPATCH(L, k_ties, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties);
+  SIP_DISPATCH(L, k_ties, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                          const JobDev *jobs, const JobScal *jscal, const uint32_t *ties) {
-  SIP_DISPATCH(L, k_final, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties);
+  SIP_DISPATCH(L, k_final, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst,
                         int cg_launch) {
-  k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst, cg_launch);
+  k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst, cg_launch, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_apply_op(const Launch &L, const InstDev *in, const void *x, void *s, int64_t rows) {

@@ -34,8 +34,8 @@ struct InstLayout {
 enum KernelCat { KT_RHS = 0, KT_CG_W0, KT_CG_STEP, KT_SETPASS, KT_SELECT, KT_TIES, KT_FINAL, KT_TAIL, KT_COUNT };
 
 // Per-kernel device time by category (opt-in): the iterations run as a CUDA
-// graph with an event pair around every launch (event record nodes); the
-// pairs' elapsed times are added up after each replay.
+// graph whose kernels stamp their first CTA start and last CTA end with the
+// global timer; the stamps are read after each replay.
 struct KernelTimer {
   double ms[KT_COUNT] = {};
   int64_t launches[KT_COUNT] = {};
@@ -69,11 +69,11 @@ struct Plan {
   std::vector<InstLayout> layouts;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
-  // timing graph: the same iterations with an event pair around every launch
+  // timing graph: the same iterations, every launch stamping its slot pair
   cudaGraphExec_t tgraph = nullptr;
   int tgraph_iters = 0;
-  std::vector<cudaEvent_t> tev;  // begin, end of launch i at 2i, 2i + 1
-  std::vector<int> tcat;         // kernel category of launch i
+  unsigned long long *d_ts = nullptr;  // 2 words per launch of the timing graph
+  std::vector<int> tcat;               // kernel category of launch i
   uint32_t *d_ctrl = nullptr;  // grid-barrier words [0..3], finished-instance count [4]
   bool packed = false;         // batched plan: x (and m) of all instances back to back
   std::vector<int64_t> pack_off;

@@ -10,6 +10,9 @@ namespace sip {
 struct Launch {
   int dtype;  // SIP_F64 / SIP_F32
   cudaStream_t stream;
+  // launch-time stamps (timing runs only): [0] earliest CTA start, [1]
+  // latest CTA end, global timer nanoseconds; null otherwise
+  unsigned long long *ts = nullptr;
 };
 
 // iteration kernels (kernels.cu)
