@@ -728,6 +728,119 @@ __device__ __forceinline__ void cg_scalars(const Tile &tl, const InstDev &in, In
   __syncthreads();
 }
 
+// Binary32 CG step on 2D grids with n_z % 4 == 0 (so every column starts on
+// a multiple of 4) whose arrays start on 16-byte boundaries: a thread takes
+// 4 consecutive z samples of one column with 16-byte loads and stores; the
+// z neighbours beyond its 4 come from the adjacent lanes, or, at a warp or
+// tile edge, from single loads.  Same arithmetic per sample as the general
+// step.
+__device__ __forceinline__ float4 ld4(const float *p, int64_t i) { return *reinterpret_cast<const float4 *>(p + i); }
+__device__ __forceinline__ void st4(float *p, int64_t i, const float4 &v) { *reinterpret_cast<float4 *>(p + i) = v; }
+
+__device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const InstDev &in, InstScal &sc, int ph) {
+  constexpr int SUB = kThreads * 4;
+  const unsigned FULL = 0xffffffffu;
+  const int c = ph & 1, n = c ^ 1;
+  const float *__restrict__ r = (const float *)in.cr[c];
+  const float *__restrict__ w = (const float *)in.cw[c];
+  const float *__restrict__ sp = (const float *)in.cs[c];  // s_{i-1}
+  float *__restrict__ rn_ = (float *)in.cr[n];
+  float *__restrict__ wn_ = (float *)in.cw[n];
+  float *__restrict__ sn_ = (float *)in.cs[n];             // s_i
+  float *__restrict__ p = (float *)in.cp;
+  float *__restrict__ x = (float *)in.x;
+  __shared__ float s_ab[2];
+  __shared__ int s_go;
+  float alpha = 0.f, beta = 0.f;
+  CSys<float> C;
+  C.load(sc);
+  const int lane = threadIdx.x & 31;
+  const int64_t end = tl.start + tl.len;  // a multiple of 4
+  float ag = 0.f, ad = 0.f;
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    const int64_t g0 = base + 4 * (int64_t)threadIdx.x;
+    const bool ok = g0 < end;
+    float4 rc, wc, sc4, pv, xv, rxm, wxm, sxm, rxp, wxp, sxp;
+    float rzm = 0.f, wzm = 0.f, szm = 0.f, rzp = 0.f, wzp = 0.f, szp = 0.f;
+    bool hzm = false, hzp = false, edge_p = false;
+    if (ok) {
+      const GridPos ps = grid_pos(in, g0);
+      rc = ld4(r, g0);
+      wc = ld4(w, g0);
+      sc4 = ld4(sp, g0);
+      pv = ld4(p, g0);
+      xv = ld4(x, g0);
+      // a missing neighbour repeats the centre, so its difference is zero
+      const bool hxm = ps.ix > 0, hxp = ps.ix < in.nx - 1;
+      rxm = hxm ? ld4(r, g0 - in.nz) : rc;
+      wxm = hxm ? ld4(w, g0 - in.nz) : wc;
+      sxm = hxm ? ld4(sp, g0 - in.nz) : sc4;
+      rxp = hxp ? ld4(r, g0 + in.nz) : rc;
+      wxp = hxp ? ld4(w, g0 + in.nz) : wc;
+      sxp = hxp ? ld4(sp, g0 + in.nz) : sc4;
+      hzm = ps.iz > 0;
+      hzp = ps.iz + 4 < in.nz;
+      edge_p = lane == 31 || g0 + 4 >= end;
+      if (hzm && lane == 0) {
+        rzm = r[g0 - 1];
+        wzm = w[g0 - 1];
+        szm = sp[g0 - 1];
+      }
+      if (hzp && edge_p) {
+        rzp = r[g0 + 4];
+        wzp = w[g0 + 4];
+        szp = sp[g0 + 4];
+      }
+    }
+    if (base == tl.start) {
+      // the previous launch's sums, while this CTA's first loads are in flight
+      cg_scalars<float>(tl, in, sc, ph, s_ab, &s_go);
+      if (!s_go) return;
+      alpha = s_ab[0];
+      beta = s_ab[1];
+    }
+    // r_{i+1} = r_i - alpha (w_i + beta s_{i-1}) at the samples and their neighbours
+    auto nr = [&](float rv, float wv, float sv) { return rv - alpha * (wv + beta * sv); };
+    auto nr4 = [&](const float4 &a, const float4 &b, const float4 &d) {
+      return make_float4(nr(a.x, b.x, d.x), nr(a.y, b.y, d.y), nr(a.z, b.z, d.z), nr(a.w, b.w, d.w));
+    };
+    float4 R = ok ? nr4(rc, wc, sc4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float zm = __shfl_up_sync(FULL, R.w, 1), zp = __shfl_down_sync(FULL, R.x, 1);
+    if (!ok) continue;
+    const float4 RXM = nr4(rxm, wxm, sxm), RXP = nr4(rxp, wxp, sxp);
+    if (lane == 0) zm = nr(rzm, wzm, szm);
+    if (edge_p) zp = nr(rzp, wzp, szp);
+    if (!hzm) zm = R.x;
+    if (!hzp) zp = R.w;
+    Nbr<float> nb;
+    float4 W;
+    nb = {R.x, zm, R.y, RXM.x, RXP.x, R.x, R.x};
+    W.x = apply_c(C, nb);
+    nb = {R.y, R.x, R.z, RXM.y, RXP.y, R.y, R.y};
+    W.y = apply_c(C, nb);
+    nb = {R.z, R.y, R.w, RXM.z, RXP.z, R.z, R.z};
+    W.z = apply_c(C, nb);
+    nb = {R.w, R.z, zp, RXM.w, RXP.w, R.w, R.w};
+    W.w = apply_c(C, nb);
+    const float4 S = make_float4(wc.x + beta * sc4.x, wc.y + beta * sc4.y, wc.z + beta * sc4.z, wc.w + beta * sc4.w);
+    const float4 Pn = make_float4(rc.x + beta * pv.x, rc.y + beta * pv.y, rc.z + beta * pv.z, rc.w + beta * pv.w);
+    st4(p, g0, Pn);
+    st4(x, g0, make_float4(xv.x + alpha * Pn.x, xv.y + alpha * Pn.y, xv.z + alpha * Pn.z, xv.w + alpha * Pn.w));
+    st4(sn_, g0, S);
+    st4(rn_, g0, R);
+    st4(wn_, g0, W);
+    ag += R.x * R.x + R.y * R.y + R.z * R.z + R.w * R.w;
+    ad += W.x * R.x + W.y * R.y + W.z * R.z + W.w * R.w;
+  }
+  float acc[2] = {ag, ad};
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    const int slot = 1 + (ph & 1);
+    cg_part<float>(in, slot, 0)[tl.seq] = acc[0];
+    cg_part<float>(in, slot, 1)[tl.seq] = acc[1];
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void body_cg_step(const Tile &tl,
                                                          const InstDev *__restrict__ insts,
@@ -737,6 +850,16 @@ __device__ __forceinline__ void body_cg_step(const Tile &tl,
   constexpr int SUB = kThreads * PT;
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
+  if constexpr (sizeof(T) == 4) {
+    // 16-byte accesses need every array on a 16-byte boundary (the x of a
+    // batched plan is packed and may not be)
+    const uintptr_t al = (uintptr_t)in.x | (uintptr_t)in.cp | (uintptr_t)in.cr[0] | (uintptr_t)in.cr[1] |
+                         (uintptr_t)in.cw[0] | (uintptr_t)in.cw[1] | (uintptr_t)in.cs[0] | (uintptr_t)in.cs[1];
+    if ((in.nz & 3) == 0 && in.ny == 1 && (al & 15) == 0) {
+      body_cg_step_v4(tl, in, sc, ph);
+      return;
+    }
+  }
   const int c = ph & 1, n = c ^ 1;
   const T *__restrict__ r = (const T *)in.cr[c];
   const T *__restrict__ w = (const T *)in.cw[c];

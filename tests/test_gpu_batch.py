@@ -35,6 +35,10 @@ def mixed_instances():
     out.append(({"n": (130, 3)}, [{"op": "DZ", "type": "card", "k_frac": 0.05},
                                   {"op": "I", "type": "l2", "sigma_rel": 0.6}]))
     out.append(({"n": (25, 25)}, [{"op": "TV", "type": "l1", "sigma_rel": 0.2}]))
+    # n_z % 4 == 0 after an odd packed offset: its x is not 16-byte aligned
+    # in the batch (4-sample CG step not taken there, taken when alone)
+    out.append(({"n": (12, 20)}, [{"op": "I", "type": "bounds", "lo": 2.5, "hi": 3.5},
+                                  {"op": "DZ", "type": "l2", "sigma_rel": 0.4}]))
     models = [3.0 + g.standard_normal(int(np.prod(gr["n"]))) for gr, _ in out]
     return out, models
 

@@ -224,6 +224,28 @@ def test_nonfinite_model_rejected():
     pr.close()
 
 
+@pytest.mark.parametrize("n", [(4, 300), (12, 37), (8, 2000), (36, 129), (12, 1001)])
+def test_fp32_four_sample_cg_step(n):
+    """Binary32 2D grids with n_z % 4 == 0 take the CG step that loads 4
+    samples of a column at once; its z neighbours come from adjacent lanes
+    or, at warp and work-item edges (here inside columns: n_z = 12, 36),
+    from single loads.  n_z = 4 puts every column in one group (both z ends
+    missing).  Fixed rho, no selection sets: the result must track the FP64
+    oracle as closely as the general step's."""
+    g = np.random.default_rng(5)
+    m = 3.0 + g.standard_normal(n[0] * n[1])
+    grid = {"n": n}
+    sets = [{"op": "I", "type": "bounds", "lo": 2.5, "hi": 3.5},
+            {"op": "DZ", "type": "l2", "sigma_rel": 0.3},
+            {"op": "DX", "type": "bounds", "lo": -0.5, "hi": 0.5}]
+    opts = dict(max_iter=30, adapt=0, rho0=1.0, gamma0=1.5)
+    m32 = m_as(m, "f32")
+    ref = oracle_run(m32, grid, sets, opts)
+    x, info, _ = run_gpu(m32, grid, sets, "f32", opts)
+    assert info["cg_steps"] == ref["cg_steps"]
+    assert rel(x, ref["x"]) <= 5e-5
+
+
 # ---------------------------------------------------------------- full size 512 x 1024
 def test_full_size_layered_first_iterations():
     """The 512 x 1024 five-set workload in the bench launch configuration:
