@@ -513,10 +513,11 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const int64_t o_jobs = take((int64_t)njobs * sizeof(JobDev));
   const int64_t o_jscal = take((int64_t)njobs * sizeof(JobScal));
   P.hist_begin = off;
-  const int64_t o_hcnt = take((int64_t)njobs * kBins * 4);
-  const int64_t o_hs1 = take((int64_t)njobs * kBins * 8);
-  const int64_t o_hs2 = take((int64_t)njobs * kBins * 8);
-  const int64_t o_hs3 = take((int64_t)njobs * kBins * 8);
+  // three histogram buffers per array: the selection passes rotate over them
+  const int64_t o_hcnt = take(3 * (int64_t)njobs * kBins * 4);
+  const int64_t o_hs1 = take(3 * (int64_t)njobs * kBins * 8);
+  const int64_t o_hs2 = take(3 * (int64_t)njobs * kBins * 8);
+  const int64_t o_hs3 = take(3 * (int64_t)njobs * kBins * 8);
   P.hist_end = off;
   const int64_t o_ties = take(ntie * 4);
   const int64_t o_tn = take((int64_t)tn.size() * sizeof(Tile));
@@ -643,7 +644,7 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
     for (int pass = 0; pass < np; ++pass) {
       T0(KT_SELECT);
       CK(launch_select(L, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
-                       P.d_hs3, pass));
+                       P.d_hs3, (int64_t)P.njobs * kBins, pass));
       T1(KT_SELECT);
     }
   }
@@ -732,6 +733,7 @@ static sip_status run_persistent(Plan &P, cudaStream_t st, int iters) {
   F.hs1 = P.d_hs1;
   F.hs2 = P.d_hs2;
   F.hs3 = P.d_hs3;
+  F.hstride = (int64_t)P.njobs * kBins;
   F.ties = P.d_ties;
   F.bar = P.d_ctrl;
   F.ndone = P.d_ctrl + 4;

@@ -463,7 +463,7 @@ sip_status sip_project_set(const sip_set *set, int dtype, const void *w_dev, int
   if (P.nt_sel)
     for (int pass = 0; pass < select_passes(dtype); ++pass)
       CKH(launch_select(Ln, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
-                        P.d_hs3, pass));
+                        P.d_hs3, (int64_t)P.njobs * kBins, pass));
   if (P.any_card) CKH(launch_ties(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
   if (P.nt_fin) CKH(launch_final(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
   CKH(cudaMemcpyAsync(y_dev, d.y, (size_t)n * esz(dtype), cudaMemcpyDeviceToDevice, cs));

@@ -462,9 +462,11 @@ __device__ __forceinline__ AdjRows adj_rows(const InstDev &in, int kind, const G
   return a;
 }
 
-template <typename T>
-__device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restrict__ insts,
-                                                  InstScal *__restrict__ scal) {
+// b = sum_i A_i^T (rho_i y_i + v_i) (+ m in the direct form) and r = b - C x
+// at the work item's grid points.  I is the index type of grid points and
+// rows (32-bit while N < 2^31).
+template <typename T, typename I>
+__device__ __forceinline__ void body_rhs_t(const Tile &tl, const InstDev &in, InstScal &sc) {
   using A = typename AccOf<T>::type;
   // points per thread per round, segments whose rows are loaded together
   // (the adds wait on the loads: batching the segments overlaps their
@@ -472,51 +474,58 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
   constexpr int PT = 2;
   constexpr int SB = sizeof(T) == 4 ? 4 : 2;
   constexpr int SUB = kThreads * PT;
-  const InstDev &in = insts[tl.inst];
-  InstScal &sc = scal[tl.inst];
   const int done = sc.done;
   const T *__restrict__ x = (const T *)in.x;
-  const T *__restrict__ y = (const T *)in.y;
-  const T *__restrict__ v = (const T *)in.v;
   const T *__restrict__ m = (const T *)in.m;
   T *__restrict__ r = (T *)in.cr[0];
   CSys<T> C;
   C.load(sc);
-  __shared__ T srho[kMaxBlocks], sih[kMaxSegs];
-  __shared__ int64_t sbase[kMaxSegs];
+  // the segments with rows (the x-history ring, always the last segment,
+  // has none): row arrays, kind, rho of the block, 1/h of the axis
+  __shared__ const T *sy[kMaxSegs], *sv[kMaxSegs];
+  __shared__ T srs[kMaxSegs], sih[kMaxSegs];
   __shared__ int skind[kMaxSegs];
-  const int nseg = in.nseg;
-  if (threadIdx.x < in.nb) srho[threadIdx.x] = SV<T>::blk(sc, threadIdx.x, BF_RHO);
+  const int nseg = in.nseg - (in.nseg > 0 && in.seg[in.nseg - 1].kind == SEG_RING ? 1 : 0);
   if (threadIdx.x < nseg) {
     const SegDev &sg = in.seg[threadIdx.x];
+    const int64_t bs = in.blk[sg.block].yoff + sg.row0;
+    sy[threadIdx.x] = (const T *)in.y + bs;
+    sv[threadIdx.x] = (const T *)in.v + bs;
     skind[threadIdx.x] = sg.kind;
-    if (sg.kind != SEG_RING) {
-      sbase[threadIdx.x] = in.blk[sg.block].yoff + sg.row0;
-      sih[threadIdx.x] = seg_ih<T>(in, sg.kind);
-    }
+    srs[threadIdx.x] = SV<T>::blk(sc, sg.block, BF_RHO);
+    sih[threadIdx.x] = seg_ih<T>(in, sg.kind);
   }
   __syncthreads();
   if (done) return;
-  // rho of a segment's block, by segment
-  __shared__ T srs[kMaxSegs];
-  if (threadIdx.x < nseg && skind[threadIdx.x] != SEG_RING) srs[threadIdx.x] = srho[in.seg[threadIdx.x].block];
-  __syncthreads();
   const int alg1 = in.alg1;
-  const int64_t end = tl.start + tl.len;
+  const I nz = (I)in.nz, sxy = (I)in.nz * (I)in.nx;
+  const I end = (I)(tl.start + tl.len);
   A a1 = A(0);
-  for (int64_t base = tl.start; base < end; base += SUB) {
-    int64_t g[PT];
-    GridPos pos[PT];
+  for (I base = (I)tl.start; base < end; base += SUB) {
+    I g[PT], rz[PT], rx[PT];
+    bool fza[PT], fzb[PT], fxa[PT], fxb[PT], fya[PT], fyb[PT];
     T b[PT];
     Nbr<T> xn[PT];
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
-      g[e] = base + threadIdx.x + (int64_t)e * kThreads;
+      g[e] = base + (I)threadIdx.x + (I)(e * kThreads);
       b[e] = T(0);
       if (g[e] < end) {
-        pos[e] = grid_pos(in, g[e]);
+        const GridPos pos = grid_pos(in, g[e]);
         if (!alg1) b[e] = m[g[e]];
-        load_nbr<T>(in, pos[e], g[e], [&](int64_t i) { return x[i]; }, xn[e]);
+        load_nbr<T>(in, pos, g[e], [&](int64_t i) { return x[i]; }, xn[e]);
+        // rows of the difference operators meeting at g (Eq. FD_mat)
+        rz[e] = g[e] - (I)pos.t;         // D_z: iz + (nz-1) t
+        rx[e] = g[e] - nz * (I)pos.iy;   // D_x: iz + nz (ix + (nx-1) iy)
+        fza[e] = pos.iz >= 1;
+        fzb[e] = pos.iz <= in.nz - 2;
+        fxa[e] = pos.ix >= 1;
+        fxb[e] = pos.ix <= in.nx - 2;
+        fya[e] = pos.iy >= 1;
+        fyb[e] = pos.iy <= in.ny - 2;
+      } else {
+        rz[e] = rx[e] = 0;
+        fza[e] = fzb[e] = fxa[e] = fxb[e] = fya[e] = fyb[e] = false;
       }
     }
     for (int s0 = 0; s0 < nseg; s0 += SB) {
@@ -524,29 +533,32 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
 #pragma unroll
       for (int j = 0; j < SB; ++j) {
         const int sgi = s0 + j;
-        const bool live = sgi < nseg && skind[sgi] != SEG_RING;
-        const int kind = live ? skind[sgi] : SEG_I;
-        const int64_t bs = live ? sbase[sgi] : 0;
+        const bool live = sgi < nseg;
+        const int kind = live ? skind[sgi] : SEG_RING;
+        const T *__restrict__ ys = live ? sy[sgi] : nullptr;
+        const T *__restrict__ vs = live ? sv[sgi] : nullptr;
 #pragma unroll
         for (int e = 0; e < PT; ++e) {
-          ya[j][e] = va[j][e] = yb[j][e] = vb[j][e] = T(0);
-          if (live && g[e] < end) {
-            const AdjRows ar = adj_rows(in, kind, pos[e], g[e]);
-            if (ar.va) {
-              ya[j][e] = y[bs + ar.ra];
-              va[j][e] = v[bs + ar.ra];
-            }
-            if (ar.vb) {
-              yb[j][e] = y[bs + ar.rb];
-              vb[j][e] = v[bs + ar.rb];
-            }
+          // (A^T u)[g] = u[ia] (if fa) - u[ib] (if fb), times 1/h
+          I ia = g[e], ib = g[e];
+          bool fa = false, fb = false;
+          switch (kind) {
+            case SEG_I: fa = g[e] < end; break;
+            case SEG_DZ: ia = rz[e] - 1; ib = rz[e]; fa = fza[e]; fb = fzb[e]; break;
+            case SEG_DX: ia = rx[e] - nz; ib = rx[e]; fa = fxa[e]; fb = fxb[e]; break;
+            case SEG_DY: ia = g[e] - sxy; fa = fya[e]; fb = fyb[e]; break;
+            default: break;
           }
+          ya[j][e] = fa ? ys[ia] : T(0);
+          va[j][e] = fa ? vs[ia] : T(0);
+          yb[j][e] = fb ? ys[ib] : T(0);
+          vb[j][e] = fb ? vs[ib] : T(0);
         }
       }
 #pragma unroll
       for (int j = 0; j < SB; ++j) {
         const int sgi = s0 + j;
-        if (sgi < nseg && skind[sgi] != SEG_RING) {
+        if (sgi < nseg) {
           const T rho = srs[sgi], ih = sih[sgi];
 #pragma unroll
           for (int e = 0; e < PT; ++e)
@@ -566,6 +578,17 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
   A acc[1] = {a1};
   block_sum<1>(acc);
   if (threadIdx.x == 0) cg_part<A>(in, 0, 0)[tl.seq] = acc[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restrict__ insts,
+                                         InstScal *__restrict__ scal) {
+  const InstDev &in = insts[tl.inst];
+  InstScal &sc = scal[tl.inst];
+  if (in.N <= (int64_t)0x7fffffff)
+    body_rhs_t<T, int>(tl, in, sc);
+  else
+    body_rhs_t<T, int64_t>(tl, in, sc);
 }
 
 template <typename T>
@@ -1390,7 +1413,10 @@ __device__ __noinline__ void select_choose_int(const JobDev &jd, JobScal &js, co
     cl2 += l2b[j];
   }
   __syncthreads();
-  if (best >= 0) atomicMax(&sbest, best);
+  {
+    const int wb = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0 && wb >= 0) atomicMax(&sbest, wb);
+  }
   __syncthreads();
   if (best >= 0 && best == sbest) {
     const uint32_t np = pre | ((uint32_t)best << lo);
@@ -1474,7 +1500,10 @@ __device__ __noinline__ void select_choose_f64(const JobDev &jd, JobScal &js, co
   __shared__ int sbest;
   if (threadIdx.x == 0) sbest = -1;
   __syncthreads();
-  if (best >= 0) atomicMax(&sbest, best);
+  {
+    const int wb = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0 && wb >= 0) atomicMax(&sbest, wb);
+  }
   __syncthreads();
   if (best >= 0 && best == sbest) {
     const int j = best - threadIdx.x * kPer;
@@ -1517,7 +1546,7 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
                                                         InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                         JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
                                                         double *__restrict__ hs1, double *__restrict__ hs2,
-                                                        double *__restrict__ hs3, int pass) {
+                                                        double *__restrict__ hs3, int64_t hstride, int pass) {
   using KT = KeyOf<T>;
   using K = typename KT::K;
   using S = typename BinAcc<T>::S;
@@ -1526,9 +1555,23 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
   constexpr int VW = (int)(sizeof(V) / sizeof(T));  // values per vector load
   constexpr int VPT = 4;                            // vector loads per thread and round
   const JobDev jd = jobs[tl.item];
-  const InstDev &in = insts[jd.inst];
-  InstScal &sc = scal[jd.inst];
+  const InstDev &in = insts[tl.inst];
+  InstScal &sc = scal[tl.inst];
   JobScal &js = jscal[tl.item];
+  // Histograms: with hstride > 0, pass p uses buffer p % 3 and the job's
+  // CTAs clear, one slice each, the buffer of pass p - 1 (whether or not
+  // the job selects in this pass), so every buffer is zero before its next
+  // use; with hstride = 0 one buffer, cleared by the last CTA.
+  if (hstride) {
+    const int64_t zb = (int64_t)((pass + 2) % 3) * hstride + jd.hist_off;
+    const int z0 = (int)((int64_t)tl.seq * kBins / jd.ntiles), z1 = (int)((int64_t)(tl.seq + 1) * kBins / jd.ntiles);
+    for (int i = z0 + (int)threadIdx.x; i < z1; i += kThreads) {
+      hcnt[zb + i] = 0u;
+      hs1[zb + i] = 0.0;
+      hs2[zb + i] = 0.0;
+      hs3[zb + i] = 0.0;
+    }
+  }
   if (sc.done || !js.active || js.mode != JM_SELECT || js.pass != pass) return;
 
   extern __shared__ unsigned char smem_raw[];
@@ -1643,10 +1686,11 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
     }
   }
   __syncthreads();
-  uint32_t *gc = hcnt + jd.hist_off;
-  S *g1 = (S *)(hs1 + jd.hist_off);
-  S *g2 = (S *)(hs2 + jd.hist_off);
-  S *g3 = (S *)(hs3 + jd.hist_off);
+  const int64_t hb = (hstride ? (int64_t)(pass % 3) * hstride : 0) + jd.hist_off;
+  uint32_t *gc = hcnt + hb;
+  S *g1 = (S *)(hs1 + hb);
+  S *g2 = (S *)(hs2 + hb);
+  S *g3 = (S *)(hs3 + hb);
   for (int i = threadIdx.x; i < nbins; i += kThreads) {
     const uint32_t c = cnt[i];
     if (c) {
@@ -1676,6 +1720,7 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
   } else {
     select_choose_f64<T>(jd, js, gc, g1, g2, pass, pre, lo, nbins, need1, need2);
   }
+  if (hstride) return;
   __syncthreads();
   for (int i = threadIdx.x; i < nbins; i += kThreads) {
     gc[i] = 0;
@@ -1692,9 +1737,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__
                                                         InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                         JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
                                                         double *__restrict__ hs1, double *__restrict__ hs2,
-                                                        double *__restrict__ hs3, int pass, unsigned long long *ts) {
+                                                        double *__restrict__ hs3, int64_t hstride, int pass,
+                                                        unsigned long long *ts) {
   const Stamp stamp(ts);
-  body_select<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, hcnt, hs1, hs2, hs3, pass);
+  body_select<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, hcnt, hs1, hs2, hs3, hstride, pass);
 }
 
 // Tie counts per final-pass work item for card sets whose k-th value is tied.
@@ -2178,6 +2224,7 @@ struct FusedArgs {
   JobScal *jscal;
   uint32_t *hcnt;
   double *hs1, *hs2, *hs3;
+  int64_t hstride;
   uint32_t *ties;
   uint32_t *bar;
   const uint32_t *ndone;
@@ -2200,7 +2247,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
     if (A.nt_sel) {
       for (int pass = 0; pass < A.npass; ++pass) {
         for (int i = blockIdx.x; i < A.nt_sel; i += gridDim.x)
-          body_select<T>(A.tsel[i], A.insts, A.scal, A.jobs, A.jscal, A.hcnt, A.hs1, A.hs2, A.hs3, pass);
+          body_select<T>(A.tsel[i], A.insts, A.scal, A.jobs, A.jscal, A.hcnt, A.hs1, A.hs2, A.hs3, A.hstride, pass);
         if (!grid_barrier(A.bar)) return;
       }
     }
@@ -2396,13 +2443,13 @@ cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const Ins
 }
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                           const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
-                          int pass) {
+                          int64_t hstride, int pass) {
   if (L.dtype == SIP_F64)
     k_select<double><<<nt, kThreads, BinAcc<double>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1,
-                                                                       hs2, hs3, pass, L.ts);
+                                                                       hs2, hs3, hstride, pass, L.ts);
   else
     k_select<float><<<nt, kThreads, BinAcc<float>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1, hs2,
-                                                                     hs3, pass, L.ts);
+                                                                     hs3, hstride, pass, L.ts);
   return cudaGetLastError();
 }
 cudaError_t kernels_setup() {
@@ -2470,6 +2517,7 @@ cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
   A.hs1 = F.hs1;
   A.hs2 = F.hs2;
   A.hs3 = F.hs3;
+  A.hstride = F.hstride;
   A.ties = F.ties;
   A.bar = F.bar;
   A.ndone = F.ndone;

@@ -24,9 +24,11 @@ cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstD
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph);
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            JobScal *jscal, const JobDev *jobs);
+// hstride: elements between the three histogram buffers the passes rotate
+// over, or 0 for a single buffer
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                           const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
-                          int pass);
+                          int64_t hstride, int pass);
 // one-time kernel attribute set-up (call outside stream capture)
 cudaError_t kernels_setup();
 // CTAs per SM for the kernels of a work-item list: 0 grid points, 1 set
@@ -44,6 +46,7 @@ struct FusedLaunch {
   JobScal *jscal;
   uint32_t *hcnt;
   double *hs1, *hs2, *hs3;
+  int64_t hstride;
   uint32_t *ties;
   uint32_t *bar;          // 4 words: arrivals, generation, error, unused
   const uint32_t *ndone;  // finished instances
