@@ -757,6 +757,19 @@ __device__ __forceinline__ void cg_scalars(const Tile &tl, const InstDev &in, In
 // z neighbours beyond its 4 come from the adjacent lanes, or, at a warp or
 // tile edge, from single loads.  Same arithmetic per sample as the general
 // step.
+// Vector type of a 16-byte load, and its components by (unrolled) index.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+__device__ __forceinline__ float vat(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vat(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4 &v, int c, float a) {
+  if (c == 0) v.x = a; else if (c == 1) v.y = a; else if (c == 2) v.z = a; else v.w = a;
+}
+__device__ __forceinline__ void vset(double2 &v, int c, double a) {
+  if (c == 0) v.x = a; else v.y = a;
+}
+
 __device__ __forceinline__ float4 ld4(const float *p, int64_t i) { return *reinterpret_cast<const float4 *>(p + i); }
 __device__ __forceinline__ void st4(float *p, int64_t i, const float4 &v) { *reinterpret_cast<float4 *>(p + i) = v; }
 
@@ -987,41 +1000,67 @@ __device__ void setpass_ring(const Tile &tl, const InstDev &in, InstScal &sc, in
   A acc[kMaxHist + 1];
 #pragma unroll
   for (int j = 0; j <= kMaxHist; ++j) acc[j] = A(0);
-  for (int64_t base = tl.start; base < end; base += SUB) {
-    T xv[PT];
+  bool vec = false;
+  if constexpr (sizeof(T) == 4)
+    vec = (N & 3) == 0 && (tl.start & 3) == 0 && (((uintptr_t)x | (uintptr_t)ring) & 15) == 0;
+  if (vec) {
+    if constexpr (sizeof(T) == 4) {
+      // 16-byte accesses: 4 consecutive samples per thread
+      for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4) {
+        const int64_t g0 = base + (int64_t)threadIdx.x * 4;
+        if (g0 >= end) continue;
+        const float4 X = ld4(x, g0);  // N % 4 == 0: no partial group
+        if (chk) {
 #pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
-      if (g < end) xv[e] = x[g];
-    }
-    if (chk) {
-#pragma unroll
-      for (int j = 1; j <= kMaxHist; ++j) {
-        if (j <= jmax) {
-          const int64_t so = (int64_t)((k - j) % H) * N;
-          T hv[PT];
-#pragma unroll
-          for (int e = 0; e < PT; ++e) {
-            const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
-            if (g < end) hv[e] = ring[so + g];
+          for (int j = 1; j <= kMaxHist; ++j) {
+            if (j <= jmax) {
+              const float4 Hv = ld4(ring, (int64_t)((k - j) % H) * N + g0);
+              const A d0 = (A)X.x - (A)Hv.x, d1 = (A)X.y - (A)Hv.y, d2 = (A)X.z - (A)Hv.z, d3 = (A)X.w - (A)Hv.w;
+              acc[j] += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            }
           }
+          acc[0] += (A)X.x * (A)X.x + (A)X.y * (A)X.y + (A)X.z * (A)X.z + (A)X.w * (A)X.w;
+        }
+        st4(ring, wslot + g0, X);
+      }
+    }
+  } else {
+    for (int64_t base = tl.start; base < end; base += SUB) {
+      T xv[PT];
 #pragma unroll
-          for (int e = 0; e < PT; ++e) {
-            const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
-            if (g < end) {
-              const A d = (A)xv[e] - (A)hv[e];
-              acc[j] += d * d;
+      for (int e = 0; e < PT; ++e) {
+        const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+        if (g < end) xv[e] = x[g];
+      }
+      if (chk) {
+#pragma unroll
+        for (int j = 1; j <= kMaxHist; ++j) {
+          if (j <= jmax) {
+            const int64_t so = (int64_t)((k - j) % H) * N;
+            T hv[PT];
+#pragma unroll
+            for (int e = 0; e < PT; ++e) {
+              const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+              if (g < end) hv[e] = ring[so + g];
+            }
+#pragma unroll
+            for (int e = 0; e < PT; ++e) {
+              const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+              if (g < end) {
+                const A d = (A)xv[e] - (A)hv[e];
+                acc[j] += d * d;
+              }
             }
           }
         }
       }
-    }
 #pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
-      if (g < end) {
-        if (chk) acc[0] += (A)xv[e] * (A)xv[e];
-        ring[wslot + g] = xv[e];
+      for (int e = 0; e < PT; ++e) {
+        const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+        if (g < end) {
+          if (chk) acc[0] += (A)xv[e] * (A)xv[e];
+          ring[wslot + g] = xv[e];
+        }
       }
     }
   }
@@ -1032,6 +1071,70 @@ __device__ void setpass_ring(const Tile &tl, const InstDev &in, InstScal &sc, in
   }
 }
 
+// The block's per-iteration scalars, in the storage type.
+template <typename T>
+struct SetpassScal {
+  T rho, irho, gam, one_m_gam, inv1p, lo, hi, ih;
+  int type, kind;
+  bool pointwise, ad, ad_dots, chk;
+};
+
+// What one row stores: the dual update's y and v (point-wise sets) or the
+// prox input w (sets projected after a selection), and the adapt copies.
+template <typename T>
+struct RowOut {
+  T yn, vn, w, vh;
+};
+
+// One row of the set pass: relaxation, prox input, point-wise prox and dual
+// update, adapt-rho-gamma and feasibility partial sums (Algorithm PARSDMM
+// FOR-body; Algorithm adapt-rho-gamma; Eq. feas_stop).
+// Partials: 0..5 adapt dots, 6 feasD2, 7 s2, 8 s1, 9 wnorm.
+template <typename T, typename A>
+__device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T y0, T v0, T mg, T ks, T kvh, T ky,
+                                                 T kv, A (&acc)[10]) {
+  RowOut<T> o;
+  const T xbar = q.gam * s + q.one_m_gam * y0;
+  o.w = xbar - v0 * q.irho;
+  o.vh = T(0);
+  if (q.ad) {
+    // vhat^{k+1} = v^k + rho (y^k - s^{k+1}); dh = s - s^{k0}; dvh = vhat - vhat^{k0}
+    o.vh = v0 + q.rho * (y0 - s);
+    if (q.ad_dots) {
+      const A dh = (A)s - (A)ks;
+      const A dvh = (A)o.vh - (A)kvh;
+      acc[0] += dh * dvh;
+      acc[1] += dh * dh;
+      acc[2] += dvh * dvh;
+    }
+  }
+  if (q.pointwise) {
+    o.yn = q.type == BT_BOUNDS ? fmin(fmax(o.w, q.lo), q.hi) : (mg + q.rho * o.w) * q.inv1p;  // Eq. prox_sq_dist
+    o.vn = v0 + q.rho * (o.yn - xbar);
+    if (q.ad_dots) {
+      const A dg = (A)ky - (A)o.yn;
+      const A dv = (A)o.vn - (A)kv;
+      acc[3] += dg * dv;
+      acc[4] += dg * dg;
+      acc[5] += dv * dv;
+    }
+    if (q.chk && q.type == BT_BOUNDS) {
+      const A d = (A)s - (A)fmin(fmax(s, q.lo), q.hi);
+      acc[6] += d * d;
+      acc[7] += (A)s * (A)s;
+    }
+  } else {
+    o.yn = o.vn = T(0);
+    if (q.type == BT_L2) acc[9] += (A)o.w * (A)o.w;
+    if (q.type == BT_L1) acc[9] += fabs((A)o.w);
+    if (q.chk) {
+      acc[7] += (A)s * (A)s;
+      if (q.type == BT_L1) acc[8] += fabs((A)s);
+    }
+  }
+  return o;
+}
+
 template <typename T>
 __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, const SegDev &sg, int k, bool ad,
                               bool ad_dots, bool chk) {
@@ -1039,14 +1142,24 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   using A = typename AccOf<T>::type;
   const int b = sg.block;
   const BlockDev &bd = in.blk[b];
-  const T rho = SV<T>::blk(sc, b, BF_RHO), irho = SV<T>::blk(sc, b, BF_IRHO);
-  const T gam = SV<T>::blk(sc, b, BF_GAMMA), one_m_gam = SV<T>::blk(sc, b, BF_OMG);
-  const T inv1p = SV<T>::blk(sc, b, BF_INV1P);
-  const T lo = (T)bd.lo, hi = (T)bd.hi;
-  const T ih = seg_ih<T>(in, sg.kind);
-  const int kind = sg.kind;
-  const int type = bd.type;
-  const bool pointwise = type == BT_BOUNDS || type == BT_DIST;
+  SetpassScal<T> q;
+  q.rho = SV<T>::blk(sc, b, BF_RHO);
+  q.irho = SV<T>::blk(sc, b, BF_IRHO);
+  q.gam = SV<T>::blk(sc, b, BF_GAMMA);
+  q.one_m_gam = SV<T>::blk(sc, b, BF_OMG);
+  q.inv1p = SV<T>::blk(sc, b, BF_INV1P);
+  q.lo = (T)bd.lo;
+  q.hi = (T)bd.hi;
+  q.ih = seg_ih<T>(in, sg.kind);
+  q.kind = sg.kind;
+  q.type = bd.type;
+  q.pointwise = bd.type == BT_BOUNDS || bd.type == BT_DIST;
+  q.ad = ad;
+  q.ad_dots = ad_dots;
+  q.chk = chk;
+  const int kind = sg.kind, type = bd.type;
+  const bool pointwise = q.pointwise;
+  const bool store_s = chk && !pointwise && type != BT_L2;
   const T *__restrict__ x = (const T *)in.x;
   T *__restrict__ y = (T *)in.y + bd.yoff + sg.row0;
   T *__restrict__ v = (T *)in.v + bd.yoff + sg.row0;
@@ -1058,83 +1171,139 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   T *__restrict__ k0v = (T *)in.k0v + bd.yoff + sg.row0;
   const T *__restrict__ m = (const T *)in.m;
   const int64_t end = tl.start + tl.len;
-  // partials: 0..5 adapt dots, 6 feasD2, 7 s2, 8 s1, 9 wnorm
   A acc[10];
 #pragma unroll
   for (int j = 0; j < 10; ++j) acc[j] = A(0);
-  for (int64_t base = tl.start; base < end; base += SUB) {
-    T x0[PT], x1[PT], y0[PT], v0[PT], mg[PT];
-    T ks[PT], kvh[PT], ky[PT], kv[PT];
-#pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
-      if (row < end) {
-        int64_t off;
-        const int64_t g = seg_base(in, kind, row, off);
-        x0[e] = x[g];
-        x1[e] = x[g + off];
-        y0[e] = y[row];
-        v0[e] = v[row];
-        if (type == BT_DIST) mg[e] = m[g];
-        if (ad_dots) {
-          ks[e] = k0s[row];
-          kvh[e] = k0vh[row];
-          if (pointwise) {
-            ky[e] = k0y[row];
-            kv[e] = k0v[row];
+  // x gathers of one row: s = A x (Eq. FD_mat) and m at the base sample
+  auto gather = [&](int64_t row, T &sv, T &mv) {
+    int64_t off;
+    const int64_t g = seg_base(in, kind, row, off);
+    const T x0 = x[g];
+    sv = kind == SEG_I ? x0 : (x[g + off] - x0) * q.ih;
+    mv = type == BT_DIST ? m[g] : T(0);
+  };
+  bool vec = false;
+  if constexpr (sizeof(T) == 4) {
+    // 16-byte accesses to the row arrays when they all start on a 16-byte
+    // boundary at this work item
+    uintptr_t al = (uintptr_t)(y + tl.start) | (uintptr_t)(v + tl.start);
+    if (ad) al |= (uintptr_t)(k0s + tl.start) | (uintptr_t)(k0vh + tl.start);
+    if (ad && pointwise) al |= (uintptr_t)(k0y + tl.start) | (uintptr_t)(k0v + tl.start);
+    if (!pointwise) al |= (uintptr_t)(wbuf + tl.start);
+    if (store_s) al |= (uintptr_t)(sbuf + tl.start);
+    vec = (al & 15) == 0;
+  }
+  if (vec) {
+    if constexpr (sizeof(T) == 4) {
+      for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4) {
+        const int64_t r0 = base + (int64_t)threadIdx.x * 4;
+        if (r0 >= end) continue;
+        const bool full = r0 + 4 <= end;
+        float4 Y, V, KS = make_float4(0.f, 0.f, 0.f, 0.f), KVH = KS, KY = KS, KV = KS;
+        auto ld = [&](const float *p) {
+          if (full) return ld4(p, r0);
+          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int c = 0; c < 4; ++c)
+            if (r0 + c < end) vset(t, c, p[r0 + c]);
+          return t;
+        };
+        auto st = [&](float *p, const float4 &t) {
+          if (full) {
+            st4(p, r0, t);
+          } else {
+            for (int c = 0; c < 4; ++c)
+              if (r0 + c < end) p[r0 + c] = vat(t, c);
           }
+        };
+        Y = ld(y);
+        V = ld(v);
+        if (ad_dots) {
+          KS = ld(k0s);
+          KVH = ld(k0vh);
+          if (pointwise) {
+            KY = ld(k0y);
+            KV = ld(k0v);
+          }
+        }
+        float sv[4], mv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          sv[c] = mv[c] = 0.f;
+          if (r0 + c < end) gather(r0 + c, sv[c], mv[c]);
+        }
+        float4 YN, VN, W, VH;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          RowOut<float> o;
+          if (r0 + c < end) {
+            o = setpass_row(q, sv[c], vat(Y, c), vat(V, c), mv[c], vat(KS, c), vat(KVH, c), vat(KY, c), vat(KV, c),
+                            acc);
+          } else {
+            o.yn = o.vn = o.w = o.vh = 0.f;
+          }
+          vset(YN, c, o.yn);
+          vset(VN, c, o.vn);
+          vset(W, c, o.w);
+          vset(VH, c, o.vh);
+        }
+        if (ad) {
+          st(k0s, make_float4(sv[0], sv[1], sv[2], sv[3]));
+          st(k0vh, VH);
+        }
+        if (pointwise) {
+          st(y, YN);
+          st(v, VN);
+          if (ad) {
+            st(k0y, YN);
+            st(k0v, VN);
+          }
+        } else {
+          st(wbuf, W);
+          if (store_s) st(sbuf, make_float4(sv[0], sv[1], sv[2], sv[3]));
         }
       }
     }
+  } else {
+    for (int64_t base = tl.start; base < end; base += SUB) {
+      T sv[PT], mg[PT], y0[PT], v0[PT];
+      T ks[PT], kvh[PT], ky[PT], kv[PT];
 #pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
-      if (row >= end) continue;
-      const T s = kind == SEG_I ? x0[e] : (x1[e] - x0[e]) * ih;
-      const T xbar = gam * s + one_m_gam * y0[e];
-      const T w = xbar - v0[e] * irho;
-      if (ad) {
-        // vhat^{k+1} = v^k + rho (y^k - s^{k+1}); dh = s - s^{k0}; dvh = vhat - vhat^{k0}
-        const T vh = v0[e] + rho * (y0[e] - s);
-        if (ad_dots) {
-          const A dh = (A)s - (A)ks[e];
-          const A dvh = (A)vh - (A)kvh[e];
-          acc[0] += dh * dvh;
-          acc[1] += dh * dh;
-          acc[2] += dvh * dvh;
-        }
-        k0s[row] = s;
-        k0vh[row] = vh;
-      }
-      if (pointwise) {
-        const T yn = type == BT_BOUNDS ? fmin(fmax(w, lo), hi) : (mg[e] + rho * w) * inv1p;  // Eq. prox_sq_dist
-        const T vn = v0[e] + rho * (yn - xbar);
-        y[row] = yn;
-        v[row] = vn;
-        if (ad) {
+      for (int e = 0; e < PT; ++e) {
+        const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+        ks[e] = kvh[e] = ky[e] = kv[e] = T(0);
+        if (row < end) {
+          gather(row, sv[e], mg[e]);
+          y0[e] = y[row];
+          v0[e] = v[row];
           if (ad_dots) {
-            const A dg = (A)ky[e] - (A)yn;
-            const A dv = (A)vn - (A)kv[e];
-            acc[3] += dg * dv;
-            acc[4] += dg * dg;
-            acc[5] += dv * dv;
+            ks[e] = k0s[row];
+            kvh[e] = k0vh[row];
+            if (pointwise) {
+              ky[e] = k0y[row];
+              kv[e] = k0v[row];
+            }
           }
-          k0y[row] = yn;
-          k0v[row] = vn;
         }
-        if (chk && type == BT_BOUNDS) {
-          const A d = (A)s - (A)fmin(fmax(s, lo), hi);
-          acc[6] += d * d;
-          acc[7] += (A)s * (A)s;
+      }
+#pragma unroll
+      for (int e = 0; e < PT; ++e) {
+        const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+        if (row >= end) continue;
+        const RowOut<T> o = setpass_row(q, sv[e], y0[e], v0[e], mg[e], ks[e], kvh[e], ky[e], kv[e], acc);
+        if (ad) {
+          k0s[row] = sv[e];
+          k0vh[row] = o.vh;
         }
-      } else {
-        wbuf[row] = w;
-        if (type == BT_L2) acc[9] += (A)w * (A)w;
-        if (type == BT_L1) acc[9] += fabs((A)w);
-        if (chk) {
-          acc[7] += (A)s * (A)s;
-          if (type == BT_L1) acc[8] += fabs((A)s);
-          if (type != BT_L2) sbuf[row] = s;
+        if (pointwise) {
+          y[row] = o.yn;
+          v[row] = o.vn;
+          if (ad) {
+            k0y[row] = o.yn;
+            k0v[row] = o.vn;
+          }
+        } else {
+          wbuf[row] = o.w;
+          if (store_s) sbuf[row] = sv[e];
         }
       }
     }
@@ -1526,19 +1695,6 @@ __device__ __noinline__ void select_choose_f64(const JobDev &jd, JobScal &js, co
     }
     js.pass = pass + 1;
   }
-}
-
-// Vector type of a 16-byte load, and its components by (unrolled) index.
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; };
-template <> struct Vec16<double> { using type = double2; };
-__device__ __forceinline__ float vat(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
-__device__ __forceinline__ double vat(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
-__device__ __forceinline__ void vset(float4 &v, int c, float a) {
-  if (c == 0) v.x = a; else if (c == 1) v.y = a; else if (c == 2) v.z = a; else v.w = a;
-}
-__device__ __forceinline__ void vset(double2 &v, int c, double a) {
-  if (c == 0) v.x = a; else v.y = a;
 }
 
 template <typename T>
