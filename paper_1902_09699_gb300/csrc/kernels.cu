@@ -409,6 +409,22 @@ struct Stamp {
   }
 };
 
+// Vector type of a 16-byte load, and its components by (unrolled) index.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+__device__ __forceinline__ float vat(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vat(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4 &v, int c, float a) {
+  if (c == 0) v.x = a; else if (c == 1) v.y = a; else if (c == 2) v.z = a; else v.w = a;
+}
+__device__ __forceinline__ void vset(double2 &v, int c, double a) {
+  if (c == 0) v.x = a; else v.y = a;
+}
+
+__device__ __forceinline__ float4 ld4(const float *p, int64_t i) { return *reinterpret_cast<const float4 *>(p + i); }
+__device__ __forceinline__ void st4(float *p, int64_t i, const float4 &v) { *reinterpret_cast<float4 *>(p + i) = v; }
+
 // --------------------------------------------------------------------------
 // x-update right-hand side and warm residual
 // --------------------------------------------------------------------------
@@ -617,6 +633,61 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ ti
 // w_0 use buffer 0, the step launch of phase ph reads buffer ph & 1 and
 // writes the other one.
 // --------------------------------------------------------------------------
+// w_0 = C r_0 on 2D grids with n_z % 4 == 0 and aligned arrays: 4
+// consecutive z samples per thread, z neighbours across lanes (single
+// loads at warp and tile edges), as in the four-sample CG step.
+__device__ __forceinline__ void body_cg_w0_v4(const Tile &tl, const InstDev &in, const InstScal &sc, int done) {
+  constexpr int SUB = kThreads * 4;
+  const unsigned FULL = 0xffffffffu;
+  const float *__restrict__ r = (const float *)in.cr[0];
+  float *__restrict__ w = (float *)in.cw[0];
+  CSys<float> C;
+  C.load(sc);
+  const int lane = threadIdx.x & 31;
+  const int64_t end = tl.start + tl.len;
+  float a0 = 0.f;
+  for (int64_t base = tl.start; base < end; base += SUB) {
+    const int64_t g0 = base + 4 * (int64_t)threadIdx.x;
+    const bool ok = g0 < end;
+    float4 R = make_float4(0.f, 0.f, 0.f, 0.f), RXM = R, RXP = R;
+    float zm = 0.f, zp = 0.f;
+    bool hzm = false, hzp = false, edge_p = false;
+    if (ok) {
+      const GridPos ps = grid_pos(in, g0);
+      R = ld4(r, g0);
+      RXM = ps.ix > 0 ? ld4(r, g0 - in.nz) : R;
+      RXP = ps.ix < in.nx - 1 ? ld4(r, g0 + in.nz) : R;
+      hzm = ps.iz > 0;
+      hzp = ps.iz + 4 < in.nz;
+      edge_p = lane == 31 || g0 + 4 >= end;
+      if (hzm && lane == 0) zm = r[g0 - 1];
+      if (hzp && edge_p) zp = r[g0 + 4];
+    }
+    const float um = __shfl_up_sync(FULL, R.w, 1), up = __shfl_down_sync(FULL, R.x, 1);
+    if (done) return;
+    if (!ok) continue;
+    if (lane != 0) zm = um;
+    if (!edge_p) zp = up;
+    if (!hzm) zm = R.x;
+    if (!hzp) zp = R.w;
+    Nbr<float> nb;
+    float4 W;
+    nb = {R.x, zm, R.y, RXM.x, RXP.x, R.x, R.x};
+    W.x = apply_c(C, nb);
+    nb = {R.y, R.x, R.z, RXM.y, RXP.y, R.y, R.y};
+    W.y = apply_c(C, nb);
+    nb = {R.z, R.y, R.w, RXM.z, RXP.z, R.z, R.z};
+    W.z = apply_c(C, nb);
+    nb = {R.w, R.z, zp, RXM.w, RXP.w, R.w, R.w};
+    W.w = apply_c(C, nb);
+    st4(w, g0, W);
+    a0 += W.x * R.x + W.y * R.y + W.z * R.z + W.w * R.w;
+  }
+  float acc[1] = {a0};
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) cg_part<float>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0
+}
+
 template <typename T>
 __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__restrict__ insts,
                                                        InstScal *__restrict__ scal) {
@@ -625,6 +696,12 @@ __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__rest
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   const int done = sc.done;
+  if constexpr (sizeof(T) == 4) {
+    if ((in.nz & 3) == 0 && in.ny == 1 && (((uintptr_t)in.cr[0] | (uintptr_t)in.cw[0]) & 15) == 0) {
+      body_cg_w0_v4(tl, in, sc, done);
+      return;
+    }
+  }
   const T *__restrict__ r = (const T *)in.cr[0];
   T *__restrict__ w = (T *)in.cw[0];
   CSys<T> C;
@@ -757,21 +834,6 @@ __device__ __forceinline__ void cg_scalars(const Tile &tl, const InstDev &in, In
 // z neighbours beyond its 4 come from the adjacent lanes, or, at a warp or
 // tile edge, from single loads.  Same arithmetic per sample as the general
 // step.
-// Vector type of a 16-byte load, and its components by (unrolled) index.
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; };
-template <> struct Vec16<double> { using type = double2; };
-__device__ __forceinline__ float vat(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
-__device__ __forceinline__ double vat(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
-__device__ __forceinline__ void vset(float4 &v, int c, float a) {
-  if (c == 0) v.x = a; else if (c == 1) v.y = a; else if (c == 2) v.z = a; else v.w = a;
-}
-__device__ __forceinline__ void vset(double2 &v, int c, double a) {
-  if (c == 0) v.x = a; else v.y = a;
-}
-
-__device__ __forceinline__ float4 ld4(const float *p, int64_t i) { return *reinterpret_cast<const float4 *>(p + i); }
-__device__ __forceinline__ void st4(float *p, int64_t i, const float4 &v) { *reinterpret_cast<float4 *>(p + i) = v; }
 
 __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const InstDev &in, InstScal &sc, int ph) {
   constexpr int SUB = kThreads * 4;
@@ -1996,72 +2058,142 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   __shared__ int wcount[kThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t end = tl.start + tl.len;
-  for (int64_t base = tl.start; base < end; base += SUB) {
-    T wv[PT], ky[PT], kv[PT];
-#pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
-      if (row < end) {
-        wv[e] = w[row];
-        if (ad_dots) {
-          ky[e] = k0y[row];
-          kv[e] = k0v[row];
-        }
-      } else {
-        wv[e] = T(0);
-      }
+  // prox of one entry (no tie rank)
+  auto prox = [&](T wv) -> T {
+    if (type == BT_L2) return wv * scale;
+    if (mode == JM_ALL) return wv;
+    if (mode == JM_NONE) return T(0);
+    if (type == BT_L1) {
+      const T a = fabs(wv) - th;
+      return a > T(0) ? copysign(a, wv) : T(0);
     }
-#pragma unroll
-    for (int e = 0; e < PT; ++e) {
-      const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
-      const bool valid = row < end;
-      T yn;
-      if (type == BT_L2) {
-        yn = wv[e] * scale;
-      } else if (mode == JM_ALL) {
-        yn = wv[e];
-      } else if (mode == JM_NONE) {
-        yn = T(0);
-      } else if (type == BT_L1) {
-        const T a = fabs(wv[e]) - th;
-        yn = a > T(0) ? copysign(a, wv[e]) : T(0);
-      } else {
-        // card: keep keys above the k-th key; at the k-th key keep all ties
-        // unless the tie rule must choose (ranked below)
-        const K key = KT::key(wv[e]);
-        yn = (key > K0 || (key == K0 && !tie)) ? wv[e] : T(0);
-      }
-      if (tie) {
-        // rank among tied entries in row order: rows are ordered by
-        // (step, e, thread), so scan this round's flags over the CTA
-        const bool f = valid && KT::key(wv[e]) == K0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) wcount[wid] = __popc(bal);
-        __syncthreads();
-        int pre = 0, total = 0;
-        for (int i = 0; i < kThreads / 32; ++i) {
-          if (i < wid) pre += wcount[i];
-          total += wcount[i];
+    return KT::key(wv) >= K0 ? wv : T(0);  // card, no tie at the k-th key
+  };
+  bool vec = false;
+  if constexpr (sizeof(T) == 4) {
+    uintptr_t al = (uintptr_t)(w + tl.start) | (uintptr_t)(y + tl.start) | (uintptr_t)(v + tl.start);
+    if (ad) al |= (uintptr_t)(k0y + tl.start) | (uintptr_t)(k0v + tl.start);
+    vec = !tie && (al & 15) == 0;
+  }
+  if (vec) {
+    if constexpr (sizeof(T) == 4) {
+      // 16-byte accesses, 4 consecutive rows per thread
+      for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4) {
+        const int64_t r0 = base + (int64_t)threadIdx.x * 4;
+        if (r0 >= end) continue;
+        const bool full = r0 + 4 <= end;
+        auto ld = [&](const float *p) {
+          if (full) return ld4(p, r0);
+          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int c = 0; c < 4; ++c)
+            if (r0 + c < end) vset(t, c, p[r0 + c]);
+          return t;
+        };
+        auto st = [&](float *p, const float4 &t) {
+          if (full) {
+            st4(p, r0, t);
+          } else {
+            for (int c = 0; c < 4; ++c)
+              if (r0 + c < end) p[r0 + c] = vat(t, c);
+          }
+        };
+        const float4 W = ld(w);
+        float4 KY = make_float4(0.f, 0.f, 0.f, 0.f), KV = KY;
+        if (ad_dots) {
+          KY = ld(k0y);
+          KV = ld(k0v);
         }
-        const int64_t rank = before + pre + __popc(bal & ((1u << lane) - 1u));
-        if (f) yn = rank < need ? wv[e] : T(0);
-        before += total;
-        __syncthreads();
-      }
-      if (valid) {
-        const T vn = rho * (yn - wv[e]);
-        y[row] = yn;
-        v[row] = vn;
-        if (ad) {
-          if (ad_dots) {
-            const A dg = (A)ky[e] - (A)yn;
-            const A dv = (A)vn - (A)kv[e];
+        float4 YN, VN;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float wc = vat(W, c);
+          const float yn = prox(wc), vn = rho * (yn - wc);
+          vset(YN, c, yn);
+          vset(VN, c, vn);
+          if (ad_dots && r0 + c < end) {
+            const A dg = (A)vat(KY, c) - (A)yn;
+            const A dv = (A)vn - (A)vat(KV, c);
             acc[0] += dg * dv;
             acc[1] += dg * dg;
             acc[2] += dv * dv;
           }
-          k0y[row] = yn;
-          k0v[row] = vn;
+        }
+        st(y, YN);
+        st(v, VN);
+        if (ad) {
+          st(k0y, YN);
+          st(k0v, VN);
+        }
+      }
+    }
+  } else {
+    for (int64_t base = tl.start; base < end; base += SUB) {
+      T wv[PT], ky[PT], kv[PT];
+#pragma unroll
+      for (int e = 0; e < PT; ++e) {
+        const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+        if (row < end) {
+          wv[e] = w[row];
+          if (ad_dots) {
+            ky[e] = k0y[row];
+            kv[e] = k0v[row];
+          }
+        } else {
+          wv[e] = T(0);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < PT; ++e) {
+        const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
+        const bool valid = row < end;
+        T yn;
+        if (type == BT_L2) {
+          yn = wv[e] * scale;
+        } else if (mode == JM_ALL) {
+          yn = wv[e];
+        } else if (mode == JM_NONE) {
+          yn = T(0);
+        } else if (type == BT_L1) {
+          const T a = fabs(wv[e]) - th;
+          yn = a > T(0) ? copysign(a, wv[e]) : T(0);
+        } else {
+          // card: keep keys above the k-th key; at the k-th key keep all ties
+          // unless the tie rule must choose (ranked below)
+          const K key = KT::key(wv[e]);
+          yn = (key > K0 || (key == K0 && !tie)) ? wv[e] : T(0);
+        }
+        if (tie) {
+          // rank among tied entries in row order: rows are ordered by
+          // (step, e, thread), so scan this round's flags over the CTA
+          const bool f = valid && KT::key(wv[e]) == K0;
+          const unsigned bal = __ballot_sync(0xffffffffu, f);
+          if (lane == 0) wcount[wid] = __popc(bal);
+          __syncthreads();
+          int pre = 0, total = 0;
+          for (int i = 0; i < kThreads / 32; ++i) {
+            if (i < wid) pre += wcount[i];
+            total += wcount[i];
+          }
+          const int64_t rank = before + pre + __popc(bal & ((1u << lane) - 1u));
+          if (f) yn = rank < need ? wv[e] : T(0);
+          before += total;
+          __syncthreads();
+        }
+        if (valid) {
+          const T vn = rho * (yn - wv[e]);
+          y[row] = yn;
+          v[row] = vn;
+          if (ad) {
+            if (ad_dots) {
+              const A dg = (A)ky[e] - (A)yn;
+              const A dv = (A)vn - (A)kv[e];
+              acc[0] += dg * dv;
+              acc[1] += dg * dg;
+              acc[2] += dv * dv;
+            }
+            k0y[row] = yn;
+            k0v[row] = vn;
+          }
         }
       }
     }
