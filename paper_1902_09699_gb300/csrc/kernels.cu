@@ -2384,7 +2384,9 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
       sc.stop_reason = 1;
       atomicAdd(in.ndone, 1u);
     }
-  } else {
+  } else if ((ad && have_k0) || (in.rho_sched && k < in.max_iter)) {
+    // rho / gamma change (an adapt step or a replayed schedule): the block
+    // scalars and the stencil coefficients follow
     double rho_b = b < nb ? s_rho[b] : 1.0, gam_b = b < nb ? s_gam[b] : 1.0;
     if (ad && have_k0) {
       // safeguard: rho_i within a factor R of rho_{p+1} (direct form: of 1)
@@ -2425,12 +2427,14 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
       sc.cx = cx * in.ihx * in.ihx;
       sc.cy = cy * in.ihy * in.ihy;
       store_coef_f32(sc);
-      if (ad) sc.have_k0 = 1;
-      sc.k = k + 1;
-      if (k >= in.max_iter) {
-        sc.done = 1;
-        atomicAdd(in.ndone, 1u);
-      }
+    }
+  }
+  if (!stop && b == 0) {
+    if (ad) sc.have_k0 = 1;
+    sc.k = k + 1;
+    if (k >= in.max_iter) {
+      sc.done = 1;
+      atomicAdd(in.ndone, 1u);
     }
   }
   __syncwarp();
