@@ -376,7 +376,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const size_t W = esize(dtype);
   // ---- sizes
   int64_t njobs = 0, ntie = 0;
-  std::vector<Tile> tn, tset, tsel, tfin;
+  std::vector<Tile> tn, trhs, tset, tsel, tfin;
   P.any_card = P.any_fin = false;
   P.cg_launch = 0;
   P.max_iter = 0;
@@ -396,6 +396,31 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   if (cudaError_t e = kernels_setup()) return fail(SIP_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e));
   const int64_t sms = sm_count();
   const int64_t ch_n = chunk_for(tot_n, sms * launch_occupancy(dtype, 0));
+  // Staged right-hand side for binary32 plans of 2D instances: the y / v
+  // windows of a work item of ch rows take about 8 (rows + halo) bytes per
+  // segment; the largest work item that lets 2 (else 1) CTAs share an SM.
+  int64_t ch_rhs = 0;
+  P.rhs_smem = 0;
+  bool stageable = dtype == SIP_F32 && !insts.empty();
+  for (auto &L : insts) stageable = stageable && L.dev.ny == 1 && L.dev.N < (int64_t(1) << 31);
+  for (int occ = 2; stageable && occ >= 1 && !P.rhs_smem; --occ) {
+    const int64_t ch = chunk_for(tot_n, sms * occ);
+    size_t need = 0;
+    for (auto &L : insts) {
+      size_t b = 0;
+      for (int sgi = 0; sgi < L.dev.nseg; ++sgi) {
+        const int kind = L.dev.seg[sgi].kind;
+        if (kind == SEG_RING) continue;
+        const int64_t win = kind == SEG_DX ? ch + L.dev.nz : ch + 2;
+        b += 2 * sizeof(float) * (size_t)(win + 8);
+      }
+      if (b > need) need = b;
+    }
+    if (need <= kRhsSmemMax && rhs_tma_occupancy(need) >= occ) {
+      P.rhs_smem = need;
+      ch_rhs = ch;
+    }
+  }
   const int64_t ch_set = chunk_for(tot_set, sms * launch_occupancy(dtype, 1));
   const int64_t ch_sel = chunk_for(tot_sel, sms * launch_occupancy(dtype, 2));
   const int64_t ch_fin = chunk_for(tot_fin, sms * launch_occupancy(dtype, 3));
@@ -420,6 +445,13 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     const size_t b0 = tn.size();
     push_tiles(tn, i, 0, d.N, ch_n);
     d.nt_n = (int32_t)(tn.size() - b0);
+    d.nt_rhs = 0;
+    if (P.rhs_smem) {
+      const size_t br = trhs.size();
+      push_tiles(trhs, i, 0, d.N, ch_rhs);
+      d.nt_rhs = (int32_t)(trhs.size() - br);
+    }
+    d.nt_part = d.nt_n > d.nt_rhs ? d.nt_n : d.nt_rhs;
     const size_t b1 = tset.size();
     for (int s = 0; s < d.nseg; ++s) push_tiles(tset, i, s, d.seg[s].len, ch_set);
     d.nt_set = (int32_t)(tset.size() - b1);
@@ -450,6 +482,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   if (P.exec == SIP_EXEC_AUTO) P.exec = SIP_EXEC_GRAPH;
   if (P.exec == SIP_EXEC_PERSISTENT && P.fused_grid <= 0) P.exec = SIP_EXEC_GRAPH;
   P.nt_n = (int)tn.size();
+  P.nt_rhs = (int)trhs.size();
   P.nt_set = (int)tset.size();
   P.nt_sel = (int)tsel.size();
   P.nt_fin = (int)tfin.size();
@@ -489,7 +522,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       offs[i].cs[j] = take(N * W);
     }
     offs[i].cp = take(N * W);
-    offs[i].cgp = take((int64_t)3 * 2 * L.dev.nt_n * W);  // accumulator type = storage type
+    offs[i].cgp = take((int64_t)3 * 2 * L.dev.nt_part * W);  // accumulator type = storage type
     offs[i].ring = take((int64_t)L.dev.hist * N * W);
     offs[i].w = take(L.Mw * W);
     offs[i].s = take(L.Ms * W);
@@ -521,6 +554,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.hist_end = off;
   const int64_t o_ties = take(ntie * 4);
   const int64_t o_tn = take((int64_t)tn.size() * sizeof(Tile));
+  const int64_t o_trhs = take((int64_t)trhs.size() * sizeof(Tile));
   const int64_t o_tset = take((int64_t)tset.size() * sizeof(Tile));
   const int64_t o_tsel = take((int64_t)tsel.size() * sizeof(Tile));
   const int64_t o_tfin = take((int64_t)tfin.size() * sizeof(Tile));
@@ -573,6 +607,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     P.h_insts[i].ndone = P.d_ctrl + 4;
     insts[i].dev.ndone = P.d_ctrl + 4;
     P.layouts[i].dev.ndone = P.d_ctrl + 4;
+    P.h_insts[i].err = insts[i].dev.err = P.layouts[i].dev.err = P.d_ctrl + 2;
   }
   P.d_insts = (InstDev *)at(o_insts);
   P.d_scal = (InstScal *)at(o_scal);
@@ -584,6 +619,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.d_hs3 = (double *)at(o_hs3);
   P.d_ties = (uint32_t *)at(o_ties);
   P.d_tn = (Tile *)at(o_tn);
+  P.d_trhs = trhs.empty() ? nullptr : (Tile *)at(o_trhs);
   P.d_tset = (Tile *)at(o_tset);
   P.d_tsel = (Tile *)at(o_tsel);
   P.d_tfin = (Tile *)at(o_tfin);
@@ -595,6 +631,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   CK(cudaMemcpy(P.d_insts, P.h_insts.data(), P.ninst * sizeof(InstDev), cudaMemcpyHostToDevice));
   if (njobs) CK(cudaMemcpy(P.d_jobs, jobs.data(), njobs * sizeof(JobDev), cudaMemcpyHostToDevice));
   if (!tn.empty()) CK(cudaMemcpy(P.d_tn, tn.data(), tn.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  if (!trhs.empty()) CK(cudaMemcpy(P.d_trhs, trhs.data(), trhs.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   if (!tset.empty()) CK(cudaMemcpy(P.d_tset, tset.data(), tset.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   if (!tsel.empty()) CK(cudaMemcpy(P.d_tsel, tsel.data(), tsel.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   if (!tfin.empty()) CK(cudaMemcpy(P.d_tfin, tfin.data(), tfin.size() * sizeof(Tile), cudaMemcpyHostToDevice));
@@ -626,7 +663,10 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   };
   auto T1 = [&](int) {};
   T0(KT_RHS);
-  CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
+  if (P.rhs_smem)
+    CK(launch_rhs_tma(L, P.d_trhs, P.nt_rhs, P.d_insts, P.d_scal, P.rhs_smem));
+  else
+    CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
   T1(KT_RHS);
   T0(KT_CG_W0);
   CK(launch_cg_w0(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));  // w_0 = C r_0

@@ -269,7 +269,8 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
   CKH(cudaStreamSynchronize(st));
   uint32_t ctrl[8];
   CKH(cudaMemcpy(ctrl, F.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
-  if (ctrl[2] != 0) return fail(SIP_ERR_TIMEOUT, "a grid barrier of the persistent kernel timed out");
+  if (ctrl[2] != 0)
+    return fail(SIP_ERR_TIMEOUT, "a bounded device wait ran out (a grid barrier or a bulk copy did not complete)");
   InstScal sc;
   CKH(cudaMemcpy(&sc, F.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
   if (o.trace) CKH(cudaMemcpy(o.trace, df.trace, (size_t)o.max_iter * df.trace_w * 8, cudaMemcpyDeviceToHost));
@@ -582,7 +583,11 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void
     CKH(cudaEventRecord(h->ev1, st));
     if (!infos && !tm) return SIP_OK;
     CKH(cudaStreamSynchronize(st));
-      if (!infos) return SIP_OK;
+    uint32_t ctrl[8];
+    CKH(cudaMemcpy(ctrl, P.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
+    if (ctrl[2] != 0)
+      return fail(SIP_ERR_TIMEOUT, "a bounded device wait ran out (a grid barrier or a bulk copy did not complete)");
+    if (!infos) return SIP_OK;
     std::vector<InstScal> sc(P.ninst);
     CKH(cudaMemcpy(sc.data(), P.d_scal, P.ninst * sizeof(InstScal), cudaMemcpyDeviceToHost));
     float ms = 0.f;

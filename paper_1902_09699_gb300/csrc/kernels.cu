@@ -430,10 +430,13 @@ __device__ __forceinline__ void st4(float *p, int64_t i, const float4 &v) { *rei
 // --------------------------------------------------------------------------
 // Partial sums of the grid-point launches: slot 0 holds r_0.r_0 of the
 // right-hand side launch; the CG launch of phase ph (1 = w_0, 2, 3, ... = the
-// steps) writes slot 1 + (ph & 1) and reads the slot of phase ph - 1.
+// steps) writes slot 1 + (ph & 1) and reads the slot of phase ph - 1.  A slot
+// has nt_part entries per quantity (the right-hand side may use its own work
+// items); a launch writes entry tl.seq of each of its work items and the
+// entries past them stay zero.
 template <typename A>
 __device__ __forceinline__ A *cg_part(const InstDev &in, int slot, int q) {
-  return (A *)in.cgp + (int64_t)(slot * 2 + q) * in.nt_n;
+  return (A *)in.cgp + (int64_t)(slot * 2 + q) * in.nt_part;
 }
 
 // Rows of a segment that meet at grid point g in (A^T u)[g] (Eq. FD_mat):
@@ -615,6 +618,178 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ ti
 }
 
 // --------------------------------------------------------------------------
+// Staged right-hand side (binary32, 2D): the y and v rows every segment's
+// adjoint reads at this work item's grid points are contiguous windows;
+// one thread moves them into shared memory with bulk copies (the TMA
+// engine, completion counted in bytes on an mbarrier) while the CTA loads
+// its x stencil, then the adjoint differences read shared memory only.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy; both addresses and the size multiples of 16 bytes
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// true once phase `parity` of the barrier completed, false after `polls` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long polls) {
+  for (long long i = 0; i < polls; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+constexpr long long kBulkWaitPolls = 1ll << 22;
+
+// Rows of the window a segment's adjoint reads at grid points [s, e) of a
+// 2D grid (Eq. FD_mat), segment-relative, [lo, hi) inside [0, M).
+__device__ __forceinline__ void rhs_window(const InstDev &in, int kind, int64_t M, int64_t s, int64_t e, int64_t &lo,
+                                           int64_t &hi) {
+  switch (kind) {
+    case SEG_DZ: {  // rows g - g / n_z; a = r - 1, b = r
+      lo = s - (int64_t)fdiv((uint32_t)s, in.fz) - 1;
+      hi = (e - 1) - (int64_t)fdiv((uint32_t)(e - 1), in.fz) + 1;
+      break;
+    }
+    case SEG_DX:  // rows g (2D); a = g - n_z, b = g
+      lo = s - in.nz;
+      hi = e;
+      break;
+    default:  // identity: rows g
+      lo = s;
+      hi = e;
+      break;
+  }
+  if (lo < 0) lo = 0;
+  if (hi > M) hi = M;
+  if (hi < lo) hi = lo;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_rhs_tma(const Tile *__restrict__ tiles,
+                                                         const InstDev *__restrict__ insts,
+                                                         InstScal *__restrict__ scal, unsigned long long *ts) {
+  const Stamp stamp(ts);
+  extern __shared__ __align__(128) float sw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int sbase_y[kMaxSegs], sbase_v[kMaxSegs];  // shared index of row 0 of each segment
+  __shared__ int64_t sg0[kMaxSegs], sgn[kMaxSegs];      // window: first absolute row, rows (multiples of 4)
+  __shared__ float srs[kMaxSegs], sih[kMaxSegs];
+  __shared__ int skind[kMaxSegs];
+  const Tile tl = tiles[blockIdx.x];
+  const InstDev &in = insts[tl.inst];
+  InstScal &sc = scal[tl.inst];
+  const int done = sc.done;
+  const float *__restrict__ x = (const float *)in.x;
+  const float *__restrict__ m = (const float *)in.m;
+  const float *__restrict__ y = (const float *)in.y;
+  const float *__restrict__ v = (const float *)in.v;
+  float *__restrict__ r = (float *)in.cr[0];
+  const int nseg = in.nseg - (in.nseg > 0 && in.seg[in.nseg - 1].kind == SEG_RING ? 1 : 0);
+  const int64_t s0 = tl.start, e0 = tl.start + tl.len;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  if (threadIdx.x < nseg) {
+    const SegDev &sg = in.seg[threadIdx.x];
+    const int64_t bs = in.blk[sg.block].yoff + sg.row0;
+    int64_t lo, hi;
+    rhs_window(in, sg.kind, sg.len, s0, e0, lo, hi);
+    const int64_t a0 = (bs + lo) & ~(int64_t)3, a1 = (bs + hi + 3) & ~(int64_t)3;
+    sg0[threadIdx.x] = a0;
+    sgn[threadIdx.x] = hi > lo ? a1 - a0 : 0;
+    skind[threadIdx.x] = sg.kind;
+    srs[threadIdx.x] = SV<float>::blk(sc, sg.block, BF_RHO);
+    sih[threadIdx.x] = seg_ih<float>(in, sg.kind);
+    // row i of the segment sits at shared index (window offset) + bs - a0 + i;
+    // bs - a0 is about -lo, so the base may lie before the window
+    sbase_y[threadIdx.x] = (int)(bs - a0);
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  if (done) return;  // no copy was issued
+  if (threadIdx.x == 0) {
+    // y windows back to back, then the v windows
+    int64_t tot = 0;
+    for (int j = 0; j < nseg; ++j) tot += sgn[j];
+    mbar_expect_tx(&bar, (uint32_t)(2 * tot * sizeof(float)));
+    int64_t oy = 0;
+    for (int j = 0; j < nseg; ++j) {
+      const int64_t n = sgn[j];
+      if (n) {
+        bulk_g2s(sw + oy, y + sg0[j], (uint32_t)(n * sizeof(float)), &bar);
+        bulk_g2s(sw + tot + oy, v + sg0[j], (uint32_t)(n * sizeof(float)), &bar);
+      }
+      sbase_v[j] = (int)(tot + oy) + sbase_y[j];
+      sbase_y[j] += (int)oy;
+      oy += n;
+    }
+  }
+  CSys<float> C;
+  C.load(sc);
+  const int alg1 = in.alg1;
+  const int nz = in.nz;
+  float a1 = 0.f;
+  bool waited = false;
+  for (int64_t g = s0 + threadIdx.x; g < e0 + threadIdx.x; g += kThreads) {
+    // (every thread runs the same number of rounds; the first round waits)
+    const bool ok = g < e0;
+    GridPos pos;
+    Nbr<float> xn;
+    float b = 0.f;
+    if (ok) {
+      pos = grid_pos(in, g);
+      if (!alg1) b = m[g];
+      load_nbr<float>(in, pos, g, [&](int64_t i) { return x[i]; }, xn);
+    }
+    if (!waited) {
+      __syncthreads();  // sbase_* written by thread 0
+      const bool late = !mbar_wait(&bar, 0, kBulkWaitPolls);
+      if (__syncthreads_or(late)) {  // the same decision in every thread
+        if (threadIdx.x == 0) atomicExch(in.err, (uint32_t)SIP_ERR_TIMEOUT);
+        mbar_wait(&bar, 0, kBulkWaitPolls);  // the copies in flight land before the CTA ends
+        return;
+      }
+      waited = true;
+    }
+    if (!ok) continue;
+    const int gi = (int)g;
+    const int rz = gi - (int)pos.t;  // D_z row base (iz + (nz-1) t)
+    for (int j = 0; j < nseg; ++j) {
+      const float *__restrict__ ys = sw + sbase_y[j];
+      const float *__restrict__ vs = sw + sbase_v[j];
+      const float rho = srs[j], ih = sih[j];
+      // (A^T u)[g] = u[ia] (if fa) - u[ib] (if fb), times 1/h
+      int ia = gi, ib = gi;
+      bool fa = true, fb = false;
+      switch (skind[j]) {
+        case SEG_DZ: ia = rz - 1; ib = rz; fa = pos.iz >= 1; fb = pos.iz <= nz - 2; break;
+        case SEG_DX: ia = gi - nz; ib = gi; fa = pos.ix >= 1; fb = pos.ix <= in.nx - 2; break;
+        default: break;
+      }
+      const float ua = fa ? rho * ys[ia] + vs[ia] : 0.f;
+      const float ub = fb ? rho * ys[ib] + vs[ib] : 0.f;
+      b += (ua - ub) * ih;
+    }
+    const float rv = b - apply_c(C, xn);
+    r[g] = rv;
+    a1 += rv * rv;
+  }
+  float acc[1] = {a1};
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) cg_part<float>(in, 0, 0)[tl.seq] = acc[0];
+}
+
+// --------------------------------------------------------------------------
 // Conjugate gradient on C x = b from the warm start x (Sec. "Solving the
 // linear system and automatic parameter selection"), in the Chronopoulos-Gear
 // arrangement of the CG recurrences: with w = C r and s = C p kept as
@@ -761,7 +936,7 @@ __device__ __forceinline__ void cg_scalars(const Tile &tl, const InstDev &in, In
                                            int *s_go) {
   using A = typename AccOf<T>::type;
   using G = CgOf<T>;
-  const int nt = in.nt_n;
+  const int nt = in.nt_part;  // entries past a launch's own work items stay zero
   const int done = *(volatile const int *)&sc.done;
   T t[2] = {T(0), T(0)};
   CgState *pv = &sc.cg[(ph - 1) & 1];
@@ -2720,6 +2895,19 @@ cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev
   SIP_DISPATCH(L, k_rhs, nt, kThreads, 0, tiles, insts, scal, L.ts);
   return cudaGetLastError();
 }
+cudaError_t launch_rhs_tma(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                           size_t smem) {
+  k_rhs_tma<<<nt, kThreads, smem, L.stream>>>(tiles, insts, scal, L.ts);
+  return cudaGetLastError();
+}
+int rhs_tma_occupancy(size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rhs_tma, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
 cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
   SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal, L.ts);
   return cudaGetLastError();
@@ -2752,6 +2940,8 @@ cudaError_t kernels_setup() {
                                        (int)BinAcc<float>::kSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_select<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rhs_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRhsSmemMax);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<float>::kSmem);
   if (e != cudaSuccess) return e;

@@ -145,6 +145,8 @@ struct InstDev {
   int64_t N;
   int32_t nb, p, alg1, nseg, njob, job0;
   int32_t nt_n, nt_set, nt_fin;
+  int32_t nt_rhs;            // work items of the staged right-hand side list (0: none)
+  int32_t nt_part;           // per-tile partial sums per quantity: max(nt_n, nt_rhs)
   int32_t hist;              // evol_hist
   // options
   int32_t max_iter, cg_iters, cg_max, check_every, stop, adapt, adapt_every;
@@ -152,6 +154,7 @@ struct InstDev {
   const double *rho_sched, *gamma_sched;  // device copies, may be null
   double *trace;             // device trace rows, may be null
   uint32_t *ndone;           // plan-wide count of finished instances
+  uint32_t *err;             // plan-wide device error word (a bounded wait that ran out)
   int32_t trace_w;
   int32_t pad;
   // device arrays, element type = the plan's dtype

@@ -63,6 +63,10 @@ struct Plan {
   uint32_t *d_ties = nullptr;
   Tile *d_tn = nullptr, *d_tset = nullptr, *d_tsel = nullptr, *d_tfin = nullptr;
   int nt_n = 0, nt_set = 0, nt_sel = 0, nt_fin = 0, njobs = 0;
+  // staged right-hand side: its own work items and shared-memory bytes (0: not staged)
+  Tile *d_trhs = nullptr;
+  int nt_rhs = 0;
+  size_t rhs_smem = 0;
   bool any_card = false, any_fin = false, any_stop = false;
   int cg_launch = 0, max_iter = 0, check_every = 1;
   std::vector<InstDev> h_insts;

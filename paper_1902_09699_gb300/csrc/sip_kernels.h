@@ -19,6 +19,12 @@ struct Launch {
 cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, int ninst);
 cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+// staged right-hand side (binary32, 2D instances): `smem` bytes of y / v
+// windows per CTA, at most kRhsSmemMax
+constexpr size_t kRhsSmemMax = 200 * 1024;
+cudaError_t launch_rhs_tma(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                           size_t smem);
+int rhs_tma_occupancy(size_t smem);
 cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 // ph: 2 for the first step launch of an iteration, then 3, 4, ...
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph);

@@ -57,9 +57,12 @@ def test_batch_matches_oracle_fixed_rho():
 
 @pytest.mark.parametrize("dt,tol", [("f64", 1e-10), ("f32", 1e-5)])
 def test_batch_equals_one_at_a_time(dt, tol):
-    """Each result alone and in the mix is the same."""
+    """Each result alone and in the mix is the same.  Binary32 runs with
+    fixed rho: alone and in a batch an instance's sums round differently
+    (other work items), and adapt-rho-gamma's threshold tests can branch
+    differently on one-ulp differences."""
     inst, models = mixed_instances()
-    opts = dict(max_iter=60, adapt=1, gamma0=1.5)
+    opts = dict(max_iter=60, adapt=1, gamma0=1.5) if dt == "f64" else dict(max_iter=40, adapt=0, gamma0=1.5)
     bp = sip.BatchProjector(inst, dtype=dt, **opts)
     xs, _ = bp.project(models)
     for i, ((grid, sets), m) in enumerate(zip(inst, models)):
