@@ -131,6 +131,13 @@ typedef struct {
      * barriers between phases).  Results are the same up to rounding order
      * of the binary64 atomics. */
     int exec;
+    /* Top-k selections of cardinality sets (Sec. Notation: projection onto
+     * {card(A x) <= k}): 1 (default) starts each iteration's selection from
+     * a window around the previous iteration's k-th value; the set pass
+     * collects the entries inside it and, when the k-th value falls inside,
+     * one CTA selects it there instead of the full radix passes.  0: radix
+     * passes only.  The selected key, and so the result, is the same. */
+    int select_window;
 } sip_options;
 
 #define SIP_EXEC_AUTO 0
@@ -149,6 +156,8 @@ typedef struct {
     double sigma[SIP_MAX_SETS];  /* resolved radii (finest level) */
     int64_t k[SIP_MAX_SETS];     /* resolved cardinalities (finest level) */
     float ms;           /* device time of the projection (CUDA events) */
+    int window_hits;    /* top-k selections resolved inside their window
+                           (summed over the cardinality sets and iterations) */
 } sip_info;
 
 typedef struct sip_handle sip_handle;
@@ -157,7 +166,7 @@ typedef struct sip_handle sip_handle;
  * max_iter 200, cg_iters 5, cg_max 100, eps_feas 1e-3, eps_evol 1e-2,
  * check_every 5, evol_hist 5, stop 0, adapt 1, adapt_every 2, rho0 1,
  * gamma0 1.5, eps_corr 0.3, rho_ratio_max 1e3, gamma_max 1.99,
- * form ALG1, dtype F32, levels 1. */
+ * form ALG1, dtype F32, levels 1, select_window 1. */
 void sip_options_default(sip_options *opts);
 
 /* Build a projector for one grid and set list.  Validates every argument,

@@ -160,6 +160,7 @@ static sip_status check_opts(const sip_options &o) {
     return fail(SIP_ERR_INVALID_ARG, "schedules and traces are single-level only");
   if (o.gamma_schedule && !o.rho_schedule) return fail(SIP_ERR_INVALID_ARG, "gamma_schedule needs rho_schedule");
   if (o.exec < SIP_EXEC_AUTO || o.exec > SIP_EXEC_PERSISTENT) return fail(SIP_ERR_INVALID_ARG, "unknown exec mode");
+  if (o.select_window != 0 && o.select_window != 1) return fail(SIP_ERR_INVALID_ARG, "select_window must be 0 or 1");
   return SIP_OK;
 }
 
@@ -221,6 +222,7 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
   d.eps_corr = o.eps_corr;
   d.rho_ratio_max = o.rho_ratio_max;
   d.gamma_max = o.gamma_max;
+  d.select_window = o.select_window;
 
   int64_t yoff = 0, woff = 0, soff = 0;
   int nseg = 0;
@@ -553,6 +555,12 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const int64_t o_hs3 = take(3 * (int64_t)njobs * kBins * 8);
   P.hist_end = off;
   const int64_t o_ties = take(ntie * 4);
+  // window candidates (keys, W bytes each) of the top-k w-jobs
+  int64_t ncand = 0;
+  for (auto &L : insts)
+    for (auto &j : L.jobs)
+      if (j.kind == JOB_TOPK && !j.feas) ncand += kWinCap;
+  const int64_t o_cand = take(ncand * W);
   const int64_t o_tn = take((int64_t)tn.size() * sizeof(Tile));
   const int64_t o_trhs = take((int64_t)trhs.size() * sizeof(Tile));
   const int64_t o_tset = take((int64_t)tset.size() * sizeof(Tile));
@@ -625,8 +633,15 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.d_tfin = (Tile *)at(o_tfin);
 
   std::vector<JobDev> jobs;
+  int64_t cand_at = o_cand;
   for (auto &L : insts)
-    for (auto &j : L.jobs) jobs.push_back(j);
+    for (auto &j : L.jobs) {
+      jobs.push_back(j);
+      if (j.kind == JOB_TOPK && !j.feas) {
+        jobs.back().cand = at(cand_at);
+        cand_at += (int64_t)kWinCap * W;
+      }
+    }
   CK(cudaMemset(P.arena, 0, (size_t)off));
   CK(cudaMemcpy(P.d_insts, P.h_insts.data(), P.ninst * sizeof(InstDev), cudaMemcpyHostToDevice));
   if (njobs) CK(cudaMemcpy(P.d_jobs, jobs.data(), njobs * sizeof(JobDev), cudaMemcpyHostToDevice));
@@ -843,7 +858,7 @@ sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm) {
   }
   CK(cudaMemsetAsync(base + P.hist_begin, 0, (size_t)(P.hist_end - P.hist_begin), st));
   CK(cudaMemsetAsync(P.d_ctrl, 0, 8 * sizeof(uint32_t), st));
-  CK(launch_init(L, P.d_insts, P.d_scal, P.ninst));
+  CK(launch_init(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst));
   CK(launch_norms(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal));
   return SIP_OK;
 }

@@ -133,6 +133,7 @@ void sip_options_default(sip_options *o) {
   o->dtype = SIP_F32;
   o->levels = 1;
   o->coarse_iter = 0;
+  o->select_window = 1;
 }
 
 const char *sip_last_error(const sip_handle *h) {
@@ -293,6 +294,7 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     info->ms = ms;
+    info->window_hits = sc.win_hits;
   }
   if (sc.stop_reason < 0) return fail(SIP_ERR_NONFINITE, "the model holds NaN or Inf");
   return SIP_OK;
@@ -612,6 +614,7 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void
         f.gamma[b] = sc[i].gamma[b];
       }
       f.ms = ms;
+      f.window_hits = sc[i].win_hits;
       if (sc[i].stop_reason < 0) nonfinite = true;
     }
     if (nonfinite) return fail(SIP_ERR_NONFINITE, "a model holds NaN or Inf");

@@ -1374,7 +1374,8 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
 
 template <typename T>
 __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, const SegDev &sg, int k, bool ad,
-                              bool ad_dots, bool chk) {
+                              bool ad_dots, bool chk, JobScal *__restrict__ jscal,
+                              const JobDev *__restrict__ jobs) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
   const int b = sg.block;
@@ -1411,6 +1412,43 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   A acc[10];
 #pragma unroll
   for (int j = 0; j < 10; ++j) acc[j] = A(0);
+  // top-k window (card w-job): count the keys above it, store the keys in it
+  using KT = KeyOf<T>;
+  using K = typename KT::K;
+  bool win = false;
+  K wlo = 0, whi = 0;
+  K *__restrict__ cand = nullptr;
+  uint32_t *wn = nullptr;
+  uint32_t above = 0;
+  if (type == BT_CARD && bd.job_w >= 0) {
+    JobScal &js = jscal[bd.job_w];
+    if (js.win_on) {
+      win = true;
+      wlo = KT::key((T)js.win_lo);
+      whi = KT::key((T)js.win_hi);
+      cand = (K *)jobs[bd.job_w].cand;
+      wn = &js.win_n;
+    }
+  }
+  // called by every active lane of the warp (warp-aggregated slot claims)
+  auto classify = [&](T wv, bool valid) {
+    const K key = KT::key(wv);
+    if (valid && key > whi) ++above;
+    const bool inw = valid && key >= wlo && key <= whi;
+    const unsigned am = __activemask();
+    const unsigned bal = __ballot_sync(am, inw);
+    if (bal) {
+      const int lane = threadIdx.x & 31;
+      const int leader = __ffs(bal) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(wn, (uint32_t)__popc(bal));
+      base = __shfl_sync(am, base, leader);
+      if (inw) {
+        const uint32_t pos = base + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+        if (pos < (uint32_t)kWinCap) cand[pos] = key;
+      }
+    }
+  };
   // x gathers of one row: s = A x (Eq. FD_mat) and m at the base sample
   auto gather = [&](int64_t row, T &sv, T &mv) {
     int64_t off;
@@ -1478,6 +1516,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           } else {
             o.yn = o.vn = o.w = o.vh = 0.f;
           }
+          if (win) classify(o.w, r0 + c < end);
           vset(YN, c, o.yn);
           vset(VN, c, o.vn);
           vset(W, c, o.w);
@@ -1527,6 +1566,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
         const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
         if (row >= end) continue;
         const RowOut<T> o = setpass_row(q, sv[e], y0[e], v0[e], mg[e], ks[e], kvh[e], ky[e], kv[e], acc);
+        if (win) classify(o.w, true);
         if (ad) {
           k0s[row] = sv[e];
           k0vh[row] = o.vh;
@@ -1576,6 +1616,16 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
     block_sum<1>(d1);
     if (threadIdx.x == 0) atomicAdd(&a[A_WNORM], (double)d1[0]);
   }
+  if (win) {
+    __shared__ uint32_t s_above;
+    if (threadIdx.x == 0) s_above = 0;
+    __syncthreads();
+    const uint32_t wa = __reduce_add_sync(0xffffffffu, above);
+    if ((threadIdx.x & 31) == 0 && wa) atomicAdd(&s_above, wa);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_above)
+      atomicAdd((unsigned long long *)&jscal[bd.job_w].win_above, (unsigned long long)s_above);
+  }
 }
 
 template <typename T>
@@ -1593,7 +1643,7 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
   if (sg.kind == SEG_RING)
     setpass_ring<T>(tl, in, sc, k, chk);
   else
-    setpass_block<T>(tl, in, sc, sg, k, ad, ad_dots, chk);
+    setpass_block<T>(tl, in, sc, sg, k, ad, ad_dots, chk, jscal, jobs);
 
   // The last CTA of the instance resolves the l2 scales and arms the
   // selection jobs of this iteration, one block per lane of warp 0.
@@ -1645,7 +1695,6 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
       js.mode = js.k == 0 ? JM_NONE : (js.k >= bd.M ? JM_ALL : JM_SELECT);
     }
   }
-  (void)jobs;
 }
 
 template <typename T>
@@ -1934,6 +1983,101 @@ __device__ __noinline__ void select_choose_f64(const JobDev &jd, JobScal &js, co
   }
 }
 
+// Top-k from the window candidates (one CTA): the k-th key overall is the
+// (k - above)-th largest candidate when above < k <= above + n.  Radix
+// passes over the candidates in shared memory, from the highest bit in
+// which the window's bounds differ (all candidates share the bits above
+// it).  Leaves the job as the last radix pass does.
+static_assert((size_t)kWinCap * sizeof(uint32_t) + kBins * sizeof(uint32_t) <= BinAcc<float>::kSmem,
+              "binary32 window candidates fit the select kernel's shared memory");
+static_assert((size_t)kWinCap * sizeof(uint64_t) + kBins * sizeof(uint32_t) <= BinAcc<double>::kSmem,
+              "binary64 window candidates fit the select kernel's shared memory");
+template <typename T>
+__device__ __noinline__ void select_window_finish(const JobDev &jd, JobScal &js, unsigned char *smem) {
+  using KT = KeyOf<T>;
+  using K = typename KT::K;
+  using U = unsigned long long;
+  constexpr int kKeyBits = (int)sizeof(K) * 8;
+  K *ck = (K *)smem;
+  uint32_t *h = (uint32_t *)(smem + (size_t)kWinCap * sizeof(K));
+  __shared__ U wsumi[kThreads / 32];
+  __shared__ U s_above;
+  __shared__ uint32_t s_cnt;
+  __shared__ int s_bin;
+  const int n = (int)js.win_n;
+  const K *cand = (const K *)jd.cand;
+  for (int i = threadIdx.x; i < n; i += kThreads) ck[i] = __ldcg(&cand[i]);
+  const K wlo = KT::key((T)js.win_lo), whi = KT::key((T)js.win_hi);
+  const K diff = wlo ^ whi;
+  int top = 0;  // bits below `top` vary among the candidates
+  if (diff) top = kKeyBits - (sizeof(K) == 8 ? __clzll((long long)diff) : __clz((int)diff));
+  K pre = wlo;
+  U need = (U)js.k - js.win_above;  // rank among the candidates, 1..n
+  U above_c = 0;                    // candidates above the k-th key
+  uint32_t cK = (uint32_t)n;        // candidates equal to it
+  __syncthreads();
+  while (top > 0) {
+    const int lo = top > kDigitBits ? top - kDigitBits : 0;
+    const int nbins = 1 << (top - lo);
+    for (int i = threadIdx.x; i < nbins; i += kThreads) h[i] = 0u;
+    if (threadIdx.x == 0) s_bin = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+      const K key = ck[i];
+      if ((key >> top) == (pre >> top)) atomicAdd(&h[(int)((key >> lo) & (K)(nbins - 1))], 1u);
+    }
+    __syncthreads();
+    uint32_t c[kPer];
+    U tc = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int bi = threadIdx.x * kPer + j;
+      c[j] = bi < nbins ? h[bi] : 0u;
+      tc += c[j];
+    }
+    U ac = cta_suffix_u64(tc, wsumi) - tc;  // candidates in the bins above this thread's
+    int best = -1;
+    U bab = 0;
+    uint32_t bcnt = 0;
+#pragma unroll
+    for (int j = kPer - 1; j >= 0; --j) {
+      const U cge = ac + c[j];
+      if (best < 0 && threadIdx.x * kPer + j < nbins && cge >= need) {
+        best = threadIdx.x * kPer + j;
+        bab = ac;
+        bcnt = c[j];
+      }
+      ac = cge;
+    }
+    const int wb = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0 && wb >= 0) atomicMax(&s_bin, wb);
+    __syncthreads();
+    if (best >= 0 && best == s_bin) {
+      s_above = bab;
+      s_cnt = bcnt;
+    }
+    __syncthreads();
+    need -= s_above;
+    above_c += s_above;
+    cK = s_cnt;
+    pre = (K)((pre >> top) << top) | ((K)s_bin << lo);
+    top = lo;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const U nab = js.win_above + above_c;
+    js.n_above = nab;
+    js.c_above = (double)nab;
+    js.prefix = (uint64_t)pre;
+    js.need = js.k - (int64_t)nab;
+    js.cK = (int64_t)cK;
+    js.kval = KT::val(pre);
+    js.tie_needed = (js.need < js.cK && pre != 0) ? 1 : 0;
+    js.pass = (KT::kBits + kDigitBits - 1) / kDigitBits;  // past the last radix pass
+    js.win_hit = 1;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__restrict__ insts,
                                                         InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
@@ -1966,8 +2110,17 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
     }
   }
   if (sc.done || !js.active || js.mode != JM_SELECT || js.pass != pass) return;
-
   extern __shared__ unsigned char smem_raw[];
+  if (pass == 0 && jd.kind == JOB_TOPK && !jd.feas && js.win_on) {
+    // the k-th key inside this iteration's window: one CTA selects it from
+    // the candidates, the radix passes are skipped
+    const unsigned long long n = js.win_n, above = js.win_above, kk = (unsigned long long)js.k;
+    if (n <= (unsigned long long)kWinCap && above < kk && kk <= above + n) {
+      if (tl.seq == 0) select_window_finish<T>(jd, js, smem_raw);
+      return;
+    }
+  }
+
   uint32_t *cnt = (uint32_t *)smem_raw;
   // binary32: 12-bit chunk sums u[0..1] of sig, u[2..5] of sig^2
   uint32_t *u = cnt + kBins;
@@ -2429,7 +2582,7 @@ __device__ __forceinline__ double spectral(double ab, double aa, double bb) {
 constexpr int kTailWarps = 8;
 
 __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ insts, InstScal *__restrict__ scal,
-                                          const JobScal *__restrict__ jscal, int cg_launch) {
+                                          JobScal *__restrict__ jscal, int cg_launch) {
   const InstDev &in = insts[i];
   InstScal &sc = scal[i];
   if (sc.done) return;
@@ -2613,6 +2766,35 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
     }
   }
   __syncwarp();
+  // top-k selection windows: re-centre on this iteration's k-th value, widen
+  // after a miss, narrow after an overflow or a crowded hit; clear the counts
+  {
+    bool hit = false;
+    if (b < nb && in.blk[b].type == BT_CARD && in.blk[b].job_w >= 0) {
+      JobScal &js = jscal[in.blk[b].job_w];
+      hit = js.win_hit != 0;
+      if (in.select_window && js.active && js.mode == JM_SELECT) {
+        double r = js.win_rel;
+        if (js.win_on) {
+          if (hit)
+            r = js.win_n > kWinCap / 4 ? 0.5 * r : r;
+          else
+            r = js.win_n > kWinCap ? 0.25 * r : 2.0 * r;
+        }
+        r = fmin(fmax(r, kWinRelMin), kWinRelMax);
+        const double kv = js.kval;
+        js.win_rel = r;
+        js.win_on = kv > 0.0 ? 1 : 0;
+        js.win_lo = kv * (1.0 - r);
+        js.win_hi = kv * (1.0 + r);
+      }
+      js.win_n = 0;
+      js.win_above = 0;
+      js.win_hit = 0;
+    }
+    const unsigned hits = __ballot_sync(FULL, hit);
+    if (b == 0 && hits) sc.win_hits += __popc(hits);
+  }
   // clear the per-iteration accumulators
   double *acc = &sc.acc[0][0];
   for (int j = b; j < kMaxBlocks * kNAcc; j += 32) acc[j] = 0.0;
@@ -2621,7 +2803,7 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
 
 __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restrict__ insts,
                                                           InstScal *__restrict__ scal,
-                                                          const JobScal *__restrict__ jscal, int ninst,
+                                                          JobScal *__restrict__ jscal, int ninst,
                                                           int cg_launch, unsigned long long *ts) {
   const Stamp stamp(ts);
   if ((int)blockIdx.x >= ninst) return;
@@ -2739,7 +2921,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
 // ==========================================================================
 namespace sip {
 
-__global__ void k_init(const InstDev *__restrict__ insts, InstScal *__restrict__ scal, int ninst) {
+__global__ void k_init(const InstDev *__restrict__ insts, InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
+                       int ninst) {
   const int i = blockIdx.x;
   if (i >= ninst) return;
   const InstDev &in = insts[i];
@@ -2757,6 +2940,15 @@ __global__ void k_init(const InstDev *__restrict__ insts, InstScal *__restrict__
   sc.have_k0 = 0;
   sc.nonfinite = 0;
   sc.cnt_set = sc.cnt_norm = 0;
+  sc.win_hits = 0;
+  for (int j = 0; j < in.njob; ++j) {  // selection windows start closed
+    JobScal &js = jscal[in.job0 + j];
+    js.win_on = js.win_hit = 0;
+    js.win_n = 0;
+    js.win_above = 0;
+    js.win_lo = js.win_hi = 0.0;
+    js.win_rel = kWinRel0;
+  }
   for (int j = 0; j < 2; ++j) sc.cg[j] = CgState{0.0, 0.0, 0.0, 0.f, 0.f, 0.f, 0, 0};
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   for (int b = 0; b < kMaxSets; ++b) sc.r_feas[b] = nan;
@@ -2883,8 +3075,8 @@ static unsigned grid_for(int64_t n) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, int ninst) {
-  k_init<<<ninst, 32, 0, L.stream>>>(insts, scal, ninst);
+cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, JobScal *jscal, int ninst) {
+  k_init<<<ninst, 32, 0, L.stream>>>(insts, scal, jscal, ninst);
   return cudaGetLastError();
 }
 cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
@@ -3039,7 +3231,7 @@ cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstD
   SIP_DISPATCH(L, k_final, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties, L.ts);
   return cudaGetLastError();
 }
-cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst,
+cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, JobScal *jscal, int ninst,
                         int cg_launch) {
   k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst, cg_launch, L.ts);
   return cudaGetLastError();

@@ -260,6 +260,7 @@ bool advance(sip_server *S, Cohort *c) {
     f.iters = sc.iters;
     f.cg_steps_total = sc.cg_total;
     f.stop_reason = sc.stop_reason;
+    f.window_hits = sc.win_hits;
     f.nblocks = c->P.h_insts[i].nb;
     f.r_evol = sc.r_evol;
     for (int b = 0; b < c->P.h_insts[i].p; ++b) {

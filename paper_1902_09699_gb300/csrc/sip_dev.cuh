@@ -117,7 +117,15 @@ struct JobDev {
   int64_t hist_off;   // into the histogram arrays (kBins per job)
   int64_t tie_off;    // into the tie-count array (one per tile)
   int32_t ntiles;
+  int32_t pad;
+  void *cand;         // card w-jobs: kWinCap window candidates (keys), else null
 };
+
+// Window candidates per cardinality job (keys of |w| inside the window),
+// and the window's half-width relative to the last k-th value: initial,
+// smallest and largest.
+constexpr int kWinCap = 4096;
+constexpr double kWinRel0 = 1.0 / 32, kWinRelMin = 1.0 / 4096, kWinRelMax = 0.5;
 
 struct JobScal {
   int32_t active, mode, pass, tie_needed;
@@ -134,6 +142,19 @@ struct JobScal {
   double kval;        // card: |value| of the final key
   float thetaf;       // theta in binary32
   int32_t pad2;
+  // Warm-started window of the top-k selection (card w-jobs).  The set pass
+  // counts the entries with |w| above win_hi and stores the keys inside
+  // [win_lo, win_hi] (bounds rounded to the storage type); when the k-th key
+  // falls inside, one CTA selects it from the candidates and the radix
+  // passes are skipped.  The tail re-centres the window on each iteration's
+  // k-th value.
+  double win_lo, win_hi;   // window bounds on |w|
+  double win_rel;          // half-width relative to the last k-th value
+  uint64_t win_above;      // entries above the window (this iteration)
+  uint32_t win_n;          // entries inside the window (may exceed kWinCap)
+  int32_t win_on;          // the set pass collects
+  int32_t win_hit;         // this iteration's selection came from the window
+  int32_t pad3;
 };
 
 struct InstDev {
@@ -156,7 +177,7 @@ struct InstDev {
   uint32_t *ndone;           // plan-wide count of finished instances
   uint32_t *err;             // plan-wide device error word (a bounded wait that ran out)
   int32_t trace_w;
-  int32_t pad;
+  int32_t select_window;     // option: warm-started window for top-k selections
   // device arrays, element type = the plan's dtype
   const void *m;
   void *x, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;
@@ -190,6 +211,8 @@ struct InstScal {
   int32_t cg_steps, cg_total;  // CG steps of the last iteration; of the run
   int32_t have_k0, nonfinite;
   uint32_t cnt_set, cnt_norm;
+  int32_t win_hits;     // top-k selections resolved from their window (run total)
+  int32_t pad_w;
   CgState cg[2];
   double rho[kMaxBlocks], gamma[kMaxBlocks], irho[kMaxBlocks], inv1p[kMaxBlocks];
   double l2scale[kMaxBlocks];

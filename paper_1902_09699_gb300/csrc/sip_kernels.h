@@ -16,7 +16,7 @@ struct Launch {
 };
 
 // iteration kernels (kernels.cu)
-cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, int ninst);
+cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, JobScal *jscal, int ninst);
 cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 // staged right-hand side (binary32, 2D instances): `smem` bytes of y / v
@@ -65,7 +65,7 @@ cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDe
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                          const JobDev *jobs, const JobScal *jscal, const uint32_t *ties);
 // cg_launch: step launches per iteration
-cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, const JobScal *jscal, int ninst,
+cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, JobScal *jscal, int ninst,
                         int cg_launch);
 
 // single-step operators on one grid (kernels.cu): `in` describes the grid and

@@ -42,14 +42,14 @@ class Options(ctypes.Structure):
                 ("eps_corr", c_dbl), ("rho_ratio_max", c_dbl), ("gamma_max", c_dbl), ("form", c_int),
                 ("dtype", c_int), ("levels", c_int), ("coarse_iter", c_int),
                 ("rho_schedule", ctypes.POINTER(c_dbl)), ("gamma_schedule", ctypes.POINTER(c_dbl)),
-                ("trace", ctypes.POINTER(c_dbl)), ("exec", c_int)]
+                ("trace", ctypes.POINTER(c_dbl)), ("exec", c_int), ("select_window", c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("cg_steps_total", c_int), ("stop_reason", c_int), ("nblocks", c_int),
                 ("r_evol", c_dbl), ("r_feas", c_dbl * MAX_SETS), ("rho", c_dbl * (MAX_SETS + 1)),
                 ("gamma", c_dbl * (MAX_SETS + 1)), ("sigma", c_dbl * MAX_SETS), ("k", c_i64 * MAX_SETS),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("window_hits", c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -272,7 +272,7 @@ class Projector:
         d = dict(iters=inf.iters, cg_steps=inf.cg_steps_total, stop_reason=inf.stop_reason,
                  r_evol=inf.r_evol, r_feas=list(inf.r_feas[:p]), rho=list(inf.rho[:self.nblocks]),
                  gamma=list(inf.gamma[:self.nblocks]), sigma=list(inf.sigma[:p]), k=list(inf.k[:p]),
-                 ms=float(inf.ms))
+                 ms=float(inf.ms), window_hits=inf.window_hits)
         return x, d
 
     def device_bytes(self):
@@ -308,7 +308,7 @@ class Projector:
 def _info_dict(inf, nsets, nblocks):
     return dict(iters=inf.iters, cg_steps=inf.cg_steps_total, stop_reason=inf.stop_reason, r_evol=inf.r_evol,
                 r_feas=list(inf.r_feas[:nsets]), rho=list(inf.rho[:nblocks]), gamma=list(inf.gamma[:nblocks]),
-                sigma=list(inf.sigma[:nsets]), k=list(inf.k[:nsets]), ms=float(inf.ms))
+                sigma=list(inf.sigma[:nsets]), k=list(inf.k[:nsets]), ms=float(inf.ms), window_hits=inf.window_hits)
 
 
 class BatchProjector:
