@@ -2830,6 +2830,14 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
   return v;
 }
 
+// Relaxed polls of barrier words (an acquire load per poll would also cost
+// the SM's other CTAs their L1 contents); the waits fence once afterwards.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid-wide barrier with a bounded wait.  A CTA that waits longer than
 // kBarrierSpins polls (seconds) records SIP_ERR_TIMEOUT in bar[2] and every
 // CTA returns false, so the kernel ends instead of hanging.
@@ -2848,8 +2856,8 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar) {
       atomicAdd(&bar[1], 1u);
     } else {
       long long spins = 0;
-      while (ld_acquire(&bar[1]) == g) {
-        if (ld_acquire(&bar[2]) != 0 || ++spins > kBarrierSpins) {
+      while (ld_relaxed(&bar[1]) == g) {
+        if (ld_relaxed(&bar[2]) != 0 || ++spins > kBarrierSpins) {
           atomicExch(&bar[2], (uint32_t)SIP_ERR_TIMEOUT);
           ok = 0;
           break;

@@ -346,6 +346,10 @@ sip_status sip_server_create(const sip_server_config *cfg, sip_server **out) {
   sip_server *S = new (std::nothrow) sip_server();
   if (!S) return fail(SIP_ERR_OOM, "host allocation failed");
   S->cfg = *cfg;
+  // cohorts run concurrently on their own streams: no persistent
+  // (cooperative) kernels, whose grid barriers could wait on CTAs that
+  // another cohort's grid keeps from becoming resident
+  S->cfg.opts.exec = SIP_EXEC_GRAPH;
   int dev = 0;
   cudaGetDevice(&dev);
   S->worker = std::thread([S, dev]() {
