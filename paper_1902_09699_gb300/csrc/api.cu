@@ -223,6 +223,9 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
   d.rho_ratio_max = o.rho_ratio_max;
   d.gamma_max = o.gamma_max;
   d.select_window = o.select_window;
+  // s^{k0} = A_i x^{k0} is recomputed from x^{k0}, which the x history ring
+  // still holds when the adapt interval is shorter than the ring
+  d.k0_ring = o.adapt_every < o.evol_hist ? 1 : 0;
 
   int64_t yoff = 0, woff = 0, soff = 0;
   int nseg = 0;
@@ -528,7 +531,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     offs[i].ring = take((int64_t)L.dev.hist * N * W);
     offs[i].w = take(L.Mw * W);
     offs[i].s = take(L.Ms * W);
-    offs[i].k0s = ad ? take(L.Mtot * W) : -1;
+    offs[i].k0s = (ad && !L.dev.k0_ring) ? take(L.Mtot * W) : -1;
     offs[i].k0vh = ad ? take(L.Mtot * W) : -1;
     offs[i].k0y = ad ? take(L.Mtot * W) : -1;
     offs[i].k0v = ad ? take(L.Mtot * W) : -1;

@@ -1449,20 +1449,31 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
       }
     }
   };
-  // x gathers of one row: s = A x (Eq. FD_mat) and m at the base sample
-  auto gather = [&](int64_t row, T &sv, T &mv) {
+  // s^{k0} = A x^{k0} of the last adapt iteration, from x^{k0} in the x
+  // history ring (k0ring) or from the stored copy k0s
+  const bool k0ring = in.k0_ring != 0;
+  const T *__restrict__ xk0 =
+      (k0ring && ad_dots) ? (const T *)in.ring + (int64_t)((k - in.adapt_every) % in.hist) * in.N : nullptr;
+  // x gathers of one row: s = A x (Eq. FD_mat), m at the base sample and,
+  // from the ring, s^{k0}
+  auto gather = [&](int64_t row, T &sv, T &mv, T &kv0) {
     int64_t off;
     const int64_t g = seg_base(in, kind, row, off);
     const T x0 = x[g];
     sv = kind == SEG_I ? x0 : (x[g + off] - x0) * q.ih;
     mv = type == BT_DIST ? m[g] : T(0);
+    if (xk0) {
+      const T z0 = xk0[g];
+      kv0 = kind == SEG_I ? z0 : (xk0[g + off] - z0) * q.ih;
+    }
   };
   bool vec = false;
   if constexpr (sizeof(T) == 4) {
     // 16-byte accesses to the row arrays when they all start on a 16-byte
     // boundary at this work item
     uintptr_t al = (uintptr_t)(y + tl.start) | (uintptr_t)(v + tl.start);
-    if (ad) al |= (uintptr_t)(k0s + tl.start) | (uintptr_t)(k0vh + tl.start);
+    if (ad) al |= (uintptr_t)(k0vh + tl.start);
+    if (ad && !k0ring) al |= (uintptr_t)(k0s + tl.start);
     if (ad && pointwise) al |= (uintptr_t)(k0y + tl.start) | (uintptr_t)(k0v + tl.start);
     if (!pointwise) al |= (uintptr_t)(wbuf + tl.start);
     if (store_s) al |= (uintptr_t)(sbuf + tl.start);
@@ -1493,19 +1504,20 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
         Y = ld(y);
         V = ld(v);
         if (ad_dots) {
-          KS = ld(k0s);
+          if (!k0ring) KS = ld(k0s);
           KVH = ld(k0vh);
           if (pointwise) {
             KY = ld(k0y);
             KV = ld(k0v);
           }
         }
-        float sv[4], mv[4];
+        float sv[4], mv[4], kr[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          sv[c] = mv[c] = 0.f;
-          if (r0 + c < end) gather(r0 + c, sv[c], mv[c]);
+          sv[c] = mv[c] = kr[c] = 0.f;
+          if (r0 + c < end) gather(r0 + c, sv[c], mv[c], kr[c]);
         }
+        if (xk0) KS = make_float4(kr[0], kr[1], kr[2], kr[3]);
         float4 YN, VN, W, VH;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -1523,7 +1535,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           vset(VH, c, o.vh);
         }
         if (ad) {
-          st(k0s, make_float4(sv[0], sv[1], sv[2], sv[3]));
+          if (!k0ring) st(k0s, make_float4(sv[0], sv[1], sv[2], sv[3]));
           st(k0vh, VH);
         }
         if (pointwise) {
@@ -1548,11 +1560,11 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
         const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
         ks[e] = kvh[e] = ky[e] = kv[e] = T(0);
         if (row < end) {
-          gather(row, sv[e], mg[e]);
+          gather(row, sv[e], mg[e], ks[e]);
           y0[e] = y[row];
           v0[e] = v[row];
           if (ad_dots) {
-            ks[e] = k0s[row];
+            if (!k0ring) ks[e] = k0s[row];
             kvh[e] = k0vh[row];
             if (pointwise) {
               ky[e] = k0y[row];
@@ -1568,7 +1580,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
         const RowOut<T> o = setpass_row(q, sv[e], y0[e], v0[e], mg[e], ks[e], kvh[e], ky[e], kv[e], acc);
         if (win) classify(o.w, true);
         if (ad) {
-          k0s[row] = sv[e];
+          if (!k0ring) k0s[row] = sv[e];
           k0vh[row] = o.vh;
         }
         if (pointwise) {
@@ -1996,65 +2008,70 @@ template <typename T>
 __device__ __noinline__ void select_window_finish(const JobDev &jd, JobScal &js, unsigned char *smem) {
   using KT = KeyOf<T>;
   using K = typename KT::K;
-  using U = unsigned long long;
   constexpr int kKeyBits = (int)sizeof(K) * 8;
+  constexpr int kWarps = kThreads / 32;
+  static_assert(kWarps * 32 * kPer == kBins, "thread t owns bins [t kPer, t kPer + kPer)");
   K *ck = (K *)smem;
   uint32_t *h = (uint32_t *)(smem + (size_t)kWinCap * sizeof(K));
-  __shared__ U wsumi[kThreads / 32];
-  __shared__ U s_above;
-  __shared__ uint32_t s_cnt;
+  __shared__ uint32_t wt[kWarps];
+  __shared__ uint32_t s_above, s_cnt;
   __shared__ int s_bin;
   const int n = (int)js.win_n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const K *cand = (const K *)jd.cand;
   for (int i = threadIdx.x; i < n; i += kThreads) ck[i] = __ldcg(&cand[i]);
+  for (int i = threadIdx.x; i < kBins; i += kThreads) h[i] = 0u;
   const K wlo = KT::key((T)js.win_lo), whi = KT::key((T)js.win_hi);
   const K diff = wlo ^ whi;
   int top = 0;  // bits below `top` vary among the candidates
   if (diff) top = kKeyBits - (sizeof(K) == 8 ? __clzll((long long)diff) : __clz((int)diff));
   K pre = wlo;
-  U need = (U)js.k - js.win_above;  // rank among the candidates, 1..n
-  U above_c = 0;                    // candidates above the k-th key
-  uint32_t cK = (uint32_t)n;        // candidates equal to it
+  uint32_t need = (uint32_t)((unsigned long long)js.k - js.win_above);  // rank among the candidates, 1..n
+  uint32_t above_c = 0;      // candidates above the k-th key
+  uint32_t cK = (uint32_t)n;  // candidates equal to it
   __syncthreads();
   while (top > 0) {
     const int lo = top > kDigitBits ? top - kDigitBits : 0;
     const int nbins = 1 << (top - lo);
-    for (int i = threadIdx.x; i < nbins; i += kThreads) h[i] = 0u;
-    if (threadIdx.x == 0) s_bin = -1;
-    __syncthreads();
     for (int i = threadIdx.x; i < n; i += kThreads) {
       const K key = ck[i];
       if ((key >> top) == (pre >> top)) atomicAdd(&h[(int)((key >> lo) & (K)(nbins - 1))], 1u);
     }
     __syncthreads();
-    uint32_t c[kPer];
-    U tc = 0;
+    // counts of this thread's bins (then cleared for the next pass), warp totals
+    uint32_t c[kPer], tc = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
-      const int bi = threadIdx.x * kPer + j;
-      c[j] = bi < nbins ? h[bi] : 0u;
+      c[j] = h[threadIdx.x * kPer + j];
+      h[threadIdx.x * kPer + j] = 0u;
       tc += c[j];
     }
-    U ac = cta_suffix_u64(tc, wsumi) - tc;  // candidates in the bins above this thread's
-    int best = -1;
-    U bab = 0;
-    uint32_t bcnt = 0;
-#pragma unroll
-    for (int j = kPer - 1; j >= 0; --j) {
-      const U cge = ac + c[j];
-      if (best < 0 && threadIdx.x * kPer + j < nbins && cge >= need) {
-        best = threadIdx.x * kPer + j;
-        bab = ac;
-        bcnt = c[j];
-      }
-      ac = cge;
-    }
-    const int wb = __reduce_max_sync(0xffffffffu, best);
-    if ((threadIdx.x & 31) == 0 && wb >= 0) atomicMax(&s_bin, wb);
+    const uint32_t ws = __reduce_add_sync(0xffffffffu, tc);
+    if (lane == 0) wt[wid] = ws;
     __syncthreads();
-    if (best >= 0 && best == s_bin) {
-      s_above = bab;
-      s_cnt = bcnt;
+    // the warp, then the lane, then the bin holding the need-th largest
+    uint32_t aw = 0;
+#pragma unroll
+    for (int w = kWarps - 1; w > wid; --w) aw += wt[w];
+    if (aw < need && need <= aw + ws) {
+      uint32_t incl = tc;  // this lane's and the higher lanes' counts
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_down_sync(0xffffffffu, incl, o);
+        if (lane + o < 32) incl += v;
+      }
+      uint32_t ac = aw + incl - tc;
+      if (ac < need && need <= ac + tc) {
+        for (int j = kPer - 1; j >= 0; --j) {
+          if (ac + c[j] >= need) {
+            s_bin = threadIdx.x * kPer + j;
+            s_above = ac;
+            s_cnt = c[j];
+            break;
+          }
+          ac += c[j];
+        }
+      }
     }
     __syncthreads();
     need -= s_above;
@@ -2062,10 +2079,9 @@ __device__ __noinline__ void select_window_finish(const JobDev &jd, JobScal &js,
     cK = s_cnt;
     pre = (K)((pre >> top) << top) | ((K)s_bin << lo);
     top = lo;
-    __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const U nab = js.win_above + above_c;
+    const unsigned long long nab = js.win_above + above_c;
     js.n_above = nab;
     js.c_above = (double)nab;
     js.prefix = (uint64_t)pre;

@@ -178,6 +178,8 @@ struct InstDev {
   uint32_t *err;             // plan-wide device error word (a bounded wait that ran out)
   int32_t trace_w;
   int32_t select_window;     // option: warm-started window for top-k selections
+  int32_t k0_ring;           // s^{k0} from x^{k0} in the history ring (adapt_every < hist), no k0s copy
+  int32_t pad_k0;
   // device arrays, element type = the plan's dtype
   const void *m;
   void *x, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;

@@ -266,3 +266,20 @@ def test_full_size_layered_first_iterations():
     rs, gs = schedules(ref32)
     x, info, _ = run_gpu(m32, c["grid"], c["sets"], "f32", opts, rho_schedule=rs, gamma_schedule=gs)
     assert rel(x, ref32["x"]) <= 1e-4
+
+
+@pytest.mark.parametrize("hist,every", [(5, 2), (2, 2), (3, 1)])
+def test_adapt_k0_quantities_ring_or_copy(hist, every):
+    """Algorithm adapt-rho-gamma compares s = A_i x with its value at the
+    previous adapt iteration k0.  With adapt_every < evol_hist, s^{k0} is
+    recomputed from x^{k0} in the x history ring; otherwise a copy is kept.
+    Either way the rho trajectory and x follow the oracle."""
+    c = layered_small()
+    opts = dict(c["opts"], evol_hist=hist, adapt_every=every)
+    ref = oracle_run(c["m"], c["grid"], c["sets"], opts)
+    x, info, tr = run_gpu(c["m"], c["grid"], c["sets"], "f64", opts, trace=True)
+    rs, _ = schedules(ref)
+    nb = len(c["sets"]) + 1
+    assert np.ptp(rs) > 0
+    assert np.allclose(tr[:, :nb], rs, rtol=1e-9, atol=0)
+    assert rel(x, ref["x"]) <= 1e-10
