@@ -609,6 +609,14 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     P.h_insts[i] = d;
     P.layouts[i] = insts[i];
   }
+  // single instance: the CG launches take their work items and descriptor
+  // fields as parameters (items of ch_n points from 0, as pushed above)
+  memset(&P.cg_one, 0, sizeof P.cg_one);
+  if (P.ninst == 1) {
+    P.cg_one.d = cg_desc(P.h_insts[0]);
+    P.cg_one.chunk = ch_n;
+    P.cg_one.on = 1;
+  }
   P.m_own = own_m;
   P.packed = packed;
   P.x_pack = packed ? at(o_xpack) : nullptr;
@@ -687,11 +695,11 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
     CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
   T1(KT_RHS);
   T0(KT_CG_W0);
-  CK(launch_cg_w0(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));  // w_0 = C r_0
+  CK(launch_cg_w0(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, P.cg_one));  // w_0 = C r_0
   T1(KT_CG_W0);
   for (int j = 0; j < P.cg_launch; ++j) {
     T0(KT_CG_STEP);
-    CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j));  // one CG step
+    CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j, P.cg_one));  // one CG step
     T1(KT_CG_STEP);
   }
   T0(KT_SETPASS);

@@ -259,7 +259,8 @@ struct GridPos {
   int32_t iz, ix, iy;
   int64_t t;  // ix + nx*iy
 };
-__device__ __forceinline__ GridPos grid_pos(const InstDev &in, int64_t g) {
+template <typename D>
+__device__ __forceinline__ GridPos grid_pos(const D &in, int64_t g) {
   GridPos p;
   const uint32_t gg = (uint32_t)g;
   const uint32_t t = fdiv(gg, in.fz);
@@ -359,8 +360,8 @@ template <typename T>
 struct Nbr {
   T c, zm, zp, xm, xp, ym, yp;
 };
-template <typename T, typename V>
-__device__ __forceinline__ void load_nbr(const InstDev &in, const GridPos &p, int64_t g, V v, Nbr<T> &o) {
+template <typename T, typename V, typename D>
+__device__ __forceinline__ void load_nbr(const D &in, const GridPos &p, int64_t g, V v, Nbr<T> &o) {
   const int64_t sxy = (int64_t)in.nz * in.nx;
   o.c = v(g);
   o.zm = p.iz > 0 ? v(g - 1) : o.c;
@@ -434,8 +435,8 @@ __device__ __forceinline__ void st4(float *p, int64_t i, const float4 &v) { *rei
 // has nt_part entries per quantity (the right-hand side may use its own work
 // items); a launch writes entry tl.seq of each of its work items and the
 // entries past them stay zero.
-template <typename A>
-__device__ __forceinline__ A *cg_part(const InstDev &in, int slot, int q) {
+template <typename A, typename D>
+__device__ __forceinline__ A *cg_part(const D &in, int slot, int q) {
   return (A *)in.cgp + (int64_t)(slot * 2 + q) * in.nt_part;
 }
 
@@ -811,7 +812,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_rhs_tma(const Tile *__restrict_
 // w_0 = C r_0 on 2D grids with n_z % 4 == 0 and aligned arrays: 4
 // consecutive z samples per thread, z neighbours across lanes (single
 // loads at warp and tile edges), as in the four-sample CG step.
-__device__ __forceinline__ void body_cg_w0_v4(const Tile &tl, const InstDev &in, const InstScal &sc, int done) {
+template <typename D>
+__device__ __forceinline__ void body_cg_w0_v4(const Tile &tl, const D &in, const InstScal &sc, int done) {
   constexpr int SUB = kThreads * 4;
   const unsigned FULL = 0xffffffffu;
   const float *__restrict__ r = (const float *)in.cr[0];
@@ -863,13 +865,10 @@ __device__ __forceinline__ void body_cg_w0_v4(const Tile &tl, const InstDev &in,
   if (threadIdx.x == 0) cg_part<float>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0
 }
 
-template <typename T>
-__device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__restrict__ insts,
-                                                       InstScal *__restrict__ scal) {
+template <typename T, typename D>
+__device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstScal &sc) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
-  const InstDev &in = insts[tl.inst];
-  InstScal &sc = scal[tl.inst];
   const int done = sc.done;
   if constexpr (sizeof(T) == 4) {
     if ((in.nz & 3) == 0 && in.ny == 1 && (((uintptr_t)in.cr[0] | (uintptr_t)in.cw[0]) & 15) == 0) {
@@ -905,12 +904,36 @@ __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__rest
   block_sum<1>(acc);
   if (threadIdx.x == 0) cg_part<A>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0 = p_0^T C p_0
 }
+template <typename T>
+__device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__restrict__ insts,
+                                           InstScal *__restrict__ scal) {
+  body_cg_w0_in<T>(tl, insts[tl.inst], scal[tl.inst]);
+}
+
+// Single-instance plans: the grid-point work item of CTA b (items of `chunk`
+// points from 0) and the CG's descriptor fields arrive as launch parameters,
+// so a CG launch starts loading without first reading its item and the
+// instance descriptor from memory.
+__device__ __forceinline__ Tile one_tile(const CgOne &one) {
+  Tile tl;
+  tl.inst = 0;
+  tl.item = 0;
+  tl.start = (int64_t)blockIdx.x * one.chunk;
+  const int64_t left = one.d.N - tl.start;
+  tl.len = (int32_t)(left < one.chunk ? left : one.chunk);
+  tl.seq = (int32_t)blockIdx.x;
+  return tl;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                       InstScal *__restrict__ scal, unsigned long long *ts) {
+                                                       InstScal *__restrict__ scal, unsigned long long *ts,
+                                                       const __grid_constant__ CgOne one) {
   const Stamp stamp(ts);
-  body_cg_w0<T>(tiles[blockIdx.x], insts, scal);
+  if (one.on)
+    body_cg_w0_in<T>(one_tile(one), one.d, scal[0]);
+  else
+    body_cg_w0<T>(tiles[blockIdx.x], insts, scal);
 }
 
 // CG state fields in the storage precision (binary32 kernels do their
@@ -931,8 +954,8 @@ template <> struct CgOf<float> {
 // threads add the partial sums, thread 0 updates the CG state (the same
 // values in every CTA) and the instance's first tile stores it for the next
 // launch.  Results in s_ab, s_go after the closing __syncthreads.
-template <typename T>
-__device__ __forceinline__ void cg_scalars(const Tile &tl, const InstDev &in, InstScal &sc, int ph, T *s_ab,
+template <typename T, typename D>
+__device__ __forceinline__ void cg_scalars(const Tile &tl, const D &in, InstScal &sc, int ph, T *s_ab,
                                            int *s_go) {
   using A = typename AccOf<T>::type;
   using G = CgOf<T>;
@@ -1010,7 +1033,8 @@ __device__ __forceinline__ void cg_scalars(const Tile &tl, const InstDev &in, In
 // tile edge, from single loads.  Same arithmetic per sample as the general
 // step.
 
-__device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const InstDev &in, InstScal &sc, int ph) {
+template <typename D>
+__device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const D &in, InstScal &sc, int ph) {
   constexpr int SUB = kThreads * 4;
   const unsigned FULL = 0xffffffffu;
   const int c = ph & 1, n = c ^ 1;
@@ -1114,15 +1138,11 @@ __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const InstDev &i
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void body_cg_step(const Tile &tl,
-                                                         const InstDev *__restrict__ insts,
-                                                         InstScal *__restrict__ scal, int ph) {
+template <typename T, typename D>
+__device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, InstScal &sc, int ph) {
   using A = typename AccOf<T>::type;
   constexpr int PT = sizeof(T) == 4 ? 2 : 1;  // 3 stencils per row: keep the register budget
   constexpr int SUB = kThreads * PT;
-  const InstDev &in = insts[tl.inst];
-  InstScal &sc = scal[tl.inst];
   if constexpr (sizeof(T) == 4) {
     // 16-byte accesses need every array on a 16-byte boundary (the x of a
     // batched plan is packed and may not be)
@@ -1210,11 +1230,27 @@ __device__ __forceinline__ void body_cg_step(const Tile &tl,
 }
 
 template <typename T>
+__device__ __forceinline__ void body_cg_step(const Tile &tl, const InstDev *__restrict__ insts,
+                                             InstScal *__restrict__ scal, int ph) {
+  body_cg_step_in<T>(tl, insts[tl.inst], scal[tl.inst], ph);
+}
+
+// out of line: the single-instance path keeps the register allocation
+template <typename T>
+__device__ __noinline__ void cg_step_call(const Tile &tl, const InstDev *insts, InstScal *scal, int ph) {
+  body_cg_step<T>(tl, insts, scal, ph);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
                                                          const InstDev *__restrict__ insts,
-                                                         InstScal *__restrict__ scal, int ph, unsigned long long *ts) {
+                                                         InstScal *__restrict__ scal, int ph, unsigned long long *ts,
+                                                         const __grid_constant__ CgOne one) {
   const Stamp stamp(ts);
-  body_cg_step<T>(tiles[blockIdx.x], insts, scal, ph);
+  if (one.on)
+    body_cg_step_in<T>(one_tile(one), one.d, scal[0], ph);
+  else
+    cg_step_call<T>(tiles[blockIdx.x], insts, scal, ph);
 }
 
 // --------------------------------------------------------------------------
@@ -3124,12 +3160,14 @@ int rhs_tma_occupancy(size_t smem) {
   }
   return n;
 }
-cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal, L.ts);
+cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                         const CgOne &one) {
+  SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal, L.ts, one);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph) {
-  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts);
+cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
+                           const CgOne &one) {
+  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,

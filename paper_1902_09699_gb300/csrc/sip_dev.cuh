@@ -196,6 +196,43 @@ struct InstDev {
   SegDev seg[kMaxSegs];
 };
 
+// The fields of an instance the CG launches read, passed by value to the
+// launches of single-instance plans (same names as in InstDev).
+struct CgDesc {
+  int32_t nz, nx, ny, cg_iters, cg_max, nt_part;
+  FastDiv fz, fx;
+  int64_t N;
+  void *x, *cp, *cgp;
+  void *cr[2], *cw[2], *cs[2];
+};
+struct CgOne {
+  CgDesc d;
+  int64_t chunk;  // points per grid-point work item
+  int32_t on;     // single-instance plan: work item b = points [b chunk, (b+1) chunk)
+  int32_t pad;
+};
+inline CgDesc cg_desc(const InstDev &in) {
+  CgDesc d;
+  d.nz = in.nz;
+  d.nx = in.nx;
+  d.ny = in.ny;
+  d.cg_iters = in.cg_iters;
+  d.cg_max = in.cg_max;
+  d.nt_part = in.nt_part;
+  d.fz = in.fz;
+  d.fx = in.fx;
+  d.N = in.N;
+  d.x = in.x;
+  d.cp = in.cp;
+  d.cgp = in.cgp;
+  for (int j = 0; j < 2; ++j) {
+    d.cr[j] = in.cr[j];
+    d.cw[j] = in.cw[j];
+    d.cs[j] = in.cs[j];
+  }
+  return d;
+}
+
 // Conjugate-gradient state between step launches.  Every CTA of a step
 // launch derives it from the previous launch's partial sums and the previous
 // state; the instance's first tile stores it in slot (phase & 1) while the

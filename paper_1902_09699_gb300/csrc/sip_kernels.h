@@ -25,9 +25,11 @@ constexpr size_t kRhsSmemMax = 200 * 1024;
 cudaError_t launch_rhs_tma(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            size_t smem);
 int rhs_tma_occupancy(size_t smem);
-cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                         const CgOne &one);
 // ph: 2 for the first step launch of an iteration, then 3, 4, ...
-cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph);
+cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
+                           const CgOne &one);
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            JobScal *jscal, const JobDev *jobs);
 // hstride: elements between the three histogram buffers the passes rotate
