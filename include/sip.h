@@ -41,6 +41,7 @@ extern "C" {
 #endif
 
 #define SIP_MAX_SETS 16
+#define SIP_MAX_LEVELS 8  /* ML-PARSDMM levels */
 
 typedef enum {
     SIP_OK = 0,
@@ -113,7 +114,10 @@ typedef struct {
     double gamma_max;   /* gamma kept below 2 (1.99) */
     int form;           /* sip_form */
     int dtype;          /* sip_dtype */
-    int levels;         /* 1, or 2 for two-level ML-PARSDMM */
+    int levels;         /* 1, or 2..SIP_MAX_LEVELS for ML-PARSDMM (Sec. "Multilevel
+                           PARSDMM"): each coarser grid halves every axis
+                           (n -> ceil(n/2), h -> 2h); every level must be a
+                           valid grid for the set list */
     int coarse_iter;    /* iterations on the coarse level (0: max_iter) */
     /* Optional host arrays [max_iter][nblocks] of rho_i / gamma_i used in
      * iteration k (row k-1); nblocks = nsets + (form == ALG1).  When set, the

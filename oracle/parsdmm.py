@@ -50,21 +50,41 @@ def options(**kw):
     return o
 
 
+_SCOPE_AXIS = {"z": 2, "x": 1, "y": 0}   # axis of the (ny, nx, nz) shape
+
+
 def resolve_sets(grid, sets, m):
-    """Resolve relative radii / cardinalities against the model m."""
+    """Resolve relative radii / cardinalities against the model m.
+
+    Per-line sets ("scope" "z", "x" or "y"): readings.  Their radius applies
+    to every line and is absolute (a relative radius is rejected); k_frac
+    resolves against the line length; the TV stack is rejected (its parts
+    live on different grids)."""
     out = []
     N = ops.grid_size(grid)
     for s in sets:
         r = dict(s)
         r.setdefault("lo", -math.inf)
         r.setdefault("hi", math.inf)
+        scope = r.setdefault("scope", "all")
+        if scope != "all":
+            if r["op"] == "TV":
+                raise ValueError("per-line sets need a single-grid operator")
+            if r.get("sigma_rel", 0.0):
+                raise ValueError("per-line sets take absolute radii")
+            r["shape"] = ops.grid_shape(grid) if r["op"] == "I" else ops.diff_shape(grid, r["op"])
+            if r["shape"][_SCOPE_AXIS[scope]] < 1 or (scope == "y" and len(grid["n"]) < 3):
+                raise ValueError("no lines along %s" % scope)
         if r["type"] in ("l1", "l2"):
             if r.get("sigma_rel", 0.0):
                 r["sigma"] = r["sigma_rel"] * ops.norm_of(grid, r["op"], r["type"], m)
             r["sigma"] = float(r["sigma"])
+        if r["type"] == "annulus":
+            r["lo"], r["hi"] = float(r["lo"]), float(r["hi"])
         if r["type"] == "card":
             if r.get("k_frac", 0.0):
-                r["k"] = int(math.floor(r["k_frac"] * N))
+                n = N if scope == "all" else r["shape"][_SCOPE_AXIS[scope]]
+                r["k"] = int(math.floor(r["k_frac"] * n))
             r["k"] = int(r["k"])
         out.append(r)
     return out

@@ -27,6 +27,40 @@ def proj_l2(w, sigma):
     return w * (sigma / nrm)
 
 
+def proj_annulus(w, lo, hi):
+    """Annulus {sigma_l <= ||w||_2 <= sigma_u} (set table, "annulus"):
+    radial scaling onto the nearer sphere when ||w||_2 lies outside
+    [sigma_l, sigma_u].  The set is not convex for sigma_l > 0.  Reading:
+    w = 0 has no nearest point of a unique direction; it is returned
+    unchanged."""
+    if not (0.0 <= lo <= hi):
+        raise ValueError("proj_annulus: need 0 <= lo <= hi")
+    w = np.asarray(w, dtype=np.float64)
+    nrm = float(np.sqrt(np.sum(w * w)))
+    if nrm > hi:
+        return w * (hi / nrm)
+    if 0.0 < nrm < lo:
+        return w * (lo / nrm)
+    return w.copy()
+
+
+def lines(shape, scope):
+    """Index arrays of the lines of an array of shape (ny, nx, nz) (z
+    fastest, Sec. "Notation") that a per-line set applies to: "z" the
+    lines along z (the columns X[:, j] of a 2D model), "x" the lines along x
+    (the rows X[i, :]), "y" the lines along y (the fibers of a 3D model).
+    Each array lists its line's linear indices in increasing order."""
+    ny, nx, nz = shape
+    idx = np.arange(ny * nx * nz).reshape(ny, nx, nz)
+    if scope == "z":
+        return list(idx.reshape(ny * nx, nz))
+    if scope == "x":
+        return list(np.transpose(idx, (0, 2, 1)).reshape(ny * nz, nx))
+    if scope == "y":
+        return list(np.transpose(idx, (1, 2, 0)).reshape(nx * nz, ny))
+    raise ValueError("unknown scope %r" % (scope,))
+
+
 def l1_threshold(w, tau):
     """Soft-threshold level theta of the l1-ball projection, by sorting
     (Duchi et al. 2008, the l1-ball projection the paper uses, Sec.
@@ -96,9 +130,23 @@ def prox_dist(w, m, rho):
 
 def project(set_spec, w):
     """Projection P_C(w) for a set specification dict with key "type" in
-    {"bounds", "l1", "l2", "card"} and the resolved parameters "lo"/"hi",
-    "sigma" or "k"."""
+    {"bounds", "l1", "l2", "card", "annulus"} and the resolved parameters
+    "lo"/"hi", "sigma" or "k".  With "scope" in {"z", "x", "y"} the set
+    constrains every line of that direction on its own (the per-column,
+    per-row and per-fiber sets of Sec. "Software and numerical examples"),
+    so the projection is the simple set's projection of each line; "shape"
+    gives the (ny, nx, nz) array shape of w."""
+    scope = set_spec.get("scope", "all")
+    if scope != "all":
+        w = np.asarray(w, dtype=np.float64)
+        y = np.empty_like(w)
+        base = dict(set_spec, scope="all")
+        for ln in lines(set_spec["shape"], scope):
+            y[ln] = project(base, w[ln])
+        return y
     t = set_spec["type"]
+    if t == "annulus":
+        return proj_annulus(w, set_spec["lo"], set_spec["hi"])
     if t == "bounds":
         return proj_bounds(w, set_spec["lo"], set_spec["hi"])
     if t == "l2":

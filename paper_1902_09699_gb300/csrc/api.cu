@@ -154,9 +154,9 @@ static sip_status check_opts(const sip_options &o) {
   if (!(o.gamma_max > 0.0) || !(o.gamma_max < 2.0)) return fail(SIP_ERR_INVALID_ARG, "gamma_max must be in (0, 2)");
   if (o.form != SIP_FORM_ALG1 && o.form != SIP_FORM_DIRECT) return fail(SIP_ERR_INVALID_ARG, "unknown form");
   if (o.dtype != SIP_F64 && o.dtype != SIP_F32) return fail(SIP_ERR_INVALID_ARG, "unknown dtype");
-  if (o.levels != 1 && o.levels != 2) return fail(SIP_ERR_INVALID_ARG, "levels must be 1 or 2");
+  if (o.levels < 1 || o.levels > SIP_MAX_LEVELS) return fail(SIP_ERR_INVALID_ARG, "levels must be in [1, %d]", SIP_MAX_LEVELS);
   if (o.coarse_iter < 0) return fail(SIP_ERR_INVALID_ARG, "coarse_iter < 0");
-  if (o.levels == 2 && (o.rho_schedule || o.gamma_schedule || o.trace))
+  if (o.levels > 1 && (o.rho_schedule || o.gamma_schedule || o.trace))
     return fail(SIP_ERR_INVALID_ARG, "schedules and traces are single-level only");
   if (o.gamma_schedule && !o.rho_schedule) return fail(SIP_ERR_INVALID_ARG, "gamma_schedule needs rho_schedule");
   if (o.exec < SIP_EXEC_AUTO || o.exec > SIP_EXEC_PERSISTENT) return fail(SIP_ERR_INVALID_ARG, "unknown exec mode");

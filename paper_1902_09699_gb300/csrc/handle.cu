@@ -14,7 +14,7 @@
 using namespace sip;
 
 struct sip_handle {
-  Plan lev[2];      // lev[0]: finest grid; lev[1]: coarse grid (two-level ML)
+  Plan lev[SIP_MAX_LEVELS];  // lev[0]: finest grid; lev[l]: the grid coarsened l times (ML-PARSDMM)
   int levels = 1;
   int batch = 0;    // > 0: a batched handle of `batch` instances (packed buffers)
   sip_options opts;
@@ -147,10 +147,11 @@ sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets, cons
   *out = nullptr;
   sip_status st = validate(grid, sets, nsets, opts);
   if (st) return st;
-  sip_grid cgrid;
-  if (opts->levels == 2) {
-    cgrid = coarse_of(*grid);
-    if ((st = validate(&cgrid, sets, nsets, opts))) return fail(st, "coarse level: %s", g_err.c_str());
+  sip_grid grids[SIP_MAX_LEVELS];
+  grids[0] = *grid;
+  for (int l = 1; l < opts->levels; ++l) {
+    grids[l] = coarse_of(grids[l - 1]);
+    if ((st = validate(&grids[l], sets, nsets, opts))) return fail(st, "level %d: %s", l, g_err.c_str());
   }
   sip_handle *h = new (std::nothrow) sip_handle();
   if (!h) return fail(SIP_ERR_OOM, "host allocation failed");
@@ -166,11 +167,11 @@ sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets, cons
     std::vector<InstLayout> L{make_layout(grid_desc(*grid), sets, nsets, *opts)};
     if ((st = plan_build(h->lev[0], L, opts->dtype, false))) return bail(st);
   }
-  if (opts->levels == 2) {
+  for (int l = 1; l < opts->levels; ++l) {
     sip_options oc = *opts;
     oc.max_iter = opts->coarse_iter > 0 ? opts->coarse_iter : opts->max_iter;
-    std::vector<InstLayout> L{make_layout(grid_desc(cgrid), sets, nsets, oc)};
-    if ((st = plan_build(h->lev[1], L, opts->dtype, true))) return bail(st);
+    std::vector<InstLayout> L{make_layout(grid_desc(grids[l]), sets, nsets, oc)};
+    if ((st = plan_build(h->lev[l], L, opts->dtype, true))) return bail(st);
   }
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(&h->pinned, sizeof(int32_t)) != cudaSuccess || cudaEventCreate(&h->ev0) != cudaSuccess ||
@@ -195,7 +196,9 @@ sip_status sip_destroy(sip_handle *h) {
 
 int64_t sip_device_bytes(const sip_handle *h) {
   if (!h) return 0;
-  return h->lev[0].arena_bytes + h->lev[1].arena_bytes;
+  int64_t b = 0;
+  for (const auto &P : h->lev) b += P.arena_bytes;
+  return b;
 }
 
 double sip_bytes_per_iter(const sip_handle *h) {
@@ -236,18 +239,26 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
   const InstDev &df = F.h_insts[0];
   KernelTimer *tm = h->timing ? &h->timer : nullptr;
   CKH(cudaEventRecord(h->ev0, st));
-  if (h->levels == 2) {
-    Plan &C = h->lev[1];
+  if (h->levels > 1) {
+    // Algorithm ML-PARSDMM: models restricted level by level; the coarsest
+    // level starts from zeros, every finer one from the interpolated x, y_i,
+    // v_i of the level below
     const Launch L{o.dtype, st};
-    int64_t fd[3], cd[3];
-    int stag;
-    part_dims(F.layouts[0].g, SEG_I, fd, stag);
-    part_dims(C.layouts[0].g, SEG_I, cd, stag);
-    CKH(launch_restrict(L, fd, cd, m_dev, (void *)C.h_insts[0].m));
-    sip_status s = plan_prepare(C, st, false);
-    if (!s) s = run_iterations(C, st, h->cap, C.max_iter, o.stop != 0, h->pinned, tm);
-    if (!s) s = prolong_state(C, F, st);
-    if (!s) s = plan_set_m(F, 0, m_dev, st);
+    for (int l = 1; l < h->levels; ++l) {
+      int64_t fd[3], cd[3];
+      int stag;
+      part_dims(h->lev[l - 1].layouts[0].g, SEG_I, fd, stag);
+      part_dims(h->lev[l].layouts[0].g, SEG_I, cd, stag);
+      CKH(launch_restrict(L, fd, cd, l == 1 ? m_dev : h->lev[l - 1].h_insts[0].m, (void *)h->lev[l].h_insts[0].m));
+    }
+    for (int l = h->levels - 1; l >= 1; --l) {
+      Plan &C = h->lev[l];
+      sip_status s = plan_prepare(C, st, l < h->levels - 1);
+      if (!s) s = run_iterations(C, st, h->cap, C.max_iter, o.stop != 0, h->pinned, tm);
+      if (!s) s = prolong_state(C, h->lev[l - 1], st);
+      if (s) return s;
+    }
+    sip_status s = plan_set_m(F, 0, m_dev, st);
     if (!s) s = plan_prepare(F, st, true);
     if (s) return s;
   } else {

@@ -87,6 +87,11 @@ def test_op_rows(sip):
     dict(opts=dict(evol_hist=9)),
     dict(opts=dict(gamma0=2.0)),
     dict(sets=[{"op": "I", "type": "bounds", "lo": 0.0, "hi": 1.0}] * 17),
+    dict(opts=dict(levels=0)),
+    dict(opts=dict(levels=9)),
+    # 4 -> 2 -> 1 samples along z: D_z has no rows on the third level
+    dict(grid={"n": (4, 8)}, sets=[{"op": "DZ", "type": "bounds", "lo": 0.0, "hi": 1.0}], opts=dict(levels=3)),
+    dict(opts=dict(select_window=2)),
 ])
 def test_invalid_arguments_rejected_on_host(sip, bad):
     grid = bad.get("grid", {"n": (8, 8)})

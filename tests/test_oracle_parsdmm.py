@@ -385,13 +385,49 @@ def test_prolongation_reproduces_linear_fields(op):
     assert np.allclose(P.prolong(gc, gf, op, uc), uf, atol=1e-12)
 
 
-def test_multilevel_reaches_single_level_solution():
+@pytest.mark.parametrize("levels", [2, 3])
+def test_multilevel_reaches_single_level_solution(levels):
+    """Convex sets: the projection is unique, so ML-PARSDMM from any coarse
+    warm start reaches the single-level solution."""
     grid = {"n": (16, 12), "h": (1.0, 1.0)}
     m = model(grid, 11)
     sets = [{"op": "I", "type": "bounds", "lo": 2.5, "hi": 3.5},
             {"op": "DZ", "type": "bounds", "lo": 0.0, "hi": math.inf}]
     o = P.options(max_iter=3000, adapt=1, gamma0=1.5)
-    ml = P.ml_parsdmm(m, grid, sets, o, levels=2, coarse_iter=300)
+    ml = P.ml_parsdmm(m, grid, sets, o, levels=levels, coarse_iter=300)
     sl = P.parsdmm(m, grid, sets, o)
     assert rel(ml["x"], sl["x"]) < 1e-5
-    assert len(ml["levels"]) == 2
+    assert len(ml["levels"]) == levels
+    assert [len(r["x"]) for r in ml["levels"]] == [int(np.prod(g)) for g in
+                                                    [((16 >> j) + 0, (12 >> j) + 0) for j in range(levels - 1, -1, -1)]]
+
+
+def test_single_per_column_l2_set_gives_columnwise_scaling():
+    """One per-line set on A = I: the projection of m onto it, i.e. every
+    column scaled into its own l2 ball."""
+    m = model(GRID, 12)
+    nz, nx = GRID["n"][0], GRID["n"][1]
+    X = m.reshape(nx, nz).T
+    sigma = 0.8 * float(np.median(np.linalg.norm(X, axis=0)))
+    expect = X * np.minimum(1.0, sigma / np.linalg.norm(X, axis=0))[None, :]
+    res = run(m, GRID, [{"op": "I", "type": "l2", "sigma": sigma, "scope": "z"}], iters=400)
+    assert rel(res["x"], expect.T.reshape(-1)) < 1e-8
+
+
+def test_single_annulus_set_gives_radial_scaling():
+    m = model(GRID, 13)
+    n = float(np.linalg.norm(m))
+    res = run(m, GRID, [{"op": "I", "type": "annulus", "lo": 1.3 * n, "hi": 2.0 * n}], iters=400)
+    assert rel(res["x"], m * 1.3) < 1e-8
+
+
+def test_per_line_sets_reject_unsupported_forms():
+    m = model(GRID, 14)
+    with pytest.raises(ValueError):
+        P.resolve_sets(GRID, [{"op": "TV", "type": "l1", "sigma": 1.0, "scope": "z"}], m)
+    with pytest.raises(ValueError):
+        P.resolve_sets(GRID, [{"op": "I", "type": "l2", "sigma_rel": 0.5, "scope": "x"}], m)
+    with pytest.raises(ValueError):
+        P.resolve_sets(GRID, [{"op": "I", "type": "l2", "sigma": 1.0, "scope": "y"}], m)
+    r = P.resolve_sets(GRID, [{"op": "DZ", "type": "card", "k_frac": 0.25, "scope": "z"}], m)[0]
+    assert r["k"] == int(0.25 * (GRID["n"][0] - 1))

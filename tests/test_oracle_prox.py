@@ -146,3 +146,85 @@ def test_prox_dist_is_minimiser():
         z = prox.prox_dist(w, m, rho)
         # gradient of 1/2||z - m||^2 + rho/2 ||z - w||^2 vanishes at z
         assert np.allclose((z - m) + rho * (z - w), 0, atol=1e-14)
+
+
+def test_annulus_nearest_point_and_special_cases():
+    """Annulus {lo <= ||w|| <= hi}: nearest point over sampled members; with
+    lo = 0 it is the l2 ball."""
+    g = np.random.default_rng(7)
+    for n, lo, hi in ((2, 1.0, 2.0), (3, 0.5, 0.8), (6, 2.0, 2.0)):
+        for scale in (0.1, 1.0, 1.5, 5.0):
+            w = g.standard_normal(n)
+            w *= scale * (lo + hi) / 2 / np.linalg.norm(w)
+            y = prox.proj_annulus(w, lo, hi)
+            ny = np.linalg.norm(y)
+            assert lo * (1 - 1e-14) <= ny <= hi * (1 + 1e-14)
+            # no sampled member of the annulus is closer
+            for _ in range(300):
+                z = g.standard_normal(n)
+                z *= g.uniform(lo, hi) / np.linalg.norm(z)
+                assert np.linalg.norm(z - w) >= np.linalg.norm(y - w) - 1e-12
+        w = g.standard_normal(n)
+        assert np.allclose(prox.proj_annulus(w, 0.0, 0.7), prox.proj_l2(w, 0.7), rtol=0, atol=1e-15)
+    assert np.allclose(prox.proj_annulus(np.array([0.3, 0.4]), 1.0, 2.0), [0.6, 0.8])
+    assert np.allclose(prox.proj_annulus(np.array([3.0, 4.0]), 1.0, 2.0), [1.2, 1.6])
+    assert np.array_equal(prox.proj_annulus(np.zeros(3), 1.0, 2.0), np.zeros(3))
+    with pytest.raises(ValueError):
+        prox.proj_annulus(np.ones(2), 2.0, 1.0)
+
+
+def test_lines_follow_the_array_layout():
+    """Lines against numpy views of the z-fastest layout: X = w.reshape(nx, nz).T
+    is the n_z x n_x model, its columns X[:, j] and rows X[i, :]."""
+    nz, nx = 4, 3
+    w = np.arange(nz * nx, dtype=float)
+    X = w.reshape(nx, nz).T
+    cols = prox.lines((1, nx, nz), "z")
+    rows = prox.lines((1, nx, nz), "x")
+    assert len(cols) == nx and len(rows) == nz
+    for j in range(nx):
+        assert np.array_equal(w[cols[j]], X[:, j])
+    for i in range(nz):
+        assert np.array_equal(w[rows[i]], X[i, :])
+    ny = 2
+    w3 = np.arange(nz * nx * ny, dtype=float)
+    V = w3.reshape(ny, nx, nz)   # V[iy, ix, iz]
+    fib = prox.lines((ny, nx, nz), "y")
+    assert len(fib) == nz * nx
+    assert any(np.array_equal(w3[f], V[:, 1, 2]) for f in fib)
+
+
+def test_per_line_card_is_nearest_point_of_the_product_set():
+    """card(X[:, j]) <= k for every column j: brute force over all supports
+    of all columns at once (the set is their Cartesian product)."""
+    g = np.random.default_rng(8)
+    nz, nx, k = 3, 3, 1
+    w = g.standard_normal(nz * nx)
+    spec = {"type": "card", "k": k, "scope": "z", "shape": (1, nx, nz)}
+    y = prox.project(spec, w)
+    best = np.inf
+    for S in itertools.product(itertools.combinations(range(nz), k), repeat=nx):
+        z = np.zeros_like(w)
+        for j, sj in enumerate(S):
+            for i in sj:
+                z[j * nz + i] = w[j * nz + i]
+        best = min(best, float(np.linalg.norm(z - w)))
+    assert float(np.linalg.norm(y - w)) == pytest.approx(best, abs=1e-14)
+    assert all(np.count_nonzero(y[j * nz:(j + 1) * nz]) <= k for j in range(nx))
+
+
+def test_per_line_l2_and_l1_row_constraints():
+    """Rows X[i, :] each in an l2 ball / l1 ball: every row satisfies its
+    constraint, and rows already inside are unchanged."""
+    g = np.random.default_rng(9)
+    nz, nx = 5, 7
+    w = g.standard_normal(nz * nx) * 2
+    X = w.reshape(nx, nz).T
+    for t, norm in (("l2", lambda r: np.linalg.norm(r)), ("l1", lambda r: np.abs(r).sum())):
+        sigma = float(np.median([norm(X[i, :]) for i in range(nz)]))
+        y = prox.project({"type": t, "sigma": sigma, "scope": "x", "shape": (1, nx, nz)}, w)
+        Y = y.reshape(nx, nz).T
+        for i in range(nz):
+            assert norm(Y[i, :]) <= sigma * (1 + 1e-12)
+            if norm(X[i, :]) <= sigma:
+                assert np.array_equal(Y[i, :], X[i, :])
