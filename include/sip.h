@@ -68,8 +68,20 @@ typedef enum {
     SIP_SET_BOUNDS = 0, /* lo <= (Ax)[j] <= hi; lo/hi may be -/+INFINITY */
     SIP_SET_L1 = 1,     /* ||Ax||_1 <= sigma */
     SIP_SET_L2 = 2,     /* ||Ax||_2 <= sigma */
-    SIP_SET_CARD = 3    /* card(Ax) <= k; ties: larger |.| first, then lower index */
+    SIP_SET_CARD = 3,   /* card(Ax) <= k; ties: larger |.| first, then lower index */
+    SIP_SET_ANNULUS = 4 /* lo <= ||Ax||_2 <= hi, 0 <= lo <= hi (absolute radii);
+                           not convex for lo > 0; Ax = 0 is left at 0 */
 } sip_set_type;
+
+/* Where a set applies (the paper's per-column / per-row / per-fiber sets):
+ * to A x as a whole, or to every line of A x's output grid along z (the
+ * columns of a 2D model), along x (its rows) or along y (3D fibers), each
+ * line on its own.  Per-line sets: l1, l2, card or annulus (bounds apply
+ * entry-wise anyway); not with SIP_OP_TV (its parts live on different
+ * grids); absolute radii only (sigma_rel = 0); k_frac resolves against the
+ * line length; card and l1 lines hold at most SIP_MAX_LINE entries. */
+typedef enum { SIP_SCOPE_ALL = 0, SIP_SCOPE_Z = 1, SIP_SCOPE_X = 2, SIP_SCOPE_Y = 3 } sip_scope;
+#define SIP_MAX_LINE 4096
 
 typedef enum { SIP_F64 = 0, SIP_F32 = 1 } sip_dtype;
 
@@ -88,12 +100,14 @@ typedef struct {
 typedef struct {
     int op;           /* sip_op */
     int type;         /* sip_set_type */
-    double lo, hi;    /* SIP_SET_BOUNDS, lo <= hi */
+    double lo, hi;    /* SIP_SET_BOUNDS, lo <= hi; SIP_SET_ANNULUS radii */
     double sigma;     /* SIP_SET_L1 / L2 radius (>= 0), used when sigma_rel == 0 */
     double sigma_rel; /* > 0: radius = sigma_rel * ||A m|| (l1 or l2 norm of the
                          set), resolved on the device from each model m */
     int64_t k;        /* SIP_SET_CARD, >= 0, used when k_frac == 0 */
-    double k_frac;    /* > 0: k = floor(k_frac * N) with N the grid size */
+    double k_frac;    /* > 0: k = floor(k_frac * N) with N the grid size (per-line
+                         sets: the line length) */
+    int scope;        /* sip_scope (SIP_SCOPE_ALL when zero-initialised) */
 } sip_set;
 
 typedef struct {

@@ -133,8 +133,24 @@ static sip_status check_set(const GridDesc &g, const sip_set &s, int i) {
       if (s.k < 0) return fail(SIP_ERR_INVALID_ARG, "set %d: k < 0", i);
       if (!(s.k_frac >= 0.0) || !(s.k_frac <= 1.0)) return fail(SIP_ERR_INVALID_ARG, "set %d: k_frac not in [0, 1]", i);
       break;
+    case SIP_SET_ANNULUS:
+      if (!(s.lo >= 0.0) || !std::isfinite(s.lo) || !(s.hi >= s.lo))
+        return fail(SIP_ERR_INVALID_ARG, "set %d: annulus needs 0 <= lo <= hi", i);
+      break;
     default:
       return fail(SIP_ERR_INVALID_ARG, "set %d: unknown set type %d", i, s.type);
+  }
+  if (s.scope < SIP_SCOPE_ALL || s.scope > SIP_SCOPE_Y) return fail(SIP_ERR_INVALID_ARG, "set %d: unknown scope", i);
+  if (s.scope != SIP_SCOPE_ALL && s.type != SIP_SET_BOUNDS) {
+    if (s.op == SIP_OP_TV) return fail(SIP_ERR_INVALID_ARG, "set %d: per-line sets need a single-grid operator", i);
+    if (s.sigma_rel != 0.0) return fail(SIP_ERR_INVALID_ARG, "set %d: per-line sets take absolute radii", i);
+    if (s.scope == SIP_SCOPE_Y && g.ndim != 3) return fail(SIP_ERR_INVALID_ARG, "set %d: lines along y need 3D", i);
+    int64_t d[3];
+    int stag;
+    part_dims(g, op_parts(g, s.op)[0], d, stag);
+    const int64_t len = d[s.scope - 1];
+    if ((s.type == SIP_SET_CARD || s.type == SIP_SET_L1) && len > SIP_MAX_LINE)
+      return fail(SIP_ERR_INVALID_ARG, "set %d: lines of %lld entries exceed %d", i, (long long)len, SIP_MAX_LINE);
   }
   return SIP_OK;
 }
@@ -234,7 +250,25 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
     if (b < nsets) {
       const sip_set &s = sets[b];
       bd.op = s.op;
-      bd.type = s.type == SIP_SET_BOUNDS ? BT_BOUNDS : s.type == SIP_SET_L1 ? BT_L1 : s.type == SIP_SET_L2 ? BT_L2 : BT_CARD;
+      const int t = s.type == SIP_SET_BOUNDS ? BT_BOUNDS
+                    : s.type == SIP_SET_L1   ? BT_L1
+                    : s.type == SIP_SET_L2   ? BT_L2
+                    : s.type == SIP_SET_CARD ? BT_CARD
+                                             : BT_ANNULUS;
+      bd.type = (s.scope != SIP_SCOPE_ALL && t != BT_BOUNDS) ? BT_LINE : t;
+      if (bd.type == BT_LINE) {
+        bd.line_type = t;
+        bd.scope = s.scope;
+        int64_t dd[3];
+        int stag;
+        part_dims(g, op_parts(g, s.op)[0], dd, stag);
+        const int a = s.scope - 1;  // axis of the lines
+        bd.line_len = dd[a];
+        bd.nlines = dd[0] * dd[1] * dd[2] / dd[a];
+        bd.line_stride = a == 0 ? 1 : a == 1 ? dd[0] : dd[0] * dd[1];
+        bd.line_a = a == 0 ? 1 : a == 1 ? dd[0] : dd[0] * dd[1];
+        bd.line_b = a == 0 ? dd[0] : a == 1 ? dd[0] * dd[1] : 0;
+      }
       bd.lo = s.lo;
       bd.hi = s.hi;
       bd.sigma_abs = s.sigma;
@@ -251,11 +285,11 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
     bd.woff = bd.soff = -1;
     bd.job_w = bd.job_s = -1;
     // w / s scratch regions start on 16-byte boundaries (vector loads)
-    if (bd.type == BT_L1 || bd.type == BT_L2 || bd.type == BT_CARD) {
+    if (bd.type == BT_L1 || bd.type == BT_L2 || bd.type == BT_CARD || bd.type == BT_ANNULUS || bd.type == BT_LINE) {
       bd.woff = woff;
       woff += (bd.M + 3) / 4 * 4;
     }
-    if (bd.type == BT_L1 || bd.type == BT_CARD) {
+    if (bd.type == BT_L1 || bd.type == BT_CARD || bd.type == BT_LINE) {
       bd.soff = soff;
       soff += (bd.M + 3) / 4 * 4;
     }
@@ -313,7 +347,7 @@ double layout_bytes_per_iter(const InstLayout &L, int dtype) {
   double feas = 0.0;
   for (int b = 0; b < d.nb; ++b) {
     const BlockDev &bd = d.blk[b];
-    if (bd.type == BT_L2) words += 2.0 * bd.M;
+    if (bd.type == BT_L2 || bd.type == BT_ANNULUS || bd.type == BT_LINE) words += 2.0 * bd.M;
     if (bd.type == BT_L1 || bd.type == BT_CARD) {
       words += (2.0 + rsel) * bd.M;
       feas += (1.0 + rsel) * bd.M;
@@ -381,20 +415,21 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const size_t W = esize(dtype);
   // ---- sizes
   int64_t njobs = 0, ntie = 0;
-  std::vector<Tile> tn, trhs, tset, tsel, tfin;
+  std::vector<Tile> tn, trhs, tset, tsel, tfin, tline;
   P.any_card = P.any_fin = false;
   P.cg_launch = 0;
   P.max_iter = 0;
   P.check_every = 1 << 30;
   P.any_stop = false;
   // rows covered by each launch kind over all instances -> work-item size
-  int64_t tot_n = 0, tot_set = 0, tot_fin = 0, tot_sel = 0;
+  int64_t tot_n = 0, tot_set = 0, tot_fin = 0, tot_sel = 0, tot_line = 0;
   for (auto &L : insts) {
     tot_n += L.dev.N;
     for (int s = 0; s < L.dev.nseg; ++s) tot_set += L.dev.seg[s].len;
     for (int b = 0; b < L.dev.nb; ++b) {
       const int t = L.dev.blk[b].type;
-      if (t == BT_L1 || t == BT_L2 || t == BT_CARD) tot_fin += L.dev.blk[b].M;
+      if (t == BT_L1 || t == BT_L2 || t == BT_CARD || t == BT_ANNULUS) tot_fin += L.dev.blk[b].M;
+      if (t == BT_LINE) tot_line += L.dev.blk[b].nlines;
     }
     for (auto &j : L.jobs) tot_sel += j.M;
   }
@@ -429,6 +464,9 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const int64_t ch_set = chunk_for(tot_set, sms * launch_occupancy(dtype, 1));
   const int64_t ch_sel = chunk_for(tot_sel, sms * launch_occupancy(dtype, 2));
   const int64_t ch_fin = chunk_for(tot_fin, sms * launch_occupancy(dtype, 3));
+  // per-line sets: one CTA works one line at a time; lines per work item so
+  // that one launch is about four CTAs per SM
+  const int64_t ch_line = tot_line > 4 * sms ? (tot_line + 4 * sms - 1) / (4 * sms) : 1;
   for (int i = 0; i < P.ninst; ++i) {
     InstLayout &L = insts[i];
     InstDev &d = L.dev;
@@ -463,7 +501,8 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     const size_t b2 = tfin.size();
     for (int b = 0; b < d.nb; ++b) {
       const int t = d.blk[b].type;
-      if (t == BT_L1 || t == BT_L2 || t == BT_CARD) {
+      if (t == BT_LINE) push_tiles(tline, i, b, d.blk[b].nlines, ch_line);
+      if (t == BT_L1 || t == BT_L2 || t == BT_CARD || t == BT_ANNULUS) {
         push_tiles(tfin, i, b, d.blk[b].M, ch_fin);
         P.any_fin = true;
       }
@@ -491,6 +530,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.nt_set = (int)tset.size();
   P.nt_sel = (int)tsel.size();
   P.nt_fin = (int)tfin.size();
+  P.nt_line = (int)tline.size();
   P.njobs = (int)njobs;
 
   // ---- arena layout
@@ -569,6 +609,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const int64_t o_tset = take((int64_t)tset.size() * sizeof(Tile));
   const int64_t o_tsel = take((int64_t)tsel.size() * sizeof(Tile));
   const int64_t o_tfin = take((int64_t)tfin.size() * sizeof(Tile));
+  const int64_t o_tline = take((int64_t)tline.size() * sizeof(Tile));
   P.arena_bytes = off;
   if (dry) return SIP_OK;  // size only (admission control)
 
@@ -642,6 +683,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.d_tset = (Tile *)at(o_tset);
   P.d_tsel = (Tile *)at(o_tsel);
   P.d_tfin = (Tile *)at(o_tfin);
+  P.d_tline = tline.empty() ? nullptr : (Tile *)at(o_tline);
 
   std::vector<JobDev> jobs;
   int64_t cand_at = o_cand;
@@ -661,6 +703,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   if (!tset.empty()) CK(cudaMemcpy(P.d_tset, tset.data(), tset.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   if (!tsel.empty()) CK(cudaMemcpy(P.d_tsel, tsel.data(), tsel.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   if (!tfin.empty()) CK(cudaMemcpy(P.d_tfin, tfin.data(), tfin.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  if (!tline.empty()) CK(cudaMemcpy(P.d_tline, tline.data(), tline.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   return SIP_OK;
 }
 
@@ -676,7 +719,8 @@ int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, 
 // ----------------------------------------------------------------------------
 // Launches of one iteration.
 static int launches_per_iter(const Plan &P) {
-  return 3 + P.cg_launch + (P.nt_sel ? select_passes(P.dtype) : 0) + (P.any_card ? 1 : 0) + (P.nt_fin ? 1 : 0) + 1;
+  return 3 + P.cg_launch + (P.nt_sel ? select_passes(P.dtype) : 0) + (P.any_card ? 1 : 0) + (P.nt_line ? 1 : 0) +
+         (P.nt_fin ? 1 : 0) + 1;
 }
 
 // marks: every launch stamps its own slot pair of P.d_ts (timing graph)
@@ -718,6 +762,11 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
     T0(KT_TIES);
     CK(launch_ties(L, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
     T1(KT_TIES);
+  }
+  if (P.nt_line) {
+    T0(KT_FINAL);  // per-line sets
+    CK(launch_lines(L, P.d_tline, P.nt_line, P.d_insts, P.d_scal));
+    T1(KT_FINAL);
   }
   if (P.nt_fin) {
     T0(KT_FINAL);
@@ -787,6 +836,8 @@ static sip_status run_persistent(Plan &P, cudaStream_t st, int iters) {
   F.tset = P.d_tset;
   F.tsel = P.d_tsel;
   F.tfin = P.d_tfin;
+  F.tline = P.d_tline;
+  F.nt_line = P.nt_line;
   F.nt_n = P.nt_n;
   F.nt_set = P.nt_set;
   F.nt_sel = P.nt_sel;

@@ -439,6 +439,7 @@ sip_status sip_project_set(const sip_set *set, int dtype, const void *w_dev, int
                            double *scalar_out) {
   if (!set || !w_dev || !y_dev) return fail(SIP_ERR_INVALID_ARG, "NULL argument");
   if (n < 1) return fail(SIP_ERR_INVALID_ARG, "n must be >= 1");
+  if (set->scope != SIP_SCOPE_ALL) return fail(SIP_ERR_INVALID_ARG, "a single-step set applies to the whole vector");
   sip_set s = *set;
   s.op = SIP_OP_I;
   s.sigma_rel = 0.0;

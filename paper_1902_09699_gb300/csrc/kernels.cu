@@ -1398,7 +1398,7 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
     }
   } else {
     o.yn = o.vn = T(0);
-    if (q.type == BT_L2) acc[9] += (A)o.w * (A)o.w;
+    if (q.type == BT_L2 || q.type == BT_ANNULUS) acc[9] += (A)o.w * (A)o.w;
     if (q.type == BT_L1) acc[9] += fabs((A)o.w);
     if (q.chk) {
       acc[7] += (A)s * (A)s;
@@ -1433,7 +1433,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   q.chk = chk;
   const int kind = sg.kind, type = bd.type;
   const bool pointwise = q.pointwise;
-  const bool store_s = chk && !pointwise && type != BT_L2;
+  const bool store_s = chk && bd.soff >= 0;  // selections and per-line sets project s
   const T *__restrict__ x = (const T *)in.x;
   T *__restrict__ y = (T *)in.y + bd.yoff + sg.row0;
   T *__restrict__ v = (T *)in.v + bd.yoff + sg.row0;
@@ -1659,7 +1659,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
       if (type == BT_L1) atomicAdd(&a[A_S1], (double)d3[2]);
     }
   }
-  if (type == BT_L1 || type == BT_L2) {
+  if (type == BT_L1 || type == BT_L2 || type == BT_ANNULUS) {
     A d1[1] = {acc[9]};
     block_sum<1>(d1);
     if (threadIdx.x == 0) atomicAdd(&a[A_WNORM], (double)d1[0]);
@@ -1707,6 +1707,11 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
     const double nrm = sqrt(ldv(&a[A_WNORM]));
     const double sg2 = sc.sigma[b];
     sc.l2scale[b] = nrm > sg2 ? sg2 / nrm : 1.0;
+    sc.bf[b][BF_L2SCALE] = (float)sc.l2scale[b];
+  }
+  if (bd.type == BT_ANNULUS) {  // radial scaling onto the nearer sphere; w = 0 stays 0
+    const double nrm = sqrt(ldv(&a[A_WNORM]));
+    sc.l2scale[b] = nrm > bd.hi ? bd.hi / nrm : (nrm > 0.0 && nrm < bd.lo ? bd.lo / nrm : 1.0);
     sc.bf[b][BF_L2SCALE] = (float)sc.l2scale[b];
   }
   if (bd.job_w >= 0) {
@@ -2413,7 +2418,7 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   K K0 = 0;
   bool tie = false;
   int64_t need = 0, before = 0;
-  if (bd.type != BT_L2) {
+  if (bd.type != BT_L2 && bd.type != BT_ANNULUS) {
     const JobScal &js = jscal[bd.job_w];
     mode = js.mode;
     theta = SV<T>::theta(js);
@@ -2440,7 +2445,7 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   const int64_t end = tl.start + tl.len;
   // prox of one entry (no tie rank)
   auto prox = [&](T wv) -> T {
-    if (type == BT_L2) return wv * scale;
+    if (type == BT_L2 || type == BT_ANNULUS) return wv * scale;
     if (mode == JM_ALL) return wv;
     if (mode == JM_NONE) return T(0);
     if (type == BT_L1) {
@@ -2527,7 +2532,7 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
         const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
         const bool valid = row < end;
         T yn;
-        if (type == BT_L2) {
+        if (type == BT_L2 || type == BT_ANNULUS) {
           yn = wv[e] * scale;
         } else if (mode == JM_ALL) {
           yn = wv[e];
@@ -2598,6 +2603,250 @@ __global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ 
 }
 
 // --------------------------------------------------------------------------
+// Per-line sets: the simple set's projection of every line of A x along z, x
+// or y on its own (the paper's per-column / per-row / per-fiber sets).  One
+// CTA projects one line at a time: l2 and annulus from the line's norm;
+// card and l1 from the line sorted by (|value| decreasing, position
+// increasing), a bitonic sort in shared memory (lines of at most
+// kLineMax entries).  Then the dual update v = rho (y - w) and the adapt
+// sums as in the final pass; on check iterations the same projection of s
+// gives the feasibility distance.
+// --------------------------------------------------------------------------
+constexpr int kLineMax = SIP_MAX_LINE;
+template <typename T>
+constexpr size_t line_smem() {
+  return (size_t)kLineMax * (sizeof(typename KeyOf<T>::K) + sizeof(uint32_t) + 1);
+}
+
+// (key, position) pairs in decreasing key order, equal keys by position.
+template <typename K>
+__device__ void cta_sort_desc(K *key, uint32_t *pos, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += kThreads) {
+        const int q = i ^ j;
+        if (q > i) {
+          const K ki = key[i], kq = key[q];
+          const uint32_t pi = pos[i], pq = pos[q];
+          const bool i_first = ki > kq || (ki == kq && pi < pq);
+          if (((i & k) == 0) != i_first) {
+            key[i] = kq;
+            key[q] = ki;
+            pos[i] = pq;
+            pos[q] = pi;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Block-wide sum in binary64, fixed order.
+__device__ __forceinline__ double cta_sum_f64(double x, double *red) {
+  double a[1] = {x};
+  block_sum<1>(a);
+  if (threadIdx.x == 0) red[0] = a[0];
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Projection of one line of src (len entries, stride apart from base).
+// out == true: y = P(w), v = rho (y - w), adapt sums into ac; otherwise
+// (s on a check iteration) the squared distance and squared norm into
+// *d2, *s2 (thread 0).
+template <typename T>
+__device__ void line_project(const BlockDev &bd, const T *__restrict__ src, int64_t base, double sigma, int64_t kk,
+                             T rho, bool out, bool ad, bool ad_dots, T *__restrict__ y, T *__restrict__ v,
+                             T *__restrict__ k0y, T *__restrict__ k0v, typename AccOf<T>::type (&ac)[3],
+                             double *d2, double *s2, unsigned char *smem) {
+  using KT = KeyOf<T>;
+  using K = typename KT::K;
+  using A = typename AccOf<T>::type;
+  __shared__ double red[1];
+  __shared__ double s_theta;
+  __shared__ int s_best;
+  const int64_t L = bd.line_len, S = bd.line_stride;
+  const int lt = bd.line_type;
+  auto at = [&](int64_t e) { return base + e * S; };
+  // mode: 0 scale, 1 keep the flagged entries, 2 soft threshold
+  int mode = 0;
+  double scale = 1.0;
+  double theta = 0.0;
+  uint8_t *flag = nullptr;
+  double ss = 0.0, sa = 0.0;
+  for (int64_t e = threadIdx.x; e < L; e += kThreads) {
+    const double x = (double)src[at(e)];
+    ss += x * x;
+    sa += fabs(x);
+  }
+  ss = cta_sum_f64(ss, red);
+  if (lt == BT_L2 || lt == BT_ANNULUS) {
+    const double nrm = sqrt(ss);
+    const double hi = lt == BT_L2 ? sigma : bd.hi, lo = lt == BT_L2 ? 0.0 : bd.lo;
+    scale = nrm > hi ? hi / nrm : (nrm > 0.0 && nrm < lo ? lo / nrm : 1.0);
+  } else if (lt == BT_L1) {
+    sa = cta_sum_f64(sa, red);
+    if (sigma == 0.0) {
+      scale = 0.0;
+    } else if (sa > sigma) {
+      // theta from the sorted magnitudes u_1 >= u_2 >= ...: the largest j
+      // with u_j > (c_j - sigma) / j, c_j the running sum (Duchi et al.)
+      K *key = (K *)smem;
+      uint32_t *pos = (uint32_t *)(smem + (size_t)kLineMax * sizeof(K));
+      int n2 = 1;
+      while (n2 < L) n2 <<= 1;
+      for (int i = threadIdx.x; i < n2; i += kThreads) {
+        key[i] = i < L ? KT::key(src[at(i)]) : K(0);
+        pos[i] = (uint32_t)i;
+      }
+      __syncthreads();
+      cta_sort_desc(key, pos, n2);
+      // each thread sums a run of sorted entries; exclusive scan of the runs
+      const int per = (int)((L + kThreads - 1) / kThreads);
+      const int i0 = threadIdx.x * per, i1 = (int)(i0 + per < L ? i0 + per : L);
+      double run = 0.0;
+      for (int i = i0; i < i1; ++i) run += KT::val(key[i]);
+      __shared__ double wrun[kThreads];
+      wrun[threadIdx.x] = run;
+      if (threadIdx.x == 0) s_best = -1;
+      __syncthreads();
+      double c = 0.0;
+      for (int t = 0; t < (int)threadIdx.x; ++t) c += wrun[t];
+      int best = -1;
+      double cbest = 0.0;
+      for (int i = i0; i < i1; ++i) {
+        const double u = KT::val(key[i]);
+        c += u;
+        if (u > (c - sigma) / (double)(i + 1)) {
+          best = i;
+          cbest = c;
+        }
+      }
+      const int wb = __reduce_max_sync(0xffffffffu, best);
+      if ((threadIdx.x & 31) == 0 && wb >= 0) atomicMax(&s_best, wb);
+      __syncthreads();
+      if (best >= 0 && best == s_best) s_theta = (cbest - sigma) / (double)(best + 1);
+      __syncthreads();
+      theta = s_theta;
+      mode = 2;
+    }
+  } else {  // card
+    if (kk <= 0) {
+      scale = 0.0;
+    } else if (kk < L) {
+      K *key = (K *)smem;
+      uint32_t *pos = (uint32_t *)(smem + (size_t)kLineMax * sizeof(K));
+      flag = smem + (size_t)kLineMax * (sizeof(K) + sizeof(uint32_t));
+      int n2 = 1;
+      while (n2 < L) n2 <<= 1;
+      for (int i = threadIdx.x; i < n2; i += kThreads) {
+        key[i] = i < L ? KT::key(src[at(i)]) : K(0);
+        pos[i] = i < L ? (uint32_t)i : 0xffffffffu;
+        if (i < L) flag[i] = 0;
+      }
+      __syncthreads();
+      cta_sort_desc(key, pos, n2);
+      for (int i = threadIdx.x; i < kk; i += kThreads) flag[pos[i]] = 1;
+      __syncthreads();
+      mode = 1;
+    }
+  }
+  const T sc_t = (T)scale, th = (T)theta;
+  double dd = 0.0;
+  for (int64_t e = threadIdx.x; e < L; e += kThreads) {
+    const int64_t r = at(e);
+    const T wv = src[r];
+    T yn;
+    if (mode == 1) {
+      yn = flag[e] ? wv : T(0);
+    } else if (mode == 2) {
+      const T a = fabs(wv) - th;
+      yn = a > T(0) ? copysign(a, wv) : T(0);
+    } else {
+      yn = wv * sc_t;
+    }
+    if (out) {
+      const T vn = rho * (yn - wv);
+      if (ad_dots) {
+        const A dg = (A)k0y[r] - (A)yn;
+        const A dv = (A)vn - (A)k0v[r];
+        ac[0] += dg * dv;
+        ac[1] += dg * dg;
+        ac[2] += dv * dv;
+      }
+      y[r] = yn;
+      v[r] = vn;
+      if (ad) {
+        k0y[r] = yn;
+        k0v[r] = vn;
+      }
+    } else {
+      const double d = (double)wv - (double)yn;
+      dd += d * d;
+    }
+  }
+  if (!out) {
+    dd = cta_sum_f64(dd, red);
+    if (threadIdx.x == 0) {
+      *d2 += dd;
+      *s2 += ss;
+    }
+  }
+  __syncthreads();  // shared arrays are reused by the next line
+}
+
+template <typename T>
+__device__ __forceinline__ void body_lines(const Tile &tl, const InstDev *__restrict__ insts,
+                                           InstScal *__restrict__ scal, unsigned char *smem) {
+  using A = typename AccOf<T>::type;
+  const InstDev &in = insts[tl.inst];
+  InstScal &sc = scal[tl.inst];
+  if (sc.done) return;
+  const int b = tl.item;
+  const BlockDev &bd = in.blk[b];
+  const int k = sc.k;
+  const bool ad = adapt_iter(in, k);
+  const bool ad_dots = ad && sc.have_k0;
+  const bool chk = check_iter(in, k);
+  const T rho = SV<T>::blk(sc, b, BF_RHO);
+  const double sigma = sc.sigma[b];
+  const int64_t kk = sc.kcard[b];
+  const T *__restrict__ w = (const T *)in.w + bd.woff;
+  const T *__restrict__ s = (const T *)in.s + bd.soff;
+  T *__restrict__ y = (T *)in.y + bd.yoff;
+  T *__restrict__ v = (T *)in.v + bd.yoff;
+  T *__restrict__ k0y = (T *)in.k0y + bd.yoff;
+  T *__restrict__ k0v = (T *)in.k0v + bd.yoff;
+  A ac[3] = {A(0), A(0), A(0)};
+  double d2 = 0.0, s2 = 0.0;
+  for (int64_t j = tl.start; j < tl.start + tl.len; ++j) {
+    const int64_t base = (j % bd.line_a) + (j / bd.line_a) * bd.line_b;
+    line_project<T>(bd, w, base, sigma, kk, rho, true, ad, ad_dots, y, v, k0y, k0v, ac, &d2, &s2, smem);
+    if (chk) line_project<T>(bd, s, base, sigma, kk, rho, false, false, false, y, v, k0y, k0v, ac, &d2, &s2, smem);
+  }
+  if (ad_dots) {
+    block_sum<3>(ac);
+    if (threadIdx.x == 0) {
+      atomicAdd(&sc.acc[b][A_GV], (double)ac[0]);
+      atomicAdd(&sc.acc[b][A_GG], (double)ac[1]);
+      atomicAdd(&sc.acc[b][A_VV], (double)ac[2]);
+    }
+  }
+  if (chk && threadIdx.x == 0) atomicAdd(&sc.acc[b][A_FEAS_D2], d2);  // ||s||^2: the set pass
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_lines(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                    InstScal *__restrict__ scal, unsigned long long *ts) {
+  const Stamp stamp(ts);
+  extern __shared__ unsigned char smem_raw[];
+  body_lines<T>(tiles[blockIdx.x], insts, scal, smem_raw);
+}
+
+// --------------------------------------------------------------------------
 // Per-instance tail: stopping quantities, Algorithm adapt-rho-gamma, C.
 // --------------------------------------------------------------------------
 __device__ void set_coefficients(const InstDev &in, InstScal &sc) {
@@ -2658,10 +2907,13 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
         // r_feas_i (Eq. feas_stop)
         const double s2 = a[A_S2];
         double d = 0.0;
-        if (bd.type == BT_BOUNDS) {
+        if (bd.type == BT_BOUNDS || bd.type == BT_LINE) {
           d = sqrt(a[A_FEAS_D2]);
         } else if (bd.type == BT_L2) {
           d = fmax(0.0, sqrt(s2) - sc.sigma[b]);  // ||s - P(s)|| = ||s|| - sigma outside the ball
+        } else if (bd.type == BT_ANNULUS) {
+          const double n = sqrt(s2);  // distance to the nearer sphere; s = 0 stays 0
+          d = n > bd.hi ? n - bd.hi : (n > 0.0 && n < bd.lo ? bd.lo - n : 0.0);
         } else {
           const JobScal &js = jscal[bd.job_s];
           if (js.mode == JM_ALL) {
@@ -2924,9 +3176,16 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar) {
   return ok != 0;
 }
 
+// dynamic shared memory of the persistent kernel: the select histogram or
+// the per-line arrays, whichever is larger
+template <typename T>
+constexpr size_t fused_smem() {
+  return BinAcc<T>::kSmem > line_smem<T>() ? BinAcc<T>::kSmem : line_smem<T>();
+}
+
 struct FusedArgs {
-  const Tile *tn, *tset, *tsel, *tfin;
-  int nt_n, nt_set, nt_sel, nt_fin;
+  const Tile *tn, *tset, *tsel, *tfin, *tline;
+  int nt_n, nt_set, nt_sel, nt_fin, nt_line;
   const InstDev *insts;
   InstScal *scal;
   const JobDev *jobs;
@@ -2962,6 +3221,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
     }
     if (A.any_card) {
       for (int i = blockIdx.x; i < A.nt_fin; i += gridDim.x) body_ties<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
+      if (!grid_barrier(A.bar)) return;
+    }
+    if (A.nt_line) {
+      extern __shared__ unsigned char smem_raw[];
+      for (int i = blockIdx.x; i < A.nt_line; i += gridDim.x) body_lines<T>(A.tline[i], A.insts, A.scal, smem_raw);
       if (!grid_barrier(A.bar)) return;
     }
     if (A.any_fin) {
@@ -3062,7 +3326,7 @@ __global__ void __launch_bounds__(kThreads) k_norms(const Tile *__restrict__ til
       const double n1 = ldv(&sc.acc[b][A_M1]), n2 = ldv(&sc.acc[b][A_M2]);
       sc.sigma[b] = bd.sigma_rel * (bd.type == BT_L1 ? n1 : sqrt(n2));
     }
-    if (bd.k_frac > 0.0) sc.kcard[b] = (int64_t)floor(bd.k_frac * (double)in.N);
+    if (bd.k_frac > 0.0) sc.kcard[b] = (int64_t)floor(bd.k_frac * (double)(bd.type == BT_LINE ? bd.line_len : in.N));
     sc.acc[b][A_M1] = 0.0;
     sc.acc[b][A_M2] = 0.0;
   }
@@ -3186,6 +3450,11 @@ cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const Inst
                                                                      hs3, hstride, pass, L.ts);
   return cudaGetLastError();
 }
+cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
+  SIP_DISPATCH(L, k_lines, nt, kThreads, (L.dtype == SIP_F64 ? line_smem<double>() : line_smem<float>()), tiles, insts,
+               scal, L.ts);
+  return cudaGetLastError();
+}
 cudaError_t kernels_setup() {
   // the binary32 select histogram needs 56 KB of shared memory: opt in once
   static bool done = false;
@@ -3197,9 +3466,13 @@ cudaError_t kernels_setup() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_rhs_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRhsSmemMax);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<float>::kSmem);
+  e = cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<float>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
+  e = cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lines<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<double>());
   if (e != cudaSuccess) return e;
   done = true;
   return cudaSuccess;
@@ -3241,6 +3514,8 @@ cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
   A.tset = F.tset;
   A.tsel = F.tsel;
   A.tfin = F.tfin;
+  A.tline = F.tline;
+  A.nt_line = F.nt_line;
   A.nt_n = F.nt_n;
   A.nt_set = F.nt_set;
   A.nt_sel = F.nt_sel;
@@ -3265,7 +3540,7 @@ cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
   A.iters = F.iters;
   void *args[] = {&A};
   const bool d = L.dtype == SIP_F64;
-  const size_t smem = d ? BinAcc<double>::kSmem : BinAcc<float>::kSmem;
+  const size_t smem = d ? fused_smem<double>() : fused_smem<float>();
   return cudaLaunchCooperativeKernel(d ? (const void *)k_fused<double> : (const void *)k_fused<float>, grid, kThreads,
                                      args, smem, L.stream);
 }
@@ -3277,7 +3552,7 @@ int fused_grid(int dtype) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const bool d = dtype == SIP_F64;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d ? (const void *)k_fused<double> : (const void *)k_fused<float>,
-                                                kThreads, d ? BinAcc<double>::kSmem : BinAcc<float>::kSmem);
+                                                kThreads, d ? fused_smem<double>() : fused_smem<float>());
   cudaGetLastError();
   return sms * n;
 }

@@ -34,7 +34,9 @@ constexpr int kDigitBits = 11;       // radix digit of the selection passes
 constexpr int kBins = 1 << kDigitBits;
 
 enum SegKind : int32_t { SEG_I = 0, SEG_DZ = 1, SEG_DX = 2, SEG_DY = 3, SEG_RING = 4 };
-enum BlkType : int32_t { BT_BOUNDS = 0, BT_L1 = 1, BT_L2 = 2, BT_CARD = 3, BT_DIST = 4 };
+// BT_ANNULUS: the annulus on A x as a whole; BT_LINE: a set applied to
+// every line of A x on its own (BlockDev.line_type says which).
+enum BlkType : int32_t { BT_BOUNDS = 0, BT_L1 = 1, BT_L2 = 2, BT_CARD = 3, BT_DIST = 4, BT_ANNULUS = 5, BT_LINE = 6 };
 enum JobKind : int32_t { JOB_L1 = 0, JOB_TOPK = 1 };
 // How a selection job resolved: run the radix select, or the set keeps
 // everything (inside the ball / k >= M), or nothing (tau = 0 / k = 0).
@@ -108,6 +110,13 @@ struct BlockDev {
   int64_t k_abs;
   int32_t job_w, job_s;  // selection jobs (global index) or -1
   int32_t seg0, nseg;
+  // BT_LINE: the simple set of every line (BT_L1, BT_L2, BT_CARD or
+  // BT_ANNULUS) and the lines on the operator's output grid (z fastest):
+  // line j holds line_len entries line_stride apart from
+  // (j % line_a) + (j / line_a) * line_b, with (line_a, line_b) = (1, len)
+  // along z, (n_z', n_z' n_x') along x and (n_z' n_x', 0) along y
+  int32_t line_type, scope;
+  int64_t line_len, line_stride, nlines, line_a, line_b;
 };
 
 struct JobDev {

@@ -61,8 +61,8 @@ struct Plan {
   uint32_t *d_hcnt = nullptr;
   double *d_hs1 = nullptr, *d_hs2 = nullptr, *d_hs3 = nullptr;
   uint32_t *d_ties = nullptr;
-  Tile *d_tn = nullptr, *d_tset = nullptr, *d_tsel = nullptr, *d_tfin = nullptr;
-  int nt_n = 0, nt_set = 0, nt_sel = 0, nt_fin = 0, njobs = 0;
+  Tile *d_tn = nullptr, *d_tset = nullptr, *d_tsel = nullptr, *d_tfin = nullptr, *d_tline = nullptr;
+  int nt_n = 0, nt_set = 0, nt_sel = 0, nt_fin = 0, nt_line = 0, njobs = 0;
   // staged right-hand side: its own work items and shared-memory bytes (0: not staged)
   Tile *d_trhs = nullptr;
   int nt_rhs = 0;

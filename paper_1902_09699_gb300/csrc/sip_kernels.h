@@ -46,8 +46,8 @@ int select_passes(int dtype);
 
 // persistent cooperative form of the iteration (kernels.cu)
 struct FusedLaunch {
-  const Tile *tn, *tset, *tsel, *tfin;
-  int nt_n, nt_set, nt_sel, nt_fin;
+  const Tile *tn, *tset, *tsel, *tfin, *tline;
+  int nt_n, nt_set, nt_sel, nt_fin, nt_line;
   const InstDev *insts;
   InstScal *scal;
   const JobDev *jobs;
@@ -64,6 +64,9 @@ cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid);
 int fused_grid(int dtype);
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                         const JobDev *jobs, JobScal *jscal, uint32_t *ties);
+// Per-line sets: one CTA per work item of lines (item = block, start/len =
+// lines), after the set pass.
+cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                          const JobDev *jobs, const JobScal *jscal, const uint32_t *ties);
 // cg_launch: step launches per iteration

