@@ -384,7 +384,7 @@ def run_grf3d(args):
     from paper_1902_09699_gb300 import workloads as W
     c = W.grf_3d()
     its = c["opts"]["max_iter"]
-    opts = dict(c["opts"], levels=2, coarse_iter=its)
+    opts = dict(c["opts"], levels=args.levels, coarse_iter=its)
     pr = sip.Projector(c["grid"], c["sets"], dtype="f32", exec=args.exec, **opts)
     m = torch.as_tensor(c["m"], dtype=torch.float32, device="cuda")
     x = torch.empty_like(m)
@@ -410,7 +410,8 @@ def run_grf3d(args):
     out = {"metric": METRIC, "value": its / (ms / 1000.0), "unit": "fine iter/s (coarse level included in time)",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": c["name"], "grid": list(c["grid"]["n"]), "levels": 2, "iterations_per_level": its,
+           "config": {"workload": c["name"], "grid": list(c["grid"]["n"]), "levels": args.levels,
+                      "iterations_per_level": its,
                       "exec": args.exec, "l2_between_steps": "flushed"},
            "projections_per_s": 1000.0 / ms, "rel_err_vs_f64_gpu": rel_err,
            "projections_per_s_at_1e-4": 1000.0 / ms if rel_err <= 1e-4 else 0.0,
@@ -419,6 +420,126 @@ def run_grf3d(args):
            "clocks": clk}
     print(json.dumps(out))
     pr.close()
+    return 0
+
+
+def run_lines(args):
+    """2D 512 x 1024 layered model with per-row and per-column cardinality
+    sets next to whole-model ones, FP32, against the FP64 GPU loop; the
+    per-kernel breakdown shows the per-line kernel under "final"."""
+    import torch
+
+    from paper_1902_09699_gb300 import sip
+    from paper_1902_09699_gb300 import workloads as W
+    c = W.lines_2d()
+    its = c["opts"]["max_iter"]
+    pr = sip.Projector(c["grid"], c["sets"], dtype="f32", exec=args.exec, **c["opts"])
+    m = torch.as_tensor(c["m"], dtype=torch.float32, device="cuda")
+    x = torch.empty_like(m)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pr.project(m, x, info=False)
+    clocks = Clocks()
+    clocks.start()
+    step_ms = _timed_steps(lambda: pr.project(m, x, info=False), args.steps, flush, st)
+    clk = clocks.stop()
+    ms = sum(step_ms) / args.steps
+    pr.set_timing(True)
+    x32, info = pr.project(m, None)
+    kt = pr.kernel_times()
+    pr.set_timing(False)
+    pr64 = sip.Projector(c["grid"], c["sets"], dtype="f64", exec=args.exec, **c["opts"])
+    m64 = m.double()
+    pr64.project(m64, info=False)
+    f64_ms = _timed_steps(lambda: pr64.project(m64, info=False), 1, flush, st)[0]
+    x64, _ = pr64.project(m64)
+    pr64.close()
+    rel_err = float((x32.double() - x64).norm() / x64.norm())
+    bpi = pr.bytes_per_iter()
+    peak, _ = peaks()
+    out = {"metric": METRIC, "value": its / (ms / 1000.0), "unit": "iter/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": c["name"], "grid": list(c["grid"]["n"]), "sets": len(c["sets"]),
+                      "iterations": its, "exec": args.exec, "l2_between_steps": "flushed"},
+           "projections_per_s": 1000.0 / ms, "rel_err_vs_f64_gpu": rel_err,
+           "projections_per_s_at_1e-4": 1000.0 / ms if rel_err <= 1e-4 else 0.0,
+           "f64_gpu_loop": {"ms_per_projection": f64_ms, "iter_per_s": its / (f64_ms / 1000.0)},
+           "r_feas": info["r_feas"], "bytes_per_iter": bpi, "pct_hbm_peak": bpi * its / (ms / 1000.0) / 1e9 / peak,
+           "kernel_breakdown_ms_per_step": {k: v["ms"] for k, v in kt.items()}, "clocks": clk}
+    print(json.dumps(out))
+    pr.close()
+    return 0
+
+
+def run_dykstra(args):
+    """The comparison of Sec. "Parallel Dykstra versus PARSDMM" on a seeded
+    341 x 400 layered model (the paper's geological model is not available):
+    bounds, anisotropic TV l1 ball (0.3 TV(m)), vertical monotonicity.  Both
+    methods run to max_i r_feas_i <= 1e-3 (Eq. feas_stop, checked on x):
+    PARSDMM with its feasibility stopping rule, parallel Dykstra with
+    single-set PARSDMM sub-problems (50 iterations each) over doubling sweep
+    counts.  Reports CG steps, l1-ball projections and device time."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_1902_09699_gb300 import sip
+    from paper_1902_09699_gb300 import workloads as W
+    n = (341, 400)
+    grid = {"n": n}
+    m = W.layered(n, seed=1007)
+    mt = torch.as_tensor(m, dtype=torch.float32, device="cuda")
+    tv = float(sip.apply_op(grid, "TV", mt.double()).abs().sum())
+    sets = [{"op": "I", "type": "bounds", "lo": 2.0, "hi": 4.0},
+            {"op": "TV", "type": "l1", "sigma": 0.3 * tv},
+            {"op": "DZ", "type": "bounds", "lo": 0.0, "hi": math.inf}]
+
+    def feas(x):
+        worst = 0.0
+        for s in sets:
+            a = sip.apply_op(grid, s["op"], x)
+            y, _ = sip.project_set(dict(s, op="I"), a)
+            na = float(a.double().norm())
+            d = float((a - y).double().norm())
+            worst = max(worst, d / na if na > 0 else d)
+        return worst
+
+    eps = 1e-3
+    pr = sip.Projector(grid, sets, dtype="f32", max_iter=20000, stop=2, eps_feas=eps, adapt=1, gamma0=1.5,
+                       check_every=5)
+    pr.project(mt)
+    x_pd, ip = pr.project(mt)
+    pr.close()
+    parsdmm = {"iters": ip["iters"], "cg_steps": ip["cg_steps"], "l1_projections": ip["iters"], "ms": ip["ms"],
+               "r_feas_max": feas(x_pd)}
+    dykstra = {}
+    for inner in (50, 250):
+        dk = sip.Dykstra(grid, sets, dtype="f32", max_iter=inner, cg_iters=5, adapt=1, gamma0=1.5)
+        curve = []
+        reached = None
+        sweeps = 1
+        while sweeps <= 128:
+            x_dk, idk = dk.project(mt, sweeps)
+            f = feas(x_dk)
+            curve.append({"sweeps": sweeps, "r_feas_max": f, "cg_steps": idk["cg_steps"],
+                          "l1_projections": idk["l1_projections"], "ms": idk["ms"]})
+            if f <= eps:
+                reached = curve[-1]
+                break
+            sweeps *= 2
+        dk.close()
+        dykstra["inner_%d" % inner] = {"reached": reached, "best_r_feas_max": min(c["r_feas_max"] for c in curve),
+                                       "curve": curve}
+    out = {"metric": "PARSDMM vs parallel Dykstra: CG steps, l1-ball projections and time to r_feas <= 1e-3",
+           "value": parsdmm["cg_steps"], "unit": "PARSDMM CG steps to r_feas <= 1e-3", "n_gpus": 1,
+           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "2d-341x400-layered-bounds-tv-monotone", "grid": list(n), "eps_feas": eps,
+                      "dykstra_sweeps_max": 128},
+           "parsdmm": parsdmm, "dykstra": dykstra}
+    print(json.dumps(out))
     return 0
 
 
@@ -475,10 +596,12 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=30)
     ap.add_argument("--exec", default="auto", choices=["auto", "graph", "persistent"],
                     help="iteration execution: persistent cooperative kernel or per-phase kernels in a CUDA graph")
-    ap.add_argument("--workload", default="layered", choices=["layered", "ragged", "grf3d", "serving"],
+    ap.add_argument("--workload", default="layered",
+                    choices=["layered", "ragged", "grf3d", "serving", "lines", "dykstra"],
                     help="layered: 512 x 1024 five-set 2D model (default line); ragged: 512-instance batch; "
                          "grf3d: 256 x 256 x 128 two-level")
     ap.add_argument("--count", type=int, default=512, help="ragged: instances")
+    ap.add_argument("--levels", type=int, default=2, help="grf3d: ML-PARSDMM levels")
     ap.add_argument("--sample", type=int, default=16, help="ragged: instances timed one at a time in FP64")
     ap.add_argument("--requests", type=int, default=64, help="serving: requests taken from the Poisson stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
@@ -487,6 +610,10 @@ def main():
         return run_reference(args)
     if args.workload == "ragged":
         return run_ragged(args)
+    if args.workload == "lines":
+        return run_lines(args)
+    if args.workload == "dykstra":
+        return run_dykstra(args)
     if args.workload == "grf3d":
         return run_grf3d(args)
     if args.workload == "serving":

@@ -236,6 +236,29 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev,
 int64_t sip_batch_offset(const sip_handle *h, int i);
 
 /* ---------------------------------------------------------------------
+ * Parallel Dykstra baseline (Appendix A; the comparison of Sec. "Parallel
+ * Dykstra versus PARSDMM").  argmin 1/2 ||x - m||^2 over the intersection
+ * of the p sets {x : A_i x in C_i} by parallel Dykstra sweeps: y_i =
+ * P_i(v_i), x = (1/p) sum_i y_i, v_i = x + v_i - y_i, from x = v_i = m.
+ * Each projection P_i is computed like the paper's sub-problem solver: the
+ * same iteration as PARSDMM with the one set i, `inner->max_iter`
+ * iterations (or its stopping rule), starting from zero state; the p
+ * sub-problems of a sweep run as one batched projection.  The sets must be
+ * fixed across sweeps: absolute radii only (sigma_rel = 0).  Errors as
+ * sip_create; levels must be 1. */
+typedef struct {
+    int sweeps;          /* Dykstra sweeps run */
+    int64_t cg_steps;    /* per sweep the largest sub-problem's CG steps, summed */
+    int64_t l1_projections; /* l1-ball projections: sweeps x sub-problem iterations of l1 sets */
+    float ms;            /* device time (CUDA events) */
+} sip_dykstra_info;
+sip_status sip_dykstra_create(const sip_grid *grid, const sip_set *sets, int nsets, const sip_options *inner,
+                              sip_handle **out);
+/* m_dev and x_dev: N elements of the handle's dtype; synchronises. */
+sip_status sip_dykstra_project(sip_handle *h, const void *m_dev, void *x_dev, int sweeps, void *stream,
+                               sip_dykstra_info *info);
+
+/* ---------------------------------------------------------------------
  * Projection server (continuous batching).  Requests may be submitted
  * from any thread at any time; a worker thread admits queued requests as
  * cohorts when the HBM budget has room for a cohort's whole state (sized

@@ -464,9 +464,9 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   const int64_t ch_set = chunk_for(tot_set, sms * launch_occupancy(dtype, 1));
   const int64_t ch_sel = chunk_for(tot_sel, sms * launch_occupancy(dtype, 2));
   const int64_t ch_fin = chunk_for(tot_fin, sms * launch_occupancy(dtype, 3));
-  // per-line sets: one CTA works one line at a time; lines per work item so
-  // that one launch is about four CTAs per SM
-  const int64_t ch_line = tot_line > 4 * sms ? (tot_line + 4 * sms - 1) / (4 * sms) : 1;
+  // per-line sets: one line per work item (a line's radix passes are short
+  // and latency-bound; more CTAs in flight beat longer CTAs in one wave)
+  const int64_t ch_line = 1;
   for (int i = 0; i < P.ninst; ++i) {
     InstLayout &L = insts[i];
     InstDev &d = L.dev;

@@ -17,6 +17,8 @@ struct sip_handle {
   Plan lev[SIP_MAX_LEVELS];  // lev[0]: finest grid; lev[l]: the grid coarsened l times (ML-PARSDMM)
   int levels = 1;
   int batch = 0;    // > 0: a batched handle of `batch` instances (packed buffers)
+  bool dykstra = false;  // parallel Dykstra: the batch holds the p single-set sub-problems
+  void *dk_x = nullptr;  // its iterate x
   sip_options opts;
   sip_grid grid;
   std::vector<sip_set> sets;
@@ -185,6 +187,7 @@ sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets, cons
 
 sip_status sip_destroy(sip_handle *h) {
   if (!h) return SIP_OK;
+  if (h->dk_x) cudaFree(h->dk_x);
   for (auto &P : h->lev) P.release();
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -630,6 +633,80 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void
       if (sc[i].stop_reason < 0) nonfinite = true;
     }
     if (nonfinite) return fail(SIP_ERR_NONFINITE, "a model holds NaN or Inf");
+    return SIP_OK;
+  };
+  return keep(h, run());
+}
+
+// ----------------------------------------------------------------------------
+// parallel Dykstra baseline
+// ----------------------------------------------------------------------------
+sip_status sip_dykstra_create(const sip_grid *grid, const sip_set *sets, int nsets, const sip_options *inner,
+                              sip_handle **out) {
+  if (!out) return fail(SIP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  sip_status st = validate(grid, sets, nsets, inner);
+  if (st) return st;
+  for (int i = 0; i < nsets; ++i)
+    if (sets[i].sigma_rel != 0.0) return fail(SIP_ERR_INVALID_ARG, "set %d: Dykstra's sets take absolute radii", i);
+  std::vector<sip_grid> grids(nsets, *grid);
+  std::vector<int> ns(nsets, 1);
+  sip_handle *h = nullptr;
+  if ((st = sip_batch_create(nsets, grids.data(), sets, ns.data(), inner, &h))) return st;
+  h->dykstra = true;
+  h->sets.assign(sets, sets + nsets);
+  const size_t bytes = (size_t)grid_desc(*grid).N() * esz(inner->dtype);
+  if (cudaMalloc(&h->dk_x, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->dk_x = nullptr;
+    sip_destroy(h);
+    return fail(SIP_ERR_OOM, "device allocation failed");
+  }
+  *out = h;
+  return SIP_OK;
+}
+
+sip_status sip_dykstra_project(sip_handle *h, const void *m_dev, void *x_dev, int sweeps, void *stream,
+                               sip_dykstra_info *info) {
+  if (!h || !h->dykstra) return fail(SIP_ERR_INVALID_ARG, "not a Dykstra handle");
+  if (!m_dev || !x_dev || sweeps < 1) return keep(h, fail(SIP_ERR_INVALID_ARG, "NULL buffer or sweeps < 1"));
+  h->err.clear();
+  Plan &P = h->lev[0];
+  cudaStream_t st = (cudaStream_t)stream;
+  const int p = P.ninst;
+  const int64_t N = P.h_insts[0].N;
+  const size_t W = esz(P.dtype);
+  auto run = [&]() -> sip_status {
+    if (info) memset(info, 0, sizeof *info);
+    CKH(cudaEventRecord(h->ev0, st));
+    for (int i = 0; i < p; ++i)  // v_i = m
+      CKH(cudaMemcpyAsync((char *)P.m_pack + (size_t)i * N * W, m_dev, (size_t)N * W, cudaMemcpyDeviceToDevice, st));
+    std::vector<InstScal> sc(p);
+    for (int sw = 0; sw < sweeps; ++sw) {
+      sip_status s = plan_prepare(P, st, false);  // every sub-problem from zero state
+      if (!s) s = run_iterations(P, st, h->cap, P.max_iter, h->opts.stop != 0, h->pinned, nullptr);
+      if (s) return s;
+      CKH(launch_dykstra_update(Launch{P.dtype, st}, P.x_pack, P.m_pack, h->dk_x, p, N));
+      if (info) {
+        CKH(cudaMemcpyAsync(sc.data(), P.d_scal, p * sizeof(InstScal), cudaMemcpyDeviceToHost, st));
+        CKH(cudaStreamSynchronize(st));
+        int64_t cg = 0;
+        for (int i = 0; i < p; ++i) {
+          if (sc[i].cg_total > cg) cg = sc[i].cg_total;
+          if (h->sets[i].type == SIP_SET_L1) info->l1_projections += sc[i].iters;
+        }
+        info->cg_steps += cg;
+        info->sweeps = sw + 1;
+      }
+    }
+    CKH(cudaMemcpyAsync(x_dev, h->dk_x, (size_t)N * W, cudaMemcpyDeviceToDevice, st));
+    CKH(cudaEventRecord(h->ev1, st));
+    CKH(cudaStreamSynchronize(st));
+    uint32_t ctrl[8];
+    CKH(cudaMemcpy(ctrl, P.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
+    if (ctrl[2] != 0)
+      return fail(SIP_ERR_TIMEOUT, "a bounded device wait ran out (a grid barrier or a bulk copy did not complete)");
+    if (info) cudaEventElapsedTime(&info->ms, h->ev0, h->ev1);
     return SIP_OK;
   };
   return keep(h, run());

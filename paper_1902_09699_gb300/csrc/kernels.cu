@@ -2675,7 +2675,6 @@ __device__ void line_project(const BlockDev &bd, const T *__restrict__ src, int6
   int mode = 0;
   double scale = 1.0;
   double theta = 0.0;
-  uint8_t *flag = nullptr;
   double ss = 0.0, sa = 0.0;
   for (int64_t e = threadIdx.x; e < L; e += kThreads) {
     const double x = (double)src[at(e)];
@@ -2737,31 +2736,110 @@ __device__ void line_project(const BlockDev &bd, const T *__restrict__ src, int6
     if (kk <= 0) {
       scale = 0.0;
     } else if (kk < L) {
-      K *key = (K *)smem;
-      uint32_t *pos = (uint32_t *)(smem + (size_t)kLineMax * sizeof(K));
-      flag = smem + (size_t)kLineMax * (sizeof(K) + sizeof(uint32_t));
-      int n2 = 1;
-      while (n2 < L) n2 <<= 1;
-      for (int i = threadIdx.x; i < n2; i += kThreads) {
-        key[i] = i < L ? KT::key(src[at(i)]) : K(0);
-        pos[i] = i < L ? (uint32_t)i : 0xffffffffu;
-        if (i < L) flag[i] = 0;
+      mode = 1;
+    }
+  }
+  // card: the k-th key K by radix passes over the line (11-bit digits, a
+  // shared-memory histogram, the bin picked through warp totals); entries
+  // above K stay, and of the cK entries equal to K the first `need` in line
+  // order.  Thread t then walks positions [t c, (t + 1) c) in order, its
+  // tie rank starting at the tied entries of the threads before it.
+  K kkey = 0;
+  uint32_t need = 0, tie0 = 0;
+  bool all_ties = true;
+  const int per = (int)((L + kThreads - 1) / kThreads);
+  const int e0 = (int)threadIdx.x * per, e1 = (int)(e0 + per < L ? e0 + per : L);
+  if (mode == 1) {
+    constexpr int kWarps = kThreads / 32;
+    uint32_t *h = (uint32_t *)smem;
+    __shared__ uint32_t wt[kWarps];
+    __shared__ uint32_t s_above, s_cnt;
+    __shared__ int s_bin;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    need = (uint32_t)kk;
+    K pre = 0;
+    uint32_t cK = 0;
+    for (int hi = KT::kBits; hi > 0;) {
+      const int lo = hi > kDigitBits ? hi - kDigitBits : 0;
+      const int nbins = 1 << (hi - lo);
+      for (int i = threadIdx.x; i < kBins; i += kThreads) h[i] = 0u;
+      __syncthreads();
+      for (int64_t e = threadIdx.x; e < L; e += kThreads) {
+        const K key = KT::key(src[at(e)]);
+        if (hi == KT::kBits || (key >> hi) == (pre >> hi)) atomicAdd(&h[(int)((key >> lo) & (K)(nbins - 1))], 1u);
       }
       __syncthreads();
-      cta_sort_desc(key, pos, n2);
-      for (int i = threadIdx.x; i < kk; i += kThreads) flag[pos[i]] = 1;
+      uint32_t c[kPer], tc = 0;
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        c[j] = h[threadIdx.x * kPer + j];
+        tc += c[j];
+      }
+      const uint32_t ws = __reduce_add_sync(0xffffffffu, tc);
+      if (lane == 0) wt[wid] = ws;
       __syncthreads();
-      mode = 1;
+      uint32_t aw = 0;
+#pragma unroll
+      for (int w2 = kWarps - 1; w2 > wid; --w2) aw += wt[w2];
+      if (aw < need && need <= aw + ws) {
+        uint32_t incl = tc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v2 = __shfl_down_sync(0xffffffffu, incl, o);
+          if (lane + o < 32) incl += v2;
+        }
+        uint32_t ac = aw + incl - tc;
+        if (ac < need && need <= ac + tc) {
+          for (int j = kPer - 1; j >= 0; --j) {
+            if (ac + c[j] >= need) {
+              s_bin = threadIdx.x * kPer + j;
+              s_above = ac;
+              s_cnt = c[j];
+              break;
+            }
+            ac += c[j];
+          }
+        }
+      }
+      __syncthreads();
+      need -= s_above;
+      cK = s_cnt;
+      pre = (K)(pre | ((K)s_bin << lo));
+      hi = lo;
+      __syncthreads();
+    }
+    kkey = pre;
+    all_ties = need >= cK;
+    if (!all_ties) {
+      // tied entries before this thread's positions (in line order)
+      uint32_t mine = 0;
+      for (int e = e0; e < e1; ++e) mine += KT::key(src[at(e)]) == kkey ? 1u : 0u;
+      uint32_t incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v2 = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v2;
+      }
+      if (lane == 31) wt[wid] = incl;
+      __syncthreads();
+      uint32_t before = 0;
+      for (int w2 = 0; w2 < wid; ++w2) before += wt[w2];
+      tie0 = before + incl - mine;
+      __syncthreads();
     }
   }
   const T sc_t = (T)scale, th = (T)theta;
   double dd = 0.0;
-  for (int64_t e = threadIdx.x; e < L; e += kThreads) {
+  uint32_t tie = tie0;
+  for (int64_t e = (mode == 1 ? e0 : threadIdx.x); e < (mode == 1 ? e1 : L); e += (mode == 1 ? 1 : kThreads)) {
     const int64_t r = at(e);
     const T wv = src[r];
     T yn;
     if (mode == 1) {
-      yn = flag[e] ? wv : T(0);
+      const K key = KT::key(wv);
+      bool keep = key > kkey;
+      if (key == kkey) keep = all_ties || tie++ < need;
+      yn = keep ? wv : T(0);
     } else if (mode == 2) {
       const T a = fabs(wv) - th;
       yn = a > T(0) ? copysign(a, wv) : T(0);
@@ -2839,7 +2917,7 @@ __device__ __forceinline__ void body_lines(const Tile &tl, const InstDev *__rest
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_lines(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kThreads, 3) k_lines(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                     InstScal *__restrict__ scal, unsigned long long *ts) {
   const Stamp stamp(ts);
   extern __shared__ unsigned char smem_raw[];
@@ -3455,6 +3533,27 @@ cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstD
                scal, L.ts);
   return cudaGetLastError();
 }
+// Parallel Dykstra sweep update (Appendix A): with y_i = P_i(v_i) packed in
+// y (instance i at i * n), x = sum_i w_i y_i and v_i = x + v_i - y_i (v packed
+// the same way, updated in place).
+template <typename T>
+__global__ void k_dykstra_update(const T *__restrict__ y, T *__restrict__ v, T *__restrict__ x, int p, int64_t n) {
+  const T wgt = T(1) / T(p);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    T acc = T(0);
+    for (int i = 0; i < p; ++i) acc += wgt * y[(int64_t)i * n + g];
+    x[g] = acc;
+    for (int i = 0; i < p; ++i) v[(int64_t)i * n + g] = acc + v[(int64_t)i * n + g] - y[(int64_t)i * n + g];
+  }
+}
+cudaError_t launch_dykstra_update(const Launch &L, const void *y, void *v, void *x, int p, int64_t n) {
+  if (L.dtype == SIP_F64)
+    k_dykstra_update<double><<<grid_for(n), 256, 0, L.stream>>>((const double *)y, (double *)v, (double *)x, p, n);
+  else
+    k_dykstra_update<float><<<grid_for(n), 256, 0, L.stream>>>((const float *)y, (float *)v, (float *)x, p, n);
+  return cudaGetLastError();
+}
+
 cudaError_t kernels_setup() {
   // the binary32 select histogram needs 56 KB of shared memory: opt in once
   static bool done = false;
@@ -3498,6 +3597,9 @@ int launch_occupancy(int dtype, int kind) {
     case 2:  // selection items
       occ(d ? (const void *)k_select<double> : (const void *)k_select<float>,
           d ? BinAcc<double>::kSmem : BinAcc<float>::kSmem);
+      break;
+    case 4:  // per-line items
+      occ(d ? (const void *)k_lines<double> : (const void *)k_lines<float>, d ? line_smem<double>() : line_smem<float>());
       break;
     default:  // final-pass items
       occ(d ? (const void *)k_final<double> : (const void *)k_final<float>, 0);

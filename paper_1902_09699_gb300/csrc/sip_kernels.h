@@ -67,6 +67,8 @@ cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDe
 // Per-line sets: one CTA per work item of lines (item = block, start/len =
 // lines), after the set pass.
 cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+// Parallel Dykstra: x = mean_i y_i, v_i = x + v_i - y_i (p blocks of n packed).
+cudaError_t launch_dykstra_update(const Launch &L, const void *y, void *v, void *x, int p, int64_t n);
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                          const JobDev *jobs, const JobScal *jscal, const uint32_t *ties);
 // cg_launch: step launches per iteration

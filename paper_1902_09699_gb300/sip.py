@@ -58,6 +58,10 @@ class ServerConfig(ctypes.Structure):
                 ("max_wait_ms", c_dbl), ("max_points", c_i64)]
 
 
+class DykstraInfo(ctypes.Structure):
+    _fields_ = [("sweeps", c_int), ("cg_steps", c_i64), ("l1_projections", c_i64), ("ms", ctypes.c_float)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("completed", c_i64), ("failed", c_i64), ("queued", c_i64), ("running_cohorts", c_int),
                 ("hbm_in_use", c_i64), ("hbm_peak", c_i64), ("p50_ms", c_dbl), ("p99_ms", c_dbl),
@@ -91,6 +95,9 @@ SIGNATURES = {
                                  ctypes.POINTER(Options), ctypes.POINTER(c_vp)]),
     "sip_batch_project": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Info)]),
     "sip_batch_offset": (c_i64, [c_vp, c_int]),
+    "sip_dykstra_create": (c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Set), c_int, ctypes.POINTER(Options),
+                                   ctypes.POINTER(c_vp)]),
+    "sip_dykstra_project": (c_int, [c_vp, c_vp, c_vp, c_int, c_vp, ctypes.POINTER(DykstraInfo)]),
     "sip_server_config_default": (None, [ctypes.POINTER(ServerConfig)]),
     "sip_server_create": (c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(c_vp)]),
     "sip_server_submit": (c_int, [c_vp, ctypes.POINTER(Grid), ctypes.POINTER(Set), c_int, c_vp, c_vp,
@@ -311,6 +318,50 @@ def _info_dict(inf, nsets, nblocks):
     return dict(iters=inf.iters, cg_steps=inf.cg_steps_total, stop_reason=inf.stop_reason, r_evol=inf.r_evol,
                 r_feas=list(inf.r_feas[:nsets]), rho=list(inf.rho[:nblocks]), gamma=list(inf.gamma[:nblocks]),
                 sigma=list(inf.sigma[:nsets]), k=list(inf.k[:nsets]), ms=float(inf.ms), window_hits=inf.window_hits)
+
+
+class Dykstra:
+    """Parallel Dykstra baseline (sip_dykstra_*): ``inner`` options (as for
+    Projector; max_iter = iterations of each single-set sub-problem) for the
+    sets' projections.  project(m, sweeps) returns (x, info dict)."""
+
+    def __init__(self, grid, sets, dtype="f32", **inner):
+        L = lib()
+        self.code = _dtype_code(dtype)
+        o = default_options()
+        for k, v in inner.items():
+            if k == "form":
+                v = FORMS[v] if isinstance(v, str) else int(v)
+            if k == "exec":
+                v = EXEC[v] if isinstance(v, str) else int(v)
+            setattr(o, k, v)
+        o.dtype = self.code
+        self.N = int(np.prod(grid["n"]))
+        self._grid = make_grid(grid)
+        self._sets = make_sets(sets)
+        h = c_vp()
+        _check(L.sip_dykstra_create(ctypes.byref(self._grid), self._sets, len(sets), ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+
+    def project(self, m, sweeps, stream=None):
+        import torch
+        m = _dev(m, self.code)
+        x = torch.empty(self.N, dtype=_torch_dtype(self.code), device=m.device)
+        inf = DykstraInfo()
+        _check(lib().sip_dykstra_project(self.handle, _ptr(m), _ptr(x), int(sweeps), _stream_ptr(stream),
+                                         ctypes.byref(inf)), self.handle)
+        return x, dict(sweeps=inf.sweeps, cg_steps=inf.cg_steps, l1_projections=inf.l1_projections, ms=float(inf.ms))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sip_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchProjector:

@@ -124,6 +124,26 @@ def layered_2d(n=(512, 1024), seed=1002):
                 m=m, sets=sets, opts=opts, dtype="f32")
 
 
+def lines_2d(n=(512, 1024), seed=1006):
+    """2D 512 x 1024 layered model under the set list of the paper's seismic
+    example with per-row and per-column sets (its rank constraint is left
+    out): bounds [2, 4]; card(D_z x) <= n_x and card(D_x x) <= n_z over the
+    whole model; at most 2 nonzeros of D_x in every row and of D_z in every
+    column.  FP32, adaptive rho, gamma = 1.5, 300 iterations, 5 CG steps."""
+    m = layered(n, seed=seed)
+    nz, nx = int(n[0]), int(n[1])
+    sets = [
+        {"op": "I", "type": "bounds", "lo": 2.0, "hi": 4.0},
+        {"op": "DZ", "type": "card", "k": nx},
+        {"op": "DX", "type": "card", "k": nz},
+        {"op": "DX", "type": "card", "k": 2, "scope": "x"},
+        {"op": "DZ", "type": "card", "k": 2, "scope": "z"},
+    ]
+    opts = dict(max_iter=300, cg_iters=5, adapt=1, rho0=1.0, gamma0=1.5)
+    return dict(name="2d-%dx%d-layered-rowcol-card" % tuple(n), grid={"n": tuple(n), "h": (1.0, 1.0)},
+                m=m, sets=sets, opts=opts, dtype="f32")
+
+
 def grf_3d(n=(256, 256, 128), seed=1003):
     """3D 256 x 256 x 128 (n_z, n_x, n_y) random field, FP32: bounds [2, 4];
     3D TV l1 ball tau = 0.4 TV(m); D_z x >= 0; card(D_x x) <= 1% of N;
