@@ -66,6 +66,11 @@ def resolve_sets(grid, sets, m):
         r = dict(s)
         r.setdefault("lo", -math.inf)
         r.setdefault("hi", math.inf)
+        if r["type"] == "bounds" and (np.ndim(r["lo"]) or np.ndim(r["hi"])):
+            # per-entry bounds (point-wise data fit): one value per row of A
+            M = ops.out_size(grid, r["op"])
+            r["lo"] = np.broadcast_to(np.asarray(r["lo"], dtype=np.float64), (M,)).copy()
+            r["hi"] = np.broadcast_to(np.asarray(r["hi"], dtype=np.float64), (M,)).copy()
         scope = r.setdefault("scope", "all")
         if scope != "all":
             if r["op"] == "TV":

@@ -10,9 +10,15 @@ import numpy as np
 
 
 def proj_bounds(w, lo, hi):
-    """Bounds {l <= w[i] <= u}: the projection is the element-wise clip
-    (set table, "bounds")."""
-    if lo > hi:
+    """Bounds {l[i] <= w[i] <= u[i]}: the projection is the element-wise
+    clip (set table, "bounds").  l and u are scalars or vectors of w's
+    length; vectors give the point-wise data-fit set {l <= F x - d_obs <= u}
+    of the paper's projection-as-inverse-problem formulation, with F the
+    set's operator and d_obs folded into the bounds (l + d_obs, u + d_obs),
+    and +-inf where nothing is observed."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    if np.any(lo > hi):
         raise ValueError("proj_bounds: lo > hi")
     return np.minimum(np.maximum(np.asarray(w, dtype=np.float64), lo), hi)
 

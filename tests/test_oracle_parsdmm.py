@@ -431,3 +431,14 @@ def test_per_line_sets_reject_unsupported_forms():
         P.resolve_sets(GRID, [{"op": "I", "type": "l2", "sigma": 1.0, "scope": "y"}], m)
     r = P.resolve_sets(GRID, [{"op": "DZ", "type": "card", "k_frac": 0.25, "scope": "z"}], m)[0]
     assert r["k"] == int(0.25 * (GRID["n"][0] - 1))
+
+
+def test_single_vector_bounds_set_gives_entrywise_clip():
+    """A per-entry bounds set on A = I alone: the projection is the clip of
+    m to its own interval at every entry."""
+    m = model(GRID, 15)
+    g = np.random.default_rng(15)
+    lo = m - g.uniform(0.0, 0.5, m.size) - 0.2
+    hi = lo + g.uniform(0.0, 0.4, m.size)
+    res = run(m, GRID, [{"op": "I", "type": "bounds", "lo": lo, "hi": hi}], iters=400)
+    assert rel(res["x"], np.clip(m, lo, hi)) < 1e-8

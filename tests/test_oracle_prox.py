@@ -228,3 +228,25 @@ def test_per_line_l2_and_l1_row_constraints():
             assert norm(Y[i, :]) <= sigma * (1 + 1e-12)
             if norm(X[i, :]) <= sigma:
                 assert np.array_equal(Y[i, :], X[i, :])
+
+
+def test_vector_bounds_nearest_point_and_data_fit_reading():
+    """Per-entry bounds: the clip is the nearest point entry by entry; with
+    l + d, u + d as bounds it is the projection onto {l <= w - d <= u}, and
+    +-inf leaves an entry free (an unobserved pixel of a mask)."""
+    g = np.random.default_rng(11)
+    n = 40
+    w = g.standard_normal(n) * 2
+    d = g.standard_normal(n)
+    lo = np.where(g.uniform(size=n) < 0.5, d - 0.3, -math.inf)
+    hi = np.where(np.isfinite(lo), d + 0.2, math.inf)
+    y = prox.proj_bounds(w, lo, hi)
+    for i in range(n):
+        if np.isfinite(lo[i]):
+            cands = np.linspace(lo[i], hi[i], 1001)
+            assert abs(y[i] - w[i]) <= np.min(np.abs(cands - w[i])) + 1e-12
+            assert -0.3 - 1e-15 <= y[i] - d[i] <= 0.2 + 1e-15
+        else:
+            assert y[i] == w[i]
+    with pytest.raises(ValueError):
+        prox.proj_bounds(w, np.zeros(n), -np.ones(n))
