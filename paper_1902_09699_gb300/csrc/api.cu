@@ -119,10 +119,19 @@ static sip_status check_set(const GridDesc &g, const sip_set &s, int i) {
   sip_status st = check_op(g, s.op);
   if (st) return fail(st, "set %d: %s", i, g_err.c_str());
   switch (s.type) {
-    case SIP_SET_BOUNDS:
-      if (std::isnan(s.lo) || std::isnan(s.hi) || s.lo > s.hi)
+    case SIP_SET_BOUNDS: {
+      if (std::isnan(s.lo) || std::isnan(s.hi) || (!s.lo_vec && !s.hi_vec && s.lo > s.hi))
         return fail(SIP_ERR_INVALID_ARG, "set %d: bounds need lo <= hi", i);
+      if (s.lo_vec || s.hi_vec) {
+        const int64_t M = op_rows(g, s.op);
+        for (int64_t j = 0; j < M; ++j) {
+          const double lo = s.lo_vec ? s.lo_vec[j] : s.lo, hi = s.hi_vec ? s.hi_vec[j] : s.hi;
+          if (std::isnan(lo) || std::isnan(hi) || lo > hi)
+            return fail(SIP_ERR_INVALID_ARG, "set %d: per-entry bounds need lo <= hi (entry %lld)", i, (long long)j);
+        }
+      }
       break;
+    }
     case SIP_SET_L1:
     case SIP_SET_L2:
       if (!(s.sigma >= 0.0) || !std::isfinite(s.sigma)) return fail(SIP_ERR_INVALID_ARG, "set %d: sigma < 0", i);
@@ -141,6 +150,8 @@ static sip_status check_set(const GridDesc &g, const sip_set &s, int i) {
       return fail(SIP_ERR_INVALID_ARG, "set %d: unknown set type %d", i, s.type);
   }
   if (s.scope < SIP_SCOPE_ALL || s.scope > SIP_SCOPE_Y) return fail(SIP_ERR_INVALID_ARG, "set %d: unknown scope", i);
+  if ((s.lo_vec || s.hi_vec) && s.type != SIP_SET_BOUNDS)
+    return fail(SIP_ERR_INVALID_ARG, "set %d: per-entry vectors are for bounds sets", i);
   if (s.scope != SIP_SCOPE_ALL && s.type != SIP_SET_BOUNDS) {
     if (s.op == SIP_OP_TV) return fail(SIP_ERR_INVALID_ARG, "set %d: per-line sets need a single-grid operator", i);
     if (s.sigma_rel != 0.0) return fail(SIP_ERR_INVALID_ARG, "set %d: per-line sets take absolute radii", i);
@@ -243,8 +254,10 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
   // still holds when the adapt interval is shorter than the ring
   d.k0_ring = o.adapt_every < o.evol_hist ? 1 : 0;
 
-  int64_t yoff = 0, woff = 0, soff = 0;
+  int64_t yoff = 0, woff = 0, soff = 0, boff = 0;
   int nseg = 0;
+  L.blo.assign(d.nb, std::vector<double>());
+  L.bhi.assign(d.nb, std::vector<double>());
   for (int b = 0; b < d.nb; ++b) {
     BlockDev &bd = d.blk[b];
     if (b < nsets) {
@@ -282,6 +295,20 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
     bd.M = op_rows(g, bd.op);
     bd.yoff = yoff;
     yoff += bd.M;
+    bd.bv_lo = bd.bv_hi = -1;
+    if (b < nsets && (sets[b].lo_vec || sets[b].hi_vec)) {
+      const sip_set &s = sets[b];
+      L.blo[b].resize(bd.M);
+      L.bhi[b].resize(bd.M);
+      for (int64_t j = 0; j < bd.M; ++j) {
+        L.blo[b][j] = s.lo_vec ? s.lo_vec[j] : s.lo;
+        L.bhi[b][j] = s.hi_vec ? s.hi_vec[j] : s.hi;
+      }
+      const int64_t Mp = (bd.M + 3) / 4 * 4;  // 16-byte aligned like y
+      bd.bv_lo = boff;
+      bd.bv_hi = boff + Mp;
+      boff += 2 * Mp;
+    }
     bd.woff = bd.soff = -1;
     bd.job_w = bd.job_s = -1;
     // w / s scratch regions start on 16-byte boundaries (vector loads)
@@ -314,6 +341,7 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
   L.Mtot = yoff;
   L.Mw = woff;
   L.Ms = soff;
+  L.Mb = boff;
   // selection jobs (local numbering; made global at placement)
   for (int b = 0; b < d.nb; ++b) {
     BlockDev &bd = d.blk[b];
@@ -541,7 +569,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     return o;
   };
   struct Offs {
-    int64_t x, y, v, cr[2], cw[2], cs[2], cp, cgp, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace;
+    int64_t x, y, v, cr[2], cw[2], cs[2], cp, cgp, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace, bvec;
   };
   std::vector<Offs> offs(P.ninst);
   // warm state (x, y, v) of all instances first, then the rest of the state,
@@ -584,6 +612,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     offs[i].sched_r = L.opts.rho_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
     offs[i].sched_g = L.opts.gamma_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
     offs[i].trace = L.opts.trace ? take((int64_t)L.opts.max_iter * (2 * L.dev.nb + 2 + L.dev.p) * 8) : -1;
+    offs[i].bvec = L.Mb ? take(L.Mb * W) : -1;
   }
   const int64_t o_ctrl = take(8 * sizeof(uint32_t));  // grid barrier words + finished count
   const int64_t o_insts = take((int64_t)P.ninst * sizeof(InstDev));
@@ -646,6 +675,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     d.rho_sched = (const double *)at(o.sched_r);
     d.gamma_sched = (const double *)at(o.sched_g);
     d.trace = (double *)at(o.trace);
+    d.bvec = at(o.bvec);
     d.trace_w = 2 * d.nb + 2 + d.p;
     P.h_insts[i] = d;
     P.layouts[i] = insts[i];
@@ -696,6 +726,24 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       }
     }
   CK(cudaMemset(P.arena, 0, (size_t)off));
+  // per-entry bound vectors, in the storage type
+  for (int i = 0; i < P.ninst; ++i) {
+    const InstLayout &L = insts[i];
+    for (int b = 0; b < L.dev.nb; ++b) {
+      const BlockDev &bd = L.dev.blk[b];
+      if (bd.bv_lo < 0) continue;
+      for (int side = 0; side < 2; ++side) {
+        const std::vector<double> &src = side ? L.bhi[b] : L.blo[b];
+        char *dst = (char *)P.h_insts[i].bvec + (side ? bd.bv_hi : bd.bv_lo) * W;
+        if (dtype == SIP_F64) {
+          CK(cudaMemcpy(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice));
+        } else {
+          std::vector<float> f(src.begin(), src.end());
+          CK(cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+        }
+      }
+    }
+  }
   CK(cudaMemcpy(P.d_insts, P.h_insts.data(), P.ninst * sizeof(InstDev), cudaMemcpyHostToDevice));
   if (njobs) CK(cudaMemcpy(P.d_jobs, jobs.data(), njobs * sizeof(JobDev), cudaMemcpyHostToDevice));
   if (!tn.empty()) CK(cudaMemcpy(P.d_tn, tn.data(), tn.size() * sizeof(Tile), cudaMemcpyHostToDevice));

@@ -1365,7 +1365,7 @@ struct RowOut {
 // Partials: 0..5 adapt dots, 6 feasD2, 7 s2, 8 s1, 9 wnorm.
 template <typename T, typename A>
 __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T y0, T v0, T mg, T ks, T kvh, T ky,
-                                                 T kv, A (&acc)[10]) {
+                                                 T kv, T lo, T hi, A (&acc)[10]) {
   RowOut<T> o;
   const T xbar = q.gam * s + q.one_m_gam * y0;
   o.w = xbar - v0 * q.irho;
@@ -1382,7 +1382,7 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
     }
   }
   if (q.pointwise) {
-    o.yn = q.type == BT_BOUNDS ? fmin(fmax(o.w, q.lo), q.hi) : (mg + q.rho * o.w) * q.inv1p;  // Eq. prox_sq_dist
+    o.yn = q.type == BT_BOUNDS ? fmin(fmax(o.w, lo), hi) : (mg + q.rho * o.w) * q.inv1p;  // Eq. prox_sq_dist
     o.vn = v0 + q.rho * (o.yn - xbar);
     if (q.ad_dots) {
       const A dg = (A)ky - (A)o.yn;
@@ -1392,7 +1392,7 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
       acc[5] += dv * dv;
     }
     if (q.chk && q.type == BT_BOUNDS) {
-      const A d = (A)s - (A)fmin(fmax(s, q.lo), q.hi);
+      const A d = (A)s - (A)fmin(fmax(s, lo), hi);
       acc[6] += d * d;
       acc[7] += (A)s * (A)s;
     }
@@ -1444,6 +1444,9 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   T *__restrict__ k0y = (T *)in.k0y + bd.yoff + sg.row0;
   T *__restrict__ k0v = (T *)in.k0v + bd.yoff + sg.row0;
   const T *__restrict__ m = (const T *)in.m;
+  // per-entry bounds (point-wise data fit), else the scalars q.lo, q.hi
+  const T *__restrict__ blo = bd.bv_lo >= 0 ? (const T *)in.bvec + bd.bv_lo + sg.row0 : nullptr;
+  const T *__restrict__ bhi = bd.bv_lo >= 0 ? (const T *)in.bvec + bd.bv_hi + sg.row0 : nullptr;
   const int64_t end = tl.start + tl.len;
   A acc[10];
 #pragma unroll
@@ -1513,7 +1516,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
     if (ad && pointwise) al |= (uintptr_t)(k0y + tl.start) | (uintptr_t)(k0v + tl.start);
     if (!pointwise) al |= (uintptr_t)(wbuf + tl.start);
     if (store_s) al |= (uintptr_t)(sbuf + tl.start);
-    vec = (al & 15) == 0;
+    vec = (al & 15) == 0 && !blo;  // per-entry bounds take the scalar path
   }
   if (vec) {
     if constexpr (sizeof(T) == 4) {
@@ -1560,7 +1563,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           RowOut<float> o;
           if (r0 + c < end) {
             o = setpass_row(q, sv[c], vat(Y, c), vat(V, c), mv[c], vat(KS, c), vat(KVH, c), vat(KY, c), vat(KV, c),
-                            acc);
+                            q.lo, q.hi, acc);
           } else {
             o.yn = o.vn = o.w = o.vh = 0.f;
           }
@@ -1613,7 +1616,8 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
       for (int e = 0; e < PT; ++e) {
         const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
         if (row >= end) continue;
-        const RowOut<T> o = setpass_row(q, sv[e], y0[e], v0[e], mg[e], ks[e], kvh[e], ky[e], kv[e], acc);
+        const RowOut<T> o = setpass_row(q, sv[e], y0[e], v0[e], mg[e], ks[e], kvh[e], ky[e], kv[e],
+                                        blo ? blo[row] : q.lo, blo ? bhi[row] : q.hi, acc);
         if (win) classify(o.w, true);
         if (ad) {
           if (!k0ring) k0s[row] = sv[e];

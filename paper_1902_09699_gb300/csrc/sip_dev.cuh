@@ -117,6 +117,9 @@ struct BlockDev {
   // along z, (n_z', n_z' n_x') along x and (n_z' n_x', 0) along y
   int32_t line_type, scope;
   int64_t line_len, line_stride, nlines, line_a, line_b;
+  // per-entry bounds (point-wise data fit): lo at bv_lo, hi at bv_hi of the
+  // instance's bvec array, M entries each; -1: the scalar lo / hi apply
+  int64_t bv_lo, bv_hi;
 };
 
 struct JobDev {
@@ -192,6 +195,7 @@ struct InstDev {
   // device arrays, element type = the plan's dtype
   const void *m;
   void *x, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;
+  void *bvec;  // per-entry bound vectors of the blocks that have them
   // conjugate-gradient vectors: residual r, w = C r and s = C p are double
   // buffered (read at stencil neighbours while the next values are written);
   // the direction p is updated in place

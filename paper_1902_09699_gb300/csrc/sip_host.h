@@ -27,6 +27,8 @@ struct InstLayout {
   sip_options opts;
   InstDev dev;
   int64_t Mtot = 0, Mw = 0, Ms = 0;
+  int64_t Mb = 0;  // per-entry bound vectors (lo and hi of every such block)
+  std::vector<std::vector<double>> blo, bhi;  // per block, empty for scalar bounds
   std::vector<JobDev> jobs;
 };
 

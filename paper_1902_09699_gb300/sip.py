@@ -33,7 +33,8 @@ class Grid(ctypes.Structure):
 
 class Set(ctypes.Structure):
     _fields_ = [("op", c_int), ("type", c_int), ("lo", c_dbl), ("hi", c_dbl), ("sigma", c_dbl),
-                ("sigma_rel", c_dbl), ("k", c_i64), ("k_frac", c_dbl), ("scope", c_int)]
+                ("sigma_rel", c_dbl), ("k", c_i64), ("k_frac", c_dbl), ("scope", c_int),
+                ("lo_vec", ctypes.POINTER(c_dbl)), ("hi_vec", ctypes.POINTER(c_dbl))]
 
 
 class Options(ctypes.Structure):
@@ -151,11 +152,21 @@ def make_grid(grid):
 
 
 def make_set(s):
+    """A sip_set from a set dict; array-valued "lo" / "hi" (bounds) become
+    per-entry bound vectors (kept alive on the returned struct)."""
     c = Set()
     c.op = OPS[s["op"]]
     c.type = SET_TYPES[s["type"]]
-    c.lo = float(s.get("lo", -math.inf))
-    c.hi = float(s.get("hi", math.inf))
+    c._keep = []
+    for name in ("lo", "hi"):
+        v = s.get(name, -math.inf if name == "lo" else math.inf)
+        if np.ndim(v):
+            a = np.ascontiguousarray(v, dtype=np.float64)
+            c._keep.append(a)
+            setattr(c, name + "_vec", a.ctypes.data_as(ctypes.POINTER(c_dbl)))
+            setattr(c, name, 0.0)
+        else:
+            setattr(c, name, float(v))
     c.sigma = float(s.get("sigma", 0.0))
     c.sigma_rel = float(s.get("sigma_rel", 0.0))
     c.k = int(s.get("k", 0))
@@ -166,8 +177,12 @@ def make_set(s):
 
 def make_sets(sets):
     arr = (Set * len(sets))()
+    keep = []
     for i, s in enumerate(sets):
-        arr[i] = make_set(s)
+        c = make_set(s)
+        keep.append(c._keep)
+        arr[i] = c
+    arr._keep = keep  # the per-entry bound vectors the structs point to
     return arr
 
 

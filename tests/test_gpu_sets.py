@@ -125,3 +125,72 @@ def test_line_limits_rejected():
     # l2 lines have no length limit
     pr = sip.Projector({"n": (5000, 2)}, [{"op": "I", "type": "l2", "sigma": 1.0, "scope": "z"}], dtype="f32")
     pr.close()
+
+
+# ---------------------------------------------------------------- point-wise data fit
+def _inpainting(n=(48, 40), seed=21, frac=0.4):
+    """Observed entries of a layered model under a random mask, with noise;
+    the data-fit set {-0.05 <= M x - d <= 0.05} (M the mask) as per-entry
+    bounds d +- 0.05 on observed entries and +-inf elsewhere."""
+    g = np.random.default_rng(seed)
+    truth = model(n, seed)
+    obs = g.uniform(size=truth.size) < frac
+    d = truth + 0.02 * g.standard_normal(truth.size)
+    lo = np.where(obs, d - 0.05, -math.inf)
+    hi = np.where(obs, d + 0.05, math.inf)
+    m = np.where(obs, d, float(d[obs].mean()))
+    grid = {"n": n}
+    tv = float(np.abs(O_apply(grid, "TV", truth)).sum())
+    sets = [{"op": "I", "type": "bounds", "lo": lo, "hi": hi},
+            {"op": "TV", "type": "l1", "sigma": tv},
+            {"op": "I", "type": "bounds", "lo": 1.5, "hi": 4.5}]
+    return grid, m, sets, obs, d
+
+
+def O_apply(grid, op, x):
+    from oracle import operators as O
+    return O.apply(grid, op, x)
+
+
+@pytest.mark.parametrize("dt,bar", [("f64", 1e-10), ("f32", 1e-4)])
+def test_data_fit_inpainting(dt, bar):
+    grid, m, sets, obs, d = _inpainting()
+    if dt == "f32":
+        m = torch.as_tensor(m, dtype=torch.float32).double().numpy()
+    opts = dict(max_iter=60, cg_iters=5, adapt=1 if dt == "f64" else 0, rho0=1.0, gamma0=1.5)
+    ref = P.parsdmm(m, grid, sets, P.options(**opts))
+    x, info = run_gpu(m, grid, sets, dt, opts)
+    assert rel(x, ref["x"]) <= bar
+    if dt == "f64":
+        for a, b in zip(info["r_feas"], ref["r_feas"]):
+            assert a == pytest.approx(b, rel=1e-8, abs=1e-13)
+
+
+def test_data_fit_on_a_derivative_and_equalities():
+    """Per-entry bounds on D_z x (some entries pinned: lo = hi) and a
+    desaturation-style identity data fit with clipped ranges."""
+    n = (32, 24)
+    grid = {"n": n}
+    g = np.random.default_rng(22)
+    m = model(n, 22)
+    Mz = (n[0] - 1) * n[1]
+    lo = g.uniform(-0.3, 0.0, Mz)
+    hi = lo + g.uniform(0.0, 0.4, Mz)
+    hi[::7] = lo[::7]
+    d = np.clip(m, 2.0, 3.5)
+    lo_x = np.where(d <= 2.0, -math.inf, np.where(d >= 3.5, 3.5, d))
+    hi_x = np.where(d <= 2.0, 2.0, np.where(d >= 3.5, math.inf, d))
+    sets = [{"op": "DZ", "type": "bounds", "lo": lo, "hi": hi},
+            {"op": "I", "type": "bounds", "lo": lo_x, "hi": hi_x}]
+    opts = dict(max_iter=50, cg_iters=5, adapt=1, rho0=1.0, gamma0=1.5)
+    ref = P.parsdmm(m, grid, sets, P.options(**opts))
+    x, _ = run_gpu(m, grid, sets, "f64", opts)
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+def test_data_fit_vectors_validated():
+    with pytest.raises(sip.SipError):   # lo > hi at one entry
+        sip.Projector({"n": (4, 4)}, [{"op": "I", "type": "bounds", "lo": np.r_[np.zeros(15), 2.0], "hi": 1.0}],
+                      dtype="f64")
+    with pytest.raises(sip.SipError):   # vectors only for bounds
+        sip.Projector({"n": (4, 4)}, [{"op": "I", "type": "l2", "sigma": 1.0, "lo": np.zeros(16)}], dtype="f64")
