@@ -744,6 +744,14 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       }
     }
   }
+  // single instance with its own model copy: the descriptor (now complete,
+  // the same bytes as its device copy) is immutable, so every kernel takes
+  // it as a launch parameter
+  memset(&P.one, 0, sizeof P.one);
+  if (P.ninst == 1 && own_m) {
+    P.one.d = P.h_insts[0];
+    P.one.on = 1;
+  }
   CK(cudaMemcpy(P.d_insts, P.h_insts.data(), P.ninst * sizeof(InstDev), cudaMemcpyHostToDevice));
   if (njobs) CK(cudaMemcpy(P.d_jobs, jobs.data(), njobs * sizeof(JobDev), cudaMemcpyHostToDevice));
   if (!tn.empty()) CK(cudaMemcpy(P.d_tn, tn.data(), tn.size() * sizeof(Tile), cudaMemcpyHostToDevice));
@@ -782,9 +790,9 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   auto T1 = [&](int) {};
   T0(KT_RHS);
   if (P.rhs_smem)
-    CK(launch_rhs_tma(L, P.d_trhs, P.nt_rhs, P.d_insts, P.d_scal, P.rhs_smem));
+    CK(launch_rhs_tma(L, P.d_trhs, P.nt_rhs, P.d_insts, P.d_scal, P.rhs_smem, P.one));
   else
-    CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
+    CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, P.one));
   T1(KT_RHS);
   T0(KT_CG_W0);
   CK(launch_cg_w0(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, P.cg_one));  // w_0 = C r_0
@@ -795,34 +803,34 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
     T1(KT_CG_STEP);
   }
   T0(KT_SETPASS);
-  CK(launch_setpass(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs));
+  CK(launch_setpass(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs, P.one));
   T1(KT_SETPASS);
   if (P.nt_sel) {
     const int np = select_passes(P.dtype);
     for (int pass = 0; pass < np; ++pass) {
       T0(KT_SELECT);
       CK(launch_select(L, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
-                       P.d_hs3, (int64_t)P.njobs * kBins, pass));
+                       P.d_hs3, (int64_t)P.njobs * kBins, pass, P.one));
       T1(KT_SELECT);
     }
   }
   if (P.any_card) {
     T0(KT_TIES);
-    CK(launch_ties(L, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
+    CK(launch_ties(L, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties, P.one));
     T1(KT_TIES);
   }
   if (P.nt_line) {
     T0(KT_FINAL);  // per-line sets
-    CK(launch_lines(L, P.d_tline, P.nt_line, P.d_insts, P.d_scal));
+    CK(launch_lines(L, P.d_tline, P.nt_line, P.d_insts, P.d_scal, P.one));
     T1(KT_FINAL);
   }
   if (P.nt_fin) {
     T0(KT_FINAL);
-    CK(launch_final(L, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
+    CK(launch_final(L, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties, P.one));
     T1(KT_FINAL);
   }
   T0(KT_TAIL);
-  CK(launch_tail(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst, P.cg_launch));
+  CK(launch_tail(L, P.d_insts, P.d_scal, P.d_jscal, P.ninst, P.cg_launch, P.one));
   T1(KT_TAIL);
   return SIP_OK;
 }
@@ -974,6 +982,13 @@ sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm) {
 }
 
 sip_status plan_set_m(Plan &P, int inst, const void *m, cudaStream_t st) {
+  if (P.m_own && !P.packed) {
+    // the plan's own copy: the descriptor (a launch parameter of the
+    // captured graphs) stays valid for every model
+    CK(cudaMemcpyAsync((void *)P.h_insts[inst].m, m, (size_t)P.h_insts[inst].N * esize(P.dtype),
+                       cudaMemcpyDeviceToDevice, st));
+    return SIP_OK;
+  }
   P.h_insts[inst].m = m;
   CK(cudaMemcpyAsync(&P.d_insts[inst].m, &P.h_insts[inst].m, sizeof(void *), cudaMemcpyHostToDevice, st));
   return SIP_OK;

@@ -167,7 +167,7 @@ sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets, cons
   };
   {
     std::vector<InstLayout> L{make_layout(grid_desc(*grid), sets, nsets, *opts)};
-    if ((st = plan_build(h->lev[0], L, opts->dtype, false))) return bail(st);
+    if ((st = plan_build(h->lev[0], L, opts->dtype, true))) return bail(st);
   }
   for (int l = 1; l < opts->levels; ++l) {
     sip_options oc = *opts;
@@ -477,13 +477,13 @@ sip_status sip_project_set(const sip_set *set, int dtype, const void *w_dev, int
   if ((st = plan_set_m(P, 0, w_dev, cs))) return st;
   if ((st = plan_prepare(P, cs, false))) return st;
   CKH(cudaMemcpyAsync(d.x, w_dev, (size_t)n * esz(dtype), cudaMemcpyDeviceToDevice, cs));
-  CKH(launch_setpass(Ln, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs));
+  CKH(launch_setpass(Ln, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs, P.one));
   if (P.nt_sel)
     for (int pass = 0; pass < select_passes(dtype); ++pass)
       CKH(launch_select(Ln, P.d_tsel, P.nt_sel, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_hcnt, P.d_hs1, P.d_hs2,
-                        P.d_hs3, (int64_t)P.njobs * kBins, pass));
-  if (P.any_card) CKH(launch_ties(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
-  if (P.nt_fin) CKH(launch_final(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties));
+                        P.d_hs3, (int64_t)P.njobs * kBins, pass, P.one));
+  if (P.any_card) CKH(launch_ties(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties, P.one));
+  if (P.nt_fin) CKH(launch_final(Ln, P.d_tfin, P.nt_fin, P.d_insts, P.d_scal, P.d_jobs, P.d_jscal, P.d_ties, P.one));
   CKH(cudaMemcpyAsync(y_dev, d.y, (size_t)n * esz(dtype), cudaMemcpyDeviceToDevice, cs));
   CKH(cudaStreamSynchronize(cs));
   if (scalar_out) {

@@ -611,11 +611,12 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
     body_rhs_t<T, int64_t>(tl, in, sc);
 }
 
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                  InstScal *__restrict__ scal, unsigned long long *ts) {
+                                                  InstScal *__restrict__ scal, unsigned long long *ts,
+                                                  const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
-  body_rhs<T>(tiles[blockIdx.x], insts, scal);
+  body_rhs<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal);
 }
 
 // --------------------------------------------------------------------------
@@ -678,9 +679,12 @@ __device__ __forceinline__ void rhs_window(const InstDev &in, int kind, int64_t 
   if (hi < lo) hi = lo;
 }
 
+template <bool ONE>
 __global__ void __launch_bounds__(kThreads, 2) k_rhs_tma(const Tile *__restrict__ tiles,
-                                                         const InstDev *__restrict__ insts,
-                                                         InstScal *__restrict__ scal, unsigned long long *ts) {
+                                                         const InstDev *__restrict__ insts_g,
+                                                         InstScal *__restrict__ scal, unsigned long long *ts,
+                                                         const __grid_constant__ InstOne one) {
+  const InstDev *__restrict__ insts = ONE ? &one.d : insts_g;
   const Stamp stamp(ts);
   extern __shared__ __align__(128) float sw[];
   __shared__ __align__(8) uint64_t bar;
@@ -1754,12 +1758,13 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
   }
 }
 
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                       InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
-                                                      const JobDev *__restrict__ jobs, unsigned long long *ts) {
+                                                      const JobDev *__restrict__ jobs, unsigned long long *ts,
+                                                      const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
-  body_setpass<T>(tiles[blockIdx.x], insts, scal, jscal, jobs);
+  body_setpass<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal, jscal, jobs);
 }
 
 // --------------------------------------------------------------------------
@@ -2339,15 +2344,15 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
   }
 }
 
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(kThreads, 3) k_select(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                         InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                         JobScal *__restrict__ jscal, uint32_t *__restrict__ hcnt,
                                                         double *__restrict__ hs1, double *__restrict__ hs2,
                                                         double *__restrict__ hs3, int64_t hstride, int pass,
-                                                        unsigned long long *ts) {
+                                                        unsigned long long *ts, const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
-  body_select<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, hcnt, hs1, hs2, hs3, hstride, pass);
+  body_select<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal, jobs, jscal, hcnt, hs1, hs2, hs3, hstride, pass);
 }
 
 // Tie counts per final-pass work item for card sets whose k-th value is tied.
@@ -2382,12 +2387,13 @@ __device__ __forceinline__ void body_ties(const Tile &tl, const InstDev *__restr
   if (threadIdx.x == 0) ties[jobs[bd.job_w].tie_off + tl.seq] = (uint32_t)tot;
 }
 
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(kThreads, 4) k_ties(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                    InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
-                                                   JobScal *__restrict__ jscal, uint32_t *__restrict__ ties, unsigned long long *ts) {
+                                                   JobScal *__restrict__ jscal, uint32_t *__restrict__ ties, unsigned long long *ts,
+                                                   const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
-  body_ties<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, ties);
+  body_ties<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal, jobs, jscal, ties);
 }
 
 // --------------------------------------------------------------------------
@@ -2597,13 +2603,14 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   }
 }
 
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                     InstScal *__restrict__ scal, const JobDev *__restrict__ jobs,
                                                     const JobScal *__restrict__ jscal,
-                                                    const uint32_t *__restrict__ ties, unsigned long long *ts) {
+                                                    const uint32_t *__restrict__ ties, unsigned long long *ts,
+                                                    const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
-  body_final<T>(tiles[blockIdx.x], insts, scal, jobs, jscal, ties);
+  body_final<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal, jobs, jscal, ties);
 }
 
 // --------------------------------------------------------------------------
@@ -2920,12 +2927,13 @@ __device__ __forceinline__ void body_lines(const Tile &tl, const InstDev *__rest
   if (chk && threadIdx.x == 0) atomicAdd(&sc.acc[b][A_FEAS_D2], d2);  // ||s||^2: the set pass
 }
 
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(kThreads, 3) k_lines(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
-                                                    InstScal *__restrict__ scal, unsigned long long *ts) {
+                                                    InstScal *__restrict__ scal, unsigned long long *ts,
+                                                    const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
   extern __shared__ unsigned char smem_raw[];
-  body_lines<T>(tiles[blockIdx.x], insts, scal, smem_raw);
+  body_lines<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal, smem_raw);
 }
 
 // --------------------------------------------------------------------------
@@ -3190,9 +3198,14 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
 __global__ void __launch_bounds__(32 * kTailWarps) k_tail(const InstDev *__restrict__ insts,
                                                           InstScal *__restrict__ scal,
                                                           JobScal *__restrict__ jscal, int ninst,
-                                                          int cg_launch, unsigned long long *ts) {
+                                                          int cg_launch, unsigned long long *ts,
+                                                          const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
   if ((int)blockIdx.x >= ninst) return;
+  if (one.on) {  // the descriptor is a launch parameter
+    body_tail(0, &one.d, scal, jscal, cg_launch);
+    return;
+  }
   // the tail's scattered descriptor reads (blocks, operators, options) from
   // a shared-memory copy
   __shared__ InstDev s_in;
@@ -3467,6 +3480,22 @@ __global__ void k_system_apply(const InstDev *__restrict__ inp, const InstScal *
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
+// by storage type and by whether the descriptor is a launch parameter
+#define SIP_DISPATCH_ONE(L, ONEP, KERNEL, GRID, BLOCK, SMEM, ...)                                   \
+  do {                                                                                            \
+    if ((L).dtype == SIP_F64) {                                                                   \
+      if ((ONEP).on)                                                                              \
+        KERNEL<double, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);              \
+      else                                                                                        \
+        KERNEL<double, false><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);             \
+    } else {                                                                                      \
+      if ((ONEP).on)                                                                              \
+        KERNEL<float, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);               \
+      else                                                                                        \
+        KERNEL<float, false><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);              \
+    }                                                                                             \
+  } while (0)
+
 #define SIP_DISPATCH(L, KERNEL, GRID, BLOCK, SMEM, ...)                          \
   do {                                                                           \
     if ((L).dtype == SIP_F64)                                                    \
@@ -3489,18 +3518,22 @@ cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstD
   SIP_DISPATCH(L, k_norms, nt, kThreads, 0, tiles, insts, scal);
   return cudaGetLastError();
 }
-cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_rhs, nt, kThreads, 0, tiles, insts, scal, L.ts);
+cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                       const InstOne &one) {
+  SIP_DISPATCH_ONE(L, one, k_rhs, nt, kThreads, 0, tiles, insts, scal, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_rhs_tma(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                           size_t smem) {
-  k_rhs_tma<<<nt, kThreads, smem, L.stream>>>(tiles, insts, scal, L.ts);
+                           size_t smem, const InstOne &one) {
+  if (one.on)
+    k_rhs_tma<true><<<nt, kThreads, smem, L.stream>>>(tiles, insts, scal, L.ts, one);
+  else
+    k_rhs_tma<false><<<nt, kThreads, smem, L.stream>>>(tiles, insts, scal, L.ts, one);
   return cudaGetLastError();
 }
 int rhs_tma_occupancy(size_t smem) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rhs_tma, kThreads, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rhs_tma<false>, kThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -3517,24 +3550,21 @@ cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const Ins
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                           JobScal *jscal, const JobDev *jobs) {
-  SIP_DISPATCH(L, k_setpass, nt, kThreads, 0, tiles, insts, scal, jscal, jobs, L.ts);
+                           JobScal *jscal, const JobDev *jobs, const InstOne &one) {
+  SIP_DISPATCH_ONE(L, one, k_setpass, nt, kThreads, 0, tiles, insts, scal, jscal, jobs, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                           const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
-                          int64_t hstride, int pass) {
-  if (L.dtype == SIP_F64)
-    k_select<double><<<nt, kThreads, BinAcc<double>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1,
-                                                                       hs2, hs3, hstride, pass, L.ts);
-  else
-    k_select<float><<<nt, kThreads, BinAcc<float>::kSmem, L.stream>>>(tiles, insts, scal, jobs, jscal, hcnt, hs1, hs2,
-                                                                     hs3, hstride, pass, L.ts);
+                          int64_t hstride, int pass, const InstOne &one) {
+  SIP_DISPATCH_ONE(L, one, k_select, nt, kThreads, (L.dtype == SIP_F64 ? BinAcc<double>::kSmem : BinAcc<float>::kSmem),
+                   tiles, insts, scal, jobs, jscal, hcnt, hs1, hs2, hs3, hstride, pass, L.ts, one);
   return cudaGetLastError();
 }
-cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal) {
-  SIP_DISPATCH(L, k_lines, nt, kThreads, (L.dtype == SIP_F64 ? line_smem<double>() : line_smem<float>()), tiles, insts,
-               scal, L.ts);
+cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                         const InstOne &one) {
+  SIP_DISPATCH_ONE(L, one, k_lines, nt, kThreads, (L.dtype == SIP_F64 ? line_smem<double>() : line_smem<float>()), tiles, insts,
+               scal, L.ts, one);
   return cudaGetLastError();
 }
 // Parallel Dykstra sweep update (Appendix A): with y_i = P_i(v_i) packed in
@@ -3562,20 +3592,31 @@ cudaError_t kernels_setup() {
   // the binary32 select histogram needs 56 KB of shared memory: opt in once
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_select<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_select<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BinAcc<float>::kSmem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_select<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
+  e = cudaFuncSetAttribute(k_select<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_rhs_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRhsSmemMax);
+  e = cudaFuncSetAttribute(k_rhs_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRhsSmemMax);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lines<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lines<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_select<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)BinAcc<float>::kSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_select<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rhs_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRhsSmemMax);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<float>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<double>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_lines<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<float>());
+  e = cudaFuncSetAttribute(k_lines<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<float>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<double>());
+  e = cudaFuncSetAttribute(k_lines<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<double>());
   if (e != cudaSuccess) return e;
   done = true;
   return cudaSuccess;
@@ -3591,23 +3632,23 @@ int launch_occupancy(int dtype, int kind) {
   const bool d = dtype == SIP_F64;
   switch (kind) {
     case 0:  // grid-point items: rhs, CG
-      occ(d ? (const void *)k_rhs<double> : (const void *)k_rhs<float>, 0);
+      occ(d ? (const void *)k_rhs<double, false> : (const void *)k_rhs<float, false>, 0);
       occ(d ? (const void *)k_cg_w0<double> : (const void *)k_cg_w0<float>, 0);
       occ(d ? (const void *)k_cg_step<double> : (const void *)k_cg_step<float>, 0);
       break;
     case 1:  // segment items: set pass
-      occ(d ? (const void *)k_setpass<double> : (const void *)k_setpass<float>, 0);
+      occ(d ? (const void *)k_setpass<double, false> : (const void *)k_setpass<float, false>, 0);
       break;
     case 2:  // selection items
-      occ(d ? (const void *)k_select<double> : (const void *)k_select<float>,
+      occ(d ? (const void *)k_select<double, false> : (const void *)k_select<float, false>,
           d ? BinAcc<double>::kSmem : BinAcc<float>::kSmem);
       break;
     case 4:  // per-line items
-      occ(d ? (const void *)k_lines<double> : (const void *)k_lines<float>, d ? line_smem<double>() : line_smem<float>());
+      occ(d ? (const void *)k_lines<double, false> : (const void *)k_lines<float, false>, d ? line_smem<double>() : line_smem<float>());
       break;
     default:  // final-pass items
-      occ(d ? (const void *)k_final<double> : (const void *)k_final<float>, 0);
-      occ(d ? (const void *)k_ties<double> : (const void *)k_ties<float>, 0);
+      occ(d ? (const void *)k_final<double, false> : (const void *)k_final<float, false>, 0);
+      occ(d ? (const void *)k_ties<double, false> : (const void *)k_ties<float, false>, 0);
       break;
   }
   cudaGetLastError();
@@ -3665,18 +3706,18 @@ int fused_grid(int dtype) {
 
 int select_passes(int dtype) { return dtype == SIP_F64 ? num_passes<double>() : num_passes<float>(); }
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                        const JobDev *jobs, JobScal *jscal, uint32_t *ties) {
-  SIP_DISPATCH(L, k_ties, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties, L.ts);
+                        const JobDev *jobs, JobScal *jscal, uint32_t *ties, const InstOne &one) {
+  SIP_DISPATCH_ONE(L, one, k_ties, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                         const JobDev *jobs, const JobScal *jscal, const uint32_t *ties) {
-  SIP_DISPATCH(L, k_final, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties, L.ts);
+                         const JobDev *jobs, const JobScal *jscal, const uint32_t *ties, const InstOne &one) {
+  SIP_DISPATCH_ONE(L, one, k_final, nt, kThreads, 0, tiles, insts, scal, jobs, jscal, ties, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, JobScal *jscal, int ninst,
-                        int cg_launch) {
-  k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst, cg_launch, L.ts);
+                        int cg_launch, const InstOne &one) {
+  k_tail<<<ninst, 32 * kTailWarps, 0, L.stream>>>(insts, scal, jscal, ninst, cg_launch, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_apply_op(const Launch &L, const InstDev *in, const void *x, void *s, int64_t rows) {

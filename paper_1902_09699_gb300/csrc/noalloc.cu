@@ -213,7 +213,7 @@ extern "C" sip_status sip_project_l1_noalloc(int dtype, const void *w_dev, int64
   const Launch L{dtype, cs};
   for (int pass = 0; pass < select_passes(dtype); ++pass)
     NA_CK(launch_select(L, S->tiles, nt, &S->inst, &S->scal, &S->job, &S->jscal, S->hcnt, S->hs1, S->hs2, S->hs3,
-                        0, pass));  // one histogram buffer, cleared by each pass's last CTA
+                        0, pass, InstOne{}));  // one histogram buffer, cleared by each pass's last CTA
   if (dtype == SIP_F64)
     k_na_soft<double><<<grid, 256, 0, cs>>>((const double *)w_dev, (double *)y_dev, n, S);
   else

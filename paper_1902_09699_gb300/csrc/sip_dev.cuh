@@ -246,6 +246,16 @@ inline CgDesc cg_desc(const InstDev &in) {
   return d;
 }
 
+// A single-instance plan's descriptor as a launch parameter (on = 1):
+// kernels then address their arrays without reading the descriptor from
+// memory first.  Valid while the descriptor does not change after the
+// plan is built (the plan owns its model copy).
+struct InstOne {
+  InstDev d;
+  int32_t on;
+  int32_t pad;
+};
+
 // Conjugate-gradient state between step launches.  Every CTA of a step
 // launch derives it from the previous launch's partial sums and the previous
 // state; the instance's first tile stores it in slot (phase & 1) while the

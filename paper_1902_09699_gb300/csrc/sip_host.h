@@ -71,6 +71,7 @@ struct Plan {
   size_t rhs_smem = 0;
   bool any_card = false, any_fin = false, any_stop = false;
   CgOne cg_one;  // CG launch parameters of a single-instance plan (on = 0 otherwise)
+  InstOne one;   // the descriptor as a launch parameter (single instance owning its model)
   int cg_launch = 0, max_iter = 0, check_every = 1;
   std::vector<InstDev> h_insts;
   std::vector<InstLayout> layouts;

@@ -18,12 +18,12 @@ struct Launch {
 // iteration kernels (kernels.cu)
 cudaError_t launch_init(const Launch &L, const InstDev *insts, InstScal *scal, JobScal *jscal, int ninst);
 cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
-cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, const InstOne &one);
 // staged right-hand side (binary32, 2D instances): `smem` bytes of y / v
 // windows per CTA, at most kRhsSmemMax
 constexpr size_t kRhsSmemMax = 200 * 1024;
 cudaError_t launch_rhs_tma(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                           size_t smem);
+                           size_t smem, const InstOne &one);
 int rhs_tma_occupancy(size_t smem);
 cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                          const CgOne &one);
@@ -31,12 +31,12 @@ cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstD
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
                            const CgOne &one);
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                           JobScal *jscal, const JobDev *jobs);
+                           JobScal *jscal, const JobDev *jobs, const InstOne &one);
 // hstride: elements between the three histogram buffers the passes rotate
 // over, or 0 for a single buffer
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                           const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
-                          int64_t hstride, int pass);
+                          int64_t hstride, int pass, const InstOne &one);
 // one-time kernel attribute set-up (call outside stream capture)
 cudaError_t kernels_setup();
 // CTAs per SM for the kernels of a work-item list: 0 grid points, 1 set
@@ -63,17 +63,17 @@ struct FusedLaunch {
 cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid);
 int fused_grid(int dtype);
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                        const JobDev *jobs, JobScal *jscal, uint32_t *ties);
+                        const JobDev *jobs, JobScal *jscal, uint32_t *ties, const InstOne &one);
 // Per-line sets: one CTA per work item of lines (item = block, start/len =
 // lines), after the set pass.
-cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal);
+cudaError_t launch_lines(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, const InstOne &one);
 // Parallel Dykstra: x = mean_i y_i, v_i = x + v_i - y_i (p blocks of n packed).
 cudaError_t launch_dykstra_update(const Launch &L, const void *y, void *v, void *x, int p, int64_t n);
 cudaError_t launch_final(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
-                         const JobDev *jobs, const JobScal *jscal, const uint32_t *ties);
+                         const JobDev *jobs, const JobScal *jscal, const uint32_t *ties, const InstOne &one);
 // cg_launch: step launches per iteration
 cudaError_t launch_tail(const Launch &L, const InstDev *insts, InstScal *scal, JobScal *jscal, int ninst,
-                        int cg_launch);
+                        int cg_launch, const InstOne &one);
 
 // single-step operators on one grid (kernels.cu): `in` describes the grid and
 // the segments of one operator; `sc` carries the stencil coefficients.
