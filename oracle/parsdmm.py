@@ -80,6 +80,13 @@ def resolve_sets(grid, sets, m):
             r["shape"] = ops.grid_shape(grid) if r["op"] == "I" else ops.diff_shape(grid, r["op"])
             if r["shape"][_SCOPE_AXIS[scope]] < 1 or (scope == "y" and len(grid["n"]) < 3):
                 raise ValueError("no lines along %s" % scope)
+        if r.get("center") is not None:
+            # l2 data fit: one observed value (or NaN) per row of A
+            if r["type"] != "l2" or r.get("sigma_rel", 0.0) or scope != "all":
+                raise ValueError("a center goes with an absolute l2 radius on the whole set")
+            r["center"] = np.asarray(r["center"], dtype=np.float64).reshape(-1).copy()
+            if r["center"].size != ops.out_size(grid, r["op"]):
+                raise ValueError("center needs one value per row of A")
         if r["type"] in ("l1", "l2"):
             if r.get("sigma_rel", 0.0):
                 r["sigma"] = r["sigma_rel"] * ops.norm_of(grid, r["op"], r["type"], m)

@@ -33,6 +33,23 @@ def proj_l2(w, sigma):
     return w * (sigma / nrm)
 
 
+def proj_l2_data(w, center, sigma):
+    """Data-fit l2 ball {||M (w - d)||_2 <= sigma} around observed values d
+    (the paper's l2 data-fit set {||F x - d_obs|| <= sigma} with F the
+    set's operator, here together with a binary mask M): ``center`` holds d,
+    NaN where nothing is observed.  Observed entries move radially toward d
+    when outside the ball; unobserved entries are not constrained and stay."""
+    w = np.asarray(w, dtype=np.float64)
+    c = np.asarray(center, dtype=np.float64)
+    obs = ~np.isnan(c)
+    y = w.copy()
+    r = w[obs] - c[obs]
+    nrm = float(np.sqrt(np.sum(r * r)))
+    if nrm > sigma:
+        y[obs] = c[obs] + r * (sigma / nrm)
+    return y
+
+
 def proj_annulus(w, lo, hi):
     """Annulus {sigma_l <= ||w||_2 <= sigma_u} (set table, "annulus"):
     radial scaling onto the nearer sphere when ||w||_2 lies outside
@@ -156,6 +173,8 @@ def project(set_spec, w):
     if t == "bounds":
         return proj_bounds(w, set_spec["lo"], set_spec["hi"])
     if t == "l2":
+        if set_spec.get("center") is not None:
+            return proj_l2_data(w, set_spec["center"], set_spec["sigma"])
         return proj_l2(w, set_spec["sigma"])
     if t == "l1":
         return proj_l1(w, set_spec["sigma"])

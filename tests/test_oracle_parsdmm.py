@@ -442,3 +442,16 @@ def test_single_vector_bounds_set_gives_entrywise_clip():
     hi = lo + g.uniform(0.0, 0.4, m.size)
     res = run(m, GRID, [{"op": "I", "type": "bounds", "lo": lo, "hi": hi}], iters=400)
     assert rel(res["x"], np.clip(m, lo, hi)) < 1e-8
+
+
+def test_single_l2_data_set_gives_the_ball_projection():
+    """A lone l2 data-fit set on A = I: the projection of m onto the ball
+    around the observed values (masked entries free)."""
+    m = model(GRID, 16)
+    g = np.random.default_rng(16)
+    d = m + 0.5 * g.standard_normal(m.size)
+    d[g.uniform(size=m.size) < 0.25] = np.nan
+    sigma = 0.3 * float(np.linalg.norm((m - d)[~np.isnan(d)]))
+    res = run(m, GRID, [{"op": "I", "type": "l2", "sigma": sigma, "center": d}], iters=400)
+    from oracle import prox as PX
+    assert rel(res["x"], PX.proj_l2_data(m, d, sigma)) < 1e-8

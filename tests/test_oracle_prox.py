@@ -250,3 +250,27 @@ def test_vector_bounds_nearest_point_and_data_fit_reading():
             assert y[i] == w[i]
     with pytest.raises(ValueError):
         prox.proj_bounds(w, np.zeros(n), -np.ones(n))
+
+
+def test_l2_data_ball_nearest_point_and_reduction():
+    """{||M (w - d)|| <= sigma}: the nearest point over sampled members (the
+    free entries equal w's, the observed ones on or inside the ball around
+    d); with no NaN and d = 0 it is the l2 ball."""
+    g = np.random.default_rng(12)
+    n = 6
+    for trial in range(20):
+        w = g.standard_normal(n) * 2
+        d = g.standard_normal(n)
+        d[g.uniform(size=n) < 0.3] = np.nan
+        obs = ~np.isnan(d)
+        sigma = 0.7
+        y = prox.proj_l2_data(w, d, sigma)
+        assert np.array_equal(y[~obs], w[~obs])
+        assert np.linalg.norm(y[obs] - d[obs]) <= sigma * (1 + 1e-14) + 1e-15
+        for _ in range(200):
+            z = w.copy()
+            u = g.standard_normal(obs.sum())
+            z[obs] = d[obs] + u * (g.uniform(0, sigma) / max(np.linalg.norm(u), 1e-300))
+            assert np.linalg.norm(z - w) >= np.linalg.norm(y - w) - 1e-12
+    w = g.standard_normal(10)
+    assert np.allclose(prox.proj_l2_data(w, np.zeros(10), 0.5), prox.proj_l2(w, 0.5), atol=1e-15, rtol=0)
