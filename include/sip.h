@@ -117,6 +117,12 @@ typedef struct {
      * Copied when the handle is created; lo_vec <= hi_vec, no NaN.  Not
      * accepted by the server. */
     const double *lo_vec, *hi_vec;
+    /* SIP_SET_L2 only, optional: host array of M_i observed values d: the
+     * set becomes the paper's l2 data-fit ball {||F x - d||_2 <= sigma} with
+     * F = A_i; NaN marks an unobserved entry (a binary mask: left out of
+     * the norm, unconstrained).  Absolute sigma, scope SIP_SCOPE_ALL;
+     * copied at create; not accepted by the server. */
+    const double *center_vec;
 } sip_set;
 
 typedef struct {

@@ -152,6 +152,8 @@ static sip_status check_set(const GridDesc &g, const sip_set &s, int i) {
   if (s.scope < SIP_SCOPE_ALL || s.scope > SIP_SCOPE_Y) return fail(SIP_ERR_INVALID_ARG, "set %d: unknown scope", i);
   if ((s.lo_vec || s.hi_vec) && s.type != SIP_SET_BOUNDS)
     return fail(SIP_ERR_INVALID_ARG, "set %d: per-entry vectors are for bounds sets", i);
+  if (s.center_vec && (s.type != SIP_SET_L2 || s.sigma_rel != 0.0 || s.scope != SIP_SCOPE_ALL))
+    return fail(SIP_ERR_INVALID_ARG, "set %d: a center goes with an absolute l2 radius on the whole set", i);
   if (s.scope != SIP_SCOPE_ALL && s.type != SIP_SET_BOUNDS) {
     if (s.op == SIP_OP_TV) return fail(SIP_ERR_INVALID_ARG, "set %d: per-line sets need a single-grid operator", i);
     if (s.sigma_rel != 0.0) return fail(SIP_ERR_INVALID_ARG, "set %d: per-line sets take absolute radii", i);
@@ -296,6 +298,12 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
     bd.yoff = yoff;
     yoff += bd.M;
     bd.bv_lo = bd.bv_hi = -1;
+    if (b < nsets && sets[b].center_vec) {
+      // l2 data fit: the observed values (NaN: unobserved) at bv_lo
+      L.blo[b].assign(sets[b].center_vec, sets[b].center_vec + bd.M);
+      bd.bv_lo = boff;
+      boff += (bd.M + 3) / 4 * 4;
+    }
     if (b < nsets && (sets[b].lo_vec || sets[b].hi_vec)) {
       const sip_set &s = sets[b];
       L.blo[b].resize(bd.M);
@@ -734,6 +742,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       if (bd.bv_lo < 0) continue;
       for (int side = 0; side < 2; ++side) {
         const std::vector<double> &src = side ? L.bhi[b] : L.blo[b];
+        if (src.empty()) continue;  // a data-fit center has no upper vector
         char *dst = (char *)P.h_insts[i].bvec + (side ? bd.bv_hi : bd.bv_lo) * W;
         if (dtype == SIP_F64) {
           CK(cudaMemcpy(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice));

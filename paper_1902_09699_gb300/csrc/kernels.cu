@@ -1354,6 +1354,7 @@ struct SetpassScal {
   T rho, irho, gam, one_m_gam, inv1p, lo, hi, ih;
   int type, kind;
   bool pointwise, ad, ad_dots, chk;
+  bool centered;  // l2 data fit: the row's observed value comes as `lo` (NaN: unobserved)
 };
 
 // What one row stores: the dual update's y and v (point-wise sets) or the
@@ -1402,7 +1403,18 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
     }
   } else {
     o.yn = o.vn = T(0);
-    if (q.type == BT_L2 || q.type == BT_ANNULUS) acc[9] += (A)o.w * (A)o.w;
+    if (q.centered) {  // ||w - d|| and ||s - d|| over the observed rows
+      if (!isnan(lo)) {
+        const A r = (A)o.w - (A)lo;
+        acc[9] += r * r;
+        if (q.chk) {
+          const A rs = (A)s - (A)lo;
+          acc[6] += rs * rs;
+        }
+      }
+    } else if (q.type == BT_L2 || q.type == BT_ANNULUS) {
+      acc[9] += (A)o.w * (A)o.w;
+    }
     if (q.type == BT_L1) acc[9] += fabs((A)o.w);
     if (q.chk) {
       acc[7] += (A)s * (A)s;
@@ -1432,6 +1444,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   q.kind = sg.kind;
   q.type = bd.type;
   q.pointwise = bd.type == BT_BOUNDS || bd.type == BT_DIST;
+  q.centered = bd.type == BT_L2 && bd.bv_lo >= 0;
   q.ad = ad;
   q.ad_dots = ad_dots;
   q.chk = chk;
@@ -1450,7 +1463,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   const T *__restrict__ m = (const T *)in.m;
   // per-entry bounds (point-wise data fit), else the scalars q.lo, q.hi
   const T *__restrict__ blo = bd.bv_lo >= 0 ? (const T *)in.bvec + bd.bv_lo + sg.row0 : nullptr;
-  const T *__restrict__ bhi = bd.bv_lo >= 0 ? (const T *)in.bvec + bd.bv_hi + sg.row0 : nullptr;
+  const T *__restrict__ bhi = bd.bv_hi >= 0 ? (const T *)in.bvec + bd.bv_hi + sg.row0 : nullptr;
   const int64_t end = tl.start + tl.len;
   A acc[10];
 #pragma unroll
@@ -1621,7 +1634,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
         const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
         if (row >= end) continue;
         const RowOut<T> o = setpass_row(q, sv[e], y0[e], v0[e], mg[e], ks[e], kvh[e], ky[e], kv[e],
-                                        blo ? blo[row] : q.lo, blo ? bhi[row] : q.hi, acc);
+                                        blo ? blo[row] : q.lo, bhi ? bhi[row] : q.hi, acc);
         if (win) classify(o.w, true);
         if (ad) {
           if (!k0ring) k0s[row] = sv[e];
@@ -1662,7 +1675,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
     A d3[3] = {acc[6], acc[7], acc[8]};
     block_sum<3>(d3);
     if (threadIdx.x == 0) {
-      if (type == BT_BOUNDS) atomicAdd(&a[A_FEAS_D2], (double)d3[0]);
+      if (type == BT_BOUNDS || q.centered) atomicAdd(&a[A_FEAS_D2], (double)d3[0]);
       atomicAdd(&a[A_S2], (double)d3[1]);
       if (type == BT_L1) atomicAdd(&a[A_S1], (double)d3[2]);
     }
@@ -2447,6 +2460,8 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
     }
   }
   const T scale = SV<T>::blk(sc, b, BF_L2SCALE);
+  // l2 data fit: observed values d (NaN: unobserved), y = d + scale (w - d)
+  const T *__restrict__ cen = (bd.type == BT_L2 && bd.bv_lo >= 0) ? (const T *)in.bvec + bd.bv_lo : nullptr;
   const T th = theta;
   const int type = bd.type;
   A acc[3] = {A(0), A(0), A(0)};
@@ -2468,7 +2483,7 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   if constexpr (sizeof(T) == 4) {
     uintptr_t al = (uintptr_t)(w + tl.start) | (uintptr_t)(y + tl.start) | (uintptr_t)(v + tl.start);
     if (ad) al |= (uintptr_t)(k0y + tl.start) | (uintptr_t)(k0v + tl.start);
-    vec = !tie && (al & 15) == 0;
+    vec = !tie && !cen && (al & 15) == 0;
   }
   if (vec) {
     if constexpr (sizeof(T) == 4) {
@@ -2542,7 +2557,10 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
         const int64_t row = base + threadIdx.x + (int64_t)e * kThreads;
         const bool valid = row < end;
         T yn;
-        if (type == BT_L2 || type == BT_ANNULUS) {
+        if (cen) {
+          const T c = valid ? cen[row] : T(0);
+          yn = isnan(c) ? wv[e] : c + (wv[e] - c) * scale;
+        } else if (type == BT_L2 || type == BT_ANNULUS) {
           yn = wv[e] * scale;
         } else if (mode == JM_ALL) {
           yn = wv[e];
@@ -3000,7 +3018,9 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
         if (bd.type == BT_BOUNDS || bd.type == BT_LINE) {
           d = sqrt(a[A_FEAS_D2]);
         } else if (bd.type == BT_L2) {
-          d = fmax(0.0, sqrt(s2) - sc.sigma[b]);  // ||s - P(s)|| = ||s|| - sigma outside the ball
+          // ||s - P(s)|| = ||s - d|| - sigma outside the ball (d = 0 unless a data fit)
+          const double r = bd.bv_lo >= 0 ? sqrt(a[A_FEAS_D2]) : sqrt(s2);
+          d = fmax(0.0, r - sc.sigma[b]);
         } else if (bd.type == BT_ANNULUS) {
           const double n = sqrt(s2);  // distance to the nearer sphere; s = 0 stays 0
           d = n > bd.hi ? n - bd.hi : (n > 0.0 && n < bd.lo ? bd.lo - n : 0.0);

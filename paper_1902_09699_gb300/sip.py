@@ -34,7 +34,8 @@ class Grid(ctypes.Structure):
 class Set(ctypes.Structure):
     _fields_ = [("op", c_int), ("type", c_int), ("lo", c_dbl), ("hi", c_dbl), ("sigma", c_dbl),
                 ("sigma_rel", c_dbl), ("k", c_i64), ("k_frac", c_dbl), ("scope", c_int),
-                ("lo_vec", ctypes.POINTER(c_dbl)), ("hi_vec", ctypes.POINTER(c_dbl))]
+                ("lo_vec", ctypes.POINTER(c_dbl)), ("hi_vec", ctypes.POINTER(c_dbl)),
+                ("center_vec", ctypes.POINTER(c_dbl))]
 
 
 class Options(ctypes.Structure):
@@ -167,6 +168,10 @@ def make_set(s):
             setattr(c, name, 0.0)
         else:
             setattr(c, name, float(v))
+    if s.get("center") is not None:
+        a = np.ascontiguousarray(s["center"], dtype=np.float64)
+        c._keep.append(a)
+        c.center_vec = a.ctypes.data_as(ctypes.POINTER(c_dbl))
     c.sigma = float(s.get("sigma", 0.0))
     c.sigma_rel = float(s.get("sigma_rel", 0.0))
     c.k = int(s.get("k", 0))

@@ -194,3 +194,41 @@ def test_data_fit_vectors_validated():
                       dtype="f64")
     with pytest.raises(sip.SipError):   # vectors only for bounds
         sip.Projector({"n": (4, 4)}, [{"op": "I", "type": "l2", "sigma": 1.0, "lo": np.zeros(16)}], dtype="f64")
+
+
+@pytest.mark.parametrize("dt,bar", [("f64", 1e-10), ("f32", 1e-4)])
+def test_l2_data_fit_ball(dt, bar):
+    """{||M (x - d)|| <= sigma} (noise-level radius) with TV and bounds:
+    the l2 data-fit formulation of the paper with a mask (NaN centers)."""
+    g = np.random.default_rng(23)
+    n = (40, 36)
+    truth = model(n, 23)
+    d = truth + 0.05 * g.standard_normal(truth.size)
+    obs = g.uniform(size=truth.size) < 0.5
+    d[~obs] = np.nan
+    sigma = 0.05 * math.sqrt(obs.sum())
+    m = np.where(obs, d, 3.0)
+    if dt == "f32":
+        m = torch.as_tensor(m, dtype=torch.float32).double().numpy()
+    grid = {"n": n}
+    tv = float(np.abs(O_apply(grid, "TV", truth)).sum())
+    sets = [{"op": "I", "type": "l2", "sigma": sigma, "center": d},
+            {"op": "TV", "type": "l1", "sigma": tv},
+            {"op": "I", "type": "bounds", "lo": 1.5, "hi": 4.5}]
+    opts = dict(max_iter=60, cg_iters=5, adapt=1 if dt == "f64" else 0, rho0=1.0, gamma0=1.5)
+    ref = P.parsdmm(m, grid, sets, P.options(**opts))
+    x, info = run_gpu(m, grid, sets, dt, opts)
+    assert rel(x, ref["x"]) <= bar
+    if dt == "f64":
+        # the ball's r_feas is ||s - d|| - sigma over ||s||: a difference of
+        # nearly equal numbers, so rounding is amplified by their ratio
+        for a, b in zip(info["r_feas"], ref["r_feas"]):
+            assert a == pytest.approx(b, rel=1e-6, abs=1e-13)
+
+
+def test_l2_data_fit_validated():
+    with pytest.raises(sip.SipError):   # a center needs an l2 set
+        sip.Projector({"n": (4, 4)}, [{"op": "I", "type": "l1", "sigma": 1.0, "center": np.zeros(16)}], dtype="f64")
+    with pytest.raises(sip.SipError):   # and an absolute radius
+        sip.Projector({"n": (4, 4)}, [{"op": "I", "type": "l2", "sigma_rel": 0.5, "center": np.zeros(16)}],
+                      dtype="f64")
