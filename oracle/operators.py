@@ -9,12 +9,77 @@ numpy array of shape (n_y, n_x, n_z) (n_y = 1 in 2D), so axis -1 is z,
 axis -2 is x and axis -3 is y.
 
 A grid is a dict ``{"n": (nz, nx[, ny]), "h": (hz, hx[, hy])}``.
-An operator name is one of "I", "DZ", "DX", "DY", "TV".
+An operator is one of the names "I", "DZ", "DX", "DY", "TV", or a blur
+``("BLUR", axis, taps)`` made by ``blur_op``.
 """
 import numpy as np
 
 _AXIS = {"DZ": -1, "DX": -2, "DY": -3}
 _HIDX = {"DZ": 0, "DX": 1, "DY": 2}
+_BLUR_AXIS = {"z": -1, "x": -2, "y": -3}
+
+
+def blur_op(axis, taps):
+    """The blurring forward operator F of the data-fit formulation (Sec.
+    "Introduction", the feasibility / projection problem with a data-fit
+    set; the motion blur of Sec. "Joint deblurring-denoising-inpainting")
+    as an operator value: a symmetric averaging kernel of 2R+1 samples along
+    one grid axis, taps = (k_0, ..., k_R) with weight k_|t| on the sample t
+    steps away.  Reading: the kernel is centred and symmetric (a 25-pixel
+    motion blur is R = 12, k_t = 1/25) and samples outside the grid count as
+    zero, so F is N x N and banded."""
+    if axis not in _BLUR_AXIS:
+        raise ValueError("blur axis must be 'z', 'x' or 'y'")
+    taps = tuple(float(t) for t in taps)
+    if len(taps) < 2:
+        raise ValueError("a blur needs taps k_0..k_R with R >= 1")
+    return ("BLUR", axis, taps)
+
+
+def is_blur(op):
+    return isinstance(op, tuple) and op[0] == "BLUR"
+
+
+def _along(grid, op, v):
+    """v as a grid array with the blur axis moved last."""
+    X = np.asarray(v, dtype=np.float64).reshape(grid_shape(grid))
+    return np.moveaxis(X, _BLUR_AXIS[op[1]], -1)
+
+
+def _back(grid, op, Y):
+    return np.moveaxis(Y, -1, _BLUR_AXIS[op[1]]).reshape(-1)
+
+
+def blur_apply(grid, op, x):
+    """(F x)[j] = sum over |t| <= R of k_|t| x[j + t] along the axis, the
+    terms whose sample j + t falls outside the grid left out: row j of F
+    gathers the samples around j."""
+    if len(grid["n"]) < 3 and op[1] == "y":
+        raise ValueError("no y axis in 2D")
+    taps = op[2]
+    X = _along(grid, op, x)
+    n = X.shape[-1]
+    Y = taps[0] * X
+    for t in range(1, len(taps)):
+        if t >= n:
+            break
+        Y[..., :n - t] += taps[t] * X[..., t:]   # sample j + t
+        Y[..., t:] += taps[t] * X[..., :n - t]   # sample j - t
+    return _back(grid, op, Y)
+
+
+def blur_apply_t(grid, op, u):
+    """(F^T u)[i] = sum over rows j of F[j, i] u[j]: every row j scatters
+    k_|i - j| u[j] to the samples i within R of it (the columns of F)."""
+    taps = op[2]
+    U = _along(grid, op, u)
+    n = U.shape[-1]
+    Z = np.zeros_like(U)
+    R = len(taps) - 1
+    for j in range(n):
+        for i in range(max(0, j - R), min(n, j + R + 1)):
+            Z[..., i] += taps[abs(i - j)] * U[..., j]
+    return _back(grid, op, Z)
 
 
 def grid_shape(grid):
@@ -55,7 +120,7 @@ def diff_shape(grid, name):
 
 def out_size(grid, op):
     """M_i, the number of rows of A_i."""
-    if op == "I":
+    if op == "I" or is_blur(op):
         return grid_size(grid)
     if op == "TV":
         return sum(out_size(grid, d) for d in tv_parts(grid))
@@ -94,8 +159,11 @@ def adjoint_diff(grid, name, u):
 
 
 def apply(grid, op, x):
-    """s = A x for A in {I, D_z, D_x, D_y, TV} (set table, Sec. "Software")."""
+    """s = A x for A in {I, D_z, D_x, D_y, TV} (set table, Sec. "Software")
+    or a blur F (``blur_op``)."""
     x = np.asarray(x, dtype=np.float64).reshape(-1)
+    if is_blur(op):
+        return blur_apply(grid, op, x)
     if op == "I":
         return x.copy()
     if op == "TV":
@@ -106,6 +174,8 @@ def apply(grid, op, x):
 def apply_t(grid, op, y):
     """A^T y, the adjoint of ``apply``."""
     y = np.asarray(y, dtype=np.float64).reshape(-1)
+    if is_blur(op):
+        return blur_apply_t(grid, op, y)
     if op == "I":
         return y.copy()
     if op == "TV":

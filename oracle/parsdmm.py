@@ -8,8 +8,10 @@ block p+1 with A_{p+1} = I_N and the prox of the squared distance to m is
 appended.  The sign convention is the one of the augmented Lagrangian
 (Eq. aug_lag): v_i^T (y_i - A_i x).
 
-Sets are dicts: {"op": "I"|"DZ"|"DX"|"DY"|"TV", "type": "bounds"|"l1"|"l2"|
-"card", "lo", "hi", "sigma", "sigma_rel", "k", "k_frac"}.  A radius given as
+Sets are dicts: {"op": "I"|"DZ"|"DX"|"DY"|"TV"|"BLUR", "type": "bounds"|"l1"|
+"l2"|"card", "lo", "hi", "sigma", "sigma_rel", "k", "k_frac"}; a "BLUR"
+operator takes "axis" ("z", "x" or "y") and "taps" (k_0..k_R, see
+``operators.blur_op``).  A radius given as
 ``sigma_rel`` is resolved against the model being projected
 (sigma = sigma_rel * ||A m|| in the set's norm); a cardinality given as
 ``k_frac`` is resolved as floor(k_frac * N) with N the grid size.
@@ -64,6 +66,8 @@ def resolve_sets(grid, sets, m):
     N = ops.grid_size(grid)
     for s in sets:
         r = dict(s)
+        if r["op"] == "BLUR":
+            r["op"] = ops.blur_op(r.pop("axis"), r.pop("taps"))
         r.setdefault("lo", -math.inf)
         r.setdefault("hi", math.inf)
         if r["type"] == "bounds" and (np.ndim(r["lo"]) or np.ndim(r["hi"])):
@@ -73,8 +77,8 @@ def resolve_sets(grid, sets, m):
             r["hi"] = np.broadcast_to(np.asarray(r["hi"], dtype=np.float64), (M,)).copy()
         scope = r.setdefault("scope", "all")
         if scope != "all":
-            if r["op"] == "TV":
-                raise ValueError("per-line sets need a single-grid operator")
+            if r["op"] == "TV" or ops.is_blur(r["op"]):
+                raise ValueError("per-line sets need I or a difference operator")
             if r.get("sigma_rel", 0.0):
                 raise ValueError("per-line sets take absolute radii")
             r["shape"] = ops.grid_shape(grid) if r["op"] == "I" else ops.diff_shape(grid, r["op"])
@@ -473,6 +477,10 @@ def ml_parsdmm(m, grid, sets, opts=None, levels=2, coarse_iter=None):
     ``coarse_iter`` (default: the fine max_iter) iterations on coarse levels.
     """
     o = options() if opts is None else dict(opts)
+    if levels > 1 and any(s["op"] == "BLUR" or ops.is_blur(s["op"]) for s in sets):
+        # reading: the paper's multilevel scheme interpolates y_i, v_i as
+        # images; a blur's taps have no stated coarse-grid counterpart
+        raise ValueError("a blur operator runs on one level only")
     grids = [grid]
     ms = [np.asarray(m, dtype=np.float64).reshape(-1)]
     for _ in range(levels - 1):

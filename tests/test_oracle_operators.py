@@ -152,3 +152,107 @@ def test_layout_is_z_fastest():
     assert np.all(ops.apply(grid, "DX", m) == 0)
     assert np.all(ops.apply(grid, "DY", m) == 0)
     assert np.all(ops.apply(grid, "DZ", m) == 1)
+
+
+# --------------------------------------------------------------------------
+# Blurring forward operator F of the data-fit set (Sec. "Introduction",
+# data-fit formulation; Sec. "Joint deblurring-denoising-inpainting").
+# --------------------------------------------------------------------------
+BLUR_CASES = [
+    ({"n": (9, 6)}, "z", (0.5, 0.25)),
+    ({"n": (9, 6)}, "x", (0.4, 0.2, 0.1)),
+    ({"n": (5, 4, 6)}, "y", (0.3, 0.2, 0.1, 0.05)),
+    ({"n": (3, 8)}, "z", (0.2,) * 5),      # R = 4 > n_z: every sample sees both ends
+    ({"n": (30, 2)}, "z", (1.0 / 25,) * 13),  # the 25-sample motion blur
+]
+_AX = {"z": 0, "x": 1, "y": 2}
+
+
+def convolve_matrix(grid, axis, taps):
+    """F from scipy's 1D convolution with zero padding ("constant" mode),
+    applied to every unit vector: column i of F is the blur of e_i."""
+    nd = pytest.importorskip("scipy.ndimage")
+    shape = ops.grid_shape(grid)
+    kfull = np.array(taps[::-1] + taps[1:])
+    N = ops.grid_size(grid)
+    cols = []
+    for e in np.eye(N):
+        E = e.reshape(shape)
+        cols.append(nd.convolve1d(E, kfull, axis=2 - _AX[axis], mode="constant", cval=0.0).reshape(-1))
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("grid,axis,taps", BLUR_CASES)
+def test_blur_matches_scipy_convolution(grid, axis, taps):
+    op = ops.blur_op(axis, taps)
+    F = convolve_matrix(grid, axis, taps)
+    x = np.random.default_rng(11).standard_normal(F.shape[1])
+    assert np.allclose(ops.apply(grid, op, x), F @ x, rtol=0, atol=1e-14)
+    assert np.allclose(ops.apply_t(grid, op, x), F.T @ x, rtol=0, atol=1e-14)
+    assert ops.out_size(grid, op) == F.shape[0] == F.shape[1]
+    # a centred symmetric kernel: F is symmetric
+    assert np.array_equal(F, F.T)
+
+
+@pytest.mark.parametrize("grid,axis,taps", BLUR_CASES)
+def test_blur_adjoint_dot_product(grid, axis, taps):
+    op = ops.blur_op(axis, taps)
+    g = np.random.default_rng(12)
+    N = ops.grid_size(grid)
+    x, u = g.standard_normal(N), g.standard_normal(N)
+    lhs = float(np.dot(ops.apply(grid, op, x), u))
+    rhs = float(np.dot(x, ops.apply_t(grid, op, u)))
+    assert lhs == pytest.approx(rhs, rel=1e-13, abs=1e-13)
+
+
+def test_box_blur_of_a_constant_closed_form():
+    """A normalised box of 2R+1 samples keeps a constant c in the interior
+    and gives c (samples inside the grid) / (2R+1) within R of an edge."""
+    R, n, c = 3, 11, 2.5
+    grid = {"n": (n, 2)}
+    op = ops.blur_op("z", (1.0 / (2 * R + 1),) * (R + 1))
+    y = ops.apply(grid, op, np.full(2 * n, c)).reshape(2, n)
+    for j in range(n):
+        inside = min(n - 1, j + R) - max(0, j - R) + 1
+        assert y[0, j] == pytest.approx(c * inside / (2 * R + 1), rel=1e-14)
+        assert y[1, j] == y[0, j]
+
+
+def test_blur_normal_matrix_interior_is_autocorrelation():
+    """Rows of F^T F at least 2R samples from both ends hold the kernel's
+    autocorrelation a_d = sum_t k_t k_{t+d} at offset d (|d| <= 2R)."""
+    taps = (0.35, 0.2, 0.1, 0.025)
+    R, n = len(taps) - 1, 20
+    grid = {"n": (n, 1)}
+    op = ops.blur_op("z", taps)
+    kfull = np.array(taps[::-1] + taps[1:])
+    auto = np.correlate(kfull, kfull, mode="full")   # offsets -2R..2R
+    FtF = np.stack([ops.apply_t(grid, op, ops.apply(grid, op, e)) for e in np.eye(n)], axis=1)
+    for i in range(2 * R, n - 2 * R):
+        row = np.zeros(n)
+        row[i - 2 * R:i + 2 * R + 1] = auto
+        assert np.allclose(FtF[i], row, rtol=0, atol=1e-15)
+    # near an end some products are missing: the diagonal is smaller there
+    assert FtF[0, 0] < auto[2 * R] - 1e-3
+
+
+@pytest.mark.parametrize("grid,axis,taps", BLUR_CASES[:3])
+def test_system_matrix_with_a_blur(grid, axis, taps):
+    """Eq. sys_mat with a blur block: C = c I + rho_D D_z^T D_z + rho_F F^T F."""
+    op = ops.blur_op(axis, taps)
+    F = convolve_matrix(grid, axis, taps)
+    N = F.shape[0]
+    D = explicit_diff_matrix(dict(grid, h=(1.0,) * len(grid["n"])), 0)
+    C = 1.3 * np.eye(N) + 0.7 * D.T @ D + 2.2 * F.T @ F
+    x = np.random.default_rng(13).standard_normal(N)
+    got = ops.system_apply(dict(grid, h=(1.0,) * len(grid["n"])), ["DZ", op], [0.7, 2.2], 1.3, x)
+    assert np.allclose(got, C @ x, rtol=0, atol=1e-12)
+
+
+def test_blur_op_rejects_bad_arguments():
+    with pytest.raises(ValueError):
+        ops.blur_op("w", (0.5, 0.25))
+    with pytest.raises(ValueError):
+        ops.blur_op("z", (1.0,))
+    with pytest.raises(ValueError):
+        ops.apply({"n": (4, 4)}, ops.blur_op("y", (0.5, 0.25)), np.zeros(16))

@@ -455,3 +455,49 @@ def test_single_l2_data_set_gives_the_ball_projection():
     res = run(m, GRID, [{"op": "I", "type": "l2", "sigma": sigma, "center": d}], iters=400)
     from oracle import prox as PX
     assert rel(res["x"], PX.proj_l2_data(m, d, sigma)) < 1e-8
+
+
+def test_blur_data_fit_matches_general_qp_solver():
+    """The projection-as-inverse-problem form with a blurring forward
+    operator (Sec. "Introduction", data-fit formulation): min 1/2||x - m||^2
+    s.t. l <= F x - d <= u on the observed samples (a restriction of the blur,
+    +-inf elsewhere) and 2 <= x <= 4, against SLSQP with F built from
+    scipy's zero-padded convolution."""
+    opt = pytest.importorskip("scipy.optimize")
+    nd = pytest.importorskip("scipy.ndimage")
+    grid = {"n": (8, 6), "h": (1.0, 1.0)}
+    N = ops.grid_size(grid)
+    taps = (0.4, 0.2, 0.1)
+    kfull = np.array(taps[::-1] + taps[1:])
+    F = np.stack([nd.convolve1d(e.reshape(6, 8), kfull, axis=0, mode="constant").reshape(-1)
+                  for e in np.eye(N)], axis=1)   # blur along x (axis 0 of the (nx, nz) array)
+    g = np.random.default_rng(21)
+    truth = 3.0 + 0.6 * g.standard_normal(N)
+    obs = g.uniform(size=N) < 0.5
+    d = F @ truth + g.uniform(-0.05, 0.05, N)
+    lo = np.where(obs, d - 0.08, -math.inf)
+    hi = np.where(obs, d + 0.08, math.inf)
+    m = truth + 0.7 * g.standard_normal(N)
+    Fo = F[obs]
+    cons = [{"type": "ineq", "fun": lambda x: hi[obs] - Fo @ x, "jac": lambda x: -Fo},
+            {"type": "ineq", "fun": lambda x: Fo @ x - lo[obs], "jac": lambda x: Fo}]
+    sol = opt.minimize(lambda x: 0.5 * np.sum((x - m) ** 2), np.clip(m, 2.0, 4.0), jac=lambda x: x - m,
+                       bounds=[(2.0, 4.0)] * N, constraints=cons, method="SLSQP",
+                       options={"maxiter": 2000, "ftol": 1e-14})
+    assert sol.success
+    sets = [{"op": "BLUR", "axis": "x", "taps": taps, "type": "bounds", "lo": lo, "hi": hi},
+            {"op": "I", "type": "bounds", "lo": 2.0, "hi": 4.0}]
+    res = run(m, grid, sets, iters=6000)
+    assert rel(res["x"], sol.x) < 1e-5
+    # the data fit binds: some observed samples sit on their bounds
+    s = F @ res["x"]
+    assert np.sum(obs & ((np.abs(s - lo) < 1e-5) | (np.abs(s - hi) < 1e-5))) > 0
+
+
+def test_blur_rejected_with_levels_and_lines():
+    m = model(GRID, 22)
+    blur = {"op": "BLUR", "axis": "z", "taps": (0.5, 0.25), "type": "bounds", "lo": 0.0, "hi": 9.0}
+    with pytest.raises(ValueError):
+        P.ml_parsdmm(m, GRID, [blur], P.options(max_iter=5), levels=2)
+    with pytest.raises(ValueError):
+        P.parsdmm(m, GRID, [dict(blur, type="l2", sigma=1.0, scope="z")], P.options(max_iter=5))
