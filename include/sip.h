@@ -60,7 +60,13 @@ typedef enum {
     SIP_OP_DZ = 1,  /* (x[iz+1]-x[iz])/h_z, output (n_z-1) x n_x (x n_y) */
     SIP_OP_DX = 2,  /* (x[ix+1]-x[ix])/h_x, output n_z x (n_x-1) (x n_y) */
     SIP_OP_DY = 3,  /* (x[iy+1]-x[iy])/h_y, 3D only */
-    SIP_OP_TV = 4   /* anisotropic TV stack [D_z; D_x (; D_y)] */
+    SIP_OP_TV = 4,  /* anisotropic TV stack [D_z; D_x (; D_y)] */
+    SIP_OP_BLUR = 5 /* blurring forward operator F of a data-fit set (Sec.
+                       "Introduction", the projection / feasibility problem
+                       with V_data; the motion blur of Sec. "Joint
+                       deblurring-denoising-inpainting"): M = N,
+                       (F x)[j] = sum_{|t| <= R} k_|t| x[j + t e_axis], samples
+                       outside the grid taken as 0; see sip_set.blur_* */
 } sip_op;
 
 /* Simple sets C_i (set table). */
@@ -82,6 +88,8 @@ typedef enum {
  * line length; card and l1 lines hold at most SIP_MAX_LINE entries. */
 typedef enum { SIP_SCOPE_ALL = 0, SIP_SCOPE_Z = 1, SIP_SCOPE_X = 2, SIP_SCOPE_Y = 3 } sip_scope;
 #define SIP_MAX_LINE 4096
+/* Largest blur radius R (2R + 1 samples: a 25-sample motion blur is R = 12). */
+#define SIP_MAX_BLUR_RADIUS 12
 
 typedef enum { SIP_F64 = 0, SIP_F32 = 1 } sip_dtype;
 
@@ -123,6 +131,18 @@ typedef struct {
      * the norm, unconstrained).  Absolute sigma, scope SIP_SCOPE_ALL;
      * copied at create; not accepted by the server. */
     const double *center_vec;
+    /* SIP_OP_BLUR only: the axis (0 = z, 1 = x, 2 = y; y needs a 3D grid),
+     * the radius R (1..SIP_MAX_BLUR_RADIUS) and a host array of the R + 1
+     * taps k_0..k_R (finite; copied at create) of the centred symmetric
+     * kernel.  F is symmetric, so F^T F adds a band of 4R + 1 samples along
+     * the axis to the x-step's system matrix (Eq. sys_mat).  A blur set
+     * takes scope SIP_SCOPE_ALL and a single level; at most one blur set
+     * per projection.  The single-operator entry points (sip_apply_op,
+     * sip_apply_op_t, sip_system_apply, sip_op_norm, sip_prolong) carry no
+     * taps and reject SIP_OP_BLUR; the server rejects blur sets. */
+    int blur_axis;
+    int blur_radius;
+    const double *blur_taps;
 } sip_set;
 
 typedef struct {

@@ -60,6 +60,7 @@ std::vector<int> op_parts(const GridDesc &g, int op) {
     case SIP_OP_DZ: return {SEG_DZ};
     case SIP_OP_DX: return {SEG_DX};
     case SIP_OP_DY: return {SEG_DY};
+    case SIP_OP_BLUR: return {SEG_BLUR};
     default:
       if (g.ndim == 3) return {SEG_DZ, SEG_DX, SEG_DY};
       return {SEG_DZ, SEG_DX};
@@ -106,7 +107,7 @@ static sip_status check_grid(const sip_grid *g) {
 }
 
 static sip_status check_op(const GridDesc &g, int op) {
-  if (op < SIP_OP_I || op > SIP_OP_TV) return fail(SIP_ERR_INVALID_ARG, "unknown operator %d", op);
+  if (op < SIP_OP_I || op > SIP_OP_BLUR) return fail(SIP_ERR_INVALID_ARG, "unknown operator %d", op);
   if (op == SIP_OP_DY && g.ndim != 3) return fail(SIP_ERR_INVALID_ARG, "D_y needs a 3D grid");
   if ((op == SIP_OP_DZ || op == SIP_OP_TV) && g.n[0] < 2) return fail(SIP_ERR_INVALID_ARG, "operator needs n_z >= 2");
   if ((op == SIP_OP_DX || op == SIP_OP_TV) && g.n[1] < 2) return fail(SIP_ERR_INVALID_ARG, "operator needs n_x >= 2");
@@ -118,6 +119,16 @@ static sip_status check_op(const GridDesc &g, int op) {
 static sip_status check_set(const GridDesc &g, const sip_set &s, int i) {
   sip_status st = check_op(g, s.op);
   if (st) return fail(st, "set %d: %s", i, g_err.c_str());
+  if (s.op == SIP_OP_BLUR) {
+    if (s.blur_axis < 0 || s.blur_axis > 2 || (s.blur_axis == 2 && g.ndim != 3))
+      return fail(SIP_ERR_INVALID_ARG, "set %d: blur axis must be 0 (z), 1 (x) or 2 (y, 3D)", i);
+    if (s.blur_radius < 1 || s.blur_radius > SIP_MAX_BLUR_RADIUS)
+      return fail(SIP_ERR_INVALID_ARG, "set %d: blur radius must be in [1, %d]", i, SIP_MAX_BLUR_RADIUS);
+    if (!s.blur_taps) return fail(SIP_ERR_INVALID_ARG, "set %d: a blur needs its taps", i);
+    for (int t = 0; t <= s.blur_radius; ++t)
+      if (!std::isfinite(s.blur_taps[t])) return fail(SIP_ERR_INVALID_ARG, "set %d: blur taps must be finite", i);
+    if (s.scope != SIP_SCOPE_ALL) return fail(SIP_ERR_INVALID_ARG, "set %d: a blur set applies to the whole model", i);
+  }
   switch (s.type) {
     case SIP_SET_BOUNDS: {
       if (std::isnan(s.lo) || std::isnan(s.hi) || (!s.lo_vec && !s.hi_vec && s.lo > s.hi))
@@ -200,8 +211,13 @@ sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const 
   if (!opts) return fail(SIP_ERR_INVALID_ARG, "opts is NULL");
   if (nsets < 1 || nsets > kMaxSets) return fail(SIP_ERR_INVALID_ARG, "nsets must be in [1, %d]", kMaxSets);
   const GridDesc g = grid_desc(*grid);
-  for (int i = 0; i < nsets; ++i)
+  int nblur = 0;
+  for (int i = 0; i < nsets; ++i) {
     if ((st = check_set(g, sets[i], i))) return st;
+    nblur += sets[i].op == SIP_OP_BLUR;
+  }
+  if (nblur > 1) return fail(SIP_ERR_INVALID_ARG, "at most one blur set per projection");
+  if (nblur && opts->levels > 1) return fail(SIP_ERR_INVALID_ARG, "a blur set runs on one level only");
   return check_opts(*opts);
 }
 
@@ -303,6 +319,32 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
       L.blo[b].assign(sets[b].center_vec, sets[b].center_vec + bd.M);
       bd.bv_lo = boff;
       boff += (bd.M + 3) / 4 * 4;
+    }
+    if (b < nsets && sets[b].op == SIP_OP_BLUR) {
+      // the blur table: taps, autocorrelation, end correction (binary64)
+      const sip_set &s = sets[b];
+      const int R = s.blur_radius;
+      auto k = [&](int t) { return t < 0 ? (-t <= R ? s.blur_taps[-t] : 0.0) : (t <= R ? s.blur_taps[t] : 0.0); };
+      std::vector<double> &tb = L.blur;
+      tb.assign(s.blur_taps, s.blur_taps + R + 1);
+      for (int dd = 0; dd <= 2 * R; ++dd) {
+        double a = 0.0;
+        for (int t = -R; t <= R; ++t) a += k(t) * k(t + dd);
+        tb.push_back(a);
+      }
+      for (int ii = 0; ii < R; ++ii)
+        for (int l = 0; l < R; ++l) {
+          double e = 0.0;
+          for (int j = -R; j < 0; ++j) e += k(ii - j) * k(l - j);
+          tb.push_back(e);
+        }
+      d.bl_R = R;
+      d.bl_axis = s.blur_axis;
+      d.bl_n = (int32_t)g.n[s.blur_axis];
+      d.bl_blk = b;
+      d.bl_st = s.blur_axis == 0 ? 1 : s.blur_axis == 1 ? g.n[0] : g.n[0] * g.n[1];
+      d.bl_off = boff;
+      boff += ((int64_t)tb.size() + 3) / 4 * 4;
     }
     if (b < nsets && (sets[b].lo_vec || sets[b].hi_vec)) {
       const sip_set &s = sets[b];
@@ -478,7 +520,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   int64_t ch_rhs = 0;
   P.rhs_smem = 0;
   bool stageable = dtype == SIP_F32 && !insts.empty();
-  for (auto &L : insts) stageable = stageable && L.dev.ny == 1 && L.dev.N < (int64_t(1) << 31);
+  for (auto &L : insts) stageable = stageable && L.dev.ny == 1 && L.dev.N < (int64_t(1) << 31) && !L.dev.bl_R;
   for (int occ = 2; stageable && occ >= 1 && !P.rhs_smem; --occ) {
     const int64_t ch = chunk_for(tot_n, sms * occ);
     size_t need = 0;
@@ -561,6 +603,11 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   // per SM) runs at half its speed
   if (P.exec == SIP_EXEC_AUTO) P.exec = SIP_EXEC_GRAPH;
   if (P.exec == SIP_EXEC_PERSISTENT && P.fused_grid <= 0) P.exec = SIP_EXEC_GRAPH;
+  // a blur block's terms live in their own instantiations of the
+  // grid-point and set-pass kernels; the persistent kernel has none
+  P.blur = false;
+  for (auto &L : insts) P.blur = P.blur || L.dev.bl_R != 0;
+  if (P.blur) P.exec = SIP_EXEC_GRAPH;
   P.nt_n = (int)tn.size();
   P.nt_rhs = (int)trhs.size();
   P.nt_set = (int)tset.size();
@@ -684,6 +731,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     d.gamma_sched = (const double *)at(o.sched_g);
     d.trace = (double *)at(o.trace);
     d.bvec = at(o.bvec);
+    d.bl_w = d.bl_R ? (const char *)d.bvec + d.bl_off * W : nullptr;
     d.trace_w = 2 * d.nb + 2 + d.p;
     P.h_insts[i] = d;
     P.layouts[i] = insts[i];
@@ -734,9 +782,18 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       }
     }
   CK(cudaMemset(P.arena, 0, (size_t)off));
-  // per-entry bound vectors, in the storage type
+  // per-entry bound vectors and blur tables, in the storage type
   for (int i = 0; i < P.ninst; ++i) {
     const InstLayout &L = insts[i];
+    if (L.dev.bl_R) {
+      char *dst = (char *)P.h_insts[i].bvec + L.dev.bl_off * W;
+      if (dtype == SIP_F64) {
+        CK(cudaMemcpy(dst, L.blur.data(), L.blur.size() * 8, cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> f(L.blur.begin(), L.blur.end());
+        CK(cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+      }
+    }
     for (int b = 0; b < L.dev.nb; ++b) {
       const BlockDev &bd = L.dev.blk[b];
       if (bd.bv_lo < 0) continue;
@@ -791,6 +848,7 @@ static int launches_per_iter(const Plan &P) {
 // marks: every launch stamps its own slot pair of P.d_ts (timing graph)
 static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   Launch L{P.dtype, st};
+  L.blur = P.blur;
   auto T0 = [&](int c) {
     if (!marks) return;
     L.ts = P.d_ts + 2 * P.tcat.size();

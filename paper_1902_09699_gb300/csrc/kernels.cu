@@ -301,6 +301,81 @@ __device__ __forceinline__ T seg_ih(const InstDev &in, int kind) {
   return kind == SEG_DZ ? SV<T>::ih(in, 0) : kind == SEG_DX ? SV<T>::ih(in, 1) : kind == SEG_DY ? SV<T>::ih(in, 2) : T(1);
 }
 
+// Blurring forward operator F of a data-fit block (sip_op SIP_OP_BLUR):
+// (F v)[g] = sum_{|t| <= R} k_|t| v[g + t st] along the blur axis, samples
+// outside the grid taken as 0.  F is symmetric, so F^T = F.
+template <typename D>
+__device__ __forceinline__ int blur_pos(const D &in, int64_t g) {
+  if (in.bl_axis == 0) return (int)((uint32_t)g - (uint32_t)in.nz * fdiv((uint32_t)g, in.fz));
+  const uint32_t t = fdiv((uint32_t)g, in.fz);  // ix + nx*iy
+  if (in.bl_axis == 1) return (int)(t - (uint32_t)in.nx * fdiv(t, in.fx));
+  return (int)fdiv(t, in.fx);
+}
+template <typename T, typename D, typename V>
+__device__ __forceinline__ T blur_fwd(const D &in, int64_t g, V v) {
+  const T *__restrict__ k = (const T *)in.bl_w;
+  const int R = in.bl_R, n = in.bl_n, i = blur_pos(in, g);
+  const int64_t st = in.bl_st;
+  T s = k[0] * v(g);
+  for (int t = 1; t <= R; ++t) {
+    const T a = i - t >= 0 ? v(g - t * st) : T(0);
+    const T b = i + t < n ? v(g + t * st) : T(0);
+    s += k[t] * (a + b);
+  }
+  return s;
+}
+// (F^T F v)[g]: row i of F^T F is sum_{0 <= j < n} k_|i-j| k_|l-j| at
+// column l.  Summed over every j it is the kernel's autocorrelation
+// a_|i-l|; the rows j < 0 are missing only where i and l are both below R
+// (the correction E[i][l]), and the rows j >= n, by the mirror symmetry
+// j -> n-1-j, only where both are within R of the far end (E[n-1-i][n-1-l]).
+template <typename T, typename D, typename V>
+__device__ __forceinline__ T blur_normal(const D &in, int64_t g, V v) {
+  const int R = in.bl_R, n = in.bl_n, i = blur_pos(in, g);
+  const T *__restrict__ a = (const T *)in.bl_w + (R + 1);
+  const T *__restrict__ E = a + (2 * R + 1);
+  const int64_t st = in.bl_st;
+  T s = a[0] * v(g);
+  for (int d = 1; d <= 2 * R; ++d) {
+    const T lo = i - d >= 0 ? v(g - d * st) : T(0);
+    const T hi = i + d < n ? v(g + d * st) : T(0);
+    s += a[d] * (lo + hi);
+  }
+  const int L = R < n ? R : n;
+  if (i < R)
+    for (int l = 0; l < L; ++l) s -= E[i * R + l] * v(g + (int64_t)(l - i) * st);
+  if (i >= n - R) {
+    const int ii = n - 1 - i;
+    for (int l = 0; l < L; ++l) s -= E[ii * R + l] * v(g + (int64_t)(n - 1 - l - i) * st);
+  }
+  return s;
+}
+// rho_F F^T F v at g for the x-step's system matrix (Eq. sys_mat), for the
+// two forms of v the launches need: a stored vector (x in the right-hand
+// side residual, r_0 in w_0 = C r_0) and r_{i+1} = r_i - alpha (w_i +
+// beta s_{i-1}) in a CG step.  Only the kernels instantiated for plans
+// with a blur block contain them.
+template <typename T, typename D>
+__device__ __forceinline__ T blur_c1(const D &in, const InstScal &sc, int64_t g, const T *__restrict__ v) {
+  return SV<T>::blk(sc, in.bl_blk, BF_RHO) * blur_normal<T>(in, g, [&](int64_t q) { return v[q]; });
+}
+// (F^T (rho_F y_F + v_F))[g], the blur block's term of the x-step's
+// right-hand side
+template <typename T>
+__device__ __forceinline__ T blur_rhs(const InstDev &in, const InstScal &sc, int64_t g) {
+  const int64_t yo = in.blk[in.bl_blk].yoff;
+  const T *__restrict__ y = (const T *)in.y + yo;
+  const T *__restrict__ v = (const T *)in.v + yo;
+  const T rho = SV<T>::blk(sc, in.bl_blk, BF_RHO);
+  return blur_fwd<T>(in, g, [&](int64_t q) { return rho * y[q] + v[q]; });
+}
+template <typename T, typename D>
+__device__ __forceinline__ T blur_c3(const D &in, const InstScal &sc, int64_t g, const T *__restrict__ r,
+                                  const T *__restrict__ w, const T *__restrict__ sp, T alpha, T beta) {
+  return SV<T>::blk(sc, in.bl_blk, BF_RHO) *
+         blur_normal<T>(in, g, [&](int64_t q) { return r[q] - alpha * (w[q] + beta * sp[q]); });
+}
+
 // s = A x for one row of a segment (used by the single-step entry points and
 // the norm kernel; the loop kernels inline the same arithmetic).
 template <typename T>
@@ -309,6 +384,7 @@ __device__ __forceinline__ T seg_forward(const InstDev &in, int kind, const T *_
   int64_t off;
   g = seg_base(in, kind, row, off);
   if (kind == SEG_I || kind == SEG_RING) return x[g];
+  if (kind == SEG_BLUR) return blur_fwd<T>(in, g, [&](int64_t q) { return x[q]; });
   return (x[g + off] - x[g]) * seg_ih<T>(in, kind);
 }
 
@@ -485,7 +561,7 @@ __device__ __forceinline__ AdjRows adj_rows(const InstDev &in, int kind, const G
 // b = sum_i A_i^T (rho_i y_i + v_i) (+ m in the direct form) and r = b - C x
 // at the work item's grid points.  I is the index type of grid points and
 // rows (32-bit while N < 2^31).
-template <typename T, typename I>
+template <typename T, typename I, bool BL = false>
 __device__ __forceinline__ void body_rhs_t(const Tile &tl, const InstDev &in, InstScal &sc) {
   using A = typename AccOf<T>::type;
   // points per thread per round, segments whose rows are loaded together
@@ -586,6 +662,14 @@ __device__ __forceinline__ void body_rhs_t(const Tile &tl, const InstDev &in, In
         }
       }
     }
+    if constexpr (BL) {
+      if (in.bl_R) {
+        // the blur block: F^T (rho y + v) and rho_F F^T F x at each point
+#pragma unroll
+        for (int e = 0; e < PT; ++e)
+          if (g[e] < end) b[e] += blur_rhs<T>(in, sc, g[e]) - blur_c1<T>(in, sc, g[e], x);
+      }
+    }
 #pragma unroll
     for (int e = 0; e < PT; ++e) {
       if (g[e] < end) {
@@ -600,23 +684,23 @@ __device__ __forceinline__ void body_rhs_t(const Tile &tl, const InstDev &in, In
   if (threadIdx.x == 0) cg_part<A>(in, 0, 0)[tl.seq] = acc[0];
 }
 
-template <typename T>
+template <typename T, bool BL = false>
 __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restrict__ insts,
                                          InstScal *__restrict__ scal) {
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   if (in.N <= (int64_t)0x7fffffff)
-    body_rhs_t<T, int>(tl, in, sc);
+    body_rhs_t<T, int, BL>(tl, in, sc);
   else
-    body_rhs_t<T, int64_t>(tl, in, sc);
+    body_rhs_t<T, int64_t, BL>(tl, in, sc);
 }
 
-template <typename T, bool ONE>
+template <typename T, bool ONE, bool BL = false>
 __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                   InstScal *__restrict__ scal, unsigned long long *ts,
                                                   const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
-  body_rhs<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal);
+  body_rhs<T, BL>(tiles[blockIdx.x], ONE ? &one.d : insts, scal);
 }
 
 // --------------------------------------------------------------------------
@@ -869,13 +953,13 @@ __device__ __forceinline__ void body_cg_w0_v4(const Tile &tl, const D &in, const
   if (threadIdx.x == 0) cg_part<float>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0
 }
 
-template <typename T, typename D>
+template <typename T, bool BL = false, typename D>
 __device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstScal &sc) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
   const int done = sc.done;
   if constexpr (sizeof(T) == 4) {
-    if ((in.nz & 3) == 0 && in.ny == 1 && (((uintptr_t)in.cr[0] | (uintptr_t)in.cw[0]) & 15) == 0) {
+    if ((in.nz & 3) == 0 && in.ny == 1 && !in.bl_R && (((uintptr_t)in.cr[0] | (uintptr_t)in.cw[0]) & 15) == 0) {
       body_cg_w0_v4(tl, in, sc, done);
       return;
     }
@@ -898,7 +982,10 @@ __device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstS
     for (int e = 0; e < PT; ++e) {
       const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
       if (g < end) {
-        const T wg = apply_c(C, rn[e]);
+        T wg = apply_c(C, rn[e]);
+        if constexpr (BL) {
+          if (in.bl_R) wg += blur_c1<T>(in, sc, g, r);
+        }
         w[g] = wg;
         a0 += (A)wg * (A)rn[e].c;
       }
@@ -908,10 +995,10 @@ __device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstS
   block_sum<1>(acc);
   if (threadIdx.x == 0) cg_part<A>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0 = p_0^T C p_0
 }
-template <typename T>
+template <typename T, bool BL = false>
 __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__restrict__ insts,
                                            InstScal *__restrict__ scal) {
-  body_cg_w0_in<T>(tl, insts[tl.inst], scal[tl.inst]);
+  body_cg_w0_in<T, BL>(tl, insts[tl.inst], scal[tl.inst]);
 }
 
 // Single-instance plans: the grid-point work item of CTA b (items of `chunk`
@@ -929,15 +1016,15 @@ __device__ __forceinline__ Tile one_tile(const CgOne &one) {
   return tl;
 }
 
-template <typename T>
+template <typename T, bool BL = false>
 __global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                        InstScal *__restrict__ scal, unsigned long long *ts,
                                                        const __grid_constant__ CgOne one) {
   const Stamp stamp(ts);
   if (one.on)
-    body_cg_w0_in<T>(one_tile(one), one.d, scal[0]);
+    body_cg_w0_in<T, BL>(one_tile(one), one.d, scal[0]);
   else
-    body_cg_w0<T>(tiles[blockIdx.x], insts, scal);
+    body_cg_w0<T, BL>(tiles[blockIdx.x], insts, scal);
 }
 
 // CG state fields in the storage precision (binary32 kernels do their
@@ -1142,7 +1229,7 @@ __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const D &in, Ins
   }
 }
 
-template <typename T, typename D>
+template <typename T, bool BL = false, typename D>
 __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, InstScal &sc, int ph) {
   using A = typename AccOf<T>::type;
   constexpr int PT = sizeof(T) == 4 ? 2 : 1;  // 3 stencils per row: keep the register budget
@@ -1152,7 +1239,7 @@ __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, Ins
     // batched plan is packed and may not be)
     const uintptr_t al = (uintptr_t)in.x | (uintptr_t)in.cp | (uintptr_t)in.cr[0] | (uintptr_t)in.cr[1] |
                          (uintptr_t)in.cw[0] | (uintptr_t)in.cw[1] | (uintptr_t)in.cs[0] | (uintptr_t)in.cs[1];
-    if ((in.nz & 3) == 0 && in.ny == 1 && (al & 15) == 0) {
+    if ((in.nz & 3) == 0 && in.ny == 1 && !in.bl_R && (al & 15) == 0) {
       body_cg_step_v4(tl, in, sc, ph);
       return;
     }
@@ -1217,7 +1304,10 @@ __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, Ins
         x[g] = xv[e] + alpha * pi;
         sn_[g] = s_c;
         rn_[g] = rnew.c;
-        const T wnew = apply_c(C, rnew);
+        T wnew = apply_c(C, rnew);
+        if constexpr (BL) {
+          if (in.bl_R) wnew += blur_c3<T>(in, sc, g, r, w, sp, alpha, beta);
+        }
         wn_[g] = wnew;
         ag += (A)rnew.c * (A)rnew.c;
         ad += (A)wnew * (A)rnew.c;
@@ -1233,28 +1323,28 @@ __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, Ins
   }
 }
 
-template <typename T>
+template <typename T, bool BL = false>
 __device__ __forceinline__ void body_cg_step(const Tile &tl, const InstDev *__restrict__ insts,
                                              InstScal *__restrict__ scal, int ph) {
-  body_cg_step_in<T>(tl, insts[tl.inst], scal[tl.inst], ph);
+  body_cg_step_in<T, BL>(tl, insts[tl.inst], scal[tl.inst], ph);
 }
 
 // out of line: the single-instance path keeps the register allocation
-template <typename T>
+template <typename T, bool BL>
 __device__ __noinline__ void cg_step_call(const Tile &tl, const InstDev *insts, InstScal *scal, int ph) {
-  body_cg_step<T>(tl, insts, scal, ph);
+  body_cg_step<T, BL>(tl, insts, scal, ph);
 }
 
-template <typename T>
+template <typename T, bool BL = false>
 __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
                                                          const InstDev *__restrict__ insts,
                                                          InstScal *__restrict__ scal, int ph, unsigned long long *ts,
                                                          const __grid_constant__ CgOne one) {
   const Stamp stamp(ts);
   if (one.on)
-    body_cg_step_in<T>(one_tile(one), one.d, scal[0], ph);
+    body_cg_step_in<T, BL>(one_tile(one), one.d, scal[0], ph);
   else
-    cg_step_call<T>(tiles[blockIdx.x], insts, scal, ph);
+    cg_step_call<T, BL>(tiles[blockIdx.x], insts, scal, ph);
 }
 
 // --------------------------------------------------------------------------
@@ -1424,7 +1514,7 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
   return o;
 }
 
-template <typename T>
+template <typename T, bool BL = false>
 __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, const SegDev &sg, int k, bool ad,
                               bool ad_dots, bool chk, JobScal *__restrict__ jscal,
                               const JobDev *__restrict__ jobs) {
@@ -1521,6 +1611,12 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
     if (xk0) {
       const T z0 = xk0[g];
       kv0 = kind == SEG_I ? z0 : (xk0[g + off] - z0) * q.ih;
+    }
+    if constexpr (BL) {
+      if (kind == SEG_BLUR) {
+        sv = blur_fwd<T>(in, g, [&](int64_t i) { return x[i]; });
+        if (xk0) kv0 = blur_fwd<T>(in, g, [&](int64_t i) { return xk0[i]; });
+      }
     }
   };
   bool vec = false;
@@ -1697,7 +1793,7 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   }
 }
 
-template <typename T>
+template <typename T, bool BL = false>
 __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__restrict__ insts,
                                                       InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
                                                       const JobDev *__restrict__ jobs) {
@@ -1712,7 +1808,7 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
   if (sg.kind == SEG_RING)
     setpass_ring<T>(tl, in, sc, k, chk);
   else
-    setpass_block<T>(tl, in, sc, sg, k, ad, ad_dots, chk, jscal, jobs);
+    setpass_block<T, BL>(tl, in, sc, sg, k, ad, ad_dots, chk, jscal, jobs);
 
   // The last CTA of the instance resolves the l2 scales and arms the
   // selection jobs of this iteration, one block per lane of warp 0.
@@ -1771,13 +1867,13 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
   }
 }
 
-template <typename T, bool ONE>
+template <typename T, bool ONE, bool BL = false>
 __global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                       InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
                                                       const JobDev *__restrict__ jobs, unsigned long long *ts,
                                                       const __grid_constant__ InstOne one) {
   const Stamp stamp(ts);
-  body_setpass<T>(tiles[blockIdx.x], ONE ? &one.d : insts, scal, jscal, jobs);
+  body_setpass<T, BL>(tiles[blockIdx.x], ONE ? &one.d : insts, scal, jscal, jobs);
 }
 
 // --------------------------------------------------------------------------
@@ -2968,6 +3064,7 @@ __device__ void set_coefficients(const InstDev &in, InstScal &sc) {
       case SIP_OP_DZ: cz += r; break;
       case SIP_OP_DX: cx += r; break;
       case SIP_OP_DY: cy += r; break;
+      case SIP_OP_BLUR: break;  // rho_F F^T F: the blur term of the CG launches
       default: cz += r; cx += r; if (in.ndim == 3) cy += r; break;
     }
   }
@@ -3153,6 +3250,7 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
         case SIP_OP_DZ: cz = rho_b; break;
         case SIP_OP_DX: cx = rho_b; break;
         case SIP_OP_DY: cy = rho_b; break;
+        case SIP_OP_BLUR: break;  // rho_F F^T F: the blur term of the CG launches
         default: cz = rho_b; cx = rho_b; if (in.ndim == 3) cy = rho_b; break;
       }
     }
@@ -3516,6 +3614,40 @@ __global__ void k_system_apply(const InstDev *__restrict__ inp, const InstScal *
     }                                                                                             \
   } while (0)
 
+// ... and by whether the plan has a blur block (kernels with the F^T F term)
+#define SIP_DISPATCH_ONE_BL(L, ONEP, KERNEL, GRID, BLOCK, SMEM, ...)                             \
+  do {                                                                                          \
+    if ((L).blur) {                                                                             \
+      if ((L).dtype == SIP_F64) {                                                               \
+        if ((ONEP).on)                                                                          \
+          KERNEL<double, true, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);     \
+        else                                                                                    \
+          KERNEL<double, false, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);    \
+      } else {                                                                                  \
+        if ((ONEP).on)                                                                          \
+          KERNEL<float, true, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);      \
+        else                                                                                    \
+          KERNEL<float, false, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);     \
+      }                                                                                         \
+    } else {                                                                                    \
+      SIP_DISPATCH_ONE(L, ONEP, KERNEL, GRID, BLOCK, SMEM, __VA_ARGS__);                        \
+    }                                                                                           \
+  } while (0)
+#define SIP_DISPATCH_BL(L, KERNEL, GRID, BLOCK, SMEM, ...)                                        \
+  do {                                                                                          \
+    if ((L).dtype == SIP_F64) {                                                                 \
+      if ((L).blur)                                                                             \
+        KERNEL<double, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);             \
+      else                                                                                      \
+        KERNEL<double, false><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);            \
+    } else {                                                                                    \
+      if ((L).blur)                                                                             \
+        KERNEL<float, true><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);              \
+      else                                                                                      \
+        KERNEL<float, false><<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);             \
+    }                                                                                           \
+  } while (0)
+
 #define SIP_DISPATCH(L, KERNEL, GRID, BLOCK, SMEM, ...)                          \
   do {                                                                           \
     if ((L).dtype == SIP_F64)                                                    \
@@ -3540,7 +3672,7 @@ cudaError_t launch_norms(const Launch &L, const Tile *tiles, int nt, const InstD
 }
 cudaError_t launch_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                        const InstOne &one) {
-  SIP_DISPATCH_ONE(L, one, k_rhs, nt, kThreads, 0, tiles, insts, scal, L.ts, one);
+  SIP_DISPATCH_ONE_BL(L, one, k_rhs, nt, kThreads, 0, tiles, insts, scal, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_rhs_tma(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
@@ -3561,17 +3693,17 @@ int rhs_tma_occupancy(size_t smem) {
 }
 cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                          const CgOne &one) {
-  SIP_DISPATCH(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal, L.ts, one);
+  SIP_DISPATCH_BL(L, k_cg_w0, nt, kThreads, 0, tiles, insts, scal, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
                            const CgOne &one) {
-  SIP_DISPATCH(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
+  SIP_DISPATCH_BL(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                            JobScal *jscal, const JobDev *jobs, const InstOne &one) {
-  SIP_DISPATCH_ONE(L, one, k_setpass, nt, kThreads, 0, tiles, insts, scal, jscal, jobs, L.ts, one);
+  SIP_DISPATCH_ONE_BL(L, one, k_setpass, nt, kThreads, 0, tiles, insts, scal, jscal, jobs, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,

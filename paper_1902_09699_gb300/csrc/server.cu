@@ -365,8 +365,8 @@ sip_status sip_server_submit(sip_server *S, const sip_grid *grid, const sip_set 
   if (!S || !m_host || !x_host || !req_id) return fail(SIP_ERR_INVALID_ARG, "NULL argument");
   if (sip_status st = validate(grid, sets, nsets, &S->cfg.opts)) return st;
   for (int i = 0; i < nsets; ++i)
-    if (sets[i].lo_vec || sets[i].hi_vec || sets[i].center_vec)
-      return fail(SIP_ERR_INVALID_ARG, "set %d: per-entry vectors are not served", i);
+    if (sets[i].lo_vec || sets[i].hi_vec || sets[i].center_vec || sets[i].op == SIP_OP_BLUR)
+      return fail(SIP_ERR_INVALID_ARG, "set %d: per-entry vectors and blur tables are not served", i);
   Request *r = new (std::nothrow) Request();
   if (!r) return fail(SIP_ERR_OOM, "host allocation failed");
   r->grid = *grid;

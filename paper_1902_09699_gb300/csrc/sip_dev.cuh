@@ -33,7 +33,7 @@ constexpr int64_t kMaxChunk = 64 * kTile;  // rows of one work item, at most
 constexpr int kDigitBits = 11;       // radix digit of the selection passes
 constexpr int kBins = 1 << kDigitBits;
 
-enum SegKind : int32_t { SEG_I = 0, SEG_DZ = 1, SEG_DX = 2, SEG_DY = 3, SEG_RING = 4 };
+enum SegKind : int32_t { SEG_I = 0, SEG_DZ = 1, SEG_DX = 2, SEG_DY = 3, SEG_RING = 4, SEG_BLUR = 5 };
 // BT_ANNULUS: the annulus on A x as a whole; BT_LINE: a set applied to
 // every line of A x on its own (BlockDev.line_type says which).
 enum BlkType : int32_t { BT_BOUNDS = 0, BT_L1 = 1, BT_L2 = 2, BT_CARD = 3, BT_DIST = 4, BT_ANNULUS = 5, BT_LINE = 6 };
@@ -192,6 +192,15 @@ struct InstDev {
   int32_t select_window;     // option: warm-started window for top-k selections
   int32_t k0_ring;           // s^{k0} from x^{k0} in the history ring (adapt_every < hist), no k0s copy
   int32_t pad_k0;
+  // blurring forward operator F of a data-fit block (bl_R = 0: none):
+  // radius, axis (0 z, 1 x, 2 y), samples along the axis, the block, the
+  // stride of one step along the axis, and the blur table in the storage
+  // type (in bvec at bl_off): the taps k_0..k_R, the autocorrelation
+  // a_0..a_2R of the kernel (F^T F away from the ends) and the R x R
+  // correction E[i][l] = sum_{j<0} k_|i-j| k_|l-j| of the first R samples
+  int32_t bl_R, bl_axis, bl_n, bl_blk;
+  int64_t bl_st, bl_off;
+  const void *bl_w;
   // device arrays, element type = the plan's dtype
   const void *m;
   void *x, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;
@@ -217,6 +226,9 @@ struct CgDesc {
   int64_t N;
   void *x, *cp, *cgp;
   void *cr[2], *cw[2], *cs[2];
+  int32_t bl_R, bl_axis, bl_n, bl_blk;
+  int64_t bl_st;
+  const void *bl_w;
 };
 struct CgOne {
   CgDesc d;
@@ -243,6 +255,12 @@ inline CgDesc cg_desc(const InstDev &in) {
     d.cw[j] = in.cw[j];
     d.cs[j] = in.cs[j];
   }
+  d.bl_R = in.bl_R;
+  d.bl_axis = in.bl_axis;
+  d.bl_n = in.bl_n;
+  d.bl_blk = in.bl_blk;
+  d.bl_st = in.bl_st;
+  d.bl_w = in.bl_w;
   return d;
 }
 

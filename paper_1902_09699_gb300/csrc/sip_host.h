@@ -29,6 +29,7 @@ struct InstLayout {
   int64_t Mtot = 0, Mw = 0, Ms = 0;
   int64_t Mb = 0;  // per-entry bound vectors (lo and hi of every such block)
   std::vector<std::vector<double>> blo, bhi;  // per block, empty for scalar bounds
+  std::vector<double> blur;                   // blur table of the blur block (empty: none)
   std::vector<JobDev> jobs;
 };
 
@@ -70,6 +71,7 @@ struct Plan {
   int nt_rhs = 0;
   size_t rhs_smem = 0;
   bool any_card = false, any_fin = false, any_stop = false;
+  bool blur = false;  // an instance has a blur block (graph path, blur kernels)
   CgOne cg_one;  // CG launch parameters of a single-instance plan (on = 0 otherwise)
   InstOne one;   // the descriptor as a launch parameter (single instance owning its model)
   int cg_launch = 0, max_iter = 0, check_every = 1;

@@ -13,6 +13,9 @@ struct Launch {
   // launch-time stamps (timing runs only): [0] earliest CTA start, [1]
   // latest CTA end, global timer nanoseconds; null otherwise
   unsigned long long *ts = nullptr;
+  // the plan has a blur block: the right-hand side, CG and set-pass
+  // launches take the instantiations with the F^T F and F terms
+  bool blur = false;
 };
 
 // iteration kernels (kernels.cu)

@@ -14,7 +14,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsip.so")
 
-OPS = {"I": 0, "DZ": 1, "DX": 2, "DY": 3, "TV": 4}
+OPS = {"I": 0, "DZ": 1, "DX": 2, "DY": 3, "TV": 4, "BLUR": 5}
+BLUR_AXES = {"z": 0, "x": 1, "y": 2}
 SET_TYPES = {"bounds": 0, "l1": 1, "l2": 2, "card": 3, "annulus": 4}
 SCOPES = {"all": 0, "z": 1, "x": 2, "y": 3}
 F64, F32 = 0, 1
@@ -35,7 +36,8 @@ class Set(ctypes.Structure):
     _fields_ = [("op", c_int), ("type", c_int), ("lo", c_dbl), ("hi", c_dbl), ("sigma", c_dbl),
                 ("sigma_rel", c_dbl), ("k", c_i64), ("k_frac", c_dbl), ("scope", c_int),
                 ("lo_vec", ctypes.POINTER(c_dbl)), ("hi_vec", ctypes.POINTER(c_dbl)),
-                ("center_vec", ctypes.POINTER(c_dbl))]
+                ("center_vec", ctypes.POINTER(c_dbl)),
+                ("blur_axis", c_int), ("blur_radius", c_int), ("blur_taps", ctypes.POINTER(c_dbl))]
 
 
 class Options(ctypes.Structure):
@@ -154,7 +156,8 @@ def make_grid(grid):
 
 def make_set(s):
     """A sip_set from a set dict; array-valued "lo" / "hi" (bounds) become
-    per-entry bound vectors (kept alive on the returned struct)."""
+    per-entry bound vectors (kept alive on the returned struct).  A "BLUR"
+    operator takes "axis" ("z", "x" or "y") and "taps" (k_0..k_R)."""
     c = Set()
     c.op = OPS[s["op"]]
     c.type = SET_TYPES[s["type"]]
@@ -177,6 +180,12 @@ def make_set(s):
     c.k = int(s.get("k", 0))
     c.k_frac = float(s.get("k_frac", 0.0))
     c.scope = SCOPES[s.get("scope", "all")]
+    if s["op"] == "BLUR":
+        taps = np.ascontiguousarray(s["taps"], dtype=np.float64).reshape(-1)
+        c._keep.append(taps)
+        c.blur_axis = BLUR_AXES[s["axis"]]
+        c.blur_radius = taps.size - 1
+        c.blur_taps = taps.ctypes.data_as(ctypes.POINTER(c_dbl))
     return c
 
 

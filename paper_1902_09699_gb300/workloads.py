@@ -9,10 +9,11 @@ not available): smooth Gaussian random fields and layered media with a
 Gaussian anomaly, plus Gaussian noise.  All randomness is numpy's Philox
 counter-based generator seeded per workload.
 
-Set dicts: {"op": "I"|"DZ"|"DX"|"DY"|"TV", "type": "bounds"|"l1"|"l2"|"card",
-"lo", "hi", "sigma", "sigma_rel", "k", "k_frac"}; ``sigma_rel`` asks for a
-radius relative to the projected model's own norm, ``k_frac`` for a
-cardinality relative to the grid size.
+Set dicts: {"op": "I"|"DZ"|"DX"|"DY"|"TV"|"BLUR", "type": "bounds"|"l1"|"l2"|
+"card", "lo", "hi", "sigma", "sigma_rel", "k", "k_frac"}; ``sigma_rel`` asks
+for a radius relative to the projected model's own norm, ``k_frac`` for a
+cardinality relative to the grid size; a "BLUR" operator also takes "axis"
+and "taps".
 """
 import math
 
@@ -142,6 +143,58 @@ def lines_2d(n=(512, 1024), seed=1006):
     opts = dict(max_iter=300, cg_iters=5, adapt=1, rho0=1.0, gamma0=1.5)
     return dict(name="2d-%dx%d-layered-rowcol-card" % tuple(n), grid={"n": tuple(n), "h": (1.0, 1.0)},
                 m=m, sets=sets, opts=opts, dtype="f32")
+
+
+def motion_blur_taps(length=25):
+    """Taps k_0..k_R of a centred box of ``length`` = 2R + 1 samples (a
+    straight motion blur of that many pixels), each 1 / length."""
+    if length < 3 or length % 2 == 0:
+        raise ValueError("an odd length >= 3")
+    return tuple([1.0 / length] * (length // 2 + 1))
+
+
+def deblur_2d(n=(1100, 1100), seed=1007, blur_len=25, frac=0.2, noise=10.0, bound=15.0, axis="x"):
+    """Stand-in for the paper's joint deblurring-denoising-inpainting example
+    (Sec. "Joint deblurring-denoising-inpainting": 1100 x 1100 grayscale
+    patches in [0, 255], a known 25-pixel motion blur, 20% of the pixels
+    observed with uniform noise in [-10, 10], data fit with the
+    over-estimate [-15, 15]).  The image is a smooth random field mapped to
+    [0, 255]; the observed data are its blur (scipy's zero-padded 1D
+    convolution with a box of ``blur_len`` samples along ``axis``) at a
+    random ``frac`` of the pixels plus uniform noise.  Data-fit set
+    {-bound <= F x - d <= bound} on the observed pixels (+-inf elsewhere),
+    with the model-property sets [0, 255] bounds, a TV l1 ball and slope
+    bounds on D_z x and D_x x whose sizes come from a second training image
+    of the same generator.  Initial guess: d at observed pixels, their mean
+    elsewhere.  FP32, adaptive rho, gamma = 1.5, 5 CG steps."""
+    from scipy import ndimage
+    g = rng(seed)
+    nz, nx = int(n[0]), int(n[1])
+    truth = grf((nz, nx), corr_len=6.0, lo=0.0, hi=255.0, noise=0.0, seed=seed)
+    train = grf((nz, nx), corr_len=6.0, lo=0.0, hi=255.0, noise=0.0, seed=seed + 1)
+    taps = motion_blur_taps(blur_len)
+    kfull = np.array(taps[::-1] + taps[1:])
+    ax = {"z": 1, "x": 0}[axis]  # axis of the (n_x, n_z) array
+    blurred = ndimage.convolve1d(truth.reshape(nx, nz), kfull, axis=ax, mode="constant", cval=0.0).reshape(-1)
+    obs = g.uniform(size=truth.size) < frac
+    d = blurred + g.uniform(-noise, noise, truth.size)
+    lo = np.where(obs, d - bound, -INF)
+    hi = np.where(obs, d + bound, INF)
+    m = np.where(obs, d, float(d[obs].mean()))
+    T = train.reshape(nx, nz)
+    dz, dx = np.diff(T, axis=1), np.diff(T, axis=0)
+    tv = float(np.abs(dz).sum() + np.abs(dx).sum())
+    sz, sx = float(np.abs(dz).max()), float(np.abs(dx).max())
+    sets = [
+        {"op": "BLUR", "axis": axis, "taps": taps, "type": "bounds", "lo": lo, "hi": hi},
+        {"op": "I", "type": "bounds", "lo": 0.0, "hi": 255.0},
+        {"op": "TV", "type": "l1", "sigma": tv},
+        {"op": "DZ", "type": "bounds", "lo": -sz, "hi": sz},
+        {"op": "DX", "type": "bounds", "lo": -sx, "hi": sx},
+    ]
+    opts = dict(max_iter=300, cg_iters=5, adapt=1, rho0=1.0, gamma0=1.5)
+    return dict(name="2d-%dx%d-deblur-inpaint-blur%d" % (nz, nx, blur_len), grid={"n": (nz, nx), "h": (1.0, 1.0)},
+                m=m, sets=sets, opts=opts, dtype="f32", truth=truth, obs=obs)
 
 
 def grf_3d(n=(256, 256, 128), seed=1003):

@@ -73,6 +73,10 @@ def test_op_rows(sip):
     assert sip.op_rows(g3, "DY") == 48
     assert sip.op_rows(g3, "TV") == 3 * 3 * 5 + 4 * 2 * 5 + 48
     assert sip.op_rows(g, "DY") == -1             # 2D grid has no y axis
+    assert sip.op_rows(g, "BLUR") == -1           # the single-operator calls carry no taps
+
+
+BLUR = {"op": "BLUR", "axis": "z", "taps": (0.5, 0.25), "type": "bounds", "lo": 0.0, "hi": 9.0}
 
 
 @pytest.mark.parametrize("bad", [
@@ -97,6 +101,13 @@ def test_op_rows(sip):
     dict(sets=[{"op": "I", "type": "l2", "sigma": 1.0, "scope": "y"}]),
     dict(grid={"n": (4100, 2)}, sets=[{"op": "I", "type": "card", "k": 1, "scope": "z"}]),
     dict(sets=[{"op": "I", "type": "annulus", "lo": -1.0, "hi": 1.0}]),
+    dict(sets=[dict(BLUR, taps=(1.0,))]),                      # radius 0
+    dict(sets=[dict(BLUR, taps=(1.0 / 27,) * 14)]),            # radius 13
+    dict(sets=[dict(BLUR, axis="y")]),                         # y in 2D
+    dict(sets=[dict(BLUR, taps=(0.5, math.inf))]),
+    dict(sets=[dict(BLUR, type="l2", sigma=1.0, scope="z")]),
+    dict(sets=[BLUR, dict(BLUR, axis="x")]),                   # two blur sets
+    dict(grid={"n": (16, 16)}, sets=[BLUR], opts=dict(levels=2)),
 ])
 def test_invalid_arguments_rejected_on_host(sip, bad):
     grid = bad.get("grid", {"n": (8, 8)})
