@@ -345,6 +345,7 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
       d.bl_st = s.blur_axis == 0 ? 1 : s.blur_axis == 1 ? g.n[0] : g.n[0] * g.n[1];
       d.bl_off = boff;
       boff += ((int64_t)tb.size() + 3) / 4 * 4;
+      d.k0_ring = 0;  // s^{k0} = F x^{k0} is kept (k0s), not re-blurred from the ring
     }
     if (b < nsets && (sets[b].lo_vec || sets[b].hi_vec)) {
       const sip_set &s = sets[b];
@@ -454,6 +455,36 @@ static void push_tiles(std::vector<Tile> &v, int inst, int item, int64_t n, int6
   }
 }
 
+// Grid-point work items of an instance with a blur block: blocks of
+// kBlurTZ z rows x kBlurTA samples along an x or y blur axis (item = kBlurTZ),
+// or for a blur along z runs of one z column of at most kBlurLen samples
+// (item = 1); start = the block's first grid point, len = item x samples.
+static void push_blur_blocks(std::vector<Tile> &v, int inst, const InstDev &d) {
+  int seq = 0;
+  auto push = [&](int64_t g0, int tz, int ta) {
+    Tile t;
+    t.inst = inst;
+    t.item = tz;
+    t.start = g0;
+    t.len = tz * ta;
+    t.seq = seq++;
+    v.push_back(t);
+  };
+  const int64_t nz = d.nz, nx = d.nx, ny = d.ny;
+  if (d.bl_axis == 0) {
+    const int64_t runs = (nz + kBlurLen - 1) / kBlurLen;
+    const int ta = (int)((nz + runs - 1) / runs);
+    for (int64_t col = 0; col < nx * ny; ++col)
+      for (int64_t a0 = 0; a0 < nz; a0 += ta) push(a0 + nz * col, 1, ta);
+    return;
+  }
+  const int64_t na = d.bl_axis == 1 ? nx : ny, no = d.bl_axis == 1 ? ny : nx;
+  for (int64_t o = 0; o < no; ++o)
+    for (int64_t a0 = 0; a0 < na; a0 += kBlurTA)
+      for (int64_t z0 = 0; z0 < nz; z0 += kBlurTZ)
+        push(z0 + nz * (d.bl_axis == 1 ? a0 + nx * o : o + nx * a0), kBlurTZ, kBlurTA);
+}
+
 // Rows per work item for a launch that covers `total` rows: `slots` CTAs
 // (SMs x resident CTAs per SM, so the launch runs in one wave), a multiple
 // of the CTA width, at most kMaxChunk.
@@ -519,8 +550,10 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   // segment; the largest work item that lets 2 (else 1) CTAs share an SM.
   int64_t ch_rhs = 0;
   P.rhs_smem = 0;
-  bool stageable = dtype == SIP_F32 && !insts.empty();
-  for (auto &L : insts) stageable = stageable && L.dev.ny == 1 && L.dev.N < (int64_t(1) << 31) && !L.dev.bl_R;
+  bool any_blur = false;
+  for (auto &L : insts) any_blur = any_blur || L.dev.bl_R != 0;
+  bool stageable = dtype == SIP_F32 && !insts.empty() && !any_blur;
+  for (auto &L : insts) stageable = stageable && L.dev.ny == 1 && L.dev.N < (int64_t(1) << 31);
   for (int occ = 2; stageable && occ >= 1 && !P.rhs_smem; --occ) {
     const int64_t ch = chunk_for(tot_n, sms * occ);
     size_t need = 0;
@@ -564,12 +597,18 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       ntie += (j.M + ch_fin - 1) / ch_fin;
     }
     const size_t b0 = tn.size();
-    push_tiles(tn, i, 0, d.N, ch_n);
+    if (d.bl_R)
+      push_blur_blocks(tn, i, d);
+    else
+      push_tiles(tn, i, 0, d.N, ch_n);
     d.nt_n = (int32_t)(tn.size() - b0);
     d.nt_rhs = 0;
-    if (P.rhs_smem) {
+    if (P.rhs_smem || any_blur) {
+      // staged right-hand side items; in a plan with a blur block, the
+      // right-hand side walks contiguous items (its blur part comes from
+      // the block items' launch before it)
       const size_t br = trhs.size();
-      push_tiles(trhs, i, 0, d.N, ch_rhs);
+      push_tiles(trhs, i, 0, d.N, P.rhs_smem ? ch_rhs : ch_n);
       d.nt_rhs = (int32_t)(trhs.size() - br);
     }
     d.nt_part = d.nt_n > d.nt_rhs ? d.nt_n : d.nt_rhs;
@@ -624,7 +663,8 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     return o;
   };
   struct Offs {
-    int64_t x, y, v, cr[2], cw[2], cs[2], cp, cgp, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace, bvec;
+    int64_t x, y, v, cr[2], cw[2], cs[2], cp, cgp, ring, w, s, k0s, k0vh, k0y, k0v, m, sched_r, sched_g, trace, bvec,
+        bls;
   };
   std::vector<Offs> offs(P.ninst);
   // warm state (x, y, v) of all instances first, then the rest of the state,
@@ -668,6 +708,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     offs[i].sched_g = L.opts.gamma_schedule ? take((int64_t)L.opts.max_iter * L.dev.nb * 8) : -1;
     offs[i].trace = L.opts.trace ? take((int64_t)L.opts.max_iter * (2 * L.dev.nb + 2 + L.dev.p) * 8) : -1;
     offs[i].bvec = L.Mb ? take(L.Mb * W) : -1;
+    offs[i].bls = L.dev.bl_R ? take(L.dev.N * W) : -1;
   }
   const int64_t o_ctrl = take(8 * sizeof(uint32_t));  // grid barrier words + finished count
   const int64_t o_insts = take((int64_t)P.ninst * sizeof(InstDev));
@@ -732,6 +773,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     d.trace = (double *)at(o.trace);
     d.bvec = at(o.bvec);
     d.bl_w = d.bl_R ? (const char *)d.bvec + d.bl_off * W : nullptr;
+    d.bl_s = at(o.bls);
     d.trace_w = 2 * d.nb + 2 + d.p;
     P.h_insts[i] = d;
     P.layouts[i] = insts[i];
@@ -739,7 +781,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   // single instance: the CG launches take their work items and descriptor
   // fields as parameters (items of ch_n points from 0, as pushed above)
   memset(&P.cg_one, 0, sizeof P.cg_one);
-  if (P.ninst == 1) {
+  if (P.ninst == 1 && !P.blur) {  // a blur instance's items are blocks
     P.cg_one.d = cg_desc(P.h_insts[0]);
     P.cg_one.chunk = ch_n;
     P.cg_one.on = 1;
@@ -842,7 +884,7 @@ int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, 
 // Launches of one iteration.
 static int launches_per_iter(const Plan &P) {
   return 3 + P.cg_launch + (P.nt_sel ? select_passes(P.dtype) : 0) + (P.any_card ? 1 : 0) + (P.nt_line ? 1 : 0) +
-         (P.nt_fin ? 1 : 0) + 1;
+         (P.nt_fin ? 1 : 0) + 1 + (P.blur ? 2 : 0);
 }
 
 // marks: every launch stamps its own slot pair of P.d_ts (timing graph)
@@ -856,10 +898,15 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   };
   auto T1 = [&](int) {};
   T0(KT_RHS);
-  if (P.rhs_smem)
+  if (P.rhs_smem) {
     CK(launch_rhs_tma(L, P.d_trhs, P.nt_rhs, P.d_insts, P.d_scal, P.rhs_smem, P.one));
-  else
+  } else if (P.blur) {
+    CK(launch_blur_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
+    T0(KT_RHS);
+    CK(launch_rhs(L, P.d_trhs, P.nt_rhs, P.d_insts, P.d_scal, P.one));
+  } else {
     CK(launch_rhs(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, P.one));
+  }
   T1(KT_RHS);
   T0(KT_CG_W0);
   CK(launch_cg_w0(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, P.cg_one));  // w_0 = C r_0
@@ -868,6 +915,11 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
     T0(KT_CG_STEP);
     CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j, P.cg_one));  // one CG step
     T1(KT_CG_STEP);
+  }
+  if (P.blur) {  // s = F x of the blur blocks, read by the set pass
+    T0(KT_SETPASS);
+    CK(launch_blur_fwd(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal));
+    T1(KT_SETPASS);
   }
   T0(KT_SETPASS);
   CK(launch_setpass(L, P.d_tset, P.nt_set, P.d_insts, P.d_scal, P.d_jscal, P.d_jobs, P.one));

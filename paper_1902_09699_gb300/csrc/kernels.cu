@@ -350,32 +350,6 @@ __device__ __forceinline__ T blur_normal(const D &in, int64_t g, V v) {
   }
   return s;
 }
-// rho_F F^T F v at g for the x-step's system matrix (Eq. sys_mat), for the
-// two forms of v the launches need: a stored vector (x in the right-hand
-// side residual, r_0 in w_0 = C r_0) and r_{i+1} = r_i - alpha (w_i +
-// beta s_{i-1}) in a CG step.  Only the kernels instantiated for plans
-// with a blur block contain them.
-template <typename T, typename D>
-__device__ __forceinline__ T blur_c1(const D &in, const InstScal &sc, int64_t g, const T *__restrict__ v) {
-  return SV<T>::blk(sc, in.bl_blk, BF_RHO) * blur_normal<T>(in, g, [&](int64_t q) { return v[q]; });
-}
-// (F^T (rho_F y_F + v_F))[g], the blur block's term of the x-step's
-// right-hand side
-template <typename T>
-__device__ __forceinline__ T blur_rhs(const InstDev &in, const InstScal &sc, int64_t g) {
-  const int64_t yo = in.blk[in.bl_blk].yoff;
-  const T *__restrict__ y = (const T *)in.y + yo;
-  const T *__restrict__ v = (const T *)in.v + yo;
-  const T rho = SV<T>::blk(sc, in.bl_blk, BF_RHO);
-  return blur_fwd<T>(in, g, [&](int64_t q) { return rho * y[q] + v[q]; });
-}
-template <typename T, typename D>
-__device__ __forceinline__ T blur_c3(const D &in, const InstScal &sc, int64_t g, const T *__restrict__ r,
-                                  const T *__restrict__ w, const T *__restrict__ sp, T alpha, T beta) {
-  return SV<T>::blk(sc, in.bl_blk, BF_RHO) *
-         blur_normal<T>(in, g, [&](int64_t q) { return r[q] - alpha * (w[q] + beta * sp[q]); });
-}
-
 // s = A x for one row of a segment (used by the single-step entry points and
 // the norm kernel; the loop kernels inline the same arithmetic).
 template <typename T>
@@ -663,11 +637,12 @@ __device__ __forceinline__ void body_rhs_t(const Tile &tl, const InstDev &in, In
       }
     }
     if constexpr (BL) {
+      // the blur block's F^T (rho y + v) - rho F^T F x (blur right-hand side launch)
       if (in.bl_R) {
-        // the blur block: F^T (rho y + v) and rho_F F^T F x at each point
+        const T *__restrict__ t = (const T *)in.bl_s;
 #pragma unroll
         for (int e = 0; e < PT; ++e)
-          if (g[e] < end) b[e] += blur_rhs<T>(in, sc, g[e]) - blur_c1<T>(in, sc, g[e], x);
+          if (g[e] < end) b[e] += t[g[e]];
       }
     }
 #pragma unroll
@@ -694,6 +669,12 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
   else
     body_rhs_t<T, int64_t, BL>(tl, in, sc);
 }
+
+// the blur block items' bodies (defined with the CG launches below)
+template <typename T>
+__device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc);
+template <typename T>
+__device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &sc, int ph);
 
 template <typename T, bool ONE, bool BL = false>
 __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
@@ -953,13 +934,13 @@ __device__ __forceinline__ void body_cg_w0_v4(const Tile &tl, const D &in, const
   if (threadIdx.x == 0) cg_part<float>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0
 }
 
-template <typename T, bool BL = false, typename D>
+template <typename T, typename D>
 __device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstScal &sc) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
   const int done = sc.done;
   if constexpr (sizeof(T) == 4) {
-    if ((in.nz & 3) == 0 && in.ny == 1 && !in.bl_R && (((uintptr_t)in.cr[0] | (uintptr_t)in.cw[0]) & 15) == 0) {
+    if ((in.nz & 3) == 0 && in.ny == 1 && (((uintptr_t)in.cr[0] | (uintptr_t)in.cw[0]) & 15) == 0) {
       body_cg_w0_v4(tl, in, sc, done);
       return;
     }
@@ -982,10 +963,7 @@ __device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstS
     for (int e = 0; e < PT; ++e) {
       const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
       if (g < end) {
-        T wg = apply_c(C, rn[e]);
-        if constexpr (BL) {
-          if (in.bl_R) wg += blur_c1<T>(in, sc, g, r);
-        }
+        const T wg = apply_c(C, rn[e]);
         w[g] = wg;
         a0 += (A)wg * (A)rn[e].c;
       }
@@ -995,10 +973,10 @@ __device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstS
   block_sum<1>(acc);
   if (threadIdx.x == 0) cg_part<A>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0 = p_0^T C p_0
 }
-template <typename T, bool BL = false>
+template <typename T>
 __device__ __forceinline__ void body_cg_w0(const Tile &tl, const InstDev *__restrict__ insts,
                                            InstScal *__restrict__ scal) {
-  body_cg_w0_in<T, BL>(tl, insts[tl.inst], scal[tl.inst]);
+  body_cg_w0_in<T>(tl, insts[tl.inst], scal[tl.inst]);
 }
 
 // Single-instance plans: the grid-point work item of CTA b (items of `chunk`
@@ -1021,10 +999,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_cg_w0(const Tile *__restrict__ 
                                                        InstScal *__restrict__ scal, unsigned long long *ts,
                                                        const __grid_constant__ CgOne one) {
   const Stamp stamp(ts);
+  if constexpr (BL) {
+    if (!one.on && tiles[blockIdx.x].item > 0) {
+      const Tile tl = tiles[blockIdx.x];
+      body_cg_w0_blur<T>(tl, insts[tl.inst], scal[tl.inst]);
+      return;
+    }
+  }
   if (one.on)
-    body_cg_w0_in<T, BL>(one_tile(one), one.d, scal[0]);
+    body_cg_w0_in<T>(one_tile(one), one.d, scal[0]);
   else
-    body_cg_w0<T, BL>(tiles[blockIdx.x], insts, scal);
+    body_cg_w0<T>(tiles[blockIdx.x], insts, scal);
 }
 
 // CG state fields in the storage precision (binary32 kernels do their
@@ -1229,7 +1214,7 @@ __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const D &in, Ins
   }
 }
 
-template <typename T, bool BL = false, typename D>
+template <typename T, typename D>
 __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, InstScal &sc, int ph) {
   using A = typename AccOf<T>::type;
   constexpr int PT = sizeof(T) == 4 ? 2 : 1;  // 3 stencils per row: keep the register budget
@@ -1239,7 +1224,7 @@ __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, Ins
     // batched plan is packed and may not be)
     const uintptr_t al = (uintptr_t)in.x | (uintptr_t)in.cp | (uintptr_t)in.cr[0] | (uintptr_t)in.cr[1] |
                          (uintptr_t)in.cw[0] | (uintptr_t)in.cw[1] | (uintptr_t)in.cs[0] | (uintptr_t)in.cs[1];
-    if ((in.nz & 3) == 0 && in.ny == 1 && !in.bl_R && (al & 15) == 0) {
+    if ((in.nz & 3) == 0 && in.ny == 1 && (al & 15) == 0) {
       body_cg_step_v4(tl, in, sc, ph);
       return;
     }
@@ -1304,10 +1289,7 @@ __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, Ins
         x[g] = xv[e] + alpha * pi;
         sn_[g] = s_c;
         rn_[g] = rnew.c;
-        T wnew = apply_c(C, rnew);
-        if constexpr (BL) {
-          if (in.bl_R) wnew += blur_c3<T>(in, sc, g, r, w, sp, alpha, beta);
-        }
+        const T wnew = apply_c(C, rnew);
         wn_[g] = wnew;
         ag += (A)rnew.c * (A)rnew.c;
         ad += (A)wnew * (A)rnew.c;
@@ -1323,16 +1305,16 @@ __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, Ins
   }
 }
 
-template <typename T, bool BL = false>
+template <typename T>
 __device__ __forceinline__ void body_cg_step(const Tile &tl, const InstDev *__restrict__ insts,
                                              InstScal *__restrict__ scal, int ph) {
-  body_cg_step_in<T, BL>(tl, insts[tl.inst], scal[tl.inst], ph);
+  body_cg_step_in<T>(tl, insts[tl.inst], scal[tl.inst], ph);
 }
 
 // out of line: the single-instance path keeps the register allocation
-template <typename T, bool BL>
+template <typename T>
 __device__ __noinline__ void cg_step_call(const Tile &tl, const InstDev *insts, InstScal *scal, int ph) {
-  body_cg_step<T, BL>(tl, insts, scal, ph);
+  body_cg_step<T>(tl, insts, scal, ph);
 }
 
 template <typename T, bool BL = false>
@@ -1341,10 +1323,317 @@ __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict_
                                                          InstScal *__restrict__ scal, int ph, unsigned long long *ts,
                                                          const __grid_constant__ CgOne one) {
   const Stamp stamp(ts);
+  if constexpr (BL) {
+    if (!one.on && tiles[blockIdx.x].item > 0) {
+      const Tile tl = tiles[blockIdx.x];
+      body_cg_step_blur<T>(tl, insts[tl.inst], scal[tl.inst], ph);
+      return;
+    }
+  }
   if (one.on)
-    body_cg_step_in<T, BL>(one_tile(one), one.d, scal[0], ph);
+    body_cg_step_in<T>(one_tile(one), one.d, scal[0], ph);
   else
-    cg_step_call<T, BL>(tiles[blockIdx.x], insts, scal, ph);
+    cg_step_call<T>(tiles[blockIdx.x], insts, scal, ph);
+}
+
+// --------------------------------------------------------------------------
+// Instances with a blur block: block work items staged in shared memory.
+// The point j of a block item (tz = item rows along z, ta samples along the
+// blur axis) is g = start + (j % tz) + (j / tz) st.  The CTA first stages
+// the block's values plus a halo of H samples (R for F, 2R for F^T F)
+// along the axis and, for an x or y blur, one z row on either side, zero
+// outside the grid: every tap of F or F^T F and the z and blur-axis
+// neighbours of the 7-point stencil read shared memory.
+// --------------------------------------------------------------------------
+struct BlurBlk {
+  int64_t g0, st;
+  int tz, ta, z0, a0, nz, na, R;
+  int P, zo;  // row pitch of the staged buffer (tz + 2, or 1 for a z blur) and its z offset
+};
+template <typename D>
+__device__ __forceinline__ BlurBlk blur_blk(const D &in, const Tile &tl) {
+  BlurBlk b;
+  b.g0 = tl.start;
+  b.st = in.bl_st;
+  b.tz = tl.item;
+  b.ta = tl.len / tl.item;
+  b.z0 = (int)((uint32_t)tl.start - (uint32_t)in.nz * fdiv((uint32_t)tl.start, in.fz));
+  b.a0 = blur_pos(in, tl.start);
+  b.nz = in.nz;
+  b.na = in.bl_n;
+  b.R = in.bl_R;
+  b.P = b.tz == 1 ? 1 : b.tz + 2;
+  b.zo = b.tz == 1 ? 0 : 1;
+  return b;
+}
+// local point j -> (z row, sample along the axis, grid point); false for
+// the slots of a ragged block that fall outside the grid
+__device__ __forceinline__ bool blur_pt(const BlurBlk &b, int j, int &zz, int &aa, int64_t &g) {
+  zz = b.tz == 1 ? 0 : (j & (kBlurTZ - 1));
+  aa = b.tz == 1 ? j : j / kBlurTZ;
+  g = b.g0 + zz + (int64_t)aa * b.st;
+  return j < b.tz * b.ta && b.a0 + aa < b.na && (b.tz == 1 || b.z0 + zz < b.nz);
+}
+// buf[(zz + zo) + (c + H) P] = f(g of z row zz, offset c along the axis)
+// for zz in [-zo, tz + zo), c in [-H, ta + H); 0 outside the grid
+template <typename T, typename F>
+__device__ __forceinline__ void blur_stage(const BlurBlk &b, int H, T *buf, F f) {
+  const int cnt = b.P * (b.ta + 2 * H);
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+    const int c = idx / b.P - H;
+    const int zz = idx - (c + H) * b.P - b.zo;
+    const int pa = b.a0 + c, pz = b.z0 + zz;
+    const bool ok = pa >= 0 && pa < b.na && (b.tz == 1 || (pz >= 0 && pz < b.nz));
+    buf[idx] = ok ? f(b.g0 + zz + (int64_t)c * b.st) : T(0);
+  }
+}
+// the staged value at (zz, aa) for a buffer with halo H
+template <typename T>
+__device__ __forceinline__ const T *blur_at(const BlurBlk &b, const T *buf, int H, int zz, int aa) {
+  return buf + (zz + b.zo) + (aa + H) * b.P;
+}
+// taps k_0..k_R and autocorrelation a_0..a_2R of the blur table
+template <typename T, typename D>
+__device__ __forceinline__ void blur_coef(const D &in, T *cf) {
+  const T *__restrict__ tab = (const T *)in.bl_w;
+  for (int t = threadIdx.x; t < 3 * in.bl_R + 2; t += blockDim.x) cf[t] = tab[t];
+}
+// (F v) at the staged point p (halo >= R)
+template <typename T>
+__device__ __forceinline__ T blur_fwd_buf(const BlurBlk &b, const T *p, const T *k) {
+  const int P = b.P;
+  T s = k[0] * p[0];
+  for (int t = 1; t <= b.R; ++t) s += k[t] * (p[-t * P] + p[t * P]);
+  return s;
+}
+// (F^T F v) at the staged point p of sample aa (halo 2R): the
+// autocorrelation band less the end corrections (as in blur_normal)
+template <typename T>
+__device__ __forceinline__ T blur_normal_buf(const BlurBlk &b, const T *p, const T *a, const T *__restrict__ E,
+                                             int aa) {
+  const int P = b.P, R = b.R, n = b.na, i = b.a0 + aa;
+  T s = a[0] * p[0];
+  for (int d = 1; d <= 2 * R; ++d) s += a[d] * (p[-d * P] + p[d * P]);
+  const int L = R < n ? R : n;
+  if (i < R)
+    for (int l = 0; l < L; ++l) s -= E[i * R + l] * p[(l - i) * P];
+  if (i >= n - R) {
+    const int ii = n - 1 - i;
+    for (int l = 0; l < L; ++l) s -= E[ii * R + l] * p[(n - 1 - l - i) * P];
+  }
+  return s;
+}
+// 7-point stencil values at g (Nbr convention: a missing neighbour repeats
+// the centre): the z and blur-axis neighbours from the staged point p, the
+// third axis from v(i)
+template <typename T, typename V>
+__device__ __forceinline__ void blur_nbr(const InstDev &in, const BlurBlk &b, const GridPos &ps, int64_t g, const T *p,
+                                         T cv, V v, Nbr<T> &o) {
+  const int64_t sxy = (int64_t)in.nz * in.nx;
+  const int P = b.P;
+  o.c = cv;
+  o.zm = ps.iz > 0 ? p[-1] : cv;
+  o.zp = ps.iz < in.nz - 1 ? p[1] : cv;
+  if (b.tz == 1 || in.bl_axis == 2) {
+    o.xm = ps.ix > 0 ? v(g - in.nz) : cv;
+    o.xp = ps.ix < in.nx - 1 ? v(g + in.nz) : cv;
+  } else {
+    o.xm = ps.ix > 0 ? p[-P] : cv;
+    o.xp = ps.ix < in.nx - 1 ? p[P] : cv;
+  }
+  if (b.tz == 1 || in.bl_axis == 1) {
+    o.ym = ps.iy > 0 ? v(g - sxy) : cv;
+    o.yp = ps.iy < in.ny - 1 ? v(g + sxy) : cv;
+  } else {
+    o.ym = ps.iy > 0 ? p[-P] : cv;
+    o.yp = ps.iy < in.ny - 1 ? p[P] : cv;
+  }
+}
+constexpr int kBlurCoef = 3 * SIP_MAX_BLUR_RADIUS + 2;
+
+// The blur block's part of the x-step's right-hand side and warm residual,
+// t = F^T (rho_F y_F + v_F) - rho_F F^T F x, into the instance's F x
+// scratch (free between the set pass and the next right-hand side); the
+// right-hand side launch adds it at every grid point.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_blur_rhs(const Tile *__restrict__ tiles,
+                                                      const InstDev *__restrict__ insts,
+                                                      const InstScal *__restrict__ scal, unsigned long long *ts) {
+  const Stamp stamp(ts);
+  __shared__ T buf[kBlurBuf];
+  __shared__ T cf[kBlurCoef];
+  const Tile tl = tiles[blockIdx.x];
+  if (tl.item <= 0) return;
+  const InstDev &in = insts[tl.inst];
+  const InstScal &sc = scal[tl.inst];
+  if (sc.done) return;
+  constexpr int NE = kBlurLen / kThreads;
+  const BlurBlk b = blur_blk(in, tl);
+  const T *__restrict__ x = (const T *)in.x;
+  T *__restrict__ t = (T *)in.bl_s;
+  const int64_t yo = in.blk[in.bl_blk].yoff;
+  const T *__restrict__ yF = (const T *)in.y + yo;
+  const T *__restrict__ vF = (const T *)in.v + yo;
+  const T rhoF = SV<T>::blk(sc, in.bl_blk, BF_RHO);
+  blur_coef<T>(in, cf);
+  blur_stage<T>(b, b.R, buf, [&](int64_t q) { return rhoF * yF[q] + vF[q]; });
+  __syncthreads();
+  T tv[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    int zz, aa;
+    int64_t g;
+    tv[e] = blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g) ? blur_fwd_buf(b, blur_at(b, buf, b.R, zz, aa), cf)
+                                                               : T(0);
+  }
+  __syncthreads();
+  blur_stage<T>(b, 2 * b.R, buf, [&](int64_t q) { return x[q]; });
+  __syncthreads();
+  const T *__restrict__ E = (const T *)in.bl_w + 3 * b.R + 2;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    int zz, aa;
+    int64_t g;
+    if (blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g))
+      t[g] = tv[e] - rhoF * blur_normal_buf(b, blur_at(b, buf, 2 * b.R, zz, aa), cf + b.R + 1, E, aa);
+  }
+}
+
+// w_0 = C r_0 of a blur block item
+template <typename T>
+__device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc) {
+  using A = typename AccOf<T>::type;
+  __shared__ T buf[kBlurBuf];
+  __shared__ T cf[kBlurCoef];
+  if (sc.done) return;
+  const BlurBlk b = blur_blk(in, tl);
+  const int H = 2 * b.R;
+  const T *__restrict__ r = (const T *)in.cr[0];
+  T *__restrict__ w = (T *)in.cw[0];
+  blur_coef<T>(in, cf);
+  blur_stage<T>(b, H, buf, [&](int64_t q) { return r[q]; });
+  __syncthreads();
+  CSys<T> C;
+  C.load(sc);
+  const T rhoF = SV<T>::blk(sc, in.bl_blk, BF_RHO);
+  const T *__restrict__ E = (const T *)in.bl_w + 3 * b.R + 2;
+  A a0 = A(0);
+  for (int j = threadIdx.x; j < tl.len; j += kThreads) {
+    int zz, aa;
+    int64_t g;
+    if (!blur_pt(b, j, zz, aa, g)) continue;
+    const T *pc = blur_at(b, buf, H, zz, aa);
+    Nbr<T> rn;
+    blur_nbr<T>(in, b, grid_pos(in, g), g, pc, pc[0], [&](int64_t i) { return r[i]; }, rn);
+    const T wg = apply_c(C, rn) + rhoF * blur_normal_buf(b, pc, cf + b.R + 1, E, aa);
+    w[g] = wg;
+    a0 += (A)wg * (A)rn.c;
+  }
+  A acc[1] = {a0};
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) cg_part<A>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0
+}
+
+// One CG step of a blur block item: the general step's arithmetic, with
+// r_{i+1} = r_i - alpha (w_i + beta s_{i-1}) staged over the block and its
+// halo for the F^T F band and the stencil neighbours
+template <typename T>
+__device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &sc, int ph) {
+  using A = typename AccOf<T>::type;
+  __shared__ T buf[kBlurBuf];
+  __shared__ T cf[kBlurCoef];
+  __shared__ T s_ab[2];
+  __shared__ int s_go;
+  const int c = ph & 1, n = c ^ 1;
+  const T *__restrict__ r = (const T *)in.cr[c];
+  const T *__restrict__ w = (const T *)in.cw[c];
+  const T *__restrict__ sp = (const T *)in.cs[c];  // s_{i-1}
+  T *__restrict__ rn_ = (T *)in.cr[n];
+  T *__restrict__ wn_ = (T *)in.cw[n];
+  T *__restrict__ sn_ = (T *)in.cs[n];             // s_i
+  T *__restrict__ p = (T *)in.cp;
+  T *__restrict__ x = (T *)in.x;
+  // the item's p and x, in flight while the scalars and the stage arrive
+  constexpr int NE = kBlurLen / kThreads;
+  const BlurBlk b = blur_blk(in, tl);
+  T pv[NE], xv[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    int zz, aa;
+    int64_t g;
+    pv[e] = xv[e] = T(0);
+    if (blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g)) {
+      pv[e] = p[g];
+      xv[e] = x[g];
+    }
+  }
+  cg_scalars<T>(tl, in, sc, ph, s_ab, &s_go);
+  if (!s_go) return;
+  const T alpha = s_ab[0], beta = s_ab[1];
+  const int H = 2 * b.R;
+  auto rnew_at = [&](int64_t q) { return r[q] - alpha * (w[q] + beta * sp[q]); };
+  blur_coef<T>(in, cf);
+  blur_stage<T>(b, H, buf, rnew_at);
+  __syncthreads();
+  CSys<T> C;
+  C.load(sc);
+  const T rhoF = SV<T>::blk(sc, in.bl_blk, BF_RHO);
+  const T *__restrict__ E = (const T *)in.bl_w + 3 * b.R + 2;
+  A ag = A(0), ad = A(0);
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    int zz, aa;
+    int64_t g;
+    if (!blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g)) continue;
+    const T rv = r[g], wv = w[g], sv = sp[g];
+    const T *pc = blur_at(b, buf, H, zz, aa);
+    const T s_c = wv + beta * sv;
+    const T rc = rv - alpha * s_c;
+    Nbr<T> rnew;
+    blur_nbr<T>(in, b, grid_pos(in, g), g, pc, rc, rnew_at, rnew);
+    const T pi = rv + beta * pv[e];
+    p[g] = pi;
+    x[g] = xv[e] + alpha * pi;
+    sn_[g] = s_c;
+    rn_[g] = rc;
+    const T wnew = apply_c(C, rnew) + rhoF * blur_normal_buf(b, pc, cf + b.R + 1, E, aa);
+    wn_[g] = wnew;
+    ag += (A)rc * (A)rc;
+    ad += (A)wnew * (A)rc;
+  }
+  A acc[2] = {ag, ad};
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    const int slot = 1 + (ph & 1);
+    cg_part<A>(in, slot, 0)[tl.seq] = acc[0];
+    cg_part<A>(in, slot, 1)[tl.seq] = acc[1];
+  }
+}
+
+// s = F x of every blur block item, for the set pass
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_blur_fwd(const Tile *__restrict__ tiles,
+                                                      const InstDev *__restrict__ insts,
+                                                      const InstScal *__restrict__ scal, unsigned long long *ts) {
+  const Stamp stamp(ts);
+  __shared__ T buf[kBlurBuf];
+  __shared__ T cf[kBlurCoef];
+  const Tile tl = tiles[blockIdx.x];
+  if (tl.item <= 0) return;
+  const InstDev &in = insts[tl.inst];
+  if (scal[tl.inst].done) return;
+  const BlurBlk b = blur_blk(in, tl);
+  const T *__restrict__ x = (const T *)in.x;
+  T *__restrict__ sF = (T *)in.bl_s;
+  blur_coef<T>(in, cf);
+  blur_stage<T>(b, b.R, buf, [&](int64_t q) { return x[q]; });
+  __syncthreads();
+  for (int j = threadIdx.x; j < tl.len; j += kThreads) {
+    int zz, aa;
+    int64_t g;
+    if (blur_pt(b, j, zz, aa, g)) sF[g] = blur_fwd_buf(b, blur_at(b, buf, b.R, zz, aa), cf);
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -1613,10 +1902,9 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
       kv0 = kind == SEG_I ? z0 : (xk0[g + off] - z0) * q.ih;
     }
     if constexpr (BL) {
-      if (kind == SEG_BLUR) {
-        sv = blur_fwd<T>(in, g, [&](int64_t i) { return x[i]; });
-        if (xk0) kv0 = blur_fwd<T>(in, g, [&](int64_t i) { return xk0[i]; });
-      }
+      // s = F x, written by the blur kernel before the set pass (blur
+      // instances keep s^{k0} in k0s: no x-history gathers)
+      if (kind == SEG_BLUR) sv = ((const T *)in.bl_s)[g];
     }
   };
   bool vec = false;
@@ -3699,6 +3987,14 @@ cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstD
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
                            const CgOne &one) {
   SIP_DISPATCH_BL(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
+  return cudaGetLastError();
+}
+cudaError_t launch_blur_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, const InstScal *scal) {
+  SIP_DISPATCH(L, k_blur_rhs, nt, kThreads, 0, tiles, insts, scal, L.ts);
+  return cudaGetLastError();
+}
+cudaError_t launch_blur_fwd(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, const InstScal *scal) {
+  SIP_DISPATCH(L, k_blur_fwd, nt, kThreads, 0, tiles, insts, scal, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,

@@ -29,6 +29,17 @@ constexpr int kMaxHist = 8;          // s of Eq. obj_stop, upper limit
 constexpr int kThreads = 256;        // threads per CTA for the streaming kernels
 constexpr int kPerThread = 4;
 constexpr int kTile = kThreads * kPerThread;
+// Grid-point work items of an instance with a blur block: blocks of kBlurTZ
+// z rows times kBlurTA samples along the blur axis (x or y), or for a blur
+// along z runs of at most kBlurLen samples of one z column; staged in
+// shared memory with the kernel's halo of up to 2 SIP_MAX_BLUR_RADIUS
+// samples along the axis.
+constexpr int kBlurTZ = 32;
+constexpr int kBlurTA = 32;
+constexpr int kBlurLen = 1024;
+constexpr int kBlurBuf = (kBlurTZ + 2) * (kBlurTA + 4 * SIP_MAX_BLUR_RADIUS);  // rows z0-1 .. z0+kBlurTZ
+static_assert(kBlurTZ * kBlurTA <= kBlurLen && kBlurLen + 4 * SIP_MAX_BLUR_RADIUS <= kBlurBuf,
+              "a staged block fits the buffer");
 constexpr int64_t kMaxChunk = 64 * kTile;  // rows of one work item, at most
 constexpr int kDigitBits = 11;       // radix digit of the selection passes
 constexpr int kBins = 1 << kDigitBits;
@@ -201,6 +212,7 @@ struct InstDev {
   int32_t bl_R, bl_axis, bl_n, bl_blk;
   int64_t bl_st, bl_off;
   const void *bl_w;
+  void *bl_s;  // s = F x of the current iteration (N entries), read by the set pass
   // device arrays, element type = the plan's dtype
   const void *m;
   void *x, *ring, *y, *v, *w, *s, *k0s, *k0vh, *k0y, *k0v;
