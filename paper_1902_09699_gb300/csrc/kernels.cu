@@ -1348,7 +1348,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict_
 struct BlurBlk {
   int64_t g0, st;
   int tz, ta, z0, a0, nz, na, R;
-  int P, zo;  // row pitch of the staged buffer (tz + 2, or 1 for a z blur) and its z offset
 };
 template <typename D>
 __device__ __forceinline__ BlurBlk blur_blk(const D &in, const Tile &tl) {
@@ -1362,36 +1361,43 @@ __device__ __forceinline__ BlurBlk blur_blk(const D &in, const Tile &tl) {
   b.nz = in.nz;
   b.na = in.bl_n;
   b.R = in.bl_R;
-  b.P = b.tz == 1 ? 1 : b.tz + 2;
-  b.zo = b.tz == 1 ? 0 : 1;
   return b;
 }
+// Row pitch of a staged buffer, a compile-time constant of the hot loops
+// (the kernels pick the instantiation from the item's z rows): 1 for a z
+// blur, else kBlurTZ + 2 (the block's z rows and one halo row either side).
+template <int PP> struct BlurPitch {
+  static constexpr int P = PP, zo = PP == 1 ? 0 : 1, tz = PP == 1 ? 1 : kBlurTZ;
+};
 // local point j -> (z row, sample along the axis, grid point); false for
 // the slots of a ragged block that fall outside the grid
+template <int PP>
 __device__ __forceinline__ bool blur_pt(const BlurBlk &b, int j, int &zz, int &aa, int64_t &g) {
-  zz = b.tz == 1 ? 0 : (j & (kBlurTZ - 1));
-  aa = b.tz == 1 ? j : j / kBlurTZ;
+  constexpr int tz = BlurPitch<PP>::tz;
+  zz = tz == 1 ? 0 : (j & (kBlurTZ - 1));
+  aa = tz == 1 ? j : j / kBlurTZ;
   g = b.g0 + zz + (int64_t)aa * b.st;
-  return j < b.tz * b.ta && b.a0 + aa < b.na && (b.tz == 1 || b.z0 + zz < b.nz);
+  return j < tz * b.ta && b.a0 + aa < b.na && (tz == 1 || b.z0 + zz < b.nz);
 }
 // buf[(zz + zo) + (c + H) P] = f(g of z row zz, offset c along the axis)
 // for zz in [-zo, tz + zo), c in [-H, ta + H); 0 outside the grid
-template <typename T, typename F>
+template <int PP, typename T, typename F>
 __device__ __forceinline__ void blur_stage(const BlurBlk &b, int H, T *buf, F f) {
-  const int cnt = b.P * (b.ta + 2 * H);
+  using BP = BlurPitch<PP>;
+  const int cnt = BP::P * (b.ta + 2 * H);
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-    const int c = idx / b.P - H;
-    const int zz = idx - (c + H) * b.P - b.zo;
+    const int c = idx / BP::P - H;
+    const int zz = idx - (c + H) * BP::P - BP::zo;
     const int pa = b.a0 + c, pz = b.z0 + zz;
-    const bool ok = pa >= 0 && pa < b.na && (b.tz == 1 || (pz >= 0 && pz < b.nz));
+    const bool ok = pa >= 0 && pa < b.na && (BP::tz == 1 || (pz >= 0 && pz < b.nz));
     buf[idx] = ok ? f(b.g0 + zz + (int64_t)c * b.st) : T(0);
   }
 }
 // the staged value at (zz, aa) for a buffer with halo H
-template <typename T>
-__device__ __forceinline__ const T *blur_at(const BlurBlk &b, const T *buf, int H, int zz, int aa) {
-  return buf + (zz + b.zo) + (aa + H) * b.P;
+template <int PP, typename T>
+__device__ __forceinline__ const T *blur_at(const T *buf, int H, int zz, int aa) {
+  return buf + (zz + BlurPitch<PP>::zo) + (aa + H) * BlurPitch<PP>::P;
 }
 // taps k_0..k_R and autocorrelation a_0..a_2R of the blur table
 template <typename T, typename D>
@@ -1400,20 +1406,23 @@ __device__ __forceinline__ void blur_coef(const D &in, T *cf) {
   for (int t = threadIdx.x; t < 3 * in.bl_R + 2; t += blockDim.x) cf[t] = tab[t];
 }
 // (F v) at the staged point p (halo >= R)
-template <typename T>
+template <int PP, typename T>
 __device__ __forceinline__ T blur_fwd_buf(const BlurBlk &b, const T *p, const T *k) {
-  const int P = b.P;
+  constexpr int P = BlurPitch<PP>::P;
   T s = k[0] * p[0];
+#pragma unroll 4
   for (int t = 1; t <= b.R; ++t) s += k[t] * (p[-t * P] + p[t * P]);
   return s;
 }
 // (F^T F v) at the staged point p of sample aa (halo 2R): the
 // autocorrelation band less the end corrections (as in blur_normal)
-template <typename T>
+template <int PP, typename T>
 __device__ __forceinline__ T blur_normal_buf(const BlurBlk &b, const T *p, const T *a, const T *__restrict__ E,
                                              int aa) {
-  const int P = b.P, R = b.R, n = b.na, i = b.a0 + aa;
+  constexpr int P = BlurPitch<PP>::P;
+  const int R = b.R, n = b.na, i = b.a0 + aa;
   T s = a[0] * p[0];
+#pragma unroll 4
   for (int d = 1; d <= 2 * R; ++d) s += a[d] * (p[-d * P] + p[d * P]);
   const int L = R < n ? R : n;
   if (i < R)
@@ -1427,22 +1436,22 @@ __device__ __forceinline__ T blur_normal_buf(const BlurBlk &b, const T *p, const
 // 7-point stencil values at g (Nbr convention: a missing neighbour repeats
 // the centre): the z and blur-axis neighbours from the staged point p, the
 // third axis from v(i)
-template <typename T, typename V>
-__device__ __forceinline__ void blur_nbr(const InstDev &in, const BlurBlk &b, const GridPos &ps, int64_t g, const T *p,
-                                         T cv, V v, Nbr<T> &o) {
+template <int PP, typename T, typename V>
+__device__ __forceinline__ void blur_nbr(const InstDev &in, const GridPos &ps, int64_t g, const T *p, T cv, V v,
+                                         Nbr<T> &o) {
   const int64_t sxy = (int64_t)in.nz * in.nx;
-  const int P = b.P;
+  constexpr int P = BlurPitch<PP>::P;
   o.c = cv;
   o.zm = ps.iz > 0 ? p[-1] : cv;
   o.zp = ps.iz < in.nz - 1 ? p[1] : cv;
-  if (b.tz == 1 || in.bl_axis == 2) {
+  if (PP == 1 || in.bl_axis == 2) {
     o.xm = ps.ix > 0 ? v(g - in.nz) : cv;
     o.xp = ps.ix < in.nx - 1 ? v(g + in.nz) : cv;
   } else {
     o.xm = ps.ix > 0 ? p[-P] : cv;
     o.xp = ps.ix < in.nx - 1 ? p[P] : cv;
   }
-  if (b.tz == 1 || in.bl_axis == 1) {
+  if (PP == 1 || in.bl_axis == 1) {
     o.ym = ps.iy > 0 ? v(g - sxy) : cv;
     o.yp = ps.iy < in.ny - 1 ? v(g + sxy) : cv;
   } else {
@@ -1456,6 +1465,39 @@ constexpr int kBlurCoef = 3 * SIP_MAX_BLUR_RADIUS + 2;
 // t = F^T (rho_F y_F + v_F) - rho_F F^T F x, into the instance's F x
 // scratch (free between the set pass and the next right-hand side); the
 // right-hand side launch adds it at every grid point.
+template <typename T, int PP>
+__device__ __forceinline__ void blur_rhs_p(const Tile &tl, const InstDev &in, const InstScal &sc, T *buf, T *cf) {
+  constexpr int NE = kBlurLen / kThreads;
+  const BlurBlk b = blur_blk(in, tl);
+  const T *__restrict__ x = (const T *)in.x;
+  T *__restrict__ t = (T *)in.bl_s;
+  const int64_t yo = in.blk[in.bl_blk].yoff;
+  const T *__restrict__ yF = (const T *)in.y + yo;
+  const T *__restrict__ vF = (const T *)in.v + yo;
+  const T rhoF = SV<T>::blk(sc, in.bl_blk, BF_RHO);
+  blur_coef<T>(in, cf);
+  blur_stage<PP>(b, b.R, buf, [&](int64_t q) { return rhoF * yF[q] + vF[q]; });
+  __syncthreads();
+  T tv[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    int zz, aa;
+    int64_t g;
+    tv[e] = blur_pt<PP>(b, threadIdx.x + e * kThreads, zz, aa, g) ? blur_fwd_buf<PP>(b, blur_at<PP>(buf, b.R, zz, aa), cf)
+                                                               : T(0);
+  }
+  __syncthreads();
+  blur_stage<PP>(b, 2 * b.R, buf, [&](int64_t q) { return x[q]; });
+  __syncthreads();
+  const T *__restrict__ E = (const T *)in.bl_w + 3 * b.R + 2;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    int zz, aa;
+    int64_t g;
+    if (blur_pt<PP>(b, threadIdx.x + e * kThreads, zz, aa, g))
+      t[g] = tv[e] - rhoF * blur_normal_buf<PP>(b, blur_at<PP>(buf, 2 * b.R, zz, aa), cf + b.R + 1, E, aa);
+  }
+}
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_blur_rhs(const Tile *__restrict__ tiles,
                                                       const InstDev *__restrict__ insts,
@@ -1468,51 +1510,22 @@ __global__ void __launch_bounds__(kThreads) k_blur_rhs(const Tile *__restrict__ 
   const InstDev &in = insts[tl.inst];
   const InstScal &sc = scal[tl.inst];
   if (sc.done) return;
-  constexpr int NE = kBlurLen / kThreads;
-  const BlurBlk b = blur_blk(in, tl);
-  const T *__restrict__ x = (const T *)in.x;
-  T *__restrict__ t = (T *)in.bl_s;
-  const int64_t yo = in.blk[in.bl_blk].yoff;
-  const T *__restrict__ yF = (const T *)in.y + yo;
-  const T *__restrict__ vF = (const T *)in.v + yo;
-  const T rhoF = SV<T>::blk(sc, in.bl_blk, BF_RHO);
-  blur_coef<T>(in, cf);
-  blur_stage<T>(b, b.R, buf, [&](int64_t q) { return rhoF * yF[q] + vF[q]; });
-  __syncthreads();
-  T tv[NE];
-#pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    int zz, aa;
-    int64_t g;
-    tv[e] = blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g) ? blur_fwd_buf(b, blur_at(b, buf, b.R, zz, aa), cf)
-                                                               : T(0);
-  }
-  __syncthreads();
-  blur_stage<T>(b, 2 * b.R, buf, [&](int64_t q) { return x[q]; });
-  __syncthreads();
-  const T *__restrict__ E = (const T *)in.bl_w + 3 * b.R + 2;
-#pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    int zz, aa;
-    int64_t g;
-    if (blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g))
-      t[g] = tv[e] - rhoF * blur_normal_buf(b, blur_at(b, buf, 2 * b.R, zz, aa), cf + b.R + 1, E, aa);
-  }
+  if (tl.item == 1)
+    blur_rhs_p<T, 1>(tl, in, sc, buf, cf);
+  else
+    blur_rhs_p<T, kBlurTZ + 2>(tl, in, sc, buf, cf);
 }
 
 // w_0 = C r_0 of a blur block item
-template <typename T>
-__device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc) {
+template <typename T, int PP>
+__device__ __forceinline__ void cg_w0_blur_p(const Tile &tl, const InstDev &in, InstScal &sc, T *buf, T *cf) {
   using A = typename AccOf<T>::type;
-  __shared__ T buf[kBlurBuf];
-  __shared__ T cf[kBlurCoef];
-  if (sc.done) return;
   const BlurBlk b = blur_blk(in, tl);
   const int H = 2 * b.R;
   const T *__restrict__ r = (const T *)in.cr[0];
   T *__restrict__ w = (T *)in.cw[0];
   blur_coef<T>(in, cf);
-  blur_stage<T>(b, H, buf, [&](int64_t q) { return r[q]; });
+  blur_stage<PP>(b, H, buf, [&](int64_t q) { return r[q]; });
   __syncthreads();
   CSys<T> C;
   C.load(sc);
@@ -1522,11 +1535,11 @@ __device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc)
   for (int j = threadIdx.x; j < tl.len; j += kThreads) {
     int zz, aa;
     int64_t g;
-    if (!blur_pt(b, j, zz, aa, g)) continue;
-    const T *pc = blur_at(b, buf, H, zz, aa);
+    if (!blur_pt<PP>(b, j, zz, aa, g)) continue;
+    const T *pc = blur_at<PP>(buf, H, zz, aa);
     Nbr<T> rn;
-    blur_nbr<T>(in, b, grid_pos(in, g), g, pc, pc[0], [&](int64_t i) { return r[i]; }, rn);
-    const T wg = apply_c(C, rn) + rhoF * blur_normal_buf(b, pc, cf + b.R + 1, E, aa);
+    blur_nbr<PP>(in, grid_pos(in, g), g, pc, pc[0], [&](int64_t i) { return r[i]; }, rn);
+    const T wg = apply_c(C, rn) + rhoF * blur_normal_buf<PP>(b, pc, cf + b.R + 1, E, aa);
     w[g] = wg;
     a0 += (A)wg * (A)rn.c;
   }
@@ -1534,17 +1547,24 @@ __device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc)
   block_sum<1>(acc);
   if (threadIdx.x == 0) cg_part<A>(in, 2, 0)[tl.seq] = acc[0];  // delta_0 = r_0^T C r_0
 }
+template <typename T>
+__device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc) {
+  __shared__ T buf[kBlurBuf];
+  __shared__ T cf[kBlurCoef];
+  if (sc.done) return;
+  if (tl.item == 1)
+    cg_w0_blur_p<T, 1>(tl, in, sc, buf, cf);
+  else
+    cg_w0_blur_p<T, kBlurTZ + 2>(tl, in, sc, buf, cf);
+}
 
 // One CG step of a blur block item: the general step's arithmetic, with
 // r_{i+1} = r_i - alpha (w_i + beta s_{i-1}) staged over the block and its
 // halo for the F^T F band and the stencil neighbours
-template <typename T>
-__device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &sc, int ph) {
+template <typename T, int PP>
+__device__ __forceinline__ void cg_step_blur_p(const Tile &tl, const InstDev &in, InstScal &sc, int ph, T *buf,
+                                               T *cf, T *s_ab, int *s_go) {
   using A = typename AccOf<T>::type;
-  __shared__ T buf[kBlurBuf];
-  __shared__ T cf[kBlurCoef];
-  __shared__ T s_ab[2];
-  __shared__ int s_go;
   const int c = ph & 1, n = c ^ 1;
   const T *__restrict__ r = (const T *)in.cr[c];
   const T *__restrict__ w = (const T *)in.cw[c];
@@ -1563,18 +1583,18 @@ __device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &s
     int zz, aa;
     int64_t g;
     pv[e] = xv[e] = T(0);
-    if (blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g)) {
+    if (blur_pt<PP>(b, threadIdx.x + e * kThreads, zz, aa, g)) {
       pv[e] = p[g];
       xv[e] = x[g];
     }
   }
-  cg_scalars<T>(tl, in, sc, ph, s_ab, &s_go);
-  if (!s_go) return;
+  cg_scalars<T>(tl, in, sc, ph, s_ab, s_go);
+  if (!*s_go) return;
   const T alpha = s_ab[0], beta = s_ab[1];
   const int H = 2 * b.R;
   auto rnew_at = [&](int64_t q) { return r[q] - alpha * (w[q] + beta * sp[q]); };
   blur_coef<T>(in, cf);
-  blur_stage<T>(b, H, buf, rnew_at);
+  blur_stage<PP>(b, H, buf, rnew_at);
   __syncthreads();
   CSys<T> C;
   C.load(sc);
@@ -1585,19 +1605,19 @@ __device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &s
   for (int e = 0; e < NE; ++e) {
     int zz, aa;
     int64_t g;
-    if (!blur_pt(b, threadIdx.x + e * kThreads, zz, aa, g)) continue;
+    if (!blur_pt<PP>(b, threadIdx.x + e * kThreads, zz, aa, g)) continue;
     const T rv = r[g], wv = w[g], sv = sp[g];
-    const T *pc = blur_at(b, buf, H, zz, aa);
+    const T *pc = blur_at<PP>(buf, H, zz, aa);
     const T s_c = wv + beta * sv;
     const T rc = rv - alpha * s_c;
     Nbr<T> rnew;
-    blur_nbr<T>(in, b, grid_pos(in, g), g, pc, rc, rnew_at, rnew);
+    blur_nbr<PP>(in, grid_pos(in, g), g, pc, rc, rnew_at, rnew);
     const T pi = rv + beta * pv[e];
     p[g] = pi;
     x[g] = xv[e] + alpha * pi;
     sn_[g] = s_c;
     rn_[g] = rc;
-    const T wnew = apply_c(C, rnew) + rhoF * blur_normal_buf(b, pc, cf + b.R + 1, E, aa);
+    const T wnew = apply_c(C, rnew) + rhoF * blur_normal_buf<PP>(b, pc, cf + b.R + 1, E, aa);
     wn_[g] = wnew;
     ag += (A)rc * (A)rc;
     ad += (A)wnew * (A)rc;
@@ -1610,8 +1630,33 @@ __device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &s
     cg_part<A>(in, slot, 1)[tl.seq] = acc[1];
   }
 }
+template <typename T>
+__device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &sc, int ph) {
+  __shared__ T buf[kBlurBuf];
+  __shared__ T cf[kBlurCoef];
+  __shared__ T s_ab[2];
+  __shared__ int s_go;
+  if (tl.item == 1)
+    cg_step_blur_p<T, 1>(tl, in, sc, ph, buf, cf, s_ab, &s_go);
+  else
+    cg_step_blur_p<T, kBlurTZ + 2>(tl, in, sc, ph, buf, cf, s_ab, &s_go);
+}
 
 // s = F x of every blur block item, for the set pass
+template <typename T, int PP>
+__device__ __forceinline__ void blur_fwd_p(const Tile &tl, const InstDev &in, T *buf, T *cf) {
+  const BlurBlk b = blur_blk(in, tl);
+  const T *__restrict__ x = (const T *)in.x;
+  T *__restrict__ sF = (T *)in.bl_s;
+  blur_coef<T>(in, cf);
+  blur_stage<PP>(b, b.R, buf, [&](int64_t q) { return x[q]; });
+  __syncthreads();
+  for (int j = threadIdx.x; j < tl.len; j += kThreads) {
+    int zz, aa;
+    int64_t g;
+    if (blur_pt<PP>(b, j, zz, aa, g)) sF[g] = blur_fwd_buf<PP>(b, blur_at<PP>(buf, b.R, zz, aa), cf);
+  }
+}
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_blur_fwd(const Tile *__restrict__ tiles,
                                                       const InstDev *__restrict__ insts,
@@ -1623,17 +1668,10 @@ __global__ void __launch_bounds__(kThreads) k_blur_fwd(const Tile *__restrict__ 
   if (tl.item <= 0) return;
   const InstDev &in = insts[tl.inst];
   if (scal[tl.inst].done) return;
-  const BlurBlk b = blur_blk(in, tl);
-  const T *__restrict__ x = (const T *)in.x;
-  T *__restrict__ sF = (T *)in.bl_s;
-  blur_coef<T>(in, cf);
-  blur_stage<T>(b, b.R, buf, [&](int64_t q) { return x[q]; });
-  __syncthreads();
-  for (int j = threadIdx.x; j < tl.len; j += kThreads) {
-    int zz, aa;
-    int64_t g;
-    if (blur_pt(b, j, zz, aa, g)) sF[g] = blur_fwd_buf(b, blur_at(b, buf, b.R, zz, aa), cf);
-  }
+  if (tl.item == 1)
+    blur_fwd_p<T, 1>(tl, in, buf, cf);
+  else
+    blur_fwd_p<T, kBlurTZ + 2>(tl, in, buf, cf);
 }
 
 // --------------------------------------------------------------------------
@@ -2156,7 +2194,7 @@ __device__ __forceinline__ void body_setpass(const Tile &tl, const InstDev *__re
 }
 
 template <typename T, bool ONE, bool BL = false>
-__global__ void __launch_bounds__(kThreads, 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_setpass(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
                                                       InstScal *__restrict__ scal, JobScal *__restrict__ jscal,
                                                       const JobDev *__restrict__ jobs, unsigned long long *ts,
                                                       const __grid_constant__ InstOne one) {
