@@ -339,6 +339,8 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
           tb.push_back(e);
         }
       d.bl_R = R;
+      d.bl_box = 1;
+      for (int t = 1; t <= R; ++t) d.bl_box = d.bl_box && s.blur_taps[t] == s.blur_taps[0];
       d.bl_axis = s.blur_axis;
       d.bl_n = (int32_t)g.n[s.blur_axis];
       d.bl_blk = b;

@@ -1461,13 +1461,63 @@ __device__ __forceinline__ void blur_nbr(const InstDev &in, const GridPos &ps, i
 }
 constexpr int kBlurCoef = 3 * SIP_MAX_BLUR_RADIUS + 2;
 
+// Box kernels (every tap k_0: the paper's motion blur) on x or y blocks:
+// F v is k_0 times a window sum, which a thread slides over kBoxRun
+// positions along the axis (one add and one subtract per step) instead of
+// summing 2R + 1 taps per point.  F^T F v = F (M F v) with M zeroing the
+// positions outside the grid (F's rows are the grid's samples), so the
+// ends need no correction table.
+constexpr int kBoxRun = 8;
+constexpr int kBoxU = kBlurTZ * (kBlurTA + 2 * SIP_MAX_BLUR_RADIUS);
+constexpr int kBoxO = kBlurTZ * kBlurTA;
+// dst(zz, c) = k sum_{|t| <= R} src(zz, c + t) for c in [lo, hi) and every
+// z row of the block, src(zz, c) = src[sz + zz + c sp], dst(zz, c) =
+// dst[zz + (c - lo) kBlurTZ]; with mask, 0 where c is outside the grid
+template <typename T>
+__device__ __forceinline__ void box_pass(const BlurBlk &b, const T *src, int sp, int sz, T *dst, int lo, int hi, T k,
+                                         bool mask) {
+  const int R = b.R, nrun = (hi - lo + kBoxRun - 1) / kBoxRun;
+  for (int w = threadIdx.x; w < kBlurTZ * nrun; w += blockDim.x) {
+    const int zz = w & (kBlurTZ - 1), c0 = lo + (w / kBlurTZ) * kBoxRun;
+    const int c1 = c0 + kBoxRun < hi ? c0 + kBoxRun : hi;
+    const T *sr = src + sz + zz;
+    T acc = T(0);
+    for (int t = -R; t <= R; ++t) acc += sr[(c0 + t) * sp];
+    for (int c = c0; c < c1; ++c) {
+      if (c > c0) acc += sr[(c + R) * sp] - sr[(c - R - 1) * sp];
+      const int pa = b.a0 + c;
+      dst[zz + (c - lo) * kBlurTZ] = (!mask || (pa >= 0 && pa < b.na)) ? k * acc : T(0);
+    }
+  }
+}
+// F^T F v at the block's points into ob(zz, aa) = ob[zz + aa kBlurTZ],
+// from v staged with halo 2R (pitch kBlurTZ + 2); ub holds M F v
+template <typename T>
+__device__ __forceinline__ void box_normal(const BlurBlk &b, const T *buf, T *ub, T *ob, T k) {
+  constexpr int P = kBlurTZ + 2;
+  const int R = b.R;
+  box_pass(b, buf, P, 1 + 2 * R * P, ub, -R, b.ta + R, k, true);
+  __syncthreads();
+  box_pass(b, ub, kBlurTZ, R * kBlurTZ, ob, 0, b.ta, k, false);
+  __syncthreads();
+}
+// F v at the block's points into ob, from v staged with halo R
+template <typename T>
+__device__ __forceinline__ void box_fwd(const BlurBlk &b, const T *buf, T *ob, T k) {
+  constexpr int P = kBlurTZ + 2;
+  box_pass(b, buf, P, 1 + b.R * P, ob, 0, b.ta, k, false);
+  __syncthreads();
+}
+
 // The blur block's part of the x-step's right-hand side and warm residual,
 // t = F^T (rho_F y_F + v_F) - rho_F F^T F x, into the instance's F x
 // scratch (free between the set pass and the next right-hand side); the
 // right-hand side launch adds it at every grid point.
 template <typename T, int PP>
-__device__ __forceinline__ void blur_rhs_p(const Tile &tl, const InstDev &in, const InstScal &sc, T *buf, T *cf) {
+__device__ __forceinline__ void blur_rhs_p(const Tile &tl, const InstDev &in, const InstScal &sc, T *buf, T *cf,
+                                           T *ub, T *ob) {
   constexpr int NE = kBlurLen / kThreads;
+  const bool box = PP != 1 && in.bl_box;
   const BlurBlk b = blur_blk(in, tl);
   const T *__restrict__ x = (const T *)in.x;
   T *__restrict__ t = (T *)in.bl_s;
@@ -1478,24 +1528,32 @@ __device__ __forceinline__ void blur_rhs_p(const Tile &tl, const InstDev &in, co
   blur_coef<T>(in, cf);
   blur_stage<PP>(b, b.R, buf, [&](int64_t q) { return rhoF * yF[q] + vF[q]; });
   __syncthreads();
+  if constexpr (PP != 1) {
+    if (box) box_fwd(b, buf, ob, cf[0]);
+  }
   T tv[NE];
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
     int zz, aa;
     int64_t g;
-    tv[e] = blur_pt<PP>(b, threadIdx.x + e * kThreads, zz, aa, g) ? blur_fwd_buf<PP>(b, blur_at<PP>(buf, b.R, zz, aa), cf)
-                                                               : T(0);
+    tv[e] = T(0);
+    if (blur_pt<PP>(b, threadIdx.x + e * kThreads, zz, aa, g))
+      tv[e] = box ? ob[zz + aa * kBlurTZ] : blur_fwd_buf<PP>(b, blur_at<PP>(buf, b.R, zz, aa), cf);
   }
   __syncthreads();
   blur_stage<PP>(b, 2 * b.R, buf, [&](int64_t q) { return x[q]; });
   __syncthreads();
+  if constexpr (PP != 1) {
+    if (box) box_normal(b, buf, ub, ob, cf[0]);
+  }
   const T *__restrict__ E = (const T *)in.bl_w + 3 * b.R + 2;
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
     int zz, aa;
     int64_t g;
     if (blur_pt<PP>(b, threadIdx.x + e * kThreads, zz, aa, g))
-      t[g] = tv[e] - rhoF * blur_normal_buf<PP>(b, blur_at<PP>(buf, 2 * b.R, zz, aa), cf + b.R + 1, E, aa);
+      t[g] = tv[e] - rhoF * (box ? ob[zz + aa * kBlurTZ]
+                                 : blur_normal_buf<PP>(b, blur_at<PP>(buf, 2 * b.R, zz, aa), cf + b.R + 1, E, aa));
   }
 }
 template <typename T>
@@ -1505,21 +1563,25 @@ __global__ void __launch_bounds__(kThreads) k_blur_rhs(const Tile *__restrict__ 
   const Stamp stamp(ts);
   __shared__ T buf[kBlurBuf];
   __shared__ T cf[kBlurCoef];
+  __shared__ T ub[kBoxU];
+  __shared__ T ob[kBoxO];
   const Tile tl = tiles[blockIdx.x];
   if (tl.item <= 0) return;
   const InstDev &in = insts[tl.inst];
   const InstScal &sc = scal[tl.inst];
   if (sc.done) return;
   if (tl.item == 1)
-    blur_rhs_p<T, 1>(tl, in, sc, buf, cf);
+    blur_rhs_p<T, 1>(tl, in, sc, buf, cf, ub, ob);
   else
-    blur_rhs_p<T, kBlurTZ + 2>(tl, in, sc, buf, cf);
+    blur_rhs_p<T, kBlurTZ + 2>(tl, in, sc, buf, cf, ub, ob);
 }
 
 // w_0 = C r_0 of a blur block item
 template <typename T, int PP>
-__device__ __forceinline__ void cg_w0_blur_p(const Tile &tl, const InstDev &in, InstScal &sc, T *buf, T *cf) {
+__device__ __forceinline__ void cg_w0_blur_p(const Tile &tl, const InstDev &in, InstScal &sc, T *buf, T *cf, T *ub,
+                                             T *ob) {
   using A = typename AccOf<T>::type;
+  const bool box = PP != 1 && in.bl_box;
   const BlurBlk b = blur_blk(in, tl);
   const int H = 2 * b.R;
   const T *__restrict__ r = (const T *)in.cr[0];
@@ -1527,6 +1589,9 @@ __device__ __forceinline__ void cg_w0_blur_p(const Tile &tl, const InstDev &in, 
   blur_coef<T>(in, cf);
   blur_stage<PP>(b, H, buf, [&](int64_t q) { return r[q]; });
   __syncthreads();
+  if constexpr (PP != 1) {
+    if (box) box_normal(b, buf, ub, ob, cf[0]);
+  }
   CSys<T> C;
   C.load(sc);
   const T rhoF = SV<T>::blk(sc, in.bl_blk, BF_RHO);
@@ -1539,7 +1604,8 @@ __device__ __forceinline__ void cg_w0_blur_p(const Tile &tl, const InstDev &in, 
     const T *pc = blur_at<PP>(buf, H, zz, aa);
     Nbr<T> rn;
     blur_nbr<PP>(in, grid_pos(in, g), g, pc, pc[0], [&](int64_t i) { return r[i]; }, rn);
-    const T wg = apply_c(C, rn) + rhoF * blur_normal_buf<PP>(b, pc, cf + b.R + 1, E, aa);
+    const T band = box ? ob[zz + aa * kBlurTZ] : blur_normal_buf<PP>(b, pc, cf + b.R + 1, E, aa);
+    const T wg = apply_c(C, rn) + rhoF * band;
     w[g] = wg;
     a0 += (A)wg * (A)rn.c;
   }
@@ -1551,11 +1617,13 @@ template <typename T>
 __device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc) {
   __shared__ T buf[kBlurBuf];
   __shared__ T cf[kBlurCoef];
+  __shared__ T ub[kBoxU];
+  __shared__ T ob[kBoxO];
   if (sc.done) return;
   if (tl.item == 1)
-    cg_w0_blur_p<T, 1>(tl, in, sc, buf, cf);
+    cg_w0_blur_p<T, 1>(tl, in, sc, buf, cf, ub, ob);
   else
-    cg_w0_blur_p<T, kBlurTZ + 2>(tl, in, sc, buf, cf);
+    cg_w0_blur_p<T, kBlurTZ + 2>(tl, in, sc, buf, cf, ub, ob);
 }
 
 // One CG step of a blur block item: the general step's arithmetic, with
@@ -1563,8 +1631,9 @@ __device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc)
 // halo for the F^T F band and the stencil neighbours
 template <typename T, int PP>
 __device__ __forceinline__ void cg_step_blur_p(const Tile &tl, const InstDev &in, InstScal &sc, int ph, T *buf,
-                                               T *cf, T *s_ab, int *s_go) {
+                                               T *cf, T *ub, T *ob, T *s_ab, int *s_go) {
   using A = typename AccOf<T>::type;
+  const bool box = PP != 1 && in.bl_box;
   const int c = ph & 1, n = c ^ 1;
   const T *__restrict__ r = (const T *)in.cr[c];
   const T *__restrict__ w = (const T *)in.cw[c];
@@ -1596,6 +1665,9 @@ __device__ __forceinline__ void cg_step_blur_p(const Tile &tl, const InstDev &in
   blur_coef<T>(in, cf);
   blur_stage<PP>(b, H, buf, rnew_at);
   __syncthreads();
+  if constexpr (PP != 1) {
+    if (box) box_normal(b, buf, ub, ob, cf[0]);
+  }
   CSys<T> C;
   C.load(sc);
   const T rhoF = SV<T>::blk(sc, in.bl_blk, BF_RHO);
@@ -1617,7 +1689,8 @@ __device__ __forceinline__ void cg_step_blur_p(const Tile &tl, const InstDev &in
     x[g] = xv[e] + alpha * pi;
     sn_[g] = s_c;
     rn_[g] = rc;
-    const T wnew = apply_c(C, rnew) + rhoF * blur_normal_buf<PP>(b, pc, cf + b.R + 1, E, aa);
+    const T band = box ? ob[zz + aa * kBlurTZ] : blur_normal_buf<PP>(b, pc, cf + b.R + 1, E, aa);
+    const T wnew = apply_c(C, rnew) + rhoF * band;
     wn_[g] = wnew;
     ag += (A)rc * (A)rc;
     ad += (A)wnew * (A)rc;
@@ -1634,27 +1707,34 @@ template <typename T>
 __device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &sc, int ph) {
   __shared__ T buf[kBlurBuf];
   __shared__ T cf[kBlurCoef];
+  __shared__ T ub[kBoxU];
+  __shared__ T ob[kBoxO];
   __shared__ T s_ab[2];
   __shared__ int s_go;
   if (tl.item == 1)
-    cg_step_blur_p<T, 1>(tl, in, sc, ph, buf, cf, s_ab, &s_go);
+    cg_step_blur_p<T, 1>(tl, in, sc, ph, buf, cf, ub, ob, s_ab, &s_go);
   else
-    cg_step_blur_p<T, kBlurTZ + 2>(tl, in, sc, ph, buf, cf, s_ab, &s_go);
+    cg_step_blur_p<T, kBlurTZ + 2>(tl, in, sc, ph, buf, cf, ub, ob, s_ab, &s_go);
 }
 
 // s = F x of every blur block item, for the set pass
 template <typename T, int PP>
-__device__ __forceinline__ void blur_fwd_p(const Tile &tl, const InstDev &in, T *buf, T *cf) {
+__device__ __forceinline__ void blur_fwd_p(const Tile &tl, const InstDev &in, T *buf, T *cf, T *ob) {
+  const bool box = PP != 1 && in.bl_box;
   const BlurBlk b = blur_blk(in, tl);
   const T *__restrict__ x = (const T *)in.x;
   T *__restrict__ sF = (T *)in.bl_s;
   blur_coef<T>(in, cf);
   blur_stage<PP>(b, b.R, buf, [&](int64_t q) { return x[q]; });
   __syncthreads();
+  if constexpr (PP != 1) {
+    if (box) box_fwd(b, buf, ob, cf[0]);
+  }
   for (int j = threadIdx.x; j < tl.len; j += kThreads) {
     int zz, aa;
     int64_t g;
-    if (blur_pt<PP>(b, j, zz, aa, g)) sF[g] = blur_fwd_buf<PP>(b, blur_at<PP>(buf, b.R, zz, aa), cf);
+    if (blur_pt<PP>(b, j, zz, aa, g))
+      sF[g] = box ? ob[zz + aa * kBlurTZ] : blur_fwd_buf<PP>(b, blur_at<PP>(buf, b.R, zz, aa), cf);
   }
 }
 template <typename T>
@@ -1664,14 +1744,15 @@ __global__ void __launch_bounds__(kThreads) k_blur_fwd(const Tile *__restrict__ 
   const Stamp stamp(ts);
   __shared__ T buf[kBlurBuf];
   __shared__ T cf[kBlurCoef];
+  __shared__ T ob[kBoxO];
   const Tile tl = tiles[blockIdx.x];
   if (tl.item <= 0) return;
   const InstDev &in = insts[tl.inst];
   if (scal[tl.inst].done) return;
   if (tl.item == 1)
-    blur_fwd_p<T, 1>(tl, in, buf, cf);
+    blur_fwd_p<T, 1>(tl, in, buf, cf, ob);
   else
-    blur_fwd_p<T, kBlurTZ + 2>(tl, in, buf, cf);
+    blur_fwd_p<T, kBlurTZ + 2>(tl, in, buf, cf, ob);
 }
 
 // --------------------------------------------------------------------------

@@ -210,6 +210,8 @@ struct InstDev {
   // a_0..a_2R of the kernel (F^T F away from the ends) and the R x R
   // correction E[i][l] = sum_{j<0} k_|i-j| k_|l-j| of the first R samples
   int32_t bl_R, bl_axis, bl_n, bl_blk;
+  int32_t bl_box;  // every tap equal (a box, e.g. a motion blur): window sums slide along the axis
+  int32_t bl_pad;
   int64_t bl_st, bl_off;
   const void *bl_w;
   void *bl_s;  // s = F x of the current iteration (N entries), read by the set pass

@@ -90,6 +90,29 @@ def test_blur_data_fit_fp64_matches_oracle(n, axis, R, seed):
         assert a == pytest.approx(b, rel=1e-8, abs=1e-13)
 
 
+BOX_CASES = [
+    ((64, 52), "x", 12, 41),     # a 25-sample motion blur
+    ((37, 70), "x", 5, 42),      # ragged blocks along z and x
+    ((24, 16, 40), "y", 3, 43),
+    ((40, 9), "x", 6, 44),       # n_x < 2R
+]
+
+
+@pytest.mark.parametrize("dt,bar", [("f64", 1e-10), ("f32", 1e-4)])
+@pytest.mark.parametrize("n,axis,R,seed", BOX_CASES)
+def test_box_blur_matches_oracle(n, axis, R, seed, dt, bar):
+    """Equal taps (a box, the paper's motion blur): the x and y blocks take
+    sliding window sums instead of the tap band."""
+    grid, m, sets = deblur_case(n, axis, R, seed)
+    sets[0]["taps"] = W.motion_blur_taps(2 * R + 1)
+    if dt == "f32":
+        m = as_f32(m)
+    opts = dict(max_iter=40, cg_iters=5, adapt=1 if dt == "f64" else 0, rho0=1.0, gamma0=1.5)
+    ref = P.parsdmm(m, grid, sets, P.options(**opts))
+    x, _ = run_gpu(m, grid, sets, dt, opts)
+    assert rel(x, ref["x"]) <= bar
+
+
 @pytest.mark.parametrize("n,axis,R,seed", CASES[:4])
 def test_blur_data_fit_fp32(n, axis, R, seed):
     grid, m, sets = deblur_case(n, axis, R, seed)
