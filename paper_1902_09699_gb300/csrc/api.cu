@@ -647,7 +647,11 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   // a blur block's terms live in their own instantiations of the
   // grid-point and set-pass kernels; the persistent kernel has none
   P.blur = false;
-  for (auto &L : insts) P.blur = P.blur || L.dev.bl_R != 0;
+  P.blur_all = !insts.empty();
+  for (auto &L : insts) {
+    P.blur = P.blur || L.dev.bl_R != 0;
+    P.blur_all = P.blur_all && L.dev.bl_R != 0;
+  }
   if (P.blur) P.exec = SIP_EXEC_GRAPH;
   P.nt_n = (int)tn.size();
   P.nt_rhs = (int)trhs.size();
@@ -886,7 +890,7 @@ int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, 
 // Launches of one iteration.
 static int launches_per_iter(const Plan &P) {
   return 3 + P.cg_launch + (P.nt_sel ? select_passes(P.dtype) : 0) + (P.any_card ? 1 : 0) + (P.nt_line ? 1 : 0) +
-         (P.nt_fin ? 1 : 0) + 1 + (P.blur ? 2 : 0);
+         (P.nt_fin ? 1 : 0) + 1 + (P.blur ? 2 : 0) + (P.blur && !P.blur_all ? P.cg_launch : 0);
 }
 
 // marks: every launch stamps its own slot pair of P.d_ts (timing graph)
@@ -915,7 +919,12 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   T1(KT_CG_W0);
   for (int j = 0; j < P.cg_launch; ++j) {
     T0(KT_CG_STEP);
-    CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j, P.cg_one));  // one CG step
+    if (!P.blur_all)
+      CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j, P.cg_one));  // one CG step
+    if (P.blur) {  // the blur instances' block items
+      if (!P.blur_all) T0(KT_CG_STEP);
+      CK(launch_cg_step_blur(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j));
+    }
     T1(KT_CG_STEP);
   }
   if (P.blur) {  // s = F x of the blur blocks, read by the set pass

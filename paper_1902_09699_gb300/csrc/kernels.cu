@@ -1324,11 +1324,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict_
                                                          const __grid_constant__ CgOne one) {
   const Stamp stamp(ts);
   if constexpr (BL) {
-    if (!one.on && tiles[blockIdx.x].item > 0) {
-      const Tile tl = tiles[blockIdx.x];
-      body_cg_step_blur<T>(tl, insts[tl.inst], scal[tl.inst], ph);
-      return;
-    }
+    if (!one.on && tiles[blockIdx.x].item > 0) return;  // k_cg_step_blur's items
   }
   if (one.on)
     body_cg_step_in<T>(one_tile(one), one.d, scal[0], ph);
@@ -1715,6 +1711,20 @@ __device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &s
     cg_step_blur_p<T, 1>(tl, in, sc, ph, buf, cf, ub, ob, s_ab, &s_go);
   else
     cg_step_blur_p<T, kBlurTZ + 2>(tl, in, sc, ph, buf, cf, ub, ob, s_ab, &s_go);
+}
+
+// The CG step of the blur block items, a kernel of its own so that its
+// register budget (and so its residency: the step is latency-bound) is not
+// the general step's
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 4) k_cg_step_blur(const Tile *__restrict__ tiles,
+                                                              const InstDev *__restrict__ insts,
+                                                              InstScal *__restrict__ scal, int ph,
+                                                              unsigned long long *ts) {
+  const Stamp stamp(ts);
+  const Tile tl = tiles[blockIdx.x];
+  if (tl.item <= 0) return;  // the general step's items
+  body_cg_step_blur<T>(tl, insts[tl.inst], scal[tl.inst], ph);
 }
 
 // s = F x of every blur block item, for the set pass
@@ -4114,6 +4124,11 @@ cudaError_t launch_blur_rhs(const Launch &L, const Tile *tiles, int nt, const In
 }
 cudaError_t launch_blur_fwd(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, const InstScal *scal) {
   SIP_DISPATCH(L, k_blur_fwd, nt, kThreads, 0, tiles, insts, scal, L.ts);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_step_blur(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                                int ph) {
+  SIP_DISPATCH(L, k_cg_step_blur, nt, kThreads, 0, tiles, insts, scal, ph, L.ts);
   return cudaGetLastError();
 }
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,

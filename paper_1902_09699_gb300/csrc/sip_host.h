@@ -71,7 +71,8 @@ struct Plan {
   int nt_rhs = 0;
   size_t rhs_smem = 0;
   bool any_card = false, any_fin = false, any_stop = false;
-  bool blur = false;  // an instance has a blur block (graph path, blur kernels)
+  bool blur = false;      // an instance has a blur block (graph path, blur kernels)
+  bool blur_all = false;  // every instance has one (no general CG step launches)
   CgOne cg_one;  // CG launch parameters of a single-instance plan (on = 0 otherwise)
   InstOne one;   // the descriptor as a launch parameter (single instance owning its model)
   int cg_launch = 0, max_iter = 0, check_every = 1;

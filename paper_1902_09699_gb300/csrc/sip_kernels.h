@@ -35,6 +35,8 @@ cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const Ins
                            const CgOne &one);
 // the blur block's right-hand side part F^T (rho y + v) - rho F^T F x, and
 // s = F x, at the blur instances' block work items (plans with a blur block)
+cudaError_t launch_cg_step_blur(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
+                                int ph);
 cudaError_t launch_blur_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, const InstScal *scal);
 cudaError_t launch_blur_fwd(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, const InstScal *scal);
 cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
