@@ -42,7 +42,7 @@ def _smooth(noise, corr_len):
         sh[ax] = k.size
         k = k.reshape(sh)
         g = k if g is None else g * k
-    return np.fft.irfftn(F * g, s=shape)
+    return np.fft.irfftn(F * g, s=shape, axes=tuple(range(len(shape))))
 
 
 def _to_range(a, lo, hi):
