@@ -33,6 +33,29 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def reduce_max(value, dist, device):
+    """The largest of every rank's value (the slowest rank sets the job's
+    time); the value itself on a single process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, its, steps, total_ms):
+    """Whole-job iterations per second: every rank ran `steps` projections
+    of `its` iterations within the slowest rank's `total_ms`."""
+    return world * its * steps / (total_ms / 1000.0)
+
+
+def replica_seed(rank, i):
+    """Seed of model i of a replica rank (rank 0's first model is the
+    workload's own): independent models on every rank."""
+    return 5000 + 7 * rank + i
+
+
 def captured_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or
     None when the kernel source changed since the capture."""
@@ -178,7 +201,7 @@ def run_ours(args):
     tdt = torch.float32 if args.dtype == "f32" else torch.float64
     # independent replicas: each rank projects its own models (seeded per rank)
     from paper_1902_09699_gb300 import workloads as W
-    models = [torch.as_tensor(c["m"] if (rank == 0 and i == 0) else W.layered((512, 1024), seed=5000 + 7 * rank + i),
+    models = [torch.as_tensor(c["m"] if (rank == 0 and i == 0) else W.layered((512, 1024), seed=replica_seed(rank, i)),
                               dtype=tdt, device=dev) for i in range(4)]
     x = torch.empty_like(models[0])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -204,13 +227,11 @@ def run_ours(args):
     clk = clocks.stop(local)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    total_ms = reduce_max(total_ms, dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * its * args.steps / (total_ms / 1000.0)
+    value = job_throughput(world, its, args.steps, total_ms)
 
     # ---- accuracy of this form against the FP64 GPU loop (projections/s at 1e-4)
     x32, _ = pr.project(models[0], None)
