@@ -324,32 +324,6 @@ __device__ __forceinline__ T blur_fwd(const D &in, int64_t g, V v) {
   }
   return s;
 }
-// (F^T F v)[g]: row i of F^T F is sum_{0 <= j < n} k_|i-j| k_|l-j| at
-// column l.  Summed over every j it is the kernel's autocorrelation
-// a_|i-l|; the rows j < 0 are missing only where i and l are both below R
-// (the correction E[i][l]), and the rows j >= n, by the mirror symmetry
-// j -> n-1-j, only where both are within R of the far end (E[n-1-i][n-1-l]).
-template <typename T, typename D, typename V>
-__device__ __forceinline__ T blur_normal(const D &in, int64_t g, V v) {
-  const int R = in.bl_R, n = in.bl_n, i = blur_pos(in, g);
-  const T *__restrict__ a = (const T *)in.bl_w + (R + 1);
-  const T *__restrict__ E = a + (2 * R + 1);
-  const int64_t st = in.bl_st;
-  T s = a[0] * v(g);
-  for (int d = 1; d <= 2 * R; ++d) {
-    const T lo = i - d >= 0 ? v(g - d * st) : T(0);
-    const T hi = i + d < n ? v(g + d * st) : T(0);
-    s += a[d] * (lo + hi);
-  }
-  const int L = R < n ? R : n;
-  if (i < R)
-    for (int l = 0; l < L; ++l) s -= E[i * R + l] * v(g + (int64_t)(l - i) * st);
-  if (i >= n - R) {
-    const int ii = n - 1 - i;
-    for (int l = 0; l < L; ++l) s -= E[ii * R + l] * v(g + (int64_t)(n - 1 - l - i) * st);
-  }
-  return s;
-}
 // s = A x for one row of a segment (used by the single-step entry points and
 // the norm kernel; the loop kernels inline the same arithmetic).
 template <typename T>
@@ -670,11 +644,9 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
     body_rhs_t<T, int64_t, BL>(tl, in, sc);
 }
 
-// the blur block items' bodies (defined with the CG launches below)
+// w_0 of the blur block items (defined with the CG launches below)
 template <typename T>
 __device__ void body_cg_w0_blur(const Tile &tl, const InstDev &in, InstScal &sc);
-template <typename T>
-__device__ void body_cg_step_blur(const Tile &tl, const InstDev &in, InstScal &sc, int ph);
 
 template <typename T, bool ONE, bool BL = false>
 __global__ void __launch_bounds__(kThreads, 3) k_rhs(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
@@ -1410,8 +1382,12 @@ __device__ __forceinline__ T blur_fwd_buf(const BlurBlk &b, const T *p, const T 
   for (int t = 1; t <= b.R; ++t) s += k[t] * (p[-t * P] + p[t * P]);
   return s;
 }
-// (F^T F v) at the staged point p of sample aa (halo 2R): the
-// autocorrelation band less the end corrections (as in blur_normal)
+// (F^T F v) at the staged point p of sample aa (halo 2R).  Row i of F^T F
+// is sum_{0 <= j < n} k_|i-j| k_|l-j| at column l.  Summed over every j it
+// is the kernel's autocorrelation a_|i-l|; the rows j < 0 are missing only
+// where i and l are both below R (the correction E[i][l]), and the rows
+// j >= n, by the mirror symmetry j -> n-1-j, only where both are within R
+// of the far end (E[n-1-i][n-1-l]).
 template <int PP, typename T>
 __device__ __forceinline__ T blur_normal_buf(const BlurBlk &b, const T *p, const T *a, const T *__restrict__ E,
                                              int aa) {
