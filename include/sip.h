@@ -243,6 +243,26 @@ sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev,
 
 sip_status sip_destroy(sip_handle *h);
 
+/* Warm start (the paper starts the iterates from a given state where one is
+ * available: ML-PARSDMM hands x, y_i, v_i from one level to the next, Sec.
+ * "Multilevel PARSDMM"; an inverse-problem loop projects nearby models
+ * one after another).  The state is x (N entries) and y, v (M' entries
+ * each: every block's rows in block order, the identity block p + 1 last
+ * in SIP_FORM_ALG1), device arrays of the handle's dtype, z fastest.
+ * sip_state_rows returns M' (-1 for a batched or multilevel handle).
+ * sip_get_state copies the handle's current state out (after a
+ * projection: its final iterates); NULL pointers are skipped.
+ * sip_set_state loads a state; the next sip_project (that one only) starts
+ * from it instead of zeros, with rho_i, gamma_i restarting from rho0,
+ * gamma0 as on a multilevel hand-over.  x_dev is required; NULL y_dev /
+ * v_dev load zeros.  Both are stream-ordered on `stream`; single-level,
+ * single-instance handles only (SIP_ERR_INVALID_ARG otherwise). */
+int64_t sip_state_rows(const sip_handle *h);
+sip_status sip_get_state(sip_handle *h, void *x_dev, void *y_dev, void *v_dev,
+                         void *stream);
+sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev,
+                         const void *v_dev, void *stream);
+
 const char *sip_last_error(const sip_handle *h);
 
 /* ---------------------------------------------------------------------

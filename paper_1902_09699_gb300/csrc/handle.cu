@@ -26,6 +26,7 @@ struct sip_handle {
   int32_t *pinned = nullptr;   // pinned flag for the stopping-rule poll
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timing = false;
+  bool warm_next = false;  // sip_set_state loaded x, y, v: the next projection starts from them
   KernelTimer timer;
   std::string err;
 };
@@ -273,7 +274,8 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
     if (o.gamma_schedule)
       CKH(cudaMemcpyAsync((void *)df.gamma_sched, o.gamma_schedule, (size_t)o.max_iter * nb * 8,
                           cudaMemcpyHostToDevice, st));
-    if ((s = plan_prepare(F, st, false))) return s;
+    if ((s = plan_prepare(F, st, h->warm_next))) return s;
+    h->warm_next = false;
   }
   sip_status s = run_iterations(F, st, h->cap, F.max_iter, o.stop != 0, h->pinned, tm);
   if (s) return s;
@@ -311,6 +313,50 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
     info->window_hits = sc.win_hits;
   }
   if (sc.stop_reason < 0) return fail(SIP_ERR_NONFINITE, "the model holds NaN or Inf");
+  return SIP_OK;
+}
+
+// Warm start: the handle's x, y and v (y and v: every block's rows, block
+// order, the identity block last in the paper's form).
+static sip_status state_check(const sip_handle *h) {
+  if (!h) return fail(SIP_ERR_INVALID_ARG, "handle is NULL");
+  if (h->batch) return fail(SIP_ERR_INVALID_ARG, "batched handle: no single state");
+  if (h->levels > 1) return fail(SIP_ERR_INVALID_ARG, "multilevel handle: each level has its own state");
+  return SIP_OK;
+}
+
+int64_t sip_state_rows(const sip_handle *h) {
+  if (state_check(h)) return -1;
+  return h->lev[0].layouts[0].Mtot;
+}
+
+sip_status sip_get_state(sip_handle *h, void *x_dev, void *y_dev, void *v_dev, void *stream) {
+  if (sip_status s = state_check(h)) return h ? keep(h, s) : s;
+  const InstDev &d = h->lev[0].h_insts[0];
+  const size_t W = esz(h->opts.dtype), M = (size_t)h->lev[0].layouts[0].Mtot;
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (x_dev) CKH(cudaMemcpyAsync(x_dev, d.x, (size_t)d.N * W, cudaMemcpyDeviceToDevice, st));
+  if (y_dev) CKH(cudaMemcpyAsync(y_dev, d.y, M * W, cudaMemcpyDeviceToDevice, st));
+  if (v_dev) CKH(cudaMemcpyAsync(v_dev, d.v, M * W, cudaMemcpyDeviceToDevice, st));
+  return SIP_OK;
+}
+
+sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev, const void *v_dev, void *stream) {
+  if (sip_status s = state_check(h)) return h ? keep(h, s) : s;
+  if (!x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "x_dev is NULL"));
+  const InstDev &d = h->lev[0].h_insts[0];
+  const size_t W = esz(h->opts.dtype), M = (size_t)h->lev[0].layouts[0].Mtot;
+  const cudaStream_t st = (cudaStream_t)stream;
+  CKH(cudaMemcpyAsync(d.x, x_dev, (size_t)d.N * W, cudaMemcpyDeviceToDevice, st));
+  if (y_dev)
+    CKH(cudaMemcpyAsync(d.y, y_dev, M * W, cudaMemcpyDeviceToDevice, st));
+  else
+    CKH(cudaMemsetAsync(d.y, 0, M * W, st));
+  if (v_dev)
+    CKH(cudaMemcpyAsync(d.v, v_dev, M * W, cudaMemcpyDeviceToDevice, st));
+  else
+    CKH(cudaMemsetAsync(d.v, 0, M * W, st));
+  h->warm_next = true;
   return SIP_OK;
 }
 

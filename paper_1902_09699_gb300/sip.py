@@ -79,6 +79,9 @@ SIGNATURES = {
                            ctypes.POINTER(c_vp)]),
     "sip_project": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Info)]),
     "sip_destroy": (c_int, [c_vp]),
+    "sip_state_rows": (c_i64, [c_vp]),
+    "sip_get_state": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "sip_set_state": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "sip_last_error": (ctypes.c_char_p, [c_vp]),
     "sip_device_bytes": (c_i64, [c_vp]),
     "sip_bytes_per_iter": (c_dbl, [c_vp]),
@@ -312,6 +315,31 @@ class Projector:
                  gamma=list(inf.gamma[:self.nblocks]), sigma=list(inf.sigma[:p]), k=list(inf.k[:p]),
                  ms=float(inf.ms), window_hits=inf.window_hits)
         return x, d
+
+    def state_rows(self):
+        """M', the entries of y (and of v): every block's rows."""
+        return int(lib().sip_state_rows(self.handle))
+
+    def get_state(self, device="cuda", stream=None):
+        """(x, y, v) of the handle: after a projection, its final iterates."""
+        import torch
+        M = self.state_rows()
+        if M < 0:  # batched or multilevel: the library reports why
+            _check(lib().sip_get_state(self.handle, None, None, None, _stream_ptr(stream)), self.handle)
+        x = torch.empty(self.N, dtype=self.torch_dtype, device=device)
+        y = torch.empty(M, dtype=self.torch_dtype, device=device)
+        v = torch.empty(M, dtype=self.torch_dtype, device=device)
+        _check(lib().sip_get_state(self.handle, _ptr(x), _ptr(y), _ptr(v), _stream_ptr(stream)), self.handle)
+        return x, y, v
+
+    def set_state(self, x, y=None, v=None, stream=None):
+        """Start the next projection from (x, y, v) (None: zeros)."""
+        x = _dev(x, self.code)
+        y = None if y is None else _dev(y, self.code)
+        v = None if v is None else _dev(v, self.code)
+        _check(lib().sip_set_state(self.handle, _ptr(x), None if y is None else _ptr(y),
+                                   None if v is None else _ptr(v), _stream_ptr(stream)), self.handle)
+        self._state_keep = (x, y, v)  # the copies are stream-ordered: keep the sources alive
 
     def device_bytes(self):
         return int(lib().sip_device_bytes(self.handle))

@@ -1,0 +1,93 @@
+"""Warm start through the C ABI: sip_get_state returns the final iterates
+(x, y_i, v_i) of a projection, and sip_set_state starts the next
+projection from a given state, as ML-PARSDMM hands the state from one
+level to the next (Sec. "Multilevel PARSDMM").  Checked against the FP64
+oracle started from the same state."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import parsdmm as P                   # noqa: E402
+from paper_1902_09699_gb300 import sip            # noqa: E402
+from paper_1902_09699_gb300 import workloads as W  # noqa: E402
+
+SETS = [{"op": "I", "type": "bounds", "lo": 1.8, "hi": 4.2},
+        {"op": "TV", "type": "l1", "sigma_rel": 0.4},
+        {"op": "DZ", "type": "bounds", "lo": -0.2, "hi": 0.6}]
+OPTS = dict(max_iter=40, cg_iters=5, adapt=1, rho0=1.0, gamma0=1.5)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def split(flat, blocks):
+    out, off = [], 0
+    for b in blocks:
+        out.append(flat[off:off + b["M"]])
+        off += b["M"]
+    assert off == flat.size
+    return out
+
+
+@pytest.mark.parametrize("form", ["alg1", "direct"])
+def test_state_round_trip_and_warm_start(form):
+    grid = {"n": (40, 36)}
+    m1 = W.layered(grid["n"], n_layers=6, seed=51)
+    m2 = m1 + 0.05 * np.random.default_rng(52).standard_normal(m1.size)
+    opts = dict(OPTS, form=form)
+    pr = sip.Projector(grid, SETS, dtype="f64", **opts)
+    x1, _ = pr.project(torch.as_tensor(m1, device="cuda"))
+    ref1 = P.parsdmm(m1, grid, SETS, P.options(**opts))
+    # get_state: the final iterates, blocks in order (identity block last in alg1)
+    xs, ys, vs = (t.cpu().numpy() for t in pr.get_state())
+    assert pr.state_rows() == sum(b["M"] for b in ref1["blocks"])
+    assert rel(xs, ref1["x"]) <= 1e-10
+    assert np.array_equal(xs, x1.cpu().numpy())
+    # per block, against the whole vector's size (an inactive set's duals
+    # are rounding noise around 0)
+    for mine, theirs in ((ys, ref1["y"]), (vs, ref1["v"])):
+        scale = np.linalg.norm(np.concatenate(theirs))
+        for got, want in zip(split(mine, ref1["blocks"]), theirs):
+            assert np.linalg.norm(got - want) <= 1e-9 * scale
+    # warm start of the next projection from that state
+    pr.set_state(xs, ys, vs)
+    x2, _ = pr.project(torch.as_tensor(m2, device="cuda"))
+    ref2 = P.parsdmm(m2, grid, SETS, P.options(**opts),
+                     init=(xs, split(ys, ref1["blocks"]), split(vs, ref1["blocks"])))
+    assert rel(x2.cpu().numpy(), ref2["x"]) <= 1e-10
+    # only that projection: the next one starts from zeros again
+    x3, _ = pr.project(torch.as_tensor(m2, device="cuda"))
+    ref3 = P.parsdmm(m2, grid, SETS, P.options(**opts))
+    assert rel(x3.cpu().numpy(), ref3["x"]) <= 1e-10
+    pr.close()
+
+
+def test_set_state_with_x_only_and_fp32():
+    grid = {"n": (33, 28)}
+    m = W.layered(grid["n"], n_layers=5, seed=53)
+    m32 = torch.as_tensor(m, dtype=torch.float32).double().numpy()
+    x0 = np.clip(m32, 2.0, 4.0)
+    x0 = torch.as_tensor(x0, dtype=torch.float32).double().numpy()
+    opts = dict(OPTS, adapt=0)
+    pr = sip.Projector(grid, SETS, dtype="f32", **opts)
+    pr.set_state(x0)                       # y, v from zeros
+    x, _ = pr.project(torch.as_tensor(m32, dtype=torch.float32, device="cuda"))
+    blocks = P.parsdmm(m32, grid, SETS, P.options(**dict(opts, max_iter=1)))["blocks"]
+    ref = P.parsdmm(m32, grid, SETS, P.options(**opts),
+                    init=(x0, [np.zeros(b["M"]) for b in blocks], [np.zeros(b["M"]) for b in blocks]))
+    assert rel(x.double().cpu().numpy(), ref["x"]) <= 1e-4
+    pr.close()
+
+
+def test_state_calls_rejected_where_there_is_no_single_state():
+    grid = {"n": (32, 32)}
+    pr = sip.Projector(grid, SETS[:1], dtype="f64", levels=2)
+    assert pr.state_rows() == -1
+    with pytest.raises(sip.SipError):
+        pr.get_state()
+    with pytest.raises(sip.SipError):
+        pr.set_state(np.zeros(32 * 32))
+    pr.close()
