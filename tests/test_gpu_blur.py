@@ -76,6 +76,8 @@ CASES = [
     ((24, 16, 12), "y", 2, 34),
     ((5, 40), "z", 4, 35),       # n_z < 2R: every sample meets both ends
     ((130, 9), "x", 6, 36),
+    ((20, 40, 6), "x", 3, 37),   # 3D, x blur: blocks over z and x, y neighbours from memory
+    ((30, 7, 5), "z", 2, 38),    # 3D, z blur: runs of one z column
 ]
 
 
@@ -95,6 +97,7 @@ BOX_CASES = [
     ((37, 70), "x", 5, 42),      # ragged blocks along z and x
     ((24, 16, 40), "y", 3, 43),
     ((40, 9), "x", 6, 44),       # n_x < 2R
+    ((18, 45, 4), "x", 4, 45),   # 3D
 ]
 
 
