@@ -501,3 +501,35 @@ def test_blur_rejected_with_levels_and_lines():
         P.ml_parsdmm(m, GRID, [blur], P.options(max_iter=5), levels=2)
     with pytest.raises(ValueError):
         P.parsdmm(m, GRID, [dict(blur, type="l2", sigma=1.0, scope="z")], P.options(max_iter=5))
+
+
+def test_blur_l2_data_ball_matches_general_qp_solver():
+    """The l2 data-fit ball with a blurring forward operator, min 1/2||x - m||^2
+    s.t. ||M (F x - d)||_2 <= sigma (M the observation mask: NaN in d),
+    against SLSQP with F from scipy's zero-padded convolution."""
+    opt = pytest.importorskip("scipy.optimize")
+    nd = pytest.importorskip("scipy.ndimage")
+    grid = {"n": (7, 6), "h": (1.0, 1.0)}
+    N = ops.grid_size(grid)
+    taps = (0.5, 0.25)
+    kfull = np.array(taps[::-1] + taps[1:])
+    F = np.stack([nd.convolve1d(e.reshape(6, 7), kfull, axis=1, mode="constant").reshape(-1)
+                  for e in np.eye(N)], axis=1)   # blur along z (axis 1 of the (nx, nz) array)
+    g = np.random.default_rng(31)
+    truth = 3.0 + 0.5 * g.standard_normal(N)
+    d = F @ truth + 0.1 * g.standard_normal(N)
+    obs = g.uniform(size=N) < 0.6
+    d[~obs] = np.nan
+    m = truth + 0.8 * g.standard_normal(N)
+    Fo, do = F[obs], d[obs]
+    sigma = 0.3 * float(np.linalg.norm(Fo @ m - do))
+    cons = [{"type": "ineq", "fun": lambda x: sigma ** 2 - np.sum((Fo @ x - do) ** 2),
+             "jac": lambda x: -2.0 * (Fo @ x - do) @ Fo}]
+    sol = opt.minimize(lambda x: 0.5 * np.sum((x - m) ** 2), m.copy(), jac=lambda x: x - m,
+                       constraints=cons, method="SLSQP", options={"maxiter": 1000, "ftol": 1e-15})
+    assert sol.success
+    sets = [{"op": "BLUR", "axis": "z", "taps": taps, "type": "l2", "sigma": sigma, "center": d}]
+    res = run(m, grid, sets, iters=4000)
+    assert rel(res["x"], sol.x) < 1e-5
+    # the ball binds
+    assert float(np.linalg.norm(Fo @ res["x"] - do)) == pytest.approx(sigma, rel=1e-5)
