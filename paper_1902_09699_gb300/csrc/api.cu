@@ -1051,6 +1051,7 @@ static sip_status run_persistent(Plan &P, cudaStream_t st, int iters) {
 
 sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,
                           KernelTimer *tm) {
+  const NvtxRange range("sip: iterations");
   if (!tm && P.exec == SIP_EXEC_PERSISTENT) return run_persistent(P, st, iters);
   const int chunk = poll ? P.check_every : (iters < 10 ? iters : 10);
   if (tm) {
@@ -1094,6 +1095,7 @@ sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters,
 }
 
 sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm) {
+  const NvtxRange range(warm ? "sip: prepare (warm state)" : "sip: prepare");
   const Launch L{P.dtype, st};
   char *base = (char *)P.arena;
   if (warm) {

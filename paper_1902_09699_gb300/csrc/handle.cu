@@ -237,6 +237,7 @@ static sip_status prolong_state(Plan &C, Plan &F, cudaStream_t st) {
 }
 
 static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cudaStream_t st, sip_info *info) {
+  const NvtxRange range("sip_project");
   Plan &F = h->lev[0];
   const sip_options &o = h->opts;
   const size_t W = esz(o.dtype);
@@ -256,6 +257,7 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
       CKH(launch_restrict(L, fd, cd, l == 1 ? m_dev : h->lev[l - 1].h_insts[0].m, (void *)h->lev[l].h_insts[0].m));
     }
     for (int l = h->levels - 1; l >= 1; --l) {
+      const NvtxRange lr("sip: coarse level");
       Plan &C = h->lev[l];
       sip_status s = plan_prepare(C, st, l < h->levels - 1);
       if (!s) s = run_iterations(C, st, h->cap, C.max_iter, o.stop != 0, h->pinned, tm);

@@ -6,11 +6,22 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "sip.h"
 #include "sip_dev.cuh"
 
 namespace sip {
+
+// A named NVTX range for the lifetime of the object: the host phases of a
+// projection (preparation, iteration replays, multilevel transfers) show as
+// ranges in a timeline profiler; without one attached the calls are no-ops.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 extern thread_local std::string g_err;
 sip_status fail(sip_status s, const char *fmt, ...);
