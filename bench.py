@@ -93,9 +93,10 @@ class Clocks:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self):
+        # the raw samples: SIP_CLOCKS_CSV names the file to keep them in
+        import tempfile
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/sip_clocks.csv"
+        self.path = os.environ.get("SIP_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), "sip_clocks.csv")
 
     def start(self):
         try:
