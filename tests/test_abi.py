@@ -125,3 +125,7 @@ def test_null_arguments(sip):
     assert L.sip_project(None, None, None, None, None) == 1
     assert L.sip_destroy(None) == 0
     assert L.sip_last_error(None)
+    # warm-start state of a missing handle
+    assert L.sip_state_rows(None) == -1
+    assert L.sip_get_state(None, None, None, None, None) == 1
+    assert L.sip_set_state(None, None, None, None, None) == 1
