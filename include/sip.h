@@ -120,8 +120,9 @@ typedef struct {
      * entries, per-entry bounds lo_vec[j] <= (A x)[j] <= hi_vec[j] in place
      * of lo / hi (either may be NULL: the scalar applies).  This is the
      * paper's point-wise data-fit set {l <= F x - d_obs <= u} for F = A_i
-     * (e.g. the identity, or a binary mask with +-INFINITY at unobserved
-     * entries), with d_obs folded in: lo_vec = l + d_obs, hi_vec = u + d_obs.
+     * (e.g. the identity or a blur, SIP_OP_BLUR; a binary mask is
+     * +-INFINITY at unobserved entries), with d_obs folded in:
+     * lo_vec = l + d_obs, hi_vec = u + d_obs.
      * Copied when the handle is created; lo_vec <= hi_vec, no NaN.  Not
      * accepted by the server. */
     const double *lo_vec, *hi_vec;
