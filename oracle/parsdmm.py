@@ -237,7 +237,7 @@ def _blocks(grid, sets, form):
 
 
 def parsdmm(m, grid, sets, opts=None, init=None, rho_schedule=None,
-            gamma_schedule=None, resolve=True):
+            gamma_schedule=None, resolve=True, init_rho=None, init_gamma=None):
     """Project m onto the intersection of {x : A_i x in C_i}, Algorithm
     PARSDMM with the iterations of Eq. SDMM_adaptive.
 
@@ -262,7 +262,10 @@ def parsdmm(m, grid, sets, opts=None, init=None, rho_schedule=None,
     (direct form: [1/R, R]) with R = rho_ratio_max.
 
     ``rho_schedule`` / ``gamma_schedule`` ([max_iter, blocks]) replay the
-    values used in each iteration instead of adapting them.
+    values used in each iteration instead of adapting them.  ``init_rho`` /
+    ``init_gamma`` (one value per block) replace rho0 / gamma0 as the
+    starting values of a warm start that carries the penalties over
+    (reading: adapt-rho-gamma then proceeds from them as from rho0).
     Returns a dict with x, y, v, rho, gamma, iters, cg_steps, stop_reason,
     r_feas, r_evol and a per-iteration ``trace``.
     """
@@ -285,8 +288,10 @@ def parsdmm(m, grid, sets, opts=None, init=None, rho_schedule=None,
         x = np.array(init[0], dtype=np.float64).reshape(-1)
         y = [np.array(a, dtype=np.float64).reshape(-1) for a in init[1]]
         v = [np.array(a, dtype=np.float64).reshape(-1) for a in init[2]]
-    rho = np.full(nb, float(o["rho0"]))
-    gamma = np.full(nb, float(o["gamma0"]))
+    rho = np.full(nb, float(o["rho0"])) if init_rho is None else np.array(init_rho, dtype=np.float64)
+    gamma = np.full(nb, float(o["gamma0"])) if init_gamma is None else np.array(init_gamma, dtype=np.float64)
+    if rho.shape != (nb,) or gamma.shape != (nb,):
+        raise ValueError("init_rho / init_gamma need one value per block")
     k0 = [None] * nb              # saved (vhat, v, s, y) of the last adapt call
     history = []                  # previous iterates for Eq. obj_stop
     trace = []

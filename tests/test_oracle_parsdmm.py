@@ -533,3 +533,19 @@ def test_blur_l2_data_ball_matches_general_qp_solver():
     assert rel(res["x"], sol.x) < 1e-5
     # the ball binds
     assert float(np.linalg.norm(Fo @ res["x"] - do)) == pytest.approx(sigma, rel=1e-5)
+
+
+def test_init_rho_gamma_equal_the_uniform_starting_values():
+    """Starting penalties given per block reproduce the rho0 / gamma0 runs
+    when they are uniform (with and without adaptation)."""
+    m = model(GRID, 41)
+    sets = [{"op": "I", "type": "bounds", "lo": 2.5, "hi": 3.5},
+            {"op": "TV", "type": "l1", "sigma_rel": 0.4}]
+    for adapt in (0, 1):
+        base = P.parsdmm(m, GRID, sets, P.options(max_iter=30, adapt=adapt, rho0=2.5, gamma0=1.3))
+        nb = len(base["blocks"])
+        same = P.parsdmm(m, GRID, sets, P.options(max_iter=30, adapt=adapt, rho0=1.0, gamma0=1.0),
+                         init_rho=[2.5] * nb, init_gamma=[1.3] * nb)
+        assert np.array_equal(same["x"], base["x"])
+    with pytest.raises(ValueError):
+        P.parsdmm(m, GRID, sets, P.options(max_iter=3), init_rho=[1.0])
