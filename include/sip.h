@@ -254,15 +254,20 @@ sip_status sip_destroy(sip_handle *h);
  * sip_get_state copies the handle's current state out (after a
  * projection: its final iterates); NULL pointers are skipped.
  * sip_set_state loads a state; the next sip_project (that one only) starts
- * from it instead of zeros, with rho_i, gamma_i restarting from rho0,
- * gamma0 as on a multilevel hand-over.  x_dev is required; NULL y_dev /
- * v_dev load zeros.  Both are stream-ordered on `stream`; single-level,
+ * from it instead of zeros.  x_dev is required; NULL y_dev / v_dev load
+ * zeros.  rho / gamma (host arrays, one value per block in block order,
+ * identity block last in SIP_FORM_ALG1; e.g. sip_info.rho / gamma of the
+ * projection the state came from) give the starting penalties and
+ * relaxations, which adapt-rho-gamma then updates as usual; NULL: rho0 /
+ * gamma0, as on a multilevel hand-over.  rho_i > 0, 0 < gamma_i < 2; a
+ * rho_schedule, when set, takes precedence.  Both are stream-ordered on `stream`; single-level,
  * single-instance handles only (SIP_ERR_INVALID_ARG otherwise). */
 int64_t sip_state_rows(const sip_handle *h);
 sip_status sip_get_state(sip_handle *h, void *x_dev, void *y_dev, void *v_dev,
                          void *stream);
 sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev,
-                         const void *v_dev, void *stream);
+                         const void *v_dev, const double *rho,
+                         const double *gamma, void *stream);
 
 const char *sip_last_error(const sip_handle *h);
 

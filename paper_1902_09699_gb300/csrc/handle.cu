@@ -27,6 +27,8 @@ struct sip_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timing = false;
   bool warm_next = false;  // sip_set_state loaded x, y, v: the next projection starts from them
+  bool warm_pen = false;   // ... and starting rho_i, gamma_i (warm_rho, warm_gamma)
+  std::vector<double> warm_rho, warm_gamma;
   KernelTimer timer;
   std::string err;
 };
@@ -236,6 +238,54 @@ static sip_status prolong_state(Plan &C, Plan &F, cudaStream_t st) {
   return SIP_OK;
 }
 
+// Starting rho_i, gamma_i of a warm start: the instance scalars the
+// initialisation derives from them (1/rho, 1/(1+rho), the system matrix's
+// stencil coefficients, the binary32 copies; as the device's own
+// coefficient update forms them), written over its rho0 / gamma0 values in
+// stream order, before the first iteration.
+static sip_status load_penalties(sip_handle *h, Plan &F, cudaStream_t st) {
+  const InstDev &in = F.h_insts[0];
+  InstScal sc;  // host staging of the copied range (pageable: the copy is synchronised below)
+  memset(&sc, 0, sizeof sc);
+  double c0 = in.alg1 ? 0.0 : 1.0, cz = 0.0, cx = 0.0, cy = 0.0;
+  for (int b = 0; b < in.nb; ++b) {
+    const double r = h->warm_rho[b], g = h->warm_gamma[b];
+    sc.rho[b] = r;
+    sc.gamma[b] = g;
+    sc.irho[b] = 1.0 / r;
+    sc.inv1p[b] = 1.0 / (1.0 + r);
+    sc.l2scale[b] = 1.0;
+    switch (in.blk[b].op) {
+      case SIP_OP_I: c0 += r; break;
+      case SIP_OP_DZ: cz += r; break;
+      case SIP_OP_DX: cx += r; break;
+      case SIP_OP_DY: cy += r; break;
+      case SIP_OP_BLUR: break;
+      default: cz += r; cx += r; if (in.ndim == 3) cy += r; break;
+    }
+  }
+  sc.c0 = c0;
+  sc.cz = cz * in.ihz * in.ihz;
+  sc.cx = cx * in.ihx * in.ihx;
+  sc.cy = cy * in.ihy * in.ihy;
+  sc.cf[0] = (float)sc.c0;
+  sc.cf[1] = (float)sc.cz;
+  sc.cf[2] = (float)sc.cx;
+  sc.cf[3] = (float)sc.cy;
+  for (int b = 0; b < in.nb; ++b) {
+    sc.bf[b][0] = (float)sc.rho[b];
+    sc.bf[b][1] = (float)sc.irho[b];
+    sc.bf[b][2] = (float)sc.gamma[b];
+    sc.bf[b][3] = (float)(1.0 - sc.gamma[b]);
+    sc.bf[b][4] = (float)sc.inv1p[b];
+    sc.bf[b][5] = (float)sc.l2scale[b];
+  }
+  const size_t a = offsetof(InstScal, rho), e = offsetof(InstScal, bf) + sizeof(sc.bf);
+  CKH(cudaMemcpyAsync((char *)F.d_scal + a, (const char *)&sc + a, e - a, cudaMemcpyHostToDevice, st));
+  CKH(cudaStreamSynchronize(st));
+  return SIP_OK;
+}
+
 static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cudaStream_t st, sip_info *info) {
   const NvtxRange range("sip_project");
   Plan &F = h->lev[0];
@@ -277,7 +327,8 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
       CKH(cudaMemcpyAsync((void *)df.gamma_sched, o.gamma_schedule, (size_t)o.max_iter * nb * 8,
                           cudaMemcpyHostToDevice, st));
     if ((s = plan_prepare(F, st, h->warm_next))) return s;
-    h->warm_next = false;
+    if (h->warm_next && h->warm_pen && !o.rho_schedule && (s = load_penalties(h, F, st))) return s;
+    h->warm_next = h->warm_pen = false;
   }
   sip_status s = run_iterations(F, st, h->cap, F.max_iter, o.stop != 0, h->pinned, tm);
   if (s) return s;
@@ -343,9 +394,23 @@ sip_status sip_get_state(sip_handle *h, void *x_dev, void *y_dev, void *v_dev, v
   return SIP_OK;
 }
 
-sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev, const void *v_dev, void *stream) {
+sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev, const void *v_dev, const double *rho,
+                         const double *gamma, void *stream) {
   if (sip_status s = state_check(h)) return h ? keep(h, s) : s;
   if (!x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "x_dev is NULL"));
+  const int nb = h->lev[0].h_insts[0].nb;
+  h->warm_pen = rho || gamma;
+  h->warm_rho.assign(nb, h->opts.rho0);
+  h->warm_gamma.assign(nb, h->opts.gamma0);
+  for (int b = 0; b < nb; ++b) {
+    if (rho) h->warm_rho[b] = rho[b];
+    if (gamma) h->warm_gamma[b] = gamma[b];
+    if (!(h->warm_rho[b] > 0.0) || !std::isfinite(h->warm_rho[b]) || !(h->warm_gamma[b] > 0.0) ||
+        !(h->warm_gamma[b] < 2.0)) {
+      h->warm_pen = false;
+      return keep(h, fail(SIP_ERR_INVALID_ARG, "block %d: rho must be finite and > 0, gamma in (0, 2)", b));
+    }
+  }
   const InstDev &d = h->lev[0].h_insts[0];
   const size_t W = esz(h->opts.dtype), M = (size_t)h->lev[0].layouts[0].Mtot;
   const cudaStream_t st = (cudaStream_t)stream;

@@ -81,7 +81,7 @@ SIGNATURES = {
     "sip_destroy": (c_int, [c_vp]),
     "sip_state_rows": (c_i64, [c_vp]),
     "sip_get_state": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
-    "sip_set_state": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "sip_set_state": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
     "sip_last_error": (ctypes.c_char_p, [c_vp]),
     "sip_device_bytes": (c_i64, [c_vp]),
     "sip_bytes_per_iter": (c_dbl, [c_vp]),
@@ -332,13 +332,26 @@ class Projector:
         _check(lib().sip_get_state(self.handle, _ptr(x), _ptr(y), _ptr(v), _stream_ptr(stream)), self.handle)
         return x, y, v
 
-    def set_state(self, x, y=None, v=None, stream=None):
-        """Start the next projection from (x, y, v) (None: zeros)."""
+    def set_state(self, x, y=None, v=None, rho=None, gamma=None, stream=None):
+        """Start the next projection from (x, y, v) (None: zeros), with
+        starting rho_i / gamma_i per block (None: rho0 / gamma0)."""
         x = _dev(x, self.code)
         y = None if y is None else _dev(y, self.code)
         v = None if v is None else _dev(v, self.code)
+
+        def host(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            if a.size != self.nblocks:
+                raise ValueError("one value per block (%d)" % self.nblocks)
+            return a
+        rh, gh = host(rho), host(gamma)
         _check(lib().sip_set_state(self.handle, _ptr(x), None if y is None else _ptr(y),
-                                   None if v is None else _ptr(v), _stream_ptr(stream)), self.handle)
+                                   None if v is None else _ptr(v),
+                                   None if rh is None else rh.ctypes.data_as(ctypes.POINTER(c_dbl)),
+                                   None if gh is None else gh.ctypes.data_as(ctypes.POINTER(c_dbl)),
+                                   _stream_ptr(stream)), self.handle)
         self._state_keep = (x, y, v)  # the copies are stream-ordered: keep the sources alive
 
     def device_bytes(self):

@@ -128,4 +128,4 @@ def test_null_arguments(sip):
     # warm-start state of a missing handle
     assert L.sip_state_rows(None) == -1
     assert L.sip_get_state(None, None, None, None, None) == 1
-    assert L.sip_set_state(None, None, None, None, None) == 1
+    assert L.sip_set_state(None, None, None, None, None, None, None) == 1

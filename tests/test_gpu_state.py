@@ -91,3 +91,27 @@ def test_state_calls_rejected_where_there_is_no_single_state():
     with pytest.raises(sip.SipError):
         pr.set_state(np.zeros(32 * 32))
     pr.close()
+
+
+def test_warm_start_carries_rho_and_gamma():
+    """The penalties and relaxations adapted in one projection (sip_info)
+    start the next one, against the oracle started from the same x, y_i,
+    v_i, rho_i and gamma_i."""
+    grid = {"n": (36, 30)}
+    m1 = W.layered(grid["n"], n_layers=6, seed=54)
+    m2 = m1 + 0.05 * np.random.default_rng(55).standard_normal(m1.size)
+    opts = dict(OPTS, adapt=2)
+    pr = sip.Projector(grid, SETS, dtype="f64", **opts)
+    _, info = pr.project(torch.as_tensor(m1, device="cuda"))
+    ref1 = P.parsdmm(m1, grid, SETS, P.options(**opts))
+    assert np.allclose(info["rho"], ref1["rho"], rtol=1e-9)
+    xs, ys, vs = (t.cpu().numpy() for t in pr.get_state())
+    pr.set_state(xs, ys, vs, rho=info["rho"], gamma=info["gamma"])
+    x2, _ = pr.project(torch.as_tensor(m2, device="cuda"))
+    blocks = ref1["blocks"]
+    ref2 = P.parsdmm(m2, grid, SETS, P.options(**opts), init=(xs, split(ys, blocks), split(vs, blocks)),
+                     init_rho=info["rho"], init_gamma=info["gamma"])
+    assert rel(x2.cpu().numpy(), ref2["x"]) <= 1e-10
+    with pytest.raises(sip.SipError):
+        pr.set_state(xs, rho=[-1.0] * len(blocks))
+    pr.close()
