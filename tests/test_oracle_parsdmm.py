@@ -549,3 +549,18 @@ def test_init_rho_gamma_equal_the_uniform_starting_values():
         assert np.array_equal(same["x"], base["x"])
     with pytest.raises(ValueError):
         P.parsdmm(m, GRID, sets, P.options(max_iter=3), init_rho=[1.0])
+
+
+def test_warm_start_from_the_fixed_point_stays_there():
+    """Started from its own converged iterates (x, y_i, v_i) and penalties,
+    the iteration is at a fixed point: a convex problem's solution does not
+    move (the state a warm start hands over is the whole ADMM state)."""
+    m = model(GRID, 42)
+    sets = [{"op": "I", "type": "bounds", "lo": 2.5, "hi": 3.5},
+            {"op": "TV", "type": "l1", "sigma": 0.2 * ops.norm_of(GRID, "TV", "l1", m)}]
+    conv = run(m, GRID, sets, iters=6000, adapt=0)
+    again = P.parsdmm(m, GRID, sets, P.options(max_iter=20, adapt=0, rho0=1.0, gamma0=1.5),
+                      init=(conv["x"], conv["y"], conv["v"]))
+    assert rel(again["x"], conv["x"]) < 1e-9
+    cold = P.parsdmm(m, GRID, sets, P.options(max_iter=20, adapt=0, rho0=1.0, gamma0=1.5))
+    assert rel(cold["x"], conv["x"]) > 1e-6   # 20 cold iterations are not there yet
