@@ -18,10 +18,19 @@
  * (Eq. FD_mat) and the same z-fastest layout on its own grid; the TV
  * operator stacks D_z, D_x (, D_y) outputs in that order.
  *
- * Precision: SIP_F64 stores and computes everything in binary64;
- * SIP_F32 stores vectors in binary32 and accumulates every inner product,
- * norm and l1 running sum in binary64.  Device buffers passed to the library
- * hold elements of the handle's dtype.
+ * Precision: SIP_F64 stores and computes everything in binary64.
+ * SIP_F32 stores vectors and computes element-wise in binary32.  Its sums
+ * are formed in two levels: each CTA adds its share (a work item of at most
+ * a few thousand entries) in binary32; the CTA totals of the set and final
+ * passes (norms, feasibility and adapt-rho-gamma inner products) are added
+ * in binary64, those of the CG's inner products in double-binary32 (a
+ * hi + lo pair whose rounding error TwoSum keeps), and the CG scalars alpha
+ * and beta are binary32.  The l1 threshold's running sums are exact (integer
+ * sums of the binary32 significands in the radix selection) and the
+ * adapt-rho-gamma ratios are binary64.  Binary64 arithmetic runs at 1/64 of
+ * the binary32 rate on this GPU, which is why the CG chain avoids it.
+ * Device buffers passed to the library hold elements of the handle's
+ * dtype.
  *
  * Errors: every call returns a sip_status; nothing throws across the ABI.
  * sip_last_error() gives a thread-local message for the last failure of
@@ -442,6 +451,28 @@ sip_status sip_prolong(const sip_grid *fine, int op, int dtype,
                        const void *uc_dev, void *uf_dev, void *stream);
 
 /* ---------------------------------------------------------------------
+ * Test hooks: host-side fault injection for the failure-handling tests.
+ * The paper has no counterpart.  Process-wide settings, read when a handle
+ * is created (allocation) or a persistent projection is launched
+ * (barriers); not synchronised with calls running on other threads.
+ *   SIP_HOOK_FAIL_ALLOC, n >= 1: the n-th next device-arena allocation of a
+ *     handle (sip_create, sip_batch_create, ...) fails as if the device were
+ *     out of memory, and that call returns SIP_ERR_OOM; 0 switches it off.
+ *   SIP_HOOK_BARRIER_EXTRA, e >= 1: the grid barriers of the persistent
+ *     kernel (SIP_EXEC_PERSISTENT) wait for e arrivals more than its CTAs
+ *     make, so the first barrier runs out of polls, every CTA returns, and
+ *     sip_project (with info) returns SIP_ERR_TIMEOUT; the handle stays
+ *     usable.  0 switches it off.
+ *   SIP_HOOK_BARRIER_SPINS, s >= 1: polls (about 0.1 us each) before a
+ *     grid barrier gives up; 0 restores the default of 2^26.
+ * Returns SIP_ERR_INVALID_ARG for an unknown hook or a value out of range.
+ * ------------------------------------------------------------------- */
+#define SIP_HOOK_FAIL_ALLOC 1
+#define SIP_HOOK_BARRIER_EXTRA 2
+#define SIP_HOOK_BARRIER_SPINS 3
+sip_status sip_test_hook(int hook, int64_t value);
+
+/* ---------------------------------------------------------------------
  * Allocation-free l1-ball projection.  The paper has no counterpart: this
  * is a deployment variant of sip_project_set with SIP_SET_L1.
  *
@@ -464,7 +495,10 @@ sip_status sip_prolong(const sip_grid *fine, int op, int dtype,
  * overlap (several streams or host threads on one device) race and must be
  * serialised by the caller.  Stream-ordered on `stream`; synchronises only
  * when theta_out (host, may be NULL; receives the threshold, 0 when w is
- * already inside the ball or tau = 0) is requested.
+ * already inside the ball or tau = 0) is requested.  w must be finite: when
+ * it holds a NaN or an infinity every y entry is NaN, and a call with
+ * theta_out returns SIP_ERR_NONFINITE (theta_out = NaN).  The launches
+ * size their grids from the device's SM count.
  * ------------------------------------------------------------------- */
 #define SIP_NOALLOC_MAX_N (INT64_C(1) << 24)
 sip_status sip_project_l1_noalloc(int dtype, const void *w_dev, int64_t n,

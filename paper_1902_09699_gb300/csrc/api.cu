@@ -19,6 +19,12 @@
 namespace sip {
 
 thread_local std::string g_err;
+TestHooks g_hooks;
+
+bool hook_alloc_fails() {
+  if (g_hooks.fail_alloc <= 0) return false;
+  return --g_hooks.fail_alloc == 0;
+}
 
 sip_status fail(sip_status s, const char *fmt, ...) {
   char buf[512];
@@ -744,7 +750,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.arena_bytes = off;
   if (dry) return SIP_OK;  // size only (admission control)
 
-  if (cudaMalloc(&P.arena, (size_t)off) != cudaSuccess) {
+  if (hook_alloc_fails() || cudaMalloc(&P.arena, (size_t)off) != cudaSuccess) {
     cudaGetLastError();
     P.arena = nullptr;
     return fail(SIP_ERR_OOM, "device allocation of %lld bytes failed", (long long)off);
@@ -1045,6 +1051,8 @@ static sip_status run_persistent(Plan &P, cudaStream_t st, int iters) {
   F.any_card = P.any_card ? 1 : 0;
   F.any_fin = P.any_fin ? 1 : 0;
   F.iters = iters;
+  F.bar_extra = g_hooks.bar_extra;
+  F.bar_spins = g_hooks.bar_spins;
   CK(launch_fused(Launch{P.dtype, st}, F, P.fused_grid));
   return SIP_OK;
 }

@@ -238,51 +238,19 @@ static sip_status prolong_state(Plan &C, Plan &F, cudaStream_t st) {
   return SIP_OK;
 }
 
-// Starting rho_i, gamma_i of a warm start: the instance scalars the
-// initialisation derives from them (1/rho, 1/(1+rho), the system matrix's
-// stencil coefficients, the binary32 copies; as the device's own
-// coefficient update forms them), written over its rho0 / gamma0 values in
-// stream order, before the first iteration.
+// Starting rho_i, gamma_i of a warm start, written over the rho0 / gamma0
+// values of the initialisation in stream order, before the first iteration;
+// the scalars derived from them come from the device's own coefficient
+// update (launch_load_penalties).
 static sip_status load_penalties(sip_handle *h, Plan &F, cudaStream_t st) {
   const InstDev &in = F.h_insts[0];
-  InstScal sc;  // host staging of the copied range (pageable: the copy is synchronised below)
-  memset(&sc, 0, sizeof sc);
-  double c0 = in.alg1 ? 0.0 : 1.0, cz = 0.0, cx = 0.0, cy = 0.0;
+  Penalties pen;
+  memset(&pen, 0, sizeof pen);
   for (int b = 0; b < in.nb; ++b) {
-    const double r = h->warm_rho[b], g = h->warm_gamma[b];
-    sc.rho[b] = r;
-    sc.gamma[b] = g;
-    sc.irho[b] = 1.0 / r;
-    sc.inv1p[b] = 1.0 / (1.0 + r);
-    sc.l2scale[b] = 1.0;
-    switch (in.blk[b].op) {
-      case SIP_OP_I: c0 += r; break;
-      case SIP_OP_DZ: cz += r; break;
-      case SIP_OP_DX: cx += r; break;
-      case SIP_OP_DY: cy += r; break;
-      case SIP_OP_BLUR: break;
-      default: cz += r; cx += r; if (in.ndim == 3) cy += r; break;
-    }
+    pen.rho[b] = h->warm_rho[b];
+    pen.gamma[b] = h->warm_gamma[b];
   }
-  sc.c0 = c0;
-  sc.cz = cz * in.ihz * in.ihz;
-  sc.cx = cx * in.ihx * in.ihx;
-  sc.cy = cy * in.ihy * in.ihy;
-  sc.cf[0] = (float)sc.c0;
-  sc.cf[1] = (float)sc.cz;
-  sc.cf[2] = (float)sc.cx;
-  sc.cf[3] = (float)sc.cy;
-  for (int b = 0; b < in.nb; ++b) {
-    sc.bf[b][0] = (float)sc.rho[b];
-    sc.bf[b][1] = (float)sc.irho[b];
-    sc.bf[b][2] = (float)sc.gamma[b];
-    sc.bf[b][3] = (float)(1.0 - sc.gamma[b]);
-    sc.bf[b][4] = (float)sc.inv1p[b];
-    sc.bf[b][5] = (float)sc.l2scale[b];
-  }
-  const size_t a = offsetof(InstScal, rho), e = offsetof(InstScal, bf) + sizeof(sc.bf);
-  CKH(cudaMemcpyAsync((char *)F.d_scal + a, (const char *)&sc + a, e - a, cudaMemcpyHostToDevice, st));
-  CKH(cudaStreamSynchronize(st));
+  CKH(launch_load_penalties(st, F.d_insts, F.d_scal, pen));
   return SIP_OK;
 }
 
@@ -398,6 +366,9 @@ sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev, co
                          const double *gamma, void *stream) {
   if (sip_status s = state_check(h)) return h ? keep(h, s) : s;
   if (!x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "x_dev is NULL"));
+  // a rejected or failed call leaves no warm start armed: the next
+  // projection starts from zeros
+  h->warm_next = false;
   const int nb = h->lev[0].h_insts[0].nb;
   h->warm_pen = rho || gamma;
   h->warm_rho.assign(nb, h->opts.rho0);
@@ -441,6 +412,26 @@ sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev, void *stre
 static const char *kKernelNames[KT_COUNT] = {"rhs", "cg_w0", "cg_step", "setpass", "select", "ties", "final", "tail"};
 
 const char *sip_kernel_name(int i) { return (i >= 0 && i < KT_COUNT) ? kKernelNames[i] : ""; }
+
+sip_status sip_test_hook(int hook, int64_t value) {
+  if (value < 0) return fail(SIP_ERR_INVALID_ARG, "hook value must be >= 0");
+  switch (hook) {
+    case SIP_HOOK_FAIL_ALLOC:
+      if (value > (1 << 30)) return fail(SIP_ERR_INVALID_ARG, "hook value too large");
+      g_hooks.fail_alloc = (int)value;
+      return SIP_OK;
+    case SIP_HOOK_BARRIER_EXTRA:
+      if (value > (1 << 20)) return fail(SIP_ERR_INVALID_ARG, "hook value too large");
+      g_hooks.bar_extra = (uint32_t)value;
+      return SIP_OK;
+    case SIP_HOOK_BARRIER_SPINS:
+      if (value > (INT64_C(1) << 40)) return fail(SIP_ERR_INVALID_ARG, "hook value too large");
+      g_hooks.bar_spins = (long long)value;
+      return SIP_OK;
+    default:
+      return fail(SIP_ERR_INVALID_ARG, "unknown hook %d", hook);
+  }
+}
 
 sip_status sip_set_timing(sip_handle *h, int on) {
   if (!h) return fail(SIP_ERR_INVALID_ARG, "handle is NULL");

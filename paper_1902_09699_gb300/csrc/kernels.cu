@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "sip_dev.cuh"
 #include "sip_kernels.h"
 
@@ -3752,7 +3754,7 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
 // kBarrierSpins polls (seconds) records SIP_ERR_TIMEOUT in bar[2] and every
 // CTA returns false, so the kernel ends instead of hanging.
 constexpr long long kBarrierSpins = 1ll << 26;
-__device__ __forceinline__ bool grid_barrier(uint32_t *bar) {
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t expected, long long max_spins) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -3760,14 +3762,14 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar) {
     const uint32_t g = ld_acquire(&bar[1]);
     __threadfence();
     const uint32_t arrived = atomicAdd(&bar[0], 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == expected) {
       atomicExch(&bar[0], 0u);
       __threadfence();
       atomicAdd(&bar[1], 1u);
     } else {
       long long spins = 0;
       while (ld_relaxed(&bar[1]) == g) {
-        if (ld_relaxed(&bar[2]) != 0 || ++spins > kBarrierSpins) {
+        if (ld_relaxed(&bar[2]) != 0 || ++spins > max_spins) {
           atomicExch(&bar[2], (uint32_t)SIP_ERR_TIMEOUT);
           ok = 0;
           break;
@@ -3803,43 +3805,45 @@ struct FusedArgs {
   uint32_t *bar;
   const uint32_t *ndone;
   int ninst, npass, cg_launch, any_card, any_fin, iters;
+  uint32_t bar_expected;  // arrivals per barrier: the grid (plus a test hook's extra)
+  long long bar_spins;    // polls before a barrier gives up
 };
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
   for (int it = 0; it < A.iters; ++it) {
     for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_rhs<T>(A.tn[i], A.insts, A.scal);
-    if (!grid_barrier(A.bar)) return;
+    if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_cg_w0<T>(A.tn[i], A.insts, A.scal);
-    if (!grid_barrier(A.bar)) return;
+    if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     for (int j = 0; j < A.cg_launch; ++j) {
       for (int i = blockIdx.x; i < A.nt_n; i += gridDim.x) body_cg_step<T>(A.tn[i], A.insts, A.scal, 2 + j);
-      if (!grid_barrier(A.bar)) return;
+      if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     }
     for (int i = blockIdx.x; i < A.nt_set; i += gridDim.x) body_setpass<T>(A.tset[i], A.insts, A.scal, A.jscal, A.jobs);
-    if (!grid_barrier(A.bar)) return;
+    if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     if (A.nt_sel) {
       for (int pass = 0; pass < A.npass; ++pass) {
         for (int i = blockIdx.x; i < A.nt_sel; i += gridDim.x)
           body_select<T>(A.tsel[i], A.insts, A.scal, A.jobs, A.jscal, A.hcnt, A.hs1, A.hs2, A.hs3, A.hstride, pass);
-        if (!grid_barrier(A.bar)) return;
+        if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
       }
     }
     if (A.any_card) {
       for (int i = blockIdx.x; i < A.nt_fin; i += gridDim.x) body_ties<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
-      if (!grid_barrier(A.bar)) return;
+      if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     }
     if (A.nt_line) {
       extern __shared__ unsigned char smem_raw[];
       for (int i = blockIdx.x; i < A.nt_line; i += gridDim.x) body_lines<T>(A.tline[i], A.insts, A.scal, smem_raw);
-      if (!grid_barrier(A.bar)) return;
+      if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     }
     if (A.any_fin) {
       for (int i = blockIdx.x; i < A.nt_fin; i += gridDim.x) body_final<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
-      if (!grid_barrier(A.bar)) return;
+      if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     }
     for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) body_tail(i, A.insts, A.scal, A.jscal, A.cg_launch);
-    if (!grid_barrier(A.bar)) return;
+    if (!grid_barrier(A.bar, A.bar_expected, A.bar_spins)) return;
     if (ld_acquire(A.ndone) >= (uint32_t)A.ninst) return;  // every instance stopped
   }
 }
@@ -3891,6 +3895,26 @@ __global__ void k_init(const InstDev *__restrict__ insts, InstScal *__restrict__
     sc.kcard[b] = in.blk[b].k_abs;
   }
   set_coefficients(in, sc);
+}
+
+// Starting rho_i, gamma_i of a warm start written over the initialised
+// rho0 / gamma0 values, with every derived scalar (1/rho, 1/(1+rho), C's
+// stencil coefficients, the binary32 copies) formed by the same device code
+// as after an adapt-rho-gamma call.  One thread.
+__global__ void k_load_penalties(const InstDev *__restrict__ insts, InstScal *__restrict__ scal, Penalties pen) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const InstDev &in = insts[0];
+  InstScal &sc = scal[0];
+  for (int b = 0; b < in.nb; ++b) {
+    sc.rho[b] = pen.rho[b];
+    sc.gamma[b] = pen.gamma[b];
+    sc.l2scale[b] = 1.0;
+  }
+  set_coefficients(in, sc);
+}
+cudaError_t launch_load_penalties(cudaStream_t st, const InstDev *insts, InstScal *scal, const Penalties &pen) {
+  k_load_penalties<<<1, 32, 0, st>>>(insts, scal, pen);
+  return cudaGetLastError();
 }
 
 // ||A_i m|| for sets with relative radii, and a finiteness check of m.
@@ -4148,9 +4172,16 @@ cudaError_t launch_dykstra_update(const Launch &L, const void *y, void *v, void 
 
 cudaError_t kernels_setup() {
   // the binary32 select histogram needs 56 KB of shared memory: opt in once
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_select<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // per device (a function attribute belongs to the current device's context)
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_select<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BinAcc<float>::kSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_select<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BinAcc<double>::kSmem);
@@ -4176,7 +4207,7 @@ cudaError_t kernels_setup() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_lines<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<double>());
   if (e != cudaSuccess) return e;
-  done = true;
+  done[dev] = true;
   return cudaSuccess;
 }
 
@@ -4243,6 +4274,8 @@ cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
   A.any_card = F.any_card;
   A.any_fin = F.any_fin;
   A.iters = F.iters;
+  A.bar_expected = (uint32_t)grid + F.bar_extra;
+  A.bar_spins = F.bar_spins > 0 ? F.bar_spins : kBarrierSpins;
   void *args[] = {&A};
   const bool d = L.dtype == SIP_F64;
   const size_t smem = d ? fused_smem<double>() : fused_smem<float>();

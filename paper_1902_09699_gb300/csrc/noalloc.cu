@@ -40,8 +40,9 @@ struct NoAllocScratch {
   Tile tiles[kNoAllocTiles];
   uint32_t hcnt[kBins];
   double hs1[kBins], hs2[kBins], hs3[kBins];
-  double l1;        // ||w||_1 (binary64)
-  uint32_t arrive;  // CTAs done in the norm kernel
+  double l1;          // ||w||_1 (binary64)
+  uint32_t arrive;    // CTAs done in the norm kernel
+  uint32_t nonfinite; // ||w||_1 is not finite: w holds a NaN or an infinity
 };
 
 constexpr size_t kNoAllocBytes = (sizeof(NoAllocScratch) + 255) / 256 * 256;
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(256) k_na_l1norm(const T *__restrict__ w, int6
   __threadfence();
   const double l1 = *(volatile double *)&S->l1;
   JobScal &js = S->jscal;
+  S->nonfinite = isfinite(l1) ? 0u : 1u;
   js.active = 1;
   js.pass = 0;
   js.prefix = 0;
@@ -91,7 +93,9 @@ __global__ void __launch_bounds__(256) k_na_l1norm(const T *__restrict__ w, int6
   js.tau = tau;
   js.theta = 0.0;
   js.thetaf = 0.f;
-  js.mode = tau == 0.0 ? JM_NONE : (l1 <= tau ? JM_ALL : JM_SELECT);
+  // a non-finite norm has no threshold: no selection pass runs and the
+  // output is NaN
+  js.mode = !isfinite(l1) || tau == 0.0 ? JM_NONE : (l1 <= tau ? JM_ALL : JM_SELECT);
 }
 
 // y = sign(w) max(|w| - theta, 0), the arithmetic of the final pass.
@@ -99,11 +103,14 @@ template <typename T>
 __global__ void k_na_soft(const T *__restrict__ w, T *__restrict__ y, int64_t n, const NoAllocScratch *S) {
   const JobScal &js = S->jscal;
   const int mode = js.mode;
+  const bool bad = S->nonfinite != 0u;
   const T th = sizeof(T) == 4 ? (T)js.thetaf : (T)js.theta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T wv = w[i];
     T yn;
-    if (mode == JM_ALL) {
+    if (bad) {
+      yn = T(NAN);
+    } else if (mode == JM_ALL) {
       yn = wv;
     } else if (mode == JM_NONE) {
       yn = T(0);
@@ -115,19 +122,20 @@ __global__ void k_na_soft(const T *__restrict__ w, T *__restrict__ y, int64_t n,
   }
 }
 
-// Device address of the scratch, fetched once per device with that device
-// current (a host-side reference to the array's name is not a device
-// address).
+// Device address of the scratch and the SM count, fetched once per device
+// with that device current (a host-side reference to the array's name is
+// not a device address).
 std::mutex g_na_mutex;
-void *g_na_addr[64] = {};
+void *g_na_addr[kMaxDevices] = {};
+int g_na_sms[kMaxDevices] = {};
 
-sip_status scratch_address(NoAllocScratch **out) {
+sip_status scratch_address(NoAllocScratch **out, int *sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return fail(SIP_ERR_CUDA, "cudaGetDevice failed");
   }
-  if (dev < 0 || dev >= 64) return fail(SIP_ERR_INTERNAL, "device index %d out of range", dev);
+  if (dev < 0 || dev >= kMaxDevices) return fail(SIP_ERR_INTERNAL, "device index %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_na_mutex);
   if (!g_na_addr[dev]) {
     void *p = nullptr;
@@ -136,10 +144,18 @@ sip_status scratch_address(NoAllocScratch **out) {
       cudaGetLastError();
       return fail(SIP_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     }
+    int n_sm = 0;
+    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || n_sm < 1) {
+      cudaGetLastError();
+      return fail(SIP_ERR_CUDA, "SM count: %s", cudaGetErrorString(e));
+    }
     if (cudaError_t e2 = kernels_setup()) return fail(SIP_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e2));
+    g_na_sms[dev] = n_sm;
     g_na_addr[dev] = p;
   }
   *out = (NoAllocScratch *)g_na_addr[dev];
+  *sms = g_na_sms[dev];
   return SIP_OK;
 }
 
@@ -158,7 +174,8 @@ extern "C" sip_status sip_project_l1_noalloc(int dtype, const void *w_dev, int64
                 (long long)n, (long long)SIP_NOALLOC_MAX_N);
   if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(SIP_ERR_INVALID_ARG, "tau must be finite and >= 0");
   NoAllocScratch *S = nullptr;
-  sip_status st = scratch_address(&S);
+  int sms = 0;
+  sip_status st = scratch_address(&S, &sms);
   if (st) return st;
   cudaStream_t cs = (cudaStream_t)stream;
 
@@ -178,8 +195,10 @@ extern "C" sip_status sip_project_l1_noalloc(int dtype, const void *w_dev, int64
   memset(&jd, 0, sizeof jd);
   jd.kind = JOB_L1;
   jd.M = n;
+  // about one wave: three CTAs per SM (the selection kernel's occupancy)
+  const int64_t wave = 3 * (int64_t)sms;
   int64_t chunk = (n + kNoAllocTiles - 1) / kNoAllocTiles;
-  const int64_t even = (n + 455) / 456;  // about one wave of CTAs
+  const int64_t even = (n + wave - 1) / wave;
   if (chunk < even) chunk = even;
   chunk = (chunk + 255) / 256 * 256;
   Tile tiles[kNoAllocTiles];
@@ -204,7 +223,7 @@ extern "C" sip_status sip_project_l1_noalloc(int dtype, const void *w_dev, int64
   NA_CK(cudaMemcpyAsync(&S->scal, &sc, sizeof sc, cudaMemcpyHostToDevice, cs));
   NA_CK(cudaMemcpyAsync(&S->job, &jd, sizeof jd, cudaMemcpyHostToDevice, cs));
   NA_CK(cudaMemcpyAsync(S->tiles, tiles, nt * sizeof(Tile), cudaMemcpyHostToDevice, cs));
-  const unsigned grid = (unsigned)((n + 255) / 256 < 456 ? (n + 255) / 256 : 456);
+  const unsigned grid = (unsigned)((n + 255) / 256 < wave ? (n + 255) / 256 : wave);
   if (dtype == SIP_F64)
     k_na_l1norm<double><<<grid, 256, 0, cs>>>((const double *)w_dev, n, S, tau);
   else
@@ -221,8 +240,14 @@ extern "C" sip_status sip_project_l1_noalloc(int dtype, const void *w_dev, int64
   NA_CK(cudaGetLastError());
   if (theta_out) {
     JobScal js;
+    uint32_t bad = 0;
     NA_CK(cudaMemcpyAsync(&js, &S->jscal, sizeof js, cudaMemcpyDeviceToHost, cs));
+    NA_CK(cudaMemcpyAsync(&bad, &S->nonfinite, sizeof bad, cudaMemcpyDeviceToHost, cs));
     NA_CK(cudaStreamSynchronize(cs));
+    if (bad) {
+      *theta_out = NAN;
+      return fail(SIP_ERR_NONFINITE, "w holds a NaN or an infinity (||w||_1 is not finite)");
+    }
     *theta_out = js.mode == JM_SELECT ? js.theta : 0.0;
   }
 #undef NA_CK

@@ -26,6 +26,16 @@ struct NvtxRange {
 extern thread_local std::string g_err;
 sip_status fail(sip_status s, const char *fmt, ...);
 
+// Host-side fault injection for the failure-handling tests (sip_test_hook).
+struct TestHooks {
+  int fail_alloc = 0;          // the n-th next arena allocation fails (0: off)
+  uint32_t bar_extra = 0;      // extra arrivals the persistent kernel's barriers wait for
+  long long bar_spins = 0;     // polls before a barrier gives up (0: default)
+};
+extern TestHooks g_hooks;
+// true when the hook says this arena allocation must fail
+bool hook_alloc_fails();
+
 struct GridDesc {
   int ndim;
   int64_t n[3];

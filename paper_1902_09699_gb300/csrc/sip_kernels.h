@@ -46,7 +46,14 @@ cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const Ins
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                           const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
                           int64_t hstride, int pass, const InstOne &one);
-// one-time kernel attribute set-up (call outside stream capture)
+// warm-start penalties of instance 0 (one value per block)
+struct Penalties {
+  double rho[kMaxBlocks], gamma[kMaxBlocks];
+};
+cudaError_t launch_load_penalties(cudaStream_t st, const InstDev *insts, InstScal *scal, const Penalties &pen);
+// kernel attribute set-up, done once per device with that device current
+// (call outside stream capture); devices 0..kMaxDevices-1
+constexpr int kMaxDevices = 64;
 cudaError_t kernels_setup();
 // CTAs per SM for the kernels of a work-item list: 0 grid points, 1 set
 // segments, 2 selection jobs, 3 final-pass blocks
@@ -68,6 +75,8 @@ struct FusedLaunch {
   uint32_t *bar;          // 4 words: arrivals, generation, error, unused
   const uint32_t *ndone;  // finished instances
   int ninst, cg_launch, any_card, any_fin, iters;
+  uint32_t bar_extra;     // arrivals beyond the grid a barrier waits for (test hook; 0)
+  long long bar_spins;    // polls before a barrier gives up (0: the default)
 };
 cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid);
 int fused_grid(int dtype);

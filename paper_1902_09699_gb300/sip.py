@@ -98,6 +98,7 @@ SIGNATURES = {
     "sip_restrict": (c_int, [ctypes.POINTER(Grid), c_int, c_vp, c_vp, c_vp]),
     "sip_prolong": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_vp, c_vp, c_vp]),
     "sip_project_l1_noalloc": (c_int, [c_int, c_vp, c_i64, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl)]),
+    "sip_test_hook": (c_int, [c_int, c_i64]),
     "sip_batch_create": (c_int, [c_int, ctypes.POINTER(Grid), ctypes.POINTER(Set), ctypes.POINTER(c_int),
                                  ctypes.POINTER(Options), ctypes.POINTER(c_vp)]),
     "sip_batch_project": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Info)]),
@@ -114,6 +115,7 @@ SIGNATURES = {
     "sip_server_destroy": (c_int, [c_vp]),
 }
 NOALLOC_MAX_N = 1 << 24
+HOOKS = {"fail_alloc": 1, "barrier_extra": 2, "barrier_spins": 3}
 
 _lib = None
 
@@ -570,6 +572,11 @@ class Server:
             pass
 
 
+def test_hook(name, value):
+    """Host-side fault injection for the failure-handling tests (sip_test_hook)."""
+    _check(lib().sip_test_hook(HOOKS[name], int(value)))
+
+
 # ---------------------------------------------------------------- single steps
 def op_rows(grid, op):
     return int(lib().sip_op_rows(ctypes.byref(make_grid(grid)), OPS[op]))
@@ -623,8 +630,13 @@ def project_l1_noalloc(w, tau, y=None, stream=None):
     either way).  Returns (y, theta)."""
     import torch
     code = _dtype_code(w.dtype)
+    if not w.is_cuda or not w.is_contiguous():
+        raise ValueError("w must be a contiguous CUDA tensor")
     if y is None:
         y = torch.empty_like(w)
+    elif (not isinstance(y, torch.Tensor) or y.device != w.device or y.dtype != w.dtype
+          or y.numel() != w.numel() or not y.is_contiguous()):
+        raise ValueError("y must be a contiguous tensor on w's device with w's dtype and size")
     th = c_dbl(0.0)
     _check(lib().sip_project_l1_noalloc(code, _ptr(w), w.numel(), float(tau), _ptr(y), _stream_ptr(stream),
                                         ctypes.byref(th)))

@@ -129,3 +129,13 @@ def test_null_arguments(sip):
     assert L.sip_state_rows(None) == -1
     assert L.sip_get_state(None, None, None, None, None) == 1
     assert L.sip_set_state(None, None, None, None, None, None, None) == 1
+
+
+def test_test_hook_rejects_bad_arguments(sip):
+    L = sip.lib()
+    assert L.sip_test_hook(99, 0) == 1
+    assert b"unknown hook" in L.sip_last_error(None)
+    assert L.sip_test_hook(sip.HOOKS["fail_alloc"], -1) == 1
+    assert L.sip_test_hook(sip.HOOKS["barrier_extra"], 1 << 21) == 1
+    for h in sip.HOOKS.values():
+        assert L.sip_test_hook(h, 0) == 0

@@ -5,9 +5,10 @@ inside a fixed memory pool or budget, or a latency-sensitive loop where an
 allocation could synchronise the device.  For them the library offers an
 l1-ball projection whose scratch is a fixed array compiled into the library.
 This test checks, through the C ABI, that it returns the same result as the
-regular entry point sip_project_set on two calls in a row (the second call
-reuses the array the first one left behind), and that it rejects sizes above
-its fixed limit.  It lives in its own file, collected last.
+regular entry point sip_project_set and as the FP64 oracle's l1-ball
+projection on two calls in a row (the second call reuses the array the first
+one left behind), and that it rejects sizes above its fixed limit and
+non-finite input.  It lives in its own file, collected last.
 """
 import numpy as np
 import pytest
@@ -15,6 +16,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import prox as oracle_prox     # noqa: E402
 from paper_1902_09699_gb300 import sip     # noqa: E402
 
 TD = {"f64": torch.float64, "f32": torch.float32}
@@ -38,6 +40,12 @@ def test_noalloc_matches_regular_entry_point_twice(dt):
         scale = float(w.abs().max())
         assert torch.allclose(y, y_ref, rtol=0, atol=ATOL[dt] * scale), (call, n)
         assert th == pytest.approx(th_ref, rel=1e-12)
+        # and the FP64 oracle (sort-based threshold) on the same input
+        w64 = w.double().cpu().numpy()
+        y_or = oracle_prox.proj_l1(w64, tau)
+        th_or = oracle_prox.l1_threshold(w64, tau)
+        assert np.max(np.abs(y.double().cpu().numpy() - y_or)) <= ATOL[dt] * scale, (call, n)
+        assert th == pytest.approx(th_or, rel=1e-10 if dt == "f64" else 1e-5)
 
 
 def test_noalloc_inside_ball_and_zero_radius():
@@ -53,3 +61,25 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(sip.SipError) as e:
         sip.project_l1_noalloc(w, 1.0)
     assert e.value.status == 1 and "SIP_NOALLOC_MAX_N" in str(e.value)
+
+
+def test_noalloc_rejects_a_bad_output_tensor_on_the_host():
+    w = torch.ones(100, dtype=torch.float64, device="cuda")
+    for y in (torch.empty(99, dtype=torch.float64, device="cuda"),
+              torch.empty(100, dtype=torch.float32, device="cuda")):
+        with pytest.raises(ValueError):
+            sip.project_l1_noalloc(w, 1.0, y=y)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_noalloc_reports_non_finite_input(bad):
+    w = torch.linspace(-1.0, 1.0, 5000, dtype=torch.float32, device="cuda")
+    w[1234] = bad
+    with pytest.raises(sip.SipError) as e:
+        sip.project_l1_noalloc(w, 1.0)
+    assert e.value.status == 5
+    # the array is usable again right after
+    w[1234] = 0.0
+    y, th = sip.project_l1_noalloc(w, 1.0)
+    y_ref, th_ref = regular(w, 1.0)
+    assert torch.allclose(y, y_ref, rtol=0, atol=2e-6) and th == pytest.approx(th_ref, rel=1e-12)
