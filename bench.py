@@ -135,21 +135,83 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- reference arm / cpu baseline
-def oracle_sample(iters, dtype_f32=True):
-    """Time the FP64 oracle (as it stands) on the first ``iters`` iterations of
-    the workload, single-threaded, in a fresh process."""
-    code = (
-        "import sys, time, json, numpy as np; sys.path.insert(0, %r)\n"
-        "from paper_1902_09699_gb300 import workloads as W\n"
-        "from oracle import parsdmm as P\n"
-        "c = W.layered_2d(); m = c['m'].astype(np.float32).astype(np.float64) if %r else c['m']\n"
-        "o = P.options(**dict(c['opts'], max_iter=%d))\n"
-        "t = time.perf_counter(); P.parsdmm(m, c['grid'], c['sets'], o); dt = time.perf_counter() - t\n"
-        "print(json.dumps({'seconds': dt}))\n" % (ROOT, dtype_f32, iters))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
-    secs = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
-    return iters / secs, secs
+def _oracle_worker(root, seed, iters, f32_model, barrier, out):
+    """One oracle process: build its model, wait for the others, then time
+    ``iters`` iterations of the workload (single-threaded numpy)."""
+    import time as _t
+    sys.path.insert(0, root)
+    import numpy as np
+
+    from oracle import parsdmm as P
+    from paper_1902_09699_gb300 import workloads as W
+    c = W.layered_2d()
+    m = c["m"] if seed is None else W.layered(c["grid"]["n"], seed=seed)
+    if f32_model:
+        m = m.astype(np.float32).astype(np.float64)
+    o = P.options(**dict(c["opts"], max_iter=iters))
+    barrier.wait()
+    t = _t.perf_counter()
+    P.parsdmm(m, c["grid"], c["sets"], o)
+    out.put(_t.perf_counter() - t)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_sample(iters, procs=1, dtype_f32=True):
+    """Time the FP64 oracle (as it stands) on the first ``iters`` iterations
+    of the workload in ``procs`` concurrent single-threaded processes, each
+    projecting its own model (the first one the workload's); processes are
+    spawned (never forked from a process that has used the GPU) and start
+    together.  Returns (whole-host iterations/s, seconds of the slowest)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        barrier = ctx.Barrier(procs)
+        out = ctx.Queue()
+        ps = [ctx.Process(target=_oracle_worker,
+                          args=(ROOT, None if i == 0 else replica_seed(0, 100 + i), iters, dtype_f32, barrier, out))
+              for i in range(procs)]
+        for p in ps:
+            p.start()
+        secs = [out.get() for _ in ps]
+        for p in ps:
+            p.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    slowest = max(secs)
+    return procs * iters / slowest, slowest
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
@@ -158,22 +220,25 @@ def run_reference(args):
         return 0
     c = workload()
     its = 12
+    cores = host_cores()
     vals = []
     for _ in range(args.warmup):
-        oracle_sample(2)
+        oracle_sample(2, procs=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, _ = oracle_sample(its)
+        v, _ = oracle_sample(its, procs=cores)
         vals.append(v)
     wall = time.perf_counter() - t0
     v = statistics.median(vals)
-    sample = "first %d of %d iterations of the workload per step (FP64 numpy oracle, 1 thread)" % (
-        its, c["opts"]["max_iter"])
+    sample = ("first %d of %d iterations of the workload per step in each of %d concurrent single-threaded "
+              "processes, one model each (FP64 numpy oracle; CPU: %s)" % (its, c["opts"]["max_iter"], cores,
+                                                                          cpu_model()))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(c), "projections_per_s": v / c["opts"]["max_iter"],
-            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": config_dict(c, {"parallelism": "replicas" if args.gpus > 1 else "single", "exec": args.exec}),
+            "projections_per_s": v / c["opts"]["max_iter"],
+            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -235,9 +300,9 @@ def run_ours(args):
     value = job_throughput(world, its, args.steps, total_ms)
 
     # ---- accuracy of this form against the FP64 GPU loop (projections/s at 1e-4)
-    x32, _ = pr.project(models[0], None)
+    x32, info32 = pr.project(models[0], None)
     pr64 = sip.Projector(c["grid"], c["sets"], dtype="f64", exec=args.exec, **c["opts"])
-    x64, _ = pr64.project(models[0].double())
+    x64, info64 = pr64.project(models[0].double())
     rel_err = float((x32.double() - x64).norm() / x64.norm())
     # plain FP64 GPU loop throughput (one step, same workload)
     torch.cuda.synchronize()
@@ -249,6 +314,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     f64_ms = e0.elapsed_time(e1)
     pr64.close()
+    # the convex subset of the set list (the cardinality set left out): FP32
+    # against FP64 on the same model, and the FP32 throughput
+    cvx = [s_ for s_ in c["sets"] if s_["type"] != "card"]
+    pc32 = sip.Projector(c["grid"], cvx, dtype="f32", exec=args.exec, **c["opts"])
+    pc64 = sip.Projector(c["grid"], cvx, dtype="f64", exec=args.exec, **c["opts"])
+    xc32, _ = pc32.project(models[0], None)
+    xc64, _ = pc64.project(models[0].double(), None)
+    cvx_err = float((xc32.double() - xc64).norm() / xc64.norm())
+    cvx_ms = statistics.median(_timed_steps(lambda: pc32.project(models[0], x, info=False), 3, flush, st))
+    pc32.close()
+    pc64.close()
+    at_1e4 = (value / its) if rel_err <= 1e-4 else 1000.0 / f64_ms
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     hm = [m.cpu().pin_memory() for m in models]
@@ -286,16 +363,23 @@ def run_ours(args):
 
     out = None
     if rank == 0:
-        cpu_v, cpu_s = oracle_sample(args.cpu_iters)
+        cores = host_cores()
+        cpu_v, cpu_s = oracle_sample(args.cpu_iters, procs=cores)
+        cpu_v1, cpu_s1 = oracle_sample(args.cpu_iters, procs=1)
         out = {
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": config_dict(c, {"parallelism": "replicas" if world > 1 else "single", "exec": args.exec}),
             "projections_per_s": value / its,
-            "projections_per_s_at_1e-4": (value / its) if rel_err <= 1e-4 else 0.0,
+            "projections_per_s_at_1e-4": at_1e4,
+            "at_1e-4_form": args.dtype if rel_err <= 1e-4 else "f64 (the FP32 result is not within 1e-4)",
             "rel_err_vs_f64_gpu": rel_err,
             "f64_gpu_loop": {"ms_per_projection": f64_ms, "iter_per_s": its / (f64_ms / 1000.0)},
+            "r_feas": info32["r_feas"], "r_feas_f64": info64["r_feas"],
+            "convex_subset": {"sets": len(cvx), "rel_err_f32_vs_f64": cvx_err, "ms_per_projection": cvx_ms,
+                              "projections_per_s": 1000.0 / cvx_ms,
+                              "projections_per_s_at_1e-4": 1000.0 / cvx_ms if cvx_err <= 1e-4 else 0.0},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "bytes_per_iter": bpi, "pct_hbm_peak": pct_hbm, "hbm_peak_gbs": peak,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -306,9 +390,12 @@ def run_ours(args):
                     "d2h_bytes_per_step": x.numel() * x.element_size()},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
-            "cpu_baseline": {"value": cpu_v, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                             "sample": "first %d of %d iterations of the workload (FP64 numpy oracle, %.1f s)" % (
-                                 args.cpu_iters, its, cpu_s)},
+            "cpu_baseline": {"value": cpu_v, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                             "sample": "first %d of %d iterations of the workload in each of %d concurrent "
+                                       "single-threaded processes, one model each (FP64 numpy oracle, slowest "
+                                       "%.1f s)" % (args.cpu_iters, its, cores, cpu_s),
+                             "cpu_model": cpu_model(),
+                             "single_core": {"value": cpu_v1, "unit": "iter/s", "cores": 1, "seconds": cpu_s1}},
         }
         print(json.dumps(out))
     pr.close()
@@ -442,6 +529,74 @@ def run_grf3d(args):
            "clocks": clk}
     print(json.dumps(out))
     pr.close()
+    return 0
+
+
+def run_small(args):
+    """The 64 x 64 FP64 workload (bounds [2, 4], TV l1 ball 0.5 TV(m),
+    D_z x >= 0; 200 iterations, 5 CG steps, rho = 1, gamma = 1): one
+    projection at a time through the single-instance handle, and --count
+    such models (own seeds) in one batched handle; the single result is
+    compared with the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    from oracle import parsdmm as P
+    from paper_1902_09699_gb300 import sip
+    from paper_1902_09699_gb300 import workloads as W
+    c = W.small_2d()
+    its = c["opts"]["max_iter"]
+    pr = sip.Projector(c["grid"], c["sets"], dtype="f64", exec=args.exec, **c["opts"])
+    m = torch.as_tensor(c["m"], device="cuda")
+    x = torch.empty_like(m)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pr.project(m, x, info=False)
+    clocks = Clocks()
+    clocks.start()
+    step_ms = _timed_steps(lambda: pr.project(m, x, info=False), args.steps, flush, st)
+    clk = clocks.stop()
+    ms = sum(step_ms) / args.steps
+    pr.set_timing(True)
+    xg, info = pr.project(m, None)
+    kt = pr.kernel_times()
+    pr.set_timing(False)
+    bpi = pr.bytes_per_iter()
+    pr.close()
+    ref = P.parsdmm(c["m"], c["grid"], c["sets"], P.options(**c["opts"]))
+    err = float(np.linalg.norm(xg.cpu().numpy() - ref["x"]) / np.linalg.norm(ref["x"]))
+    # batched: many 64 x 64 models in one handle (one launch per phase for all)
+    models = [c["m"]] + [W.small_2d(seed=3000 + i)["m"] for i in range(args.count - 1)]
+    bp = sip.BatchProjector([(c["grid"], c["sets"])] * args.count, dtype="f64", exec=args.exec, **c["opts"])
+    mp = bp.pack(models)
+    xb = torch.empty_like(mp)
+    for _ in range(args.warmup):
+        bp.project(mp, xb, info=False)
+    bms = _timed_steps(lambda: bp.project(mp, xb, info=False), args.steps, flush, st)
+    bms_mean = sum(bms) / args.steps
+    xs, _ = bp.project(mp, None)
+    berr = float(np.linalg.norm(xs[0].cpu().numpy() - ref["x"]) / np.linalg.norm(ref["x"]))
+    bbpi = bp.bytes_per_iter()
+    bp.close()
+    peak, peak_src = peaks()
+    out = {"metric": METRIC, "value": its / (ms / 1000.0), "unit": "iter/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": c["name"], "grid": list(c["grid"]["n"]), "sets": len(c["sets"]),
+                      "iterations": its, "exec": args.exec, "l2_between_steps": "flushed (512 MB write)"},
+           "projections_per_s": 1000.0 / ms, "us_per_projection": 1000.0 * ms,
+           "rel_err_vs_oracle": err, "projections_per_s_at_1e-4": 1000.0 / ms if err <= 1e-4 else 0.0,
+           "r_feas": info["r_feas"], "r_feas_oracle": ref["r_feas"],
+           "bytes_per_iter": bpi, "pct_hbm_peak": bpi * its / (ms / 1000.0) / 1e9 / peak, "hbm_peak_gbs": peak,
+           "peak_source": peak_src,
+           "kernel_breakdown_ms_per_step": {k: v["ms"] for k, v in kt.items()},
+           "batched": {"instances": args.count, "ms_per_step": bms_mean,
+                       "projections_per_s": args.count / (bms_mean / 1000.0),
+                       "rel_err_vs_oracle_first": berr,
+                       "pct_hbm_peak": bbpi * its / (bms_mean / 1000.0) / 1e9 / peak},
+           "clocks": clk}
+    print(json.dumps(out))
     return 0
 
 
@@ -643,12 +798,13 @@ def main():
     ap.add_argument("--exec", default="auto", choices=["auto", "graph", "persistent"],
                     help="iteration execution: persistent cooperative kernel or per-phase kernels in a CUDA graph")
     ap.add_argument("--workload", default="layered",
-                    choices=["layered", "ragged", "grf3d", "serving", "lines", "dykstra", "deblur"],
-                    help="layered: 512 x 1024 five-set 2D model (default line); ragged: 512-instance batch; "
+                    choices=["layered", "small", "ragged", "grf3d", "serving", "lines", "dykstra", "deblur"],
+                    help="layered: 512 x 1024 five-set 2D model (default line); small: 64 x 64 FP64 "
+                         "three-set model, single and batched; ragged: 512-instance batch; "
                          "grf3d: 256 x 256 x 128 multilevel; serving: Poisson request stream; lines: per-row "
                          "and per-column sets; dykstra: parallel Dykstra against PARSDMM; deblur: 1100 x 1100 "
                          "data fit with a 25-pixel motion blur")
-    ap.add_argument("--count", type=int, default=512, help="ragged: instances")
+    ap.add_argument("--count", type=int, default=512, help="ragged / small: instances in the batched handle")
     ap.add_argument("--levels", type=int, default=2, help="grf3d: ML-PARSDMM levels")
     ap.add_argument("--sample", type=int, default=16, help="ragged: instances timed one at a time in FP64")
     ap.add_argument("--requests", type=int, default=64, help="serving: requests taken from the Poisson stream")
@@ -658,6 +814,8 @@ def main():
         return run_reference(args)
     if args.workload == "ragged":
         return run_ragged(args)
+    if args.workload == "small":
+        return run_small(args)
     if args.workload == "deblur":
         return run_deblur(args)
     if args.workload == "lines":
