@@ -189,10 +189,15 @@ typedef struct {
      * iteration). */
     double *trace;
     /* Execution of the iterations: SIP_EXEC_AUTO (currently the graph path),
-     * SIP_EXEC_GRAPH (one kernel per phase, replayed from a CUDA graph) or
+     * SIP_EXEC_GRAPH (one kernel per phase, replayed from a CUDA graph),
      * SIP_EXEC_PERSISTENT (one cooperative kernel for all iterations, grid
-     * barriers between phases).  Results are the same up to rounding order
-     * of the binary64 atomics. */
+     * barriers between phases) or SIP_EXEC_CLUSTER (one launch for all
+     * iterations; each instance runs on one thread-block cluster of
+     * cluster_ctas CTAs with the cluster's hardware barrier between phases,
+     * and a cluster takes the next instance when its own has stopped; for
+     * small grids, where the graph path is bound by launch latency).  Results
+     * are the same up to rounding order of the binary64 atomics.  Plans with
+     * a blur block take the graph path. */
     int exec;
     /* Top-k selections of cardinality sets (Sec. Notation: projection onto
      * {card(A x) <= k}): 1 (default) starts each iteration's selection from
@@ -201,11 +206,15 @@ typedef struct {
      * one CTA selects it there instead of the full radix passes.  0: radix
      * passes only.  The selected key, and so the result, is the same. */
     int select_window;
+    /* CTAs per cluster in SIP_EXEC_CLUSTER: 1, 2, 4, 8 or 16; 0 picks one
+     * from the instance sizes (about 8192 grid points per CTA). */
+    int cluster_ctas;
 } sip_options;
 
 #define SIP_EXEC_AUTO 0
 #define SIP_EXEC_GRAPH 1
 #define SIP_EXEC_PERSISTENT 2
+#define SIP_EXEC_CLUSTER 3
 
 typedef struct {
     int iters;          /* iterations run (finest level) */
@@ -229,7 +238,7 @@ typedef struct sip_handle sip_handle;
  * max_iter 200, cg_iters 5, cg_max 100, eps_feas 1e-3, eps_evol 1e-2,
  * check_every 5, evol_hist 5, stop 0, adapt 1, adapt_every 2, rho0 1,
  * gamma0 1.5, eps_corr 0.3, rho_ratio_max 1e3, gamma_max 1.99,
- * form ALG1, dtype F32, levels 1, select_window 1. */
+ * form ALG1, dtype F32, levels 1, select_window 1, cluster_ctas 0. */
 void sip_options_default(sip_options *opts);
 
 /* Build a projector for one grid and set list.  Validates every argument,

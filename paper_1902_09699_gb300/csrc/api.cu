@@ -205,7 +205,10 @@ static sip_status check_opts(const sip_options &o) {
   if (o.levels > 1 && (o.rho_schedule || o.gamma_schedule || o.trace))
     return fail(SIP_ERR_INVALID_ARG, "schedules and traces are single-level only");
   if (o.gamma_schedule && !o.rho_schedule) return fail(SIP_ERR_INVALID_ARG, "gamma_schedule needs rho_schedule");
-  if (o.exec < SIP_EXEC_AUTO || o.exec > SIP_EXEC_PERSISTENT) return fail(SIP_ERR_INVALID_ARG, "unknown exec mode");
+  if (o.exec < SIP_EXEC_AUTO || o.exec > SIP_EXEC_CLUSTER) return fail(SIP_ERR_INVALID_ARG, "unknown exec mode");
+  if (o.cluster_ctas != 0 && o.cluster_ctas != 1 && o.cluster_ctas != 2 && o.cluster_ctas != 4 &&
+      o.cluster_ctas != 8 && o.cluster_ctas != 16)
+    return fail(SIP_ERR_INVALID_ARG, "cluster_ctas must be 0, 1, 2, 4, 8 or 16");
   if (o.select_window != 0 && o.select_window != 1) return fail(SIP_ERR_INVALID_ARG, "select_window must be 0 or 1");
   return SIP_OK;
 }
@@ -505,6 +508,14 @@ static int64_t chunk_for(int64_t total, int64_t slots) {
   return c;
 }
 
+// CTAs per cluster for instances of up to n grid points: about 8192 points
+// per CTA, a power of two in [1, 16].
+static int cluster_ctas_for(int64_t n) {
+  int c = 1;
+  while (c < 16 && (int64_t)c * 8192 < n) c *= 2;
+  return c;
+}
+
 static int sm_count() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -552,6 +563,27 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   }
   if (cudaError_t e = kernels_setup()) return fail(SIP_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e));
   const int64_t sms = sm_count();
+  // cluster execution: each instance's work items are sized for the CTAs of
+  // one cluster (no blur blocks: their terms have no cluster-form bodies)
+  bool any_blur0 = false;
+  int64_t max_n = 0;
+  for (auto &L : insts) {
+    any_blur0 = any_blur0 || L.dev.bl_R != 0;
+    if (L.dev.N > max_n) max_n = L.dev.N;
+  }
+  const int exec_req = insts.empty() ? SIP_EXEC_GRAPH : insts[0].opts.exec;
+  P.cluster = 0;
+  P.cluster_grid = 0;
+  if (exec_req == SIP_EXEC_CLUSTER && !any_blur0) {
+    int cs = insts[0].opts.cluster_ctas;
+    if (cs <= 0) cs = cluster_ctas_for(max_n);
+    const int cap = fused_cluster_capacity(dtype, cs);
+    if (cap > 0) {
+      P.cluster = cs;
+      P.cluster_grid = cap < P.ninst ? cap : P.ninst;
+    }
+  }
+  const bool clustered = P.cluster > 0;
   const int64_t ch_n = chunk_for(tot_n, sms * launch_occupancy(dtype, 0));
   // Staged right-hand side for binary32 plans of 2D instances: the y / v
   // windows of a work item of ch rows take about 8 (rows + halo) bytes per
@@ -560,7 +592,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.rhs_smem = 0;
   bool any_blur = false;
   for (auto &L : insts) any_blur = any_blur || L.dev.bl_R != 0;
-  bool stageable = dtype == SIP_F32 && !insts.empty() && !any_blur;
+  bool stageable = dtype == SIP_F32 && !insts.empty() && !any_blur && !clustered;
   for (auto &L : insts) stageable = stageable && L.dev.ny == 1 && L.dev.N < (int64_t(1) << 31);
   for (int occ = 2; stageable && occ >= 1 && !P.rhs_smem; --occ) {
     const int64_t ch = chunk_for(tot_n, sms * occ);
@@ -589,6 +621,22 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   for (int i = 0; i < P.ninst; ++i) {
     InstLayout &L = insts[i];
     InstDev &d = L.dev;
+    // work-item sizes: one wave of the whole GPU over all instances, or, in
+    // cluster execution, this instance's rows over the cluster's CTAs
+    int64_t ci_n = ch_n, ci_set = ch_set, ci_sel = ch_sel, ci_fin = ch_fin;
+    if (clustered) {
+      int64_t rows_set = 0, rows_fin = 0, rows_sel = 0;
+      for (int sg = 0; sg < d.nseg; ++sg) rows_set += d.seg[sg].len;
+      for (int b = 0; b < d.nb; ++b) {
+        const int t = d.blk[b].type;
+        if (t == BT_L1 || t == BT_L2 || t == BT_CARD || t == BT_ANNULUS) rows_fin += d.blk[b].M;
+      }
+      for (auto &j : L.jobs) rows_sel += j.M;
+      ci_n = chunk_for(d.N, P.cluster);
+      ci_set = chunk_for(rows_set, P.cluster);
+      ci_sel = chunk_for(rows_sel, P.cluster);
+      ci_fin = chunk_for(rows_fin, P.cluster);
+    }
     d.job0 = (int32_t)njobs;
     d.njob = (int32_t)L.jobs.size();
     for (int b = 0; b < d.nb; ++b) {
@@ -600,16 +648,17 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       j.hist_off = (int64_t)(njobs++) * kBins;
       // select passes walk the job in ch_sel items; tie counts follow the
       // final pass's ch_fin items of the job's block
-      j.ntiles = (int32_t)((j.M + ch_sel - 1) / ch_sel);
+      j.ntiles = (int32_t)((j.M + ci_sel - 1) / ci_sel);
       j.tie_off = ntie;
-      ntie += (j.M + ch_fin - 1) / ch_fin;
+      ntie += (j.M + ci_fin - 1) / ci_fin;
     }
     const size_t b0 = tn.size();
     if (d.bl_R)
       push_blur_blocks(tn, i, d);
     else
-      push_tiles(tn, i, 0, d.N, ch_n);
+      push_tiles(tn, i, 0, d.N, ci_n);
     d.nt_n = (int32_t)(tn.size() - b0);
+    d.tn0 = (int32_t)b0;
     d.nt_rhs = 0;
     if (P.rhs_smem || any_blur) {
       // staged right-hand side items; in a plan with a blur block, the
@@ -621,20 +670,27 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     }
     d.nt_part = d.nt_n > d.nt_rhs ? d.nt_n : d.nt_rhs;
     const size_t b1 = tset.size();
-    for (int s = 0; s < d.nseg; ++s) push_tiles(tset, i, s, d.seg[s].len, ch_set);
+    for (int s = 0; s < d.nseg; ++s) push_tiles(tset, i, s, d.seg[s].len, ci_set);
     d.nt_set = (int32_t)(tset.size() - b1);
-    const size_t b2 = tfin.size();
+    d.tset0 = (int32_t)b1;
+    const size_t b2 = tfin.size(), bl = tline.size();
     for (int b = 0; b < d.nb; ++b) {
       const int t = d.blk[b].type;
       if (t == BT_LINE) push_tiles(tline, i, b, d.blk[b].nlines, ch_line);
       if (t == BT_L1 || t == BT_L2 || t == BT_CARD || t == BT_ANNULUS) {
-        push_tiles(tfin, i, b, d.blk[b].M, ch_fin);
+        push_tiles(tfin, i, b, d.blk[b].M, ci_fin);
         P.any_fin = true;
       }
       if (t == BT_CARD) P.any_card = true;
     }
     d.nt_fin = (int32_t)(tfin.size() - b2);
-    for (int j = 0; j < (int)L.jobs.size(); ++j) push_tiles(tsel, i, d.job0 + j, L.jobs[j].M, ch_sel);
+    d.tfin0 = (int32_t)b2;
+    d.tline0 = (int32_t)bl;
+    d.nt_line = (int32_t)(tline.size() - bl);
+    const size_t bq = tsel.size();
+    for (int j = 0; j < (int)L.jobs.size(); ++j) push_tiles(tsel, i, d.job0 + j, L.jobs[j].M, ci_sel);
+    d.tsel0 = (int32_t)bq;
+    d.nt_sel = (int32_t)(tsel.size() - bq);
     const int cgl = L.opts.cg_iters > 0 ? L.opts.cg_iters : L.opts.cg_max;
     if (cgl > P.cg_launch) P.cg_launch = cgl;
     if (L.opts.max_iter > P.max_iter) P.max_iter = L.opts.max_iter;
@@ -650,6 +706,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   // per SM) runs at half its speed
   if (P.exec == SIP_EXEC_AUTO) P.exec = SIP_EXEC_GRAPH;
   if (P.exec == SIP_EXEC_PERSISTENT && P.fused_grid <= 0) P.exec = SIP_EXEC_GRAPH;
+  if (P.exec == SIP_EXEC_CLUSTER && !clustered) P.exec = SIP_EXEC_GRAPH;
   // a blur block's terms live in their own instantiations of the
   // grid-point and set-pass kernels; the persistent kernel has none
   P.blur = false;
@@ -795,7 +852,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   memset(&P.cg_one, 0, sizeof P.cg_one);
   if (P.ninst == 1 && !P.blur) {  // a blur instance's items are blocks
     P.cg_one.d = cg_desc(P.h_insts[0]);
-    P.cg_one.chunk = ch_n;
+    P.cg_one.chunk = clustered ? chunk_for(P.h_insts[0].N, P.cluster) : ch_n;
     P.cg_one.on = 1;
   }
   P.m_own = own_m;
@@ -1057,10 +1114,47 @@ static sip_status run_persistent(Plan &P, cudaStream_t st, int iters) {
   return SIP_OK;
 }
 
+// Cluster form: one launch runs every iteration; each instance stops on its
+// own (max_iter or the stopping rule), so the host polls nothing.
+static sip_status run_cluster(Plan &P, cudaStream_t st, int iters) {
+  FusedLaunch F;
+  memset(&F, 0, sizeof F);
+  F.tn = P.d_tn;
+  F.tset = P.d_tset;
+  F.tsel = P.d_tsel;
+  F.tfin = P.d_tfin;
+  F.tline = P.d_tline;
+  F.nt_line = P.nt_line;
+  F.nt_n = P.nt_n;
+  F.nt_set = P.nt_set;
+  F.nt_sel = P.nt_sel;
+  F.nt_fin = P.nt_fin;
+  F.insts = P.d_insts;
+  F.scal = P.d_scal;
+  F.jobs = P.d_jobs;
+  F.jscal = P.d_jscal;
+  F.hcnt = P.d_hcnt;
+  F.hs1 = P.d_hs1;
+  F.hs2 = P.d_hs2;
+  F.hs3 = P.d_hs3;
+  F.hstride = (int64_t)P.njobs * kBins;
+  F.ties = P.d_ties;
+  F.bar = P.d_ctrl;
+  F.ndone = P.d_ctrl + 4;
+  F.ninst = P.ninst;
+  F.cg_launch = P.cg_launch;
+  F.any_card = P.any_card ? 1 : 0;
+  F.any_fin = P.any_fin ? 1 : 0;
+  F.iters = iters;
+  CK(launch_fused_cluster(Launch{P.dtype, st}, F, P.cluster_grid, P.cluster));
+  return SIP_OK;
+}
+
 sip_status run_iterations(Plan &P, cudaStream_t st, cudaStream_t cap, int iters, bool poll, int32_t *pinned_flag,
                           KernelTimer *tm) {
   const NvtxRange range("sip: iterations");
   if (!tm && P.exec == SIP_EXEC_PERSISTENT) return run_persistent(P, st, iters);
+  if (!tm && P.exec == SIP_EXEC_CLUSTER) return run_cluster(P, st, iters);
   const int chunk = poll ? P.check_every : (iters < 10 ? iters : 10);
   if (tm) {
     // per-kernel device time: the stamping graph, its stamps read after each replay

@@ -139,6 +139,7 @@ void sip_options_default(sip_options *o) {
   o->levels = 1;
   o->coarse_iter = 0;
   o->select_window = 1;
+  o->cluster_ctas = 0;
 }
 
 const char *sip_last_error(const sip_handle *h) {

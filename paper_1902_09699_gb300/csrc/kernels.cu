@@ -28,6 +28,7 @@
 // independent requests per thread.  Per-CTA partial sums are merged with one
 // set of binary64 atomics per CTA.
 #include <cstdint>
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -3848,6 +3849,79 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A) {
   }
 }
 
+// Cluster form of the iteration: the same phase bodies, one thread-block
+// cluster per instance.  The cluster's CTAs walk the instance's own work
+// items (rank r takes items r, r + C, ...) and meet at the cluster's
+// hardware barrier between phases instead of at a kernel boundary or a
+// software grid barrier; every phase's data stays in L2.  A cluster runs its
+// instance until the instance stops (max_iter or the stopping rule), then
+// takes the next one (cid, cid + clusters, ...).  No wait here can outlast
+// the cluster's own progress: the barrier completes once every CTA of the
+// cluster arrives, and every CTA runs the same sequence of phases.
+// The barrier's arrive has release and its wait acquire semantics at
+// cluster scope: every CTA's global writes of a phase are visible to the
+// cluster's CTAs in the next.
+__device__ __forceinline__ void cluster_phase_sync() { cooperative_groups::this_cluster().sync(); }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) k_fused_cluster(const FusedArgs A) {
+  namespace cg = cooperative_groups;
+  const cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int r = (int)cl.block_rank();
+  const int ncl = (int)(gridDim.x / C);
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int s_done;
+  for (int inst = (int)(blockIdx.x / C); inst < A.ninst; inst += ncl) {
+    const InstDev &in = A.insts[inst];
+    const int tn0 = in.tn0, tn1 = in.tn0 + in.nt_n;
+    const int ts0 = in.tset0, ts1 = in.tset0 + in.nt_set;
+    const int tq0 = in.tsel0, tq1 = in.tsel0 + in.nt_sel;
+    const int tf0 = in.tfin0, tf1 = in.tfin0 + in.nt_fin;
+    const int tl0 = in.tline0, tl1 = in.tline0 + in.nt_line;
+    bool has_card = false, has_fin = in.nt_fin > 0;
+    for (int b = 0; b < in.nb; ++b) has_card = has_card || in.blk[b].type == BT_CARD;
+    for (int it = 0; it < A.iters; ++it) {
+      for (int i = tn0 + r; i < tn1; i += C) body_rhs<T>(A.tn[i], A.insts, A.scal);
+      cluster_phase_sync();
+      for (int i = tn0 + r; i < tn1; i += C) body_cg_w0<T>(A.tn[i], A.insts, A.scal);
+      cluster_phase_sync();
+      for (int j = 0; j < A.cg_launch; ++j) {
+        for (int i = tn0 + r; i < tn1; i += C) body_cg_step<T>(A.tn[i], A.insts, A.scal, 2 + j);
+        cluster_phase_sync();
+      }
+      for (int i = ts0 + r; i < ts1; i += C) body_setpass<T>(A.tset[i], A.insts, A.scal, A.jscal, A.jobs);
+      cluster_phase_sync();
+      if (tq1 > tq0) {
+        for (int pass = 0; pass < A.npass; ++pass) {
+          for (int i = tq0 + r; i < tq1; i += C)
+            body_select<T>(A.tsel[i], A.insts, A.scal, A.jobs, A.jscal, A.hcnt, A.hs1, A.hs2, A.hs3, A.hstride, pass);
+          cluster_phase_sync();
+        }
+      }
+      if (has_card) {
+        for (int i = tf0 + r; i < tf1; i += C) body_ties<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
+        cluster_phase_sync();
+      }
+      if (tl1 > tl0) {
+        for (int i = tl0 + r; i < tl1; i += C) body_lines<T>(A.tline[i], A.insts, A.scal, smem_raw);
+        cluster_phase_sync();
+      }
+      if (has_fin) {
+        for (int i = tf0 + r; i < tf1; i += C) body_final<T>(A.tfin[i], A.insts, A.scal, A.jobs, A.jscal, A.ties);
+        cluster_phase_sync();
+      }
+      if (r == 0) body_tail(inst, A.insts, A.scal, A.jscal, A.cg_launch);
+      cluster_phase_sync();
+      // the tail's stop decision, read by every CTA after the barrier: the
+      // whole cluster leaves the instance together
+      if (threadIdx.x == 0) s_done = ld_acquire((const uint32_t *)&A.scal[inst].done) != 0u;
+      __syncthreads();
+      if (s_done) break;
+    }
+  }
+}
+
 }  // namespace sip
 
 // ==========================================================================
@@ -4207,6 +4281,16 @@ cudaError_t kernels_setup() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_lines<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem<double>());
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_cluster<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_smem<double>());
+  if (e != cudaSuccess) return e;
+  // clusters of 16 CTAs are beyond the portable limit of 8
+  e = cudaFuncSetAttribute(k_fused_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_cluster<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
   done[dev] = true;
   return cudaSuccess;
 }
@@ -4244,7 +4328,7 @@ int launch_occupancy(int dtype, int kind) {
   return best == (1 << 30) ? 1 : best;
 }
 
-cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
+static FusedArgs fused_args(const Launch &L, const FusedLaunch &F) {
   FusedArgs A;
   A.tn = F.tn;
   A.tset = F.tset;
@@ -4274,6 +4358,51 @@ cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
   A.any_card = F.any_card;
   A.any_fin = F.any_fin;
   A.iters = F.iters;
+  A.bar_expected = 0;
+  A.bar_spins = kBarrierSpins;
+  return A;
+}
+
+static cudaLaunchConfig_t cluster_config(int dtype, int clusters, int csize, cudaStream_t st,
+                                         cudaLaunchAttribute *attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * csize), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = dtype == SIP_F64 ? fused_smem<double>() : fused_smem<float>();
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+cudaError_t launch_fused_cluster(const Launch &L, const FusedLaunch &F, int clusters, int csize) {
+  const FusedArgs A = fused_args(L, F);
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config(L.dtype, clusters, csize, L.stream, attr);
+  if (L.dtype == SIP_F64) return cudaLaunchKernelEx(&cfg, k_fused_cluster<double>, A);
+  return cudaLaunchKernelEx(&cfg, k_fused_cluster<float>, A);
+}
+
+int fused_cluster_capacity(int dtype, int csize) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config(dtype, 1, csize, nullptr, attr);
+  int n = 0;
+  const cudaError_t e = dtype == SIP_F64
+                            ? cudaOccupancyMaxActiveClusters(&n, (const void *)k_fused_cluster<double>, &cfg)
+                            : cudaOccupancyMaxActiveClusters(&n, (const void *)k_fused_cluster<float>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid) {
+  FusedArgs A = fused_args(L, F);
   A.bar_expected = (uint32_t)grid + F.bar_extra;
   A.bar_spins = F.bar_spins > 0 ? F.bar_spins : kBarrierSpins;
   void *args[] = {&A};

@@ -189,6 +189,10 @@ struct InstDev {
   int64_t N;
   int32_t nb, p, alg1, nseg, njob, job0;
   int32_t nt_n, nt_set, nt_fin;
+  // this instance's first work item in each plan-wide list (lists hold the
+  // instances' items one instance after another), and its selection and
+  // per-line item counts
+  int32_t tn0, tset0, tsel0, tfin0, tline0, nt_sel, nt_line, pad_t;
   int32_t nt_rhs;            // work items of the staged right-hand side list (0: none)
   int32_t nt_part;           // per-tile partial sums per quantity: max(nt_n, nt_rhs)
   int32_t hist;              // evol_hist

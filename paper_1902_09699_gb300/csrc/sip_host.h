@@ -112,6 +112,8 @@ struct Plan {
   void *x_pack = nullptr, *m_pack = nullptr;
   int exec = SIP_EXEC_GRAPH;
   int fused_grid = 0;
+  int cluster = 0;       // CTAs per cluster in cluster execution (0: not clustered)
+  int cluster_grid = 0;  // clusters launched: min(instances, clusters resident at once)
   void release();
 };
 

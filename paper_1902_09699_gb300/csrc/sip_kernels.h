@@ -80,6 +80,11 @@ struct FusedLaunch {
 };
 cudaError_t launch_fused(const Launch &L, const FusedLaunch &F, int grid);
 int fused_grid(int dtype);
+// cluster form: `clusters` clusters of `csize` CTAs, each running whole
+// instances (all iterations) with the cluster barrier between phases
+cudaError_t launch_fused_cluster(const Launch &L, const FusedLaunch &F, int clusters, int csize);
+// clusters of csize CTAs of the cluster kernel resident at once (0: none fits)
+int fused_cluster_capacity(int dtype, int csize);
 cudaError_t launch_ties(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                         const JobDev *jobs, JobScal *jscal, uint32_t *ties, const InstOne &one);
 // Per-line sets: one CTA per work item of lines (item = block, start/len =

@@ -20,7 +20,7 @@ SET_TYPES = {"bounds": 0, "l1": 1, "l2": 2, "card": 3, "annulus": 4}
 SCOPES = {"all": 0, "z": 1, "x": 2, "y": 3}
 F64, F32 = 0, 1
 FORMS = {"alg1": 0, "direct": 1}
-EXEC = {"auto": 0, "graph": 1, "persistent": 2}
+EXEC = {"auto": 0, "graph": 1, "persistent": 2, "cluster": 3}
 STATUS = {0: "SIP_OK", 1: "SIP_ERR_INVALID_ARG", 2: "SIP_ERR_OOM", 3: "SIP_ERR_CUDA", 4: "SIP_ERR_TIMEOUT",
           5: "SIP_ERR_NONFINITE", 6: "SIP_ERR_BUDGET", 7: "SIP_ERR_INTERNAL"}
 MAX_SETS = 16
@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("eps_corr", c_dbl), ("rho_ratio_max", c_dbl), ("gamma_max", c_dbl), ("form", c_int),
                 ("dtype", c_int), ("levels", c_int), ("coarse_iter", c_int),
                 ("rho_schedule", ctypes.POINTER(c_dbl)), ("gamma_schedule", ctypes.POINTER(c_dbl)),
-                ("trace", ctypes.POINTER(c_dbl)), ("exec", c_int), ("select_window", c_int)]
+                ("trace", ctypes.POINTER(c_dbl)), ("exec", c_int), ("select_window", c_int),
+                ("cluster_ctas", c_int)]
 
 
 class Info(ctypes.Structure):

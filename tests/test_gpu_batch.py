@@ -105,3 +105,19 @@ def test_batch_rejects_bad_instance():
     with pytest.raises(sip.SipError) as e:
         sip.BatchProjector([({"n": (8, 8)}, [{"op": "I", "type": "bounds", "lo": 1.0, "hi": 0.0}])], dtype="f64")
     assert e.value.status == 1
+
+
+def test_cluster_batch_matches_oracle():
+    """A batch of uneven small instances in cluster execution (one cluster per
+    instance, a cluster taking the next instance when its own stops), FP64,
+    against the oracle instance by instance."""
+    rb = W.ragged_batch(count=6, lo=16, hi=48, seed=91)
+    opts = dict(rb["opts"], max_iter=40)
+    inst = [(it["grid"], it["sets"]) for it in rb["instances"]]
+    bp = sip.BatchProjector(inst, dtype="f64", exec="cluster", cluster_ctas=2, **opts)
+    xs, infos = bp.project([it["m"] for it in rb["instances"]])
+    bp.close()
+    for it, x, info in zip(rb["instances"], xs, infos):
+        ref = P.parsdmm(it["m"], it["grid"], it["sets"], P.options(**opts))
+        assert info["iters"] == 40
+        assert rel(x.cpu().numpy(), ref["x"]) <= 1e-10

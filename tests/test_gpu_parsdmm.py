@@ -108,7 +108,7 @@ def test_layered_replayed_schedule(dt):
     assert rel(x, ref["x"]) <= BAR[dt]
 
 
-@pytest.mark.parametrize("mode", ["graph", "persistent"])
+@pytest.mark.parametrize("mode", ["graph", "persistent", "cluster"])
 def test_execution_modes_agree_with_oracle(mode):
     # both ways of running the iterations: one kernel per phase replayed from
     # a CUDA graph, and one cooperative kernel with grid barriers
@@ -329,3 +329,37 @@ def test_full_size_fp32_tracks_fp64_while_supports_hold():
         x64, _, _ = run_gpu(c["m"], c["grid"], sets, "f64", opts)
         x32, _, _ = run_gpu(c["m"], c["grid"], sets, "f32", opts)
         assert rel(x32, x64) <= bar, (len(sets), its)
+
+
+# ---------------------------------------------------------------- cluster execution
+@pytest.mark.parametrize("ctas", [1, 4, 16])
+def test_cluster_execution_small_fp64(ctas):
+    """The 64 x 64 FP64 workload on one thread-block cluster of 1, 4 or 16
+    CTAs (all 200 iterations in one launch) against the oracle."""
+    c = W.small_2d()
+    ref = oracle_run(c["m"], c["grid"], c["sets"], c["opts"])
+    x, info, tr = run_gpu(c["m"], c["grid"], c["sets"], "f64", dict(c["opts"], exec="cluster", cluster_ctas=ctas),
+                          trace=True)
+    assert info["iters"] == 200
+    assert rel(x, ref["x"]) <= 1e-10
+    assert info["cg_steps"] == ref["cg_steps"]
+    for a, b in zip(info["r_feas"], ref["r_feas"]):
+        assert a == pytest.approx(b, rel=1e-8, abs=1e-14)
+
+
+def test_cluster_execution_stopping_rule_and_fp32():
+    """Cluster execution with the feasibility stopping rule (each instance
+    leaves the loop on its own) and in FP32 with a replayed schedule."""
+    c = layered_small((48, 64))
+    opts = dict(c["opts"], max_iter=200, stop=2, eps_feas=5e-2, exec="cluster", cluster_ctas=4)
+    ref = oracle_run(c["m"], c["grid"], c["sets"], {k: v for k, v in opts.items() if k not in ("exec", "cluster_ctas")})
+    x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", opts)
+    assert info["iters"] == ref["iters"] < 200
+    assert rel(x, ref["x"]) <= 1e-10
+    sets = [s_ for s_ in c["sets"] if s_["type"] != "card"]
+    o32 = dict(c["opts"], exec="cluster", cluster_ctas=8)
+    m = m_as(c["m"], "f32")
+    ref32 = oracle_run(m, c["grid"], sets, c["opts"])
+    rs, gs = schedules(ref32)
+    x, info, _ = run_gpu(m, c["grid"], sets, "f32", o32, rho_schedule=rs, gamma_schedule=gs)
+    assert rel(x, ref32["x"]) <= 1e-4

@@ -69,3 +69,28 @@ def test_budget_is_respected_and_oversize_requests_fail():
     st = srv.stats()
     srv.close()
     assert 0 < st["hbm_peak"] <= 64 << 20
+
+
+def test_served_results_match_the_oracle():
+    """Every served result against the FP64 oracle run alone on the same
+    request (adaptive rho, feasibility stopping rule): the same stopping
+    iteration and x within 1e-9 (the GPU's own rho trajectory follows the
+    oracle's to 1e-9)."""
+    from oracle import parsdmm as P
+    opts = dict(max_iter=150, adapt=1, gamma0=1.5, stop=2, eps_feas=1e-2)
+    g = np.random.default_rng(21)
+    pool = W.small_2d()["sets"]
+    reqs = []
+    for i in range(8):
+        n = (int(g.integers(8, 14)), int(g.integers(8, 14)), 4) if i % 4 == 3 else \
+            (int(g.integers(12, 40)), int(g.integers(12, 40)))
+        sets = [dict(pool[j]) for j in g.integers(0, len(pool), size=int(g.integers(2, 4)))]
+        reqs.append(({"n": n}, sets, W.grf(n, seed=300 + i)))
+    srv = sip.Server(dtype="f64", max_batch=4, max_cohorts=2, max_wait_ms=0.5, **opts)
+    ids = [srv.submit(gr, s, m) for gr, s, m in reqs]
+    got = [srv.wait(i) for i in ids]
+    srv.close()
+    for (gr, s, m), (x, info, lat) in zip(reqs, got):
+        ref = P.parsdmm(m, gr, s, P.options(**opts))
+        assert info["iters"] == ref["iters"]
+        assert rel(x, ref["x"]) <= 1e-9
