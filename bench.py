@@ -263,7 +263,8 @@ def run_ours(args):
 
     c = workload()
     its = c["opts"]["max_iter"]
-    pr = sip.Projector(c["grid"], c["sets"], dtype=args.dtype, exec=args.exec, cluster_ctas=args.cluster_ctas, **c["opts"])
+    pr = sip.Projector(c["grid"], c["sets"], dtype=args.dtype, exec=args.exec, cluster_ctas=args.cluster_ctas,
+                       tune=1 if args.tune else 0, **c["opts"])
     tdt = torch.float32 if args.dtype == "f32" else torch.float64
     # independent replicas: each rank projects its own models (seeded per rank)
     from paper_1902_09699_gb300 import workloads as W
@@ -386,6 +387,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": captured_traffic(dom), "peak_source": peak_src,
                          "kernel_ms_per_launch": avg_s * 1000.0},
             "kernel_breakdown_ms_per_step": {k: v["ms"] for k, v in kt.items()},
+            "plan": pr.tuning(),
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": models[0].numel() * models[0].element_size(),
                     "d2h_bytes_per_step": x.numel() * x.element_size()},
             "gpu_launches": launches_per_step * args.steps,
@@ -463,6 +465,26 @@ def run_ragged(args):
         within += e <= 1e-4
     proj_s = args.count / (ms / 1000.0)
     f64_proj_s = len(sample) / (f64_ms / 1000.0)
+    tuned = None
+    if args.tune:
+        # the same batch with plan tuning: the first projection measures the
+        # candidates (outside the timed steps), the steps run the chosen plan
+        bt = sip.BatchProjector(inst, dtype="f32", exec=args.exec, cluster_ctas=args.cluster_ctas, tune=1,
+                                **rb["opts"])
+        t_tune = time.perf_counter()
+        bt.project(mp, x, info=False)
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - t_tune
+        for _ in range(args.warmup):
+            bt.project(mp, x, info=False)
+        tms = _timed_steps(lambda: bt.project(mp, x, info=False), args.steps, flush, st)
+        knobs = bt.tuning()
+        xt, _ = bt.project(mp, None)
+        bt.close()
+        terr = [float((a.double() - b.double()).norm() / b.double().norm()) for a, b in zip(xt, xs)]
+        tuned = {"projections_per_s": args.count / (sum(tms) / args.steps / 1000.0),
+                 "ms_per_step": sum(tms) / args.steps, "first_projection_with_tuning_s": t_tune,
+                 "knobs": knobs, "max_rel_diff_vs_default_plan": max(terr)}
     bpi = bp.bytes_per_iter()
     peak, _ = peaks()
     out = {"metric": METRIC, "value": args.count * its / (ms / 1000.0), "unit": "instance-iter/s", "n_gpus": 1,
@@ -478,6 +500,9 @@ def run_ragged(args):
                               "within_1e-4": within, "sample": len(sample)},
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
            "bytes_per_iter": bpi, "pct_hbm_peak": bpi * its / (ms / 1000.0) / 1e9 / peak, "clocks": clk}
+    if tuned:
+        out["tuned"] = tuned
+        out["tuned_vs_default"] = tuned["projections_per_s"] / proj_s
     print(json.dumps(out))
     bp.close()
     return 0
@@ -833,6 +858,8 @@ def main():
                     help="iteration execution: per-phase kernels in a CUDA graph, one persistent cooperative "
                          "kernel, or one thread-block cluster per instance")
     ap.add_argument("--cluster-ctas", type=int, default=0, help="CTAs per cluster for --exec cluster (0: auto)")
+    ap.add_argument("--tune", action="store_true",
+                    help="plan tuning on the first (untimed) projection; ragged: time the default and the tuned plan")
     ap.add_argument("--workload", default="layered",
                     choices=["layered", "small", "ragged", "grf3d", "serving", "lines", "dykstra", "deblur"],
                     help="layered: 512 x 1024 five-set 2D model (default line); small: 64 x 64 FP64 "

@@ -209,6 +209,9 @@ typedef struct {
     /* CTAs per cluster in SIP_EXEC_CLUSTER: 1, 2, 4, 8 or 16; 0 picks one
      * from the instance sizes (about 8192 grid points per CTA). */
     int cluster_ctas;
+    /* 1: tune the plan on the handle's first projection (see sip_tuning);
+     * 0 (default): the built-in heuristic. */
+    int tune;
 } sip_options;
 
 #define SIP_EXEC_AUTO 0
@@ -238,7 +241,7 @@ typedef struct sip_handle sip_handle;
  * max_iter 200, cg_iters 5, cg_max 100, eps_feas 1e-3, eps_evol 1e-2,
  * check_every 5, evol_hist 5, stop 0, adapt 1, adapt_every 2, rho0 1,
  * gamma0 1.5, eps_corr 0.3, rho_ratio_max 1e3, gamma_max 1.99,
- * form ALG1, dtype F32, levels 1, select_window 1, cluster_ctas 0. */
+ * form ALG1, dtype F32, levels 1, select_window 1, cluster_ctas 0, tune 0. */
 void sip_options_default(sip_options *opts);
 
 /* Build a projector for one grid and set list.  Validates every argument,
@@ -458,6 +461,49 @@ sip_status sip_restrict(const sip_grid *fine, int dtype, const void *m_dev,
  * of `fine` to `fine` (same op), extrapolating linearly at the ends. */
 sip_status sip_prolong(const sip_grid *fine, int op, int dtype,
                        const void *uc_dev, void *uf_dev, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Plan tuning.  The paper has no counterpart (its parallelism is one
+ * thread per set, Sec. "Parallelism"); on the GPU the launch shapes decide
+ * the speed.  A plan's work items are sized so that one launch fills the
+ * GPU once at the kernel's occupancy; the knobs below scale that per launch
+ * kind (grid points: right-hand side and CG; set pass; selection passes;
+ * final pass), choose the execution form (graph or cluster) and the
+ * warm-started top-k window, and switch the staged right-hand side.  Every
+ * choice computes the same iteration; results differ only in the rounding
+ * order of sums.
+ *
+ * With sip_options.tune = 1 the handle's first projection (single-level or
+ * batched handles) measures candidate plans on its own model, a few
+ * iterations each, one knob after another (coordinate search), keeps the
+ * fastest, and records it in a process-wide cache keyed by the instances'
+ * grids, set lists and options, so later handles of the same shape start
+ * from the cached choice without measuring.
+ *
+ * sip_get_tuning reports the plan's knobs and, after tuning, the measured
+ * milliseconds per iteration of the default and of the chosen plan.
+ * sip_set_tuning rebuilds the plan with the given knobs (scales in
+ * [1/16, 16], exec SIP_EXEC_GRAPH or SIP_EXEC_CLUSTER, cluster_ctas as in
+ * sip_options, select_window and stage_rhs 0 or 1); a warm state loaded by
+ * sip_set_state is dropped.  Multilevel and parallel-Dykstra handles return
+ * SIP_ERR_INVALID_ARG.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    double scale_n, scale_set, scale_sel, scale_fin;
+    int exec;
+    int cluster_ctas;
+    int select_window;
+    int stage_rhs;
+    /* reported by sip_get_tuning (ignored by sip_set_tuning) */
+    int tuned;          /* the knobs come from a measurement (or the cache) */
+    int from_cache;     /* ... taken from the process-wide cache */
+    int candidates;     /* plans measured */
+    double ms_default;  /* ms per iteration of the default plan (measured) */
+    double ms_best;     /* ms per iteration of the chosen plan (measured) */
+} sip_tuning;
+
+sip_status sip_get_tuning(const sip_handle *h, sip_tuning *out);
+sip_status sip_set_tuning(sip_handle *h, const sip_tuning *in);
 
 /* ---------------------------------------------------------------------
  * Test hooks: host-side fault injection for the failure-handling tests.

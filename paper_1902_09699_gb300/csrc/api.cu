@@ -209,6 +209,7 @@ static sip_status check_opts(const sip_options &o) {
   if (o.cluster_ctas != 0 && o.cluster_ctas != 1 && o.cluster_ctas != 2 && o.cluster_ctas != 4 &&
       o.cluster_ctas != 8 && o.cluster_ctas != 16)
     return fail(SIP_ERR_INVALID_ARG, "cluster_ctas must be 0, 1, 2, 4, 8 or 16");
+  if (o.tune != 0 && o.tune != 1) return fail(SIP_ERR_INVALID_ARG, "tune must be 0 or 1");
   if (o.select_window != 0 && o.select_window != 1) return fail(SIP_ERR_INVALID_ARG, "select_window must be 0 or 1");
   return SIP_OK;
 }
@@ -537,7 +538,12 @@ void Plan::release() {
   arena = nullptr;
 }
 
-sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed, bool dry) {
+static double clamp_scale(double v) { return v >= 1.0 / 16 && v <= 16.0 ? v : 1.0; }
+
+void plan_tuning(const Plan &P, sip_tuning *out) { *out = P.knobs; }
+
+sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed, bool dry,
+                      const sip_tuning *tune) {
   P.dtype = dtype;
   P.ninst = (int)insts.size();
   const size_t W = esize(dtype);
@@ -571,11 +577,19 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     any_blur0 = any_blur0 || L.dev.bl_R != 0;
     if (L.dev.N > max_n) max_n = L.dev.N;
   }
-  const int exec_req = insts.empty() ? SIP_EXEC_GRAPH : insts[0].opts.exec;
+  int exec_req = insts.empty() ? SIP_EXEC_GRAPH : insts[0].opts.exec;
+  if (tune && (tune->exec == SIP_EXEC_GRAPH || tune->exec == SIP_EXEC_CLUSTER)) exec_req = tune->exec;
+  const double sc_n = tune ? clamp_scale(tune->scale_n) : 1.0, sc_set = tune ? clamp_scale(tune->scale_set) : 1.0;
+  const double sc_sel = tune ? clamp_scale(tune->scale_sel) : 1.0, sc_fin = tune ? clamp_scale(tune->scale_fin) : 1.0;
+  auto slots = [&](int kind, double scale) {
+    const double v = (double)sms * launch_occupancy(dtype, kind) * scale;
+    return (int64_t)(v < 1.0 ? 1.0 : v);
+  };
   P.cluster = 0;
   P.cluster_grid = 0;
   if (exec_req == SIP_EXEC_CLUSTER && !any_blur0) {
-    int cs = insts[0].opts.cluster_ctas;
+    int cs = (tune && tune->exec == SIP_EXEC_CLUSTER && tune->cluster_ctas > 0) ? tune->cluster_ctas
+                                                                             : insts[0].opts.cluster_ctas;
     if (cs <= 0) cs = cluster_ctas_for(max_n);
     const int cap = fused_cluster_capacity(dtype, cs);
     if (cap > 0) {
@@ -584,7 +598,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     }
   }
   const bool clustered = P.cluster > 0;
-  const int64_t ch_n = chunk_for(tot_n, sms * launch_occupancy(dtype, 0));
+  const int64_t ch_n = chunk_for(tot_n, slots(0, sc_n));
   // Staged right-hand side for binary32 plans of 2D instances: the y / v
   // windows of a work item of ch rows take about 8 (rows + halo) bytes per
   // segment; the largest work item that lets 2 (else 1) CTAs share an SM.
@@ -592,10 +606,10 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   P.rhs_smem = 0;
   bool any_blur = false;
   for (auto &L : insts) any_blur = any_blur || L.dev.bl_R != 0;
-  bool stageable = dtype == SIP_F32 && !insts.empty() && !any_blur && !clustered;
+  bool stageable = dtype == SIP_F32 && !insts.empty() && !any_blur && !clustered && !(tune && tune->stage_rhs == 0);
   for (auto &L : insts) stageable = stageable && L.dev.ny == 1 && L.dev.N < (int64_t(1) << 31);
   for (int occ = 2; stageable && occ >= 1 && !P.rhs_smem; --occ) {
-    const int64_t ch = chunk_for(tot_n, sms * occ);
+    const int64_t ch = chunk_for(tot_n, (int64_t)((double)sms * occ * sc_n > 1.0 ? (double)sms * occ * sc_n : 1.0));
     size_t need = 0;
     for (auto &L : insts) {
       size_t b = 0;
@@ -612,9 +626,9 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       ch_rhs = ch;
     }
   }
-  const int64_t ch_set = chunk_for(tot_set, sms * launch_occupancy(dtype, 1));
-  const int64_t ch_sel = chunk_for(tot_sel, sms * launch_occupancy(dtype, 2));
-  const int64_t ch_fin = chunk_for(tot_fin, sms * launch_occupancy(dtype, 3));
+  const int64_t ch_set = chunk_for(tot_set, slots(1, sc_set));
+  const int64_t ch_sel = chunk_for(tot_sel, slots(2, sc_sel));
+  const int64_t ch_fin = chunk_for(tot_fin, slots(3, sc_fin));
   // per-line sets: one line per work item (a line's radix passes are short
   // and latency-bound; more CTAs in flight beat longer CTAs in one wave)
   const int64_t ch_line = 1;
@@ -637,6 +651,7 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
       ci_sel = chunk_for(rows_sel, P.cluster);
       ci_fin = chunk_for(rows_fin, P.cluster);
     }
+    if (tune && (tune->select_window == 0 || tune->select_window == 1)) d.select_window = tune->select_window;
     d.job0 = (int32_t)njobs;
     d.njob = (int32_t)L.jobs.size();
     for (int b = 0; b < d.nb; ++b) {
@@ -706,7 +721,11 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
   // per SM) runs at half its speed
   if (P.exec == SIP_EXEC_AUTO) P.exec = SIP_EXEC_GRAPH;
   if (P.exec == SIP_EXEC_PERSISTENT && P.fused_grid <= 0) P.exec = SIP_EXEC_GRAPH;
-  if (P.exec == SIP_EXEC_CLUSTER && !clustered) P.exec = SIP_EXEC_GRAPH;
+  if (clustered)
+    P.exec = SIP_EXEC_CLUSTER;
+  else if (P.exec == SIP_EXEC_CLUSTER)
+    P.exec = SIP_EXEC_GRAPH;
+  if (tune && tune->exec == SIP_EXEC_GRAPH) P.exec = SIP_EXEC_GRAPH;
   // a blur block's terms live in their own instantiations of the
   // grid-point and set-pass kernels; the persistent kernel has none
   P.blur = false;
@@ -716,6 +735,16 @@ sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool o
     P.blur_all = P.blur_all && L.dev.bl_R != 0;
   }
   if (P.blur) P.exec = SIP_EXEC_GRAPH;
+  // the knobs this plan is built with
+  memset(&P.knobs, 0, sizeof P.knobs);
+  P.knobs.scale_n = sc_n;
+  P.knobs.scale_set = sc_set;
+  P.knobs.scale_sel = sc_sel;
+  P.knobs.scale_fin = sc_fin;
+  P.knobs.exec = P.exec;
+  P.knobs.cluster_ctas = P.cluster;
+  P.knobs.select_window = insts.empty() ? 1 : insts[0].dev.select_window;
+  P.knobs.stage_rhs = P.rhs_smem ? 1 : 0;
   P.nt_n = (int)tn.size();
   P.nt_rhs = (int)trhs.size();
   P.nt_set = (int)tset.size();

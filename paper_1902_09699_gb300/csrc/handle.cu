@@ -1,6 +1,9 @@
 // extern "C" entry points of libsip.so (declared in include/sip.h).
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +34,11 @@ struct sip_handle {
   std::vector<double> warm_rho, warm_gamma;
   KernelTimer timer;
   std::string err;
+  // the instances as built (before plan_build resolves them), for rebuilding
+  // the plan with other launch-shape knobs; single-level and batched handles
+  std::vector<InstLayout> layouts0;
+  bool tuned = false;     // the first projection's tuning has run (or was not asked for)
+  sip_tuning report;      // what tuning measured
 };
 
 namespace {
@@ -140,6 +148,7 @@ void sip_options_default(sip_options *o) {
   o->coarse_iter = 0;
   o->select_window = 1;
   o->cluster_ctas = 0;
+  o->tune = 0;
 }
 
 const char *sip_last_error(const sip_handle *h) {
@@ -171,8 +180,10 @@ sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets, cons
   };
   {
     std::vector<InstLayout> L{make_layout(grid_desc(*grid), sets, nsets, *opts)};
+    if (opts->levels == 1) h->layouts0 = L;
     if ((st = plan_build(h->lev[0], L, opts->dtype, true))) return bail(st);
   }
+  memset(&h->report, 0, sizeof h->report);
   for (int l = 1; l < opts->levels; ++l) {
     sip_options oc = *opts;
     oc.max_iter = opts->coarse_iter > 0 ? opts->coarse_iter : opts->max_iter;
@@ -252,6 +263,168 @@ static sip_status load_penalties(sip_handle *h, Plan &F, cudaStream_t st) {
     pen.gamma[b] = h->warm_gamma[b];
   }
   CKH(launch_load_penalties(st, F.d_insts, F.d_scal, pen));
+  return SIP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// plan tuning (sip_tuning): coordinate search over launch-shape knobs,
+// measured on the handle's own model, cached process-wide per shape
+// ----------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::string, sip_tuning> g_tune_cache;
+
+static bool tunable(const sip_handle *h) { return !h->layouts0.empty() && !h->dykstra && h->levels == 1; }
+
+// Everything the knobs' effect depends on: dtype, options, every instance's
+// grid and blocks.
+static std::string tune_key(const sip_handle *h) {
+  char buf[160];
+  const sip_options &o = h->opts;
+  snprintf(buf, sizeof buf, "t%d b%d f%d cg%d/%d a%d/%d w%d e%d c%d s%d;", o.dtype, h->batch, o.form, o.cg_iters,
+           o.cg_max, o.adapt, o.adapt_every, o.select_window, o.exec, o.cluster_ctas, o.stop);
+  std::string k = buf;
+  for (const InstLayout &L : h->layouts0) {
+    snprintf(buf, sizeof buf, "%lldx%lldx%lld:", (long long)L.g.n[0], (long long)L.g.n[1], (long long)L.g.n[2]);
+    k += buf;
+    for (int b = 0; b < L.dev.nb; ++b) {
+      snprintf(buf, sizeof buf, "%d.%d.%lld,", L.dev.blk[b].op, L.dev.blk[b].type, (long long)L.dev.blk[b].M);
+      k += buf;
+    }
+    k += ';';
+  }
+  return k;
+}
+
+static sip_status rebuild_plan(sip_handle *h, const sip_tuning *t) {
+  std::vector<InstLayout> L = h->layouts0;
+  h->lev[0].release();
+  h->lev[0] = Plan();
+  h->warm_next = h->warm_pen = false;
+  return plan_build(h->lev[0], L, h->opts.dtype, true, h->batch > 0, false, t);
+}
+
+// Milliseconds per iteration of a plan built with knobs t, on model m_dev:
+// the best of two timed runs of a few iterations (after one that captures
+// the graph), each from the initial state.
+static sip_status measure_plan(sip_handle *h, const sip_tuning &t, const void *m_dev, cudaStream_t st,
+                               double *ms_iter, sip_tuning *built) {
+  Plan T;
+  std::vector<InstLayout> L = h->layouts0;
+  sip_status s = plan_build(T, L, h->opts.dtype, true, h->batch > 0, false, &t);
+  if (!s && h->batch)
+    s = cudaMemcpyAsync(T.m_pack, m_dev, (size_t)T.pack_off[T.ninst] * esz(T.dtype), cudaMemcpyDeviceToDevice, st)
+            ? fail(SIP_ERR_CUDA, "model copy failed")
+            : SIP_OK;
+  else if (!s)
+    s = plan_set_m(T, 0, m_dev, st);
+  const int K = T.max_iter < 10 ? T.max_iter : 10;
+  double best = 1e300;
+  for (int rep = 0; rep < 3 && !s; ++rep) {
+    s = plan_prepare(T, st, false);
+    if (s) break;
+    if (cudaEventRecord(h->ev0, st) != cudaSuccess) s = fail(SIP_ERR_CUDA, "event record failed");
+    if (!s) s = run_iterations(T, st, h->cap, K, false, h->pinned, nullptr);
+    if (!s && cudaEventRecord(h->ev1, st) != cudaSuccess) s = fail(SIP_ERR_CUDA, "event record failed");
+    if (!s && cudaStreamSynchronize(st) != cudaSuccess) s = fail(SIP_ERR_CUDA, "tuning run failed");
+    float ms = 0.f;
+    if (!s && rep > 0 && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess && ms < best) best = ms;
+  }
+  if (built) plan_tuning(T, built);
+  T.release();
+  *ms_iter = best / (K > 0 ? K : 1);
+  return s;
+}
+
+static bool same_knobs(const sip_tuning &a, const sip_tuning &b) {
+  return a.scale_n == b.scale_n && a.scale_set == b.scale_set && a.scale_sel == b.scale_sel &&
+         a.scale_fin == b.scale_fin && a.exec == b.exec && a.cluster_ctas == b.cluster_ctas &&
+         a.select_window == b.select_window && a.stage_rhs == b.stage_rhs;
+}
+
+static sip_status tune_handle(sip_handle *h, const void *m_dev, cudaStream_t st) {
+  h->tuned = true;
+  const std::string key = tune_key(h);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      sip_tuning cur;
+      plan_tuning(h->lev[0], &cur);
+      sip_status s = same_knobs(cur, it->second) ? SIP_OK : rebuild_plan(h, &it->second);
+      h->report = it->second;
+      h->report.from_cache = 1;
+      return s;
+    }
+  }
+  sip_tuning base;
+  plan_tuning(h->lev[0], &base);
+  double ms0 = 0.0;
+  sip_status s = measure_plan(h, base, m_dev, st, &ms0, nullptr);
+  if (s) return s;
+  sip_tuning best = base;
+  double best_ms = ms0;
+  int tried = 1;
+  auto consider = [&](sip_tuning t) -> sip_status {
+    sip_tuning built;
+    double ms = 0.0;
+    sip_status e = measure_plan(h, t, m_dev, st, &ms, &built);
+    if (e) return e;
+    ++tried;
+    if (ms < 0.97 * best_ms) {  // a clear gain only: measurements carry a few % of noise
+      best = built;
+      best_ms = ms;
+    }
+    return SIP_OK;
+  };
+  // 1. execution form: the cluster form for small instances
+  int64_t max_n = 0;
+  bool blur = false, card = false;
+  for (const InstLayout &L : h->layouts0) {
+    if (L.dev.N > max_n) max_n = L.dev.N;
+    blur = blur || L.dev.bl_R != 0;
+    for (int b = 0; b < L.dev.nb; ++b) card = card || L.dev.blk[b].type == BT_CARD;
+  }
+  if (h->opts.exec == SIP_EXEC_AUTO && !blur && max_n <= 65536) {
+    for (int c : {4, 8, 16}) {
+      sip_tuning t = best;
+      t.exec = SIP_EXEC_CLUSTER;
+      t.cluster_ctas = c;
+      if ((s = consider(t))) return s;
+    }
+  }
+  // 2. work-item sizes per launch kind (graph form), 3. the top-k window,
+  // 4. the staged right-hand side
+  if (best.exec != SIP_EXEC_CLUSTER) {
+    double sip_tuning::*knob[4] = {&sip_tuning::scale_n, &sip_tuning::scale_set, &sip_tuning::scale_sel,
+                                   &sip_tuning::scale_fin};
+    for (auto k : knob) {
+      const double v0 = best.*k;
+      for (double f : {0.5, 2.0, 0.25}) {
+        sip_tuning t = best;
+        t.*k = v0 * f;
+        if ((s = consider(t))) return s;
+      }
+    }
+    if (card) {
+      sip_tuning t = best;
+      t.select_window = 1 - best.select_window;
+      if ((s = consider(t))) return s;
+    }
+    if (best.stage_rhs) {
+      sip_tuning t = best;
+      t.stage_rhs = 0;
+      if ((s = consider(t))) return s;
+    }
+  }
+  if (!same_knobs(best, base) && (s = rebuild_plan(h, &best))) return s;
+  plan_tuning(h->lev[0], &h->report);
+  h->report.tuned = 1;
+  h->report.from_cache = 0;
+  h->report.candidates = tried;
+  h->report.ms_default = ms0;
+  h->report.ms_best = best_ms;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = h->report;
   return SIP_OK;
 }
 
@@ -404,6 +577,10 @@ sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev, void *stre
   if (h->batch) return keep(h, fail(SIP_ERR_INVALID_ARG, "batched handle: use sip_batch_project"));
   if (!m_dev || !x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "m_dev / x_dev is NULL"));
   h->err.clear();
+  if (h->opts.tune && !h->tuned && tunable(h) && !h->opts.rho_schedule && !h->opts.gamma_schedule &&
+      !h->opts.trace && !h->warm_next) {
+    if (sip_status s = tune_handle(h, m_dev, (cudaStream_t)stream)) return keep(h, s);
+  }
   return keep(h, project_impl(h, m_dev, x_dev, (cudaStream_t)stream, info));
 }
 
@@ -413,6 +590,39 @@ sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev, void *stre
 static const char *kKernelNames[KT_COUNT] = {"rhs", "cg_w0", "cg_step", "setpass", "select", "ties", "final", "tail"};
 
 const char *sip_kernel_name(int i) { return (i >= 0 && i < KT_COUNT) ? kKernelNames[i] : ""; }
+
+sip_status sip_get_tuning(const sip_handle *h, sip_tuning *out) {
+  if (!h || !out) return fail(SIP_ERR_INVALID_ARG, "NULL argument");
+  *out = h->report;
+  sip_tuning k;
+  plan_tuning(h->lev[0], &k);
+  out->scale_n = k.scale_n;
+  out->scale_set = k.scale_set;
+  out->scale_sel = k.scale_sel;
+  out->scale_fin = k.scale_fin;
+  out->exec = k.exec;
+  out->cluster_ctas = k.cluster_ctas;
+  out->select_window = k.select_window;
+  out->stage_rhs = k.stage_rhs;
+  return SIP_OK;
+}
+
+sip_status sip_set_tuning(sip_handle *h, const sip_tuning *in) {
+  if (!h || !in) return fail(SIP_ERR_INVALID_ARG, "NULL argument");
+  if (!tunable(h)) return keep(h, fail(SIP_ERR_INVALID_ARG, "multilevel and parallel-Dykstra handles are not tunable"));
+  for (double v : {in->scale_n, in->scale_set, in->scale_sel, in->scale_fin})
+    if (!(v >= 1.0 / 16 && v <= 16.0)) return keep(h, fail(SIP_ERR_INVALID_ARG, "scales must lie in [1/16, 16]"));
+  if (in->exec != SIP_EXEC_GRAPH && in->exec != SIP_EXEC_CLUSTER)
+    return keep(h, fail(SIP_ERR_INVALID_ARG, "exec must be SIP_EXEC_GRAPH or SIP_EXEC_CLUSTER"));
+  if (in->exec == SIP_EXEC_CLUSTER && in->cluster_ctas != 0 && in->cluster_ctas != 1 && in->cluster_ctas != 2 &&
+      in->cluster_ctas != 4 && in->cluster_ctas != 8 && in->cluster_ctas != 16)
+    return keep(h, fail(SIP_ERR_INVALID_ARG, "cluster_ctas must be 0, 1, 2, 4, 8 or 16"));
+  if ((in->select_window != 0 && in->select_window != 1) || (in->stage_rhs != 0 && in->stage_rhs != 1))
+    return keep(h, fail(SIP_ERR_INVALID_ARG, "select_window and stage_rhs must be 0 or 1"));
+  h->tuned = true;  // the caller's knobs replace any tuning
+  memset(&h->report, 0, sizeof h->report);
+  return keep(h, rebuild_plan(h, in));
+}
 
 sip_status sip_test_hook(int hook, int64_t value) {
   if (value < 0) return fail(SIP_ERR_INVALID_ARG, "hook value must be >= 0");
@@ -666,6 +876,8 @@ sip_status sip_batch_create(int count, const sip_grid *grids, const sip_set *set
   h->opts = *opts;
   h->grid = grids[0];
   h->batch = count;
+  h->layouts0 = L;
+  memset(&h->report, 0, sizeof h->report);
   sip_status st = plan_build(h->lev[0], L, opts->dtype, true, true);
   if (st) {
     sip_destroy(h);
@@ -691,6 +903,9 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void
   if (!h || !h->batch) return fail(SIP_ERR_INVALID_ARG, "not a batched handle");
   if (!m_dev || !x_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "m_dev / x_dev is NULL"));
   h->err.clear();
+  if (h->opts.tune && !h->tuned && tunable(h)) {
+    if (sip_status s = tune_handle(h, m_dev, (cudaStream_t)stream)) return keep(h, s);
+  }
   Plan &P = h->lev[0];
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)P.pack_off[P.ninst] * esz(P.dtype);

@@ -112,6 +112,7 @@ struct Plan {
   void *x_pack = nullptr, *m_pack = nullptr;
   int exec = SIP_EXEC_GRAPH;
   int fused_grid = 0;
+  sip_tuning knobs;      // the launch-shape knobs it was built with
   int cluster = 0;       // CTAs per cluster in cluster execution (0: not clustered)
   int cluster_grid = 0;  // clusters launched: min(instances, clusters resident at once)
   void release();
@@ -126,8 +127,11 @@ sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const 
 void set_fastdiv(InstDev &d);
 InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const sip_options &o);
 double layout_bytes_per_iter(const InstLayout &L, int dtype);
+// The plan's launch-shape knobs (sip_tuning): null = the heuristic.
 sip_status plan_build(Plan &P, std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed = false,
-                      bool dry = false);
+                      bool dry = false, const sip_tuning *tune = nullptr);
+// the knobs a plan was built with (the heuristic's values when untuned)
+void plan_tuning(const Plan &P, sip_tuning *out);
 // device bytes plan_build would allocate for these instances (no allocation)
 int64_t plan_bytes(const std::vector<InstLayout> &insts, int dtype, bool own_m, bool packed);
 sip_status plan_prepare(Plan &P, cudaStream_t st, bool warm);

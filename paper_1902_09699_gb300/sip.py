@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
                 ("dtype", c_int), ("levels", c_int), ("coarse_iter", c_int),
                 ("rho_schedule", ctypes.POINTER(c_dbl)), ("gamma_schedule", ctypes.POINTER(c_dbl)),
                 ("trace", ctypes.POINTER(c_dbl)), ("exec", c_int), ("select_window", c_int),
-                ("cluster_ctas", c_int)]
+                ("cluster_ctas", c_int), ("tune", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -56,6 +56,13 @@ class Info(ctypes.Structure):
                 ("r_evol", c_dbl), ("r_feas", c_dbl * MAX_SETS), ("rho", c_dbl * (MAX_SETS + 1)),
                 ("gamma", c_dbl * (MAX_SETS + 1)), ("sigma", c_dbl * MAX_SETS), ("k", c_i64 * MAX_SETS),
                 ("ms", ctypes.c_float), ("window_hits", c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("scale_n", c_dbl), ("scale_set", c_dbl), ("scale_sel", c_dbl), ("scale_fin", c_dbl),
+                ("exec", c_int), ("cluster_ctas", c_int), ("select_window", c_int), ("stage_rhs", c_int),
+                ("tuned", c_int), ("from_cache", c_int), ("candidates", c_int), ("ms_default", c_dbl),
+                ("ms_best", c_dbl)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -100,6 +107,8 @@ SIGNATURES = {
     "sip_prolong": (c_int, [ctypes.POINTER(Grid), c_int, c_int, c_vp, c_vp, c_vp]),
     "sip_project_l1_noalloc": (c_int, [c_int, c_vp, c_i64, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl)]),
     "sip_test_hook": (c_int, [c_int, c_i64]),
+    "sip_get_tuning": (c_int, [c_vp, ctypes.POINTER(Tuning)]),
+    "sip_set_tuning": (c_int, [c_vp, ctypes.POINTER(Tuning)]),
     "sip_batch_create": (c_int, [c_int, ctypes.POINTER(Grid), ctypes.POINTER(Set), ctypes.POINTER(c_int),
                                  ctypes.POINTER(Options), ctypes.POINTER(c_vp)]),
     "sip_batch_project": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Info)]),
@@ -360,6 +369,12 @@ class Projector:
     def device_bytes(self):
         return int(lib().sip_device_bytes(self.handle))
 
+    def tuning(self):
+        return get_tuning(self.handle)
+
+    def set_tuning(self, **knobs):
+        set_tuning(self.handle, **knobs)
+
     def bytes_per_iter(self):
         return float(lib().sip_bytes_per_iter(self.handle))
 
@@ -385,6 +400,26 @@ class Projector:
             self.close()
         except Exception:
             pass
+
+
+def get_tuning(handle):
+    """The plan's launch-shape knobs and what tuning measured (sip_get_tuning)."""
+    t = Tuning()
+    _check(lib().sip_get_tuning(handle, ctypes.byref(t)), handle)
+    return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+
+def set_tuning(handle, **knobs):
+    """Rebuild the plan with the given knobs (others keep their values)."""
+    t = Tuning()
+    _check(lib().sip_get_tuning(handle, ctypes.byref(t)), handle)
+    for k, v in knobs.items():
+        if k == "exec":
+            v = EXEC[v] if isinstance(v, str) else int(v)
+        if not hasattr(t, k):
+            raise KeyError("unknown knob %r" % (k,))
+        setattr(t, k, v)
+    _check(lib().sip_set_tuning(handle, ctypes.byref(t)), handle)
 
 
 def _info_dict(inf, nsets, nblocks):
@@ -496,6 +531,12 @@ class BatchProjector:
 
     def bytes_per_iter(self):
         return float(lib().sip_bytes_per_iter(self.handle))
+
+    def tuning(self):
+        return get_tuning(self.handle)
+
+    def set_tuning(self, **knobs):
+        set_tuning(self.handle, **knobs)
 
     def close(self):
         if getattr(self, "handle", None):

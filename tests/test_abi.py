@@ -44,16 +44,18 @@ def test_header_functions_exported_and_bound(sip):
 def test_struct_layouts_match_c(sip, tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sip.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sip_grid), sizeof(sip_set),'
-                    ' sizeof(sip_options), sizeof(sip_info), offsetof(sip_options, rho0),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sip_grid),'
+                    ' sizeof(sip_set), sizeof(sip_options), sizeof(sip_info), offsetof(sip_options, rho0),'
                     ' offsetof(sip_options, trace), offsetof(sip_info, ms), sizeof(sip_server_config),'
-                    ' sizeof(sip_server_stats), offsetof(sip_server_config, max_points)); return 0;}\n')
+                    ' sizeof(sip_server_stats), offsetof(sip_server_config, max_points), sizeof(sip_tuning),'
+                    ' offsetof(sip_tuning, tuned), offsetof(sip_options, tune)); return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(sip.Grid), ctypes.sizeof(sip.Set), ctypes.sizeof(sip.Options), ctypes.sizeof(sip.Info),
             sip.Options.rho0.offset, sip.Options.trace.offset, sip.Info.ms.offset, ctypes.sizeof(sip.ServerConfig),
-            ctypes.sizeof(sip.ServerStats), sip.ServerConfig.max_points.offset]
+            ctypes.sizeof(sip.ServerStats), sip.ServerConfig.max_points.offset, ctypes.sizeof(sip.Tuning),
+            sip.Tuning.tuned.offset, sip.Options.tune.offset]
     assert got == want
 
 
