@@ -539,6 +539,26 @@ def run_grf3d(args):
     x64, _ = pr64.project(m64)
     pr64.close()
     rel_err = float((x32.double() - x64).norm() / x64.norm())
+    # BF16 storage trial: y_i, v_i and m rounded to bfloat16 at every store
+    prb = sip.Projector(c["grid"], c["sets"], dtype="f32", exec=args.exec, cluster_ctas=args.cluster_ctas,
+                        store_bf16=1, **opts)
+    prb.project(m, info=False)
+    bf_ms = _timed_steps(lambda: prb.project(m, x, info=False), 1, flush, st)[0]
+    xb, infob = prb.project(m, None)
+    prb.close()
+    # the convex sets alone (cardinality left out): the trial's own error, free
+    # of the cardinality set's binary32 conditioning
+    cvx = [s_ for s_ in c["sets"] if s_["type"] != "card"]
+    cvx_err = {}
+    for name, kw in (("f32", {}), ("bf16", {"store_bf16": 1})):
+        pc = sip.Projector(c["grid"], cvx, dtype="f32", exec=args.exec, cluster_ctas=args.cluster_ctas, **kw, **opts)
+        xc, _ = pc.project(m, None)
+        pc.close()
+        cvx_err[name] = xc
+    pc64 = sip.Projector(c["grid"], cvx, dtype="f64", exec=args.exec, cluster_ctas=args.cluster_ctas, **opts)
+    xc64, _ = pc64.project(m64, None)
+    pc64.close()
+    cvx_err = {k: float((v.double() - xc64).norm() / xc64.norm()) for k, v in cvx_err.items()}
     bpi = pr.bytes_per_iter()
     peak, _ = peaks()
     out = {"metric": METRIC, "value": its / (ms / 1000.0), "unit": "fine iter/s (coarse level included in time)",
@@ -548,9 +568,14 @@ def run_grf3d(args):
                       "iterations_per_level": its,
                       "exec": args.exec, "l2_between_steps": "flushed"},
            "projections_per_s": 1000.0 / ms, "rel_err_vs_f64_gpu": rel_err,
-           "projections_per_s_at_1e-4": 1000.0 / ms if rel_err <= 1e-4 else 0.0,
+           "projections_per_s_at_1e-4": 1000.0 / ms if rel_err <= 1e-4 else 1000.0 / f64_ms,
+           "at_1e-4_form": "f32" if rel_err <= 1e-4 else "f64 (the FP32 result is not within 1e-4)",
            "f64_gpu_loop": {"ms_per_projection": f64_ms},
            "r_feas": info["r_feas"], "bytes_per_iter_fine": bpi,
+           "bf16_storage_trial": {"rel_err_vs_f64_gpu": float((xb.double() - x64).norm() / x64.norm()),
+                                  "r_feas": infob["r_feas"], "ms_per_projection": bf_ms,
+                                  "note": "y_i, v_i and m rounded to bfloat16 at every store; arrays stay binary32"},
+           "convex_sets_rel_err_vs_f64_gpu": cvx_err,
            "clocks": clk}
     print(json.dumps(out))
     pr.close()

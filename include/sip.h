@@ -212,6 +212,14 @@ typedef struct {
     /* 1: tune the plan on the handle's first projection (see sip_tuning);
      * 0 (default): the built-in heuristic. */
     int tune;
+    /* 1 (SIP_F32 only): BF16 storage trial for m and the duals.  Every
+     * store of y_i and v_i (and their adapt-rho-gamma copies) and the model m
+     * are rounded to bfloat16 (round to nearest even), so the iteration
+     * follows exactly the numbers a BF16 storage of those arrays would hold;
+     * the arrays stay binary32 (the trial measures the accuracy, not the
+     * bandwidth).  Coarse multilevel models are restricted from the binary32
+     * model and then rounded.  Not with per-line sets or blur sets. */
+    int store_bf16;
 } sip_options;
 
 #define SIP_EXEC_AUTO 0
@@ -241,7 +249,8 @@ typedef struct sip_handle sip_handle;
  * max_iter 200, cg_iters 5, cg_max 100, eps_feas 1e-3, eps_evol 1e-2,
  * check_every 5, evol_hist 5, stop 0, adapt 1, adapt_every 2, rho0 1,
  * gamma0 1.5, eps_corr 0.3, rho_ratio_max 1e3, gamma_max 1.99,
- * form ALG1, dtype F32, levels 1, select_window 1, cluster_ctas 0, tune 0. */
+ * form ALG1, dtype F32, levels 1, select_window 1, cluster_ctas 0, tune 0,
+ * store_bf16 0. */
 void sip_options_default(sip_options *opts);
 
 /* Build a projector for one grid and set list.  Validates every argument,

@@ -210,6 +210,8 @@ static sip_status check_opts(const sip_options &o) {
       o.cluster_ctas != 8 && o.cluster_ctas != 16)
     return fail(SIP_ERR_INVALID_ARG, "cluster_ctas must be 0, 1, 2, 4, 8 or 16");
   if (o.tune != 0 && o.tune != 1) return fail(SIP_ERR_INVALID_ARG, "tune must be 0 or 1");
+  if (o.store_bf16 != 0 && o.store_bf16 != 1) return fail(SIP_ERR_INVALID_ARG, "store_bf16 must be 0 or 1");
+  if (o.store_bf16 && o.dtype != SIP_F32) return fail(SIP_ERR_INVALID_ARG, "store_bf16 needs SIP_F32");
   if (o.select_window != 0 && o.select_window != 1) return fail(SIP_ERR_INVALID_ARG, "select_window must be 0 or 1");
   return SIP_OK;
 }
@@ -227,6 +229,10 @@ sip_status validate(const sip_grid *grid, const sip_set *sets, int nsets, const 
     nblur += sets[i].op == SIP_OP_BLUR;
   }
   if (nblur > 1) return fail(SIP_ERR_INVALID_ARG, "at most one blur set per projection");
+  if (opts->store_bf16)
+    for (int i = 0; i < nsets; ++i)
+      if (sets[i].op == SIP_OP_BLUR || sets[i].scope != SIP_SCOPE_ALL)
+        return fail(SIP_ERR_INVALID_ARG, "store_bf16 is not available with blur or per-line sets");
   if (nblur && opts->levels > 1) return fail(SIP_ERR_INVALID_ARG, "a blur set runs on one level only");
   return check_opts(*opts);
 }
@@ -278,6 +284,7 @@ InstLayout make_layout(const GridDesc &g, const sip_set *sets, int nsets, const 
   d.rho_ratio_max = o.rho_ratio_max;
   d.gamma_max = o.gamma_max;
   d.select_window = o.select_window;
+  d.bf16 = o.store_bf16;
   // s^{k0} = A_i x^{k0} is recomputed from x^{k0}, which the x history ring
   // still holds when the adapt interval is shorter than the ring
   d.k0_ring = o.adapt_every < o.evol_hist ? 1 : 0;

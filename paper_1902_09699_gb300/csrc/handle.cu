@@ -149,6 +149,7 @@ void sip_options_default(sip_options *o) {
   o->select_window = 1;
   o->cluster_ctas = 0;
   o->tune = 0;
+  o->store_bf16 = 0;
 }
 
 const char *sip_last_error(const sip_handle *h) {
@@ -428,6 +429,14 @@ static sip_status tune_handle(sip_handle *h, const void *m_dev, cudaStream_t st)
   return SIP_OK;
 }
 
+// BF16 storage trial (sip_options.store_bf16): n values of a plan-owned
+// binary32 array rounded to bfloat16 in place.
+static sip_status round_bf16(const Plan &P, void *a, int64_t n, cudaStream_t st) {
+  if (P.h_insts.empty() || !P.h_insts[0].bf16) return SIP_OK;
+  CKH(launch_round_bf16(Launch{P.dtype, st}, a, n));
+  return SIP_OK;
+}
+
 static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cudaStream_t st, sip_info *info) {
   const NvtxRange range("sip_project");
   Plan &F = h->lev[0];
@@ -448,19 +457,31 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
       part_dims(h->lev[l].layouts[0].g, SEG_I, cd, stag);
       CKH(launch_restrict(L, fd, cd, l == 1 ? m_dev : h->lev[l - 1].h_insts[0].m, (void *)h->lev[l].h_insts[0].m));
     }
+    for (int l = 1; l < h->levels; ++l) {
+      const InstDev &dl = h->lev[l].h_insts[0];
+      if (sip_status s = round_bf16(h->lev[l], (void *)dl.m, dl.N, st)) return s;
+    }
     for (int l = h->levels - 1; l >= 1; --l) {
       const NvtxRange lr("sip: coarse level");
       Plan &C = h->lev[l];
       sip_status s = plan_prepare(C, st, l < h->levels - 1);
       if (!s) s = run_iterations(C, st, h->cap, C.max_iter, o.stop != 0, h->pinned, tm);
       if (!s) s = prolong_state(C, h->lev[l - 1], st);
+      if (!s) {
+        const Plan &Fl = h->lev[l - 1];
+        const int64_t M = Fl.layouts[0].Mtot;
+        s = round_bf16(Fl, Fl.h_insts[0].y, M, st);
+        if (!s) s = round_bf16(Fl, Fl.h_insts[0].v, M, st);
+      }
       if (s) return s;
     }
     sip_status s = plan_set_m(F, 0, m_dev, st);
+    if (!s) s = round_bf16(F, (void *)df.m, df.N, st);
     if (!s) s = plan_prepare(F, st, true);
     if (s) return s;
   } else {
     sip_status s = plan_set_m(F, 0, m_dev, st);
+    if (!s) s = round_bf16(F, (void *)df.m, df.N, st);
     if (s) return s;
     const int nb = df.nb;
     if (o.rho_schedule)
@@ -568,6 +589,11 @@ sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev, co
     CKH(cudaMemcpyAsync(d.v, v_dev, M * W, cudaMemcpyDeviceToDevice, st));
   else
     CKH(cudaMemsetAsync(d.v, 0, M * W, st));
+  {
+    const Plan &F0 = h->lev[0];
+    if (sip_status s2 = round_bf16(F0, d.y, (int64_t)M, st)) return keep(h, s2);
+    if (sip_status s2 = round_bf16(F0, d.v, (int64_t)M, st)) return keep(h, s2);
+  }
   h->warm_next = true;
   return SIP_OK;
 }
@@ -913,6 +939,7 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void
   auto run = [&]() -> sip_status {
     CKH(cudaEventRecord(h->ev0, st));
     CKH(cudaMemcpyAsync(P.m_pack, m_dev, bytes, cudaMemcpyDeviceToDevice, st));
+    if (sip_status s0 = round_bf16(P, P.m_pack, (int64_t)P.pack_off[P.ninst], st)) return s0;
     sip_status s = plan_prepare(P, st, false);
     if (!s) s = run_iterations(P, st, h->cap, P.max_iter, h->opts.stop != 0, h->pinned, tm);
     if (s) return s;

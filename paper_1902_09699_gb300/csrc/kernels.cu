@@ -29,6 +29,7 @@
 // set of binary64 atomics per CTA.
 #include <cstdint>
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -436,6 +437,12 @@ struct Stamp {
     if (ts && threadIdx.x == 0) atomicMin(&ts[1], ~gtimer());
   }
 };
+
+// BF16 storage trial: a value as a bfloat16 store would hold it (round to
+// nearest even); binary64 plans never round.
+__device__ __forceinline__ float rbf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ double rbf(double v) { return v; }
+__device__ __forceinline__ float4 rbf4(const float4 &a) { return make_float4(rbf(a.x), rbf(a.y), rbf(a.z), rbf(a.w)); }
 
 // Vector type of a 16-byte load, and its components by (unrolled) index.
 template <typename T> struct Vec16;
@@ -2087,6 +2094,10 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           st(k0vh, VH);
         }
         if (pointwise) {
+          if (in.bf16) {
+            YN = rbf4(YN);
+            VN = rbf4(VN);
+          }
           st(y, YN);
           st(v, VN);
           if (ad) {
@@ -2133,11 +2144,12 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           k0vh[row] = o.vh;
         }
         if (pointwise) {
-          y[row] = o.yn;
-          v[row] = o.vn;
+          const T yst = in.bf16 ? rbf(o.yn) : o.yn, vst = in.bf16 ? rbf(o.vn) : o.vn;
+          y[row] = yst;
+          v[row] = vst;
           if (ad) {
-            k0y[row] = o.yn;
-            k0v[row] = o.vn;
+            k0y[row] = yst;
+            k0v[row] = vst;
           }
         } else {
           wbuf[row] = o.w;
@@ -3020,6 +3032,10 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
             acc[2] += dv * dv;
           }
         }
+        if (in.bf16) {
+          YN = rbf4(YN);
+          VN = rbf4(VN);
+        }
         st(y, YN);
         st(v, VN);
         if (ad) {
@@ -3086,8 +3102,9 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
         }
         if (valid) {
           const T vn = rho * (yn - wv[e]);
-          y[row] = yn;
-          v[row] = vn;
+          const T yst = in.bf16 ? rbf(yn) : yn, vst = in.bf16 ? rbf(vn) : vn;
+          y[row] = yst;
+          v[row] = vst;
           if (ad) {
             if (ad_dots) {
               const A dg = (A)ky[e] - (A)yn;
@@ -3096,8 +3113,8 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
               acc[1] += dg * dg;
               acc[2] += dv * dv;
             }
-            k0y[row] = yn;
-            k0v[row] = vn;
+            k0y[row] = yst;
+            k0v[row] = vst;
           }
         }
       }
@@ -4235,6 +4252,16 @@ __global__ void k_dykstra_update(const T *__restrict__ y, T *__restrict__ v, T *
     x[g] = acc;
     for (int i = 0; i < p; ++i) v[(int64_t)i * n + g] = acc + v[(int64_t)i * n + g] - y[(int64_t)i * n + g];
   }
+}
+// BF16 storage trial: round n binary32 values in place to bfloat16.
+__global__ void k_round_bf16(float *__restrict__ a, int64_t n) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    a[g] = rbf(a[g]);
+}
+cudaError_t launch_round_bf16(const Launch &L, void *a, int64_t n) {
+  if (n <= 0 || L.dtype != SIP_F32) return cudaSuccess;
+  k_round_bf16<<<grid_for(n), 256, 0, L.stream>>>((float *)a, n);
+  return cudaGetLastError();
 }
 cudaError_t launch_dykstra_update(const Launch &L, const void *y, void *v, void *x, int p, int64_t n) {
   if (L.dtype == SIP_F64)

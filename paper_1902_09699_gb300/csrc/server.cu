@@ -343,6 +343,8 @@ sip_status sip_server_create(const sip_server_config *cfg, sip_server **out) {
   g.n[0] = g.n[1] = 2;
   g.h[0] = g.h[1] = 1.0;
   if (sip_status st = validate(&g, &s, 1, &cfg->opts)) return st;
+  if (cfg->opts.store_bf16) return fail(SIP_ERR_INVALID_ARG, "the server does not run the BF16 storage trial");
+  if (cfg->opts.tune) return fail(SIP_ERR_INVALID_ARG, "the server's cohorts are not tuned");
   sip_server *S = new (std::nothrow) sip_server();
   if (!S) return fail(SIP_ERR_OOM, "host allocation failed");
   S->cfg = *cfg;

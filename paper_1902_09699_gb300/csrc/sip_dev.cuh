@@ -206,7 +206,7 @@ struct InstDev {
   int32_t trace_w;
   int32_t select_window;     // option: warm-started window for top-k selections
   int32_t k0_ring;           // s^{k0} from x^{k0} in the history ring (adapt_every < hist), no k0s copy
-  int32_t pad_k0;
+  int32_t bf16;              // option: y_i, v_i (and their adapt copies) rounded to bfloat16 at every store
   // blurring forward operator F of a data-fit block (bl_R = 0: none):
   // radius, axis (0 z, 1 x, 2 y), samples along the axis, the block, the
   // stride of one step along the axis, and the blur table in the storage

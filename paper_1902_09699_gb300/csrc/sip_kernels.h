@@ -46,6 +46,8 @@ cudaError_t launch_setpass(const Launch &L, const Tile *tiles, int nt, const Ins
 cudaError_t launch_select(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,
                           const JobDev *jobs, JobScal *jscal, uint32_t *hcnt, double *hs1, double *hs2, double *hs3,
                           int64_t hstride, int pass, const InstOne &one);
+// BF16 storage trial: n binary32 values rounded in place to bfloat16
+cudaError_t launch_round_bf16(const Launch &L, void *a, int64_t n);
 // warm-start penalties of instance 0 (one value per block)
 struct Penalties {
   double rho[kMaxBlocks], gamma[kMaxBlocks];

@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
                 ("dtype", c_int), ("levels", c_int), ("coarse_iter", c_int),
                 ("rho_schedule", ctypes.POINTER(c_dbl)), ("gamma_schedule", ctypes.POINTER(c_dbl)),
                 ("trace", ctypes.POINTER(c_dbl)), ("exec", c_int), ("select_window", c_int),
-                ("cluster_ctas", c_int), ("tune", c_int)]
+                ("cluster_ctas", c_int), ("tune", c_int), ("store_bf16", c_int)]
 
 
 class Info(ctypes.Structure):

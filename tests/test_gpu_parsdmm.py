@@ -363,3 +363,18 @@ def test_cluster_execution_stopping_rule_and_fp32():
     rs, gs = schedules(ref32)
     x, info, _ = run_gpu(m, c["grid"], sets, "f32", o32, rho_schedule=rs, gamma_schedule=gs)
     assert rel(x, ref32["x"]) <= 1e-4
+
+
+def test_multilevel_3d_reduced_at_full_iteration_counts():
+    """The 3D four-set workload (bounds, 3D TV l1 ball, D_z x >= 0, card(D_x x)
+    at 1% of N) on a reduced 48 x 48 x 24 grid with its full iteration counts:
+    two levels, 300 coarse + 300 fine iterations, FP64, adaptive rho, against
+    the oracle.  The per-set feasibility must be the oracle's, so the r_feas a
+    full-size run ends with is the method's at that iteration count."""
+    c = W.grf_3d(n=(48, 48, 24), seed=1003)
+    opts = dict(c["opts"])
+    ref = P.ml_parsdmm(c["m"], c["grid"], c["sets"], P.options(**opts), levels=2, coarse_iter=300)
+    x, info, _ = run_gpu(c["m"], c["grid"], c["sets"], "f64", dict(opts, levels=2, coarse_iter=300))
+    assert rel(x, ref["x"]) <= 1e-9
+    for a, b in zip(info["r_feas"], ref["r_feas"]):
+        assert a == pytest.approx(b, rel=1e-6, abs=1e-12)
