@@ -2036,6 +2036,18 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   }
   if (vec) {
     if constexpr (sizeof(T) == 4) {
+      // grouped x gathers of four rows (no blur segment): 1 = identity rows
+      // or 2D x-difference rows with 16-byte aligned x (and m, x^{k0}) and
+      // n_z % 4 == 0; 2 = z-difference rows; 0 = row by row
+      int xfast = 0;
+      if (kind == SEG_I || (kind == SEG_DX && in.ny == 1 && (in.nz & 3) == 0)) {
+        uintptr_t xa = (uintptr_t)x;
+        if (type == BT_DIST) xa |= (uintptr_t)m;
+        if (xk0) xa |= (uintptr_t)xk0;
+        if ((xa & 15) == 0) xfast = 1;
+      } else if (kind == SEG_DZ) {
+        xfast = 2;
+      }
       for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4) {
         const int64_t r0 = base + (int64_t)threadIdx.x * 4;
         if (r0 >= end) continue;
@@ -2067,10 +2079,51 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           }
         }
         float sv[4], mv[4], kr[4];
+        if (full && xfast == 1) {
+          // identity rows (row = grid point) and 2D x-difference rows (row =
+          // grid point, neighbour nz further): 16-byte loads of x
+          const float4 xa = ld4(x, r0);
+          float4 sa = xa;
+          if (kind == SEG_DX) {
+            const float4 xb = ld4(x, r0 + in.nz);
+            sa = make_float4((xb.x - xa.x) * q.ih, (xb.y - xa.y) * q.ih, (xb.z - xa.z) * q.ih, (xb.w - xa.w) * q.ih);
+          }
+          float4 ma = make_float4(0.f, 0.f, 0.f, 0.f), ka = ma;
+          if (type == BT_DIST) ma = ld4(m, r0);
+          if (xk0) {
+            const float4 za = ld4(xk0, r0);
+            ka = za;
+            if (kind == SEG_DX) {
+              const float4 zb = ld4(xk0, r0 + in.nz);
+              ka = make_float4((zb.x - za.x) * q.ih, (zb.y - za.y) * q.ih, (zb.z - za.z) * q.ih,
+                               (zb.w - za.w) * q.ih);
+            }
+          }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          sv[c] = mv[c] = kr[c] = 0.f;
-          if (r0 + c < end) gather(r0 + c, sv[c], mv[c], kr[c]);
+          for (int c = 0; c < 4; ++c) {
+            sv[c] = vat(sa, c);
+            mv[c] = vat(ma, c);
+            kr[c] = vat(ka, c);
+          }
+        } else if (full && xfast == 2) {
+          // z-difference rows: one division for the four rows; a row past
+          // the end of its column moves on to the next column (grid point
+          // = row + column index)
+          const uint32_t t = fdiv((uint32_t)r0, in.fzm);
+          const int64_t iz0 = r0 - (int64_t)t * (in.nz - 1);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int64_t g = r0 + c + t + (iz0 + c >= in.nz - 1 ? 1 : 0);
+            sv[c] = (x[g + 1] - x[g]) * q.ih;
+            mv[c] = 0.f;
+            kr[c] = xk0 ? (xk0[g + 1] - xk0[g]) * q.ih : 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            sv[c] = mv[c] = kr[c] = 0.f;
+            if (r0 + c < end) gather(r0 + c, sv[c], mv[c], kr[c]);
+          }
         }
         if (xk0) KS = make_float4(kr[0], kr[1], kr[2], kr[3]);
         float4 YN, VN, W, VH;
