@@ -3523,8 +3523,8 @@ __device__ void set_coefficients(const InstDev &in, InstScal &sc) {
   double c0 = in.alg1 ? 0.0 : 1.0, cz = 0.0, cx = 0.0, cy = 0.0;
   for (int b = 0; b < in.nb; ++b) {
     const double r = sc.rho[b];
-    sc.irho[b] = 1.0 / r;
-    sc.inv1p[b] = 1.0 / (1.0 + r);
+    sc.irho[b] = __drcp_rn(r);  // = 1 / r correctly rounded, as the division
+    sc.inv1p[b] = __drcp_rn(1.0 + r);
     switch (in.blk[b].op) {
       case SIP_OP_I: c0 += r; break;
       case SIP_OP_DZ: cz += r; break;
@@ -3567,50 +3567,62 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
   const bool have_k0 = sc.have_k0 != 0;
   __shared__ double s_rho[kMaxBlocks], s_gam[kMaxBlocks], s_feas[kMaxBlocks];
 
-  // ---- phase 1: per block, lane 0 of warp b % kTailWarps (binary64 chains
-  // of different blocks run on different SM sub-partitions)
-  if (lane == 0) {
-    for (int b = wid; b < nb; b += kTailWarps) {
-      double rho_b = sc.rho[b], gam_b = sc.gamma[b];
-      const BlockDev &bd = in.blk[b];
-      const double *a = sc.acc[b];
-      if (chk && b < p) {
-        // r_feas_i (Eq. feas_stop)
-        const double s2 = a[A_S2];
-        double d = 0.0;
-        if (bd.type == BT_BOUNDS || bd.type == BT_LINE) {
-          d = sqrt(a[A_FEAS_D2]);
-        } else if (bd.type == BT_L2) {
-          // ||s - P(s)|| = ||s - d|| - sigma outside the ball (d = 0 unless a data fit)
-          const double r = bd.bv_lo >= 0 ? sqrt(a[A_FEAS_D2]) : sqrt(s2);
-          d = fmax(0.0, r - sc.sigma[b]);
-        } else if (bd.type == BT_ANNULUS) {
-          const double n = sqrt(s2);  // distance to the nearer sphere; s = 0 stays 0
-          d = n > bd.hi ? n - bd.hi : (n > 0.0 && n < bd.lo ? bd.lo - n : 0.0);
+  // ---- phase 1: per block, warp b % kTailWarps (binary64 chains of
+  // different blocks run on different SM sub-partitions).  Within the warp
+  // the two correlation tests of Algorithm adapt-rho-gamma and the
+  // feasibility run on lanes 0, 1 and 2 at once (binary64 divisions and
+  // square roots are long on this GPU), lane 0 combines them.
+  for (int b = wid; b < nb; b += kTailWarps) {
+    const BlockDev &bd = in.blk[b];
+    const double *a = sc.acc[b];
+    int ok = 0;
+    double hat = 0.0, fe = 0.0;
+    if (ad && have_k0 && lane < 2) {
+      // lane 0: dh with dvh (alpha); lane 1: dg with dv (beta)
+      const double ab = lane == 0 ? a[A_HV] : a[A_GV];
+      const double aa = lane == 0 ? a[A_HH] : a[A_GG];
+      const double bb = lane == 0 ? a[A_VHVH] : a[A_VV];
+      ok = corr(ab, aa, bb) > in.eps_corr ? 1 : 0;
+      if (ok) hat = spectral(ab, aa, bb);
+    }
+    if (chk && b < p && lane == 2) {
+      // r_feas_i (Eq. feas_stop)
+      const double s2 = a[A_S2];
+      double d = 0.0;
+      if (bd.type == BT_BOUNDS || bd.type == BT_LINE) {
+        d = sqrt(a[A_FEAS_D2]);
+      } else if (bd.type == BT_L2) {
+        // ||s - P(s)|| = ||s - d|| - sigma outside the ball (d = 0 unless a data fit)
+        const double r = bd.bv_lo >= 0 ? sqrt(a[A_FEAS_D2]) : sqrt(s2);
+        d = fmax(0.0, r - sc.sigma[b]);
+      } else if (bd.type == BT_ANNULUS) {
+        const double n = sqrt(s2);  // distance to the nearer sphere; s = 0 stays 0
+        d = n > bd.hi ? n - bd.hi : (n > 0.0 && n < bd.lo ? bd.lo - n : 0.0);
+      } else {
+        const JobScal &js = jscal[bd.job_s];
+        if (js.mode == JM_ALL) {
+          d = 0.0;
+        } else if (js.mode == JM_NONE) {
+          d = sqrt(s2);
+        } else if (bd.type == BT_L1) {
+          // s - P(s) = sign(s) min(|s|, theta)
+          d = sqrt(fmax(js.c_above * js.theta * js.theta + (s2 - js.s2_above), 0.0));
         } else {
-          const JobScal &js = jscal[bd.job_s];
-          if (js.mode == JM_ALL) {
-            d = 0.0;
-          } else if (js.mode == JM_NONE) {
-            d = sqrt(s2);
-          } else if (bd.type == BT_L1) {
-            // s - P(s) = sign(s) min(|s|, theta)
-            d = sqrt(fmax(js.c_above * js.theta * js.theta + (s2 - js.s2_above), 0.0));
-          } else {
-            // ||s - P(s)||^2 = ||s||^2 - (squares of the k kept entries)
-            d = sqrt(fmax(s2 - js.s2_above - (double)js.need * js.kval * js.kval, 0.0));
-          }
+          // ||s - P(s)||^2 = ||s||^2 - (squares of the k kept entries)
+          d = sqrt(fmax(s2 - js.s2_above - (double)js.need * js.kval * js.kval, 0.0));
         }
-        s_feas[b] = s2 > 0.0 ? d / sqrt(s2) : d;
       }
+      fe = s2 > 0.0 ? d / sqrt(s2) : d;
+    }
+    const bool aok = __shfl_sync(FULL, ok, 0) != 0, bok = __shfl_sync(FULL, ok, 1) != 0;
+    const double ah = __shfl_sync(FULL, hat, 0), bh = __shfl_sync(FULL, hat, 1);
+    fe = __shfl_sync(FULL, fe, 2);
+    if (lane == 0) {
+      double rho_b = sc.rho[b], gam_b = sc.gamma[b];
+      if (chk && b < p) s_feas[b] = fe;
       if (ad && have_k0) {
         // Algorithm adapt-rho-gamma; the first call only stores the k0
         // quantities (done by the set and final passes)
-        const double ac = corr(a[A_HV], a[A_HH], a[A_VHVH]);
-        const double bc = corr(a[A_GV], a[A_GG], a[A_VV]);
-        const bool aok = ac > in.eps_corr, bok = bc > in.eps_corr;
-        const double ah = aok ? spectral(a[A_HV], a[A_HH], a[A_VHVH]) : 0.0;
-        const double bh = bok ? spectral(a[A_GV], a[A_GG], a[A_VV]) : 0.0;
         double r, g;
         if (aok && bok) {
           r = sqrt(ah * bh);
@@ -3703,32 +3715,31 @@ __device__ __forceinline__ void body_tail(int i, const InstDev *__restrict__ ins
       rho_b = in.rho_sched[(int64_t)k * nb + b];
       if (in.gamma_sched) gam_b = in.gamma_sched[(int64_t)k * nb + b];
     }
-    // stencil coefficients of C (Eq. sys_mat), summed over the lanes
-    double c0 = 0.0, cz = 0.0, cx = 0.0, cy = 0.0;
+    // block scalars per lane; the stencil coefficients of C (Eq. sys_mat)
+    // summed by lane 0 in block order, as set_coefficients does
     if (b < nb) {
       sc.rho[b] = rho_b;
       sc.gamma[b] = gam_b;
-      sc.irho[b] = 1.0 / rho_b;
-      sc.inv1p[b] = 1.0 / (1.0 + rho_b);
+      sc.irho[b] = __drcp_rn(rho_b);  // = 1 / rho correctly rounded, as the division
+      sc.inv1p[b] = __drcp_rn(1.0 + rho_b);
       store_block_f32(sc, b);
-      switch (in.blk[b].op) {
-        case SIP_OP_I: c0 = rho_b; break;
-        case SIP_OP_DZ: cz = rho_b; break;
-        case SIP_OP_DX: cx = rho_b; break;
-        case SIP_OP_DY: cy = rho_b; break;
-        case SIP_OP_BLUR: break;  // rho_F F^T F: the blur term of the CG launches
-        default: cz = rho_b; cx = rho_b; if (in.ndim == 3) cy = rho_b; break;
-      }
+      s_rho[b] = rho_b;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      c0 += __shfl_xor_sync(FULL, c0, o);
-      cz += __shfl_xor_sync(FULL, cz, o);
-      cx += __shfl_xor_sync(FULL, cx, o);
-      cy += __shfl_xor_sync(FULL, cy, o);
-    }
+    __syncwarp();
     if (b == 0) {
-      sc.c0 = (in.alg1 ? 0.0 : 1.0) + c0;
+      double c0 = in.alg1 ? 0.0 : 1.0, cz = 0.0, cx = 0.0, cy = 0.0;
+      for (int j = 0; j < nb; ++j) {
+        const double r = s_rho[j];
+        switch (in.blk[j].op) {
+          case SIP_OP_I: c0 += r; break;
+          case SIP_OP_DZ: cz += r; break;
+          case SIP_OP_DX: cx += r; break;
+          case SIP_OP_DY: cy += r; break;
+          case SIP_OP_BLUR: break;  // rho_F F^T F: the blur term of the CG launches
+          default: cz += r; cx += r; if (in.ndim == 3) cy += r; break;
+        }
+      }
+      sc.c0 = c0;
       sc.cz = cz * in.ihz * in.ihz;
       sc.cx = cx * in.ihx * in.ihx;
       sc.cy = cy * in.ihy * in.ihy;
