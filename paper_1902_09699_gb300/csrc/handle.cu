@@ -56,6 +56,16 @@ sip_status keep(sip_handle *h, sip_status s) {
   return s;
 }
 
+// The plan's device error word after a projection (control words [2], [3],
+// [5], [6]): a bounded wait that ran out, or, in builds with index guards,
+// the first guard that failed and its index.
+sip_status device_error(const uint32_t ctrl[8]) {
+  if (ctrl[2] == (uint32_t)SIP_ERR_INTERNAL)
+    return fail(SIP_ERR_INTERNAL, "device index guard %u failed at index %lld", ctrl[3],
+                (long long)(((uint64_t)ctrl[6] << 32) | ctrl[5]));
+  return fail(SIP_ERR_TIMEOUT, "a bounded device wait ran out (a grid barrier or a bulk copy did not complete)");
+}
+
 sip_grid coarse_of(const sip_grid &g) {
   sip_grid c = g;
   for (int a = 0; a < g.ndim; ++a) {
@@ -503,7 +513,7 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
   uint32_t ctrl[8];
   CKH(cudaMemcpy(ctrl, F.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
   if (ctrl[2] != 0)
-    return fail(SIP_ERR_TIMEOUT, "a bounded device wait ran out (a grid barrier or a bulk copy did not complete)");
+    return device_error(ctrl);
   InstScal sc;
   CKH(cudaMemcpy(&sc, F.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
   if (o.trace) CKH(cudaMemcpy(o.trace, df.trace, (size_t)o.max_iter * df.trace_w * 8, cudaMemcpyDeviceToHost));
@@ -950,7 +960,7 @@ sip_status sip_batch_project(sip_handle *h, const void *m_dev, void *x_dev, void
     uint32_t ctrl[8];
     CKH(cudaMemcpy(ctrl, P.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
     if (ctrl[2] != 0)
-      return fail(SIP_ERR_TIMEOUT, "a bounded device wait ran out (a grid barrier or a bulk copy did not complete)");
+      return device_error(ctrl);
     if (!infos) return SIP_OK;
     std::vector<InstScal> sc(P.ninst);
     CKH(cudaMemcpy(sc.data(), P.d_scal, P.ninst * sizeof(InstScal), cudaMemcpyDeviceToHost));
@@ -1052,7 +1062,7 @@ sip_status sip_dykstra_project(sip_handle *h, const void *m_dev, void *x_dev, in
     uint32_t ctrl[8];
     CKH(cudaMemcpy(ctrl, P.d_ctrl, sizeof ctrl, cudaMemcpyDeviceToHost));
     if (ctrl[2] != 0)
-      return fail(SIP_ERR_TIMEOUT, "a bounded device wait ran out (a grid barrier or a bulk copy did not complete)");
+      return device_error(ctrl);
     if (info) cudaEventElapsedTime(&info->ms, h->ev0, h->ev1);
     return SIP_OK;
   };

@@ -648,6 +648,7 @@ __device__ __forceinline__ void body_rhs(const Tile &tl, const InstDev *__restri
                                          InstScal *__restrict__ scal) {
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= in.N, 1u, tl.start + tl.len);
   if (in.N <= (int64_t)0x7fffffff)
     body_rhs_t<T, int, BL>(tl, in, sc);
   else
@@ -742,6 +743,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rhs_tma(const Tile *__restrict_
   const Tile tl = tiles[blockIdx.x];
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= in.N, 1u, tl.start + tl.len);
   const int done = sc.done;
   const float *__restrict__ x = (const float *)in.x;
   const float *__restrict__ m = (const float *)in.m;
@@ -920,6 +922,7 @@ template <typename T, typename D>
 __device__ __forceinline__ void body_cg_w0_in(const Tile &tl, const D &in, InstScal &sc) {
   SIP_STEP_CONSTANTS;
   using A = typename AccOf<T>::type;
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= in.N, 2u, tl.start + tl.len);
   const int done = sc.done;
   if constexpr (sizeof(T) == 4) {
     if ((in.nz & 3) == 0 && in.ny == 1 && (((uintptr_t)in.cr[0] | (uintptr_t)in.cw[0]) & 15) == 0) {
@@ -1199,6 +1202,7 @@ __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const D &in, Ins
 template <typename T, typename D>
 __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, InstScal &sc, int ph) {
   using A = typename AccOf<T>::type;
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= in.N, 3u, tl.start + tl.len);
   constexpr int PT = sizeof(T) == 4 ? 2 : 1;  // 3 stencils per row: keep the register budget
   constexpr int SUB = kThreads * PT;
   if constexpr (sizeof(T) == 4) {
@@ -1926,6 +1930,8 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   using A = typename AccOf<T>::type;
   const int b = sg.block;
   const BlockDev &bd = in.blk[b];
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= sg.len && sg.row0 + sg.len <= bd.M, 4u,
+                 sg.row0 + tl.start + tl.len);
   SetpassScal<T> q;
   q.rho = SV<T>::blk(sc, b, BF_RHO);
   q.irho = SV<T>::blk(sc, b, BF_IRHO);
@@ -2008,7 +2014,8 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   // from the ring, s^{k0}
   auto gather = [&](int64_t row, T &sv, T &mv, T &kv0) {
     int64_t off;
-    const int64_t g = seg_base(in, kind, row, off);
+    int64_t g = seg_base(in, kind, row, off);
+    if (!SIP_GUARD_IDX(in.err, g >= 0 && g + off >= 0 && g < in.N && g + off < in.N, 5u, g)) g = off = 0;
     const T x0 = x[g];
     sv = kind == SEG_I ? x0 : (x[g + off] - x0) * q.ih;
     mv = type == BT_DIST ? m[g] : T(0);
@@ -2079,7 +2086,8 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           }
         }
         float sv[4], mv[4], kr[4];
-        if (full && xfast == 1) {
+        if (full && xfast == 1 &&
+            SIP_GUARD_IDX(in.err, r0 >= 0 && r0 + 4 + (kind == SEG_DX ? in.nz : 0) <= in.N, 6u, r0)) {
           // identity rows (row = grid point) and 2D x-difference rows (row =
           // grid point, neighbour nz further): 16-byte loads of x
           const float4 xa = ld4(x, r0);
@@ -2113,7 +2121,8 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
           const int64_t iz0 = r0 - (int64_t)t * (in.nz - 1);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const int64_t g = r0 + c + t + (iz0 + c >= in.nz - 1 ? 1 : 0);
+            int64_t g = r0 + c + t + (iz0 + c >= in.nz - 1 ? 1 : 0);
+            if (!SIP_GUARD_IDX(in.err, g >= 0 && g + 1 < in.N, 6u, g)) g = 0;
             sv[c] = (x[g + 1] - x[g]) * q.ih;
             mv[c] = 0.f;
             kr[c] = xk0 ? (xk0[g + 1] - xk0[g]) * q.ih : 0.f;
@@ -2731,6 +2740,7 @@ __device__ __forceinline__ void body_select(const Tile &tl, const InstDev *__res
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   JobScal &js = jscal[tl.item];
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= jd.M, 7u, tl.start + tl.len);
   // Histograms: with hstride > 0, pass p uses buffer p % 3 and the job's
   // CTAs clear, one slice each, the buffer of pass p - 1 (whether or not
   // the job selects in this pass), so every buffer is zero before its next
@@ -2935,6 +2945,7 @@ __device__ __forceinline__ void body_ties(const Tile &tl, const InstDev *__restr
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
   const BlockDev &bd = in.blk[tl.item];
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= bd.M, 8u, tl.start + tl.len);
   if (sc.done || bd.type != BT_CARD) return;
   const JobScal &js = jscal[bd.job_w];
   if (js.mode != JM_SELECT || !js.tie_needed) return;
@@ -2984,6 +2995,7 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   if (sc.done) return;
   const int b = tl.item;
   const BlockDev &bd = in.blk[b];
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= bd.M, 9u, tl.start + tl.len);
   const int k = sc.k;
   const bool ad = adapt_iter(in, k);
   const bool ad_dots = ad && sc.have_k0;
@@ -3476,6 +3488,7 @@ __device__ __forceinline__ void body_lines(const Tile &tl, const InstDev *__rest
   if (sc.done) return;
   const int b = tl.item;
   const BlockDev &bd = in.blk[b];
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= bd.nlines, 10u, tl.start + tl.len);
   const int k = sc.k;
   const bool ad = adapt_iter(in, k);
   const bool ad_dots = ad && sc.have_k0;

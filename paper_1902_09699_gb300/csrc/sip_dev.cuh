@@ -242,6 +242,7 @@ struct CgDesc {
   int32_t nz, nx, ny, cg_iters, cg_max, nt_part;
   FastDiv fz, fx;
   int64_t N;
+  uint32_t *err;  // the plan's device error word (index guards of debug builds)
   void *x, *cp, *cgp;
   void *cr[2], *cw[2], *cs[2];
   int32_t bl_R, bl_axis, bl_n, bl_blk;
@@ -265,6 +266,7 @@ inline CgDesc cg_desc(const InstDev &in) {
   d.fz = in.fz;
   d.fx = in.fx;
   d.N = in.N;
+  d.err = in.err;
   d.x = in.x;
   d.cp = in.cp;
   d.cgp = in.cgp;
@@ -344,5 +346,38 @@ template <> struct KeyOf<double> {
 };
 
 template <typename T> constexpr int num_passes() { return (KeyOf<T>::kBits + kDigitBits - 1) / kDigitBits; }
+
+// Index guards of debug builds (compiled with -DSIP_GUARDS, the library
+// libsip_guarded.so): a work item or an index outside its array records
+// SIP_ERR_INTERNAL in the plan's error word (err[0]), the number of the
+// check (err[1]) and the offending index (err[3], err[4]: low and high
+// words), and the access is skipped; the host reports it after the
+// projection.  Release builds compile the guards away.
+#if defined(__CUDACC__) && defined(SIP_GUARDS)
+static __device__ __noinline__ void guard_fail(uint32_t *err, uint32_t check, int64_t idx) {
+  if (err && atomicCAS(err, 0u, (uint32_t)SIP_ERR_INTERNAL) == 0u) {
+    err[1] = check;
+    err[3] = (uint32_t)((uint64_t)idx & 0xffffffffu);
+    err[4] = (uint32_t)((uint64_t)idx >> 32);
+    __threadfence();
+  }
+}
+// a CTA-uniform check at a work item's start: the whole CTA leaves the item
+#define SIP_GUARD_TILE(ERR, OK, CHECK, IDX)                                  \
+  do {                                                                       \
+    if (!(OK)) {                                                             \
+      if (threadIdx.x == 0) ::sip::guard_fail((ERR), (CHECK), (int64_t)(IDX)); \
+      return;                                                                \
+    }                                                                        \
+  } while (0)
+// a per-thread check of one index: false (after recording) when it fails
+#define SIP_GUARD_IDX(ERR, OK, CHECK, IDX) \
+  ((OK) ? true : (::sip::guard_fail((ERR), (CHECK), (int64_t)(IDX)), false))
+#else
+#define SIP_GUARD_TILE(ERR, OK, CHECK, IDX) \
+  do {                                      \
+  } while (0)
+#define SIP_GUARD_IDX(ERR, OK, CHECK, IDX) true
+#endif
 
 }  // namespace sip

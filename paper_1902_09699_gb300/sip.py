@@ -12,7 +12,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsip.so")
+# SIP_GUARDS=1 selects the debug build whose kernels check their work items
+# and indices (a failed check makes the call return SIP_ERR_INTERNAL)
+LIB_PATH = os.path.join(_HERE, "libsip_guarded.so" if os.environ.get("SIP_GUARDS") == "1" else "libsip.so")
 
 OPS = {"I": 0, "DZ": 1, "DX": 2, "DY": 3, "TV": 4, "BLUR": 5}
 BLUR_AXES = {"z": 0, "x": 1, "y": 2}

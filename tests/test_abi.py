@@ -141,3 +141,12 @@ def test_test_hook_rejects_bad_arguments(sip):
     assert L.sip_test_hook(sip.HOOKS["barrier_extra"], 1 << 21) == 1
     for h in sip.HOOKS.values():
         assert L.sip_test_hook(h, 0) == 0
+
+
+def test_guard_macros_compile_away_in_release_and_on_in_debug():
+    """The index guards exist only in the debug build: the release kernels
+    source compiles the macros to nothing, the guarded one to checks."""
+    src = open(os.path.join(ROOT, "paper_1902_09699_gb300", "csrc", "sip_dev.cuh")).read()
+    assert "#if defined(__CUDACC__) && defined(SIP_GUARDS)" in src
+    k = open(os.path.join(ROOT, "paper_1902_09699_gb300", "csrc", "kernels.cu")).read()
+    assert k.count("SIP_GUARD_TILE(") >= 9 and k.count("SIP_GUARD_IDX(") >= 3
