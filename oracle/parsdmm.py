@@ -237,7 +237,8 @@ def _blocks(grid, sets, form):
 
 
 def parsdmm(m, grid, sets, opts=None, init=None, rho_schedule=None,
-            gamma_schedule=None, resolve=True, init_rho=None, init_gamma=None):
+            gamma_schedule=None, resolve=True, init_rho=None, init_gamma=None,
+            init_k0=None):
     """Project m onto the intersection of {x : A_i x in C_i}, Algorithm
     PARSDMM with the iterations of Eq. SDMM_adaptive.
 
@@ -266,8 +267,13 @@ def parsdmm(m, grid, sets, opts=None, init=None, rho_schedule=None,
     ``init_gamma`` (one value per block) replace rho0 / gamma0 as the
     starting values of a warm start that carries the penalties over
     (reading: adapt-rho-gamma then proceeds from them as from rho0).
+    ``init_k0`` (one (vhat, v, s, y) tuple per block, as returned in ``k0``)
+    gives the quantities Algorithm adapt-rho-gamma saved at its last call
+    ("save for next call"), so that the first call of this run forms its
+    differences against them instead of only saving.
     Returns a dict with x, y, v, rho, gamma, iters, cg_steps, stop_reason,
-    r_feas, r_evol and a per-iteration ``trace``.
+    r_feas, r_evol, k0 (the saved quantities at the end) and a per-iteration
+    ``trace``.
     """
     o = options() if opts is None else dict(opts)
     m = np.asarray(m, dtype=np.float64).reshape(-1)
@@ -293,6 +299,11 @@ def parsdmm(m, grid, sets, opts=None, init=None, rho_schedule=None,
     if rho.shape != (nb,) or gamma.shape != (nb,):
         raise ValueError("init_rho / init_gamma need one value per block")
     k0 = [None] * nb              # saved (vhat, v, s, y) of the last adapt call
+    if init_k0 is not None:
+        if len(init_k0) != nb:
+            raise ValueError("init_k0 needs one tuple per block")
+        k0 = [None if t is None else tuple(np.array(a, dtype=np.float64).reshape(-1) for a in t)
+              for t in init_k0]
     history = []                  # previous iterates for Eq. obj_stop
     trace = []
     cg_total = 0
@@ -385,7 +396,7 @@ def parsdmm(m, grid, sets, opts=None, init=None, rho_schedule=None,
 
     return dict(x=x, y=y, v=v, rho=rho, gamma=gamma, iters=it,
                 cg_steps=cg_total, stop_reason=stop_reason, r_feas=r_feas,
-                r_evol=r_evol, trace=trace, sets=rsets, blocks=blocks)
+                r_evol=r_evol, trace=trace, sets=rsets, blocks=blocks, k0=k0)
 
 
 # --------------------------------------------------------------------------

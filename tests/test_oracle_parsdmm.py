@@ -564,3 +564,27 @@ def test_warm_start_from_the_fixed_point_stays_there():
     assert rel(again["x"], conv["x"]) < 1e-9
     cold = P.parsdmm(m, GRID, sets, P.options(max_iter=20, adapt=0, rho0=1.0, gamma0=1.5))
     assert rel(cold["x"], conv["x"]) > 1e-6   # 20 cold iterations are not there yet
+
+
+def test_warm_start_with_adapt_state_continues_the_run():
+    """A run of 2K iterations equals K iterations followed by a warm start
+    that carries x, y_i, v_i, rho_i, gamma_i and the quantities Algorithm
+    adapt-rho-gamma saved at its last call (K even: the continued run's adapt
+    calls fall on the same iterations).  Without the saved quantities the
+    continuation differs (its first call only saves)."""
+    grid = {"n": (9, 7)}
+    m = model(grid, seed=4)
+    sets = [{"op": "I", "type": "bounds", "lo": 2.0, "hi": 4.0},
+            {"op": "TV", "type": "l1", "sigma_rel": 0.4},
+            {"op": "DZ", "type": "bounds", "lo": 0.0, "hi": math.inf}]
+    o = P.options(max_iter=60, adapt=2, adapt_every=2, rho0=1.0, gamma0=1.5)
+    full = P.parsdmm(m, grid, sets, o)
+    half = P.parsdmm(m, grid, sets, dict(o, max_iter=30))
+    init = (half["x"], half["y"], half["v"])
+    cont = P.parsdmm(m, grid, sets, dict(o, max_iter=30), init=init, init_rho=half["rho"],
+                     init_gamma=half["gamma"], init_k0=half["k0"])
+    np.testing.assert_allclose(cont["x"], full["x"], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(cont["rho"], full["rho"], rtol=1e-13)
+    cold = P.parsdmm(m, grid, sets, dict(o, max_iter=30), init=init, init_rho=half["rho"],
+                     init_gamma=half["gamma"])
+    assert not np.allclose(cold["rho"], full["rho"], rtol=1e-6)
