@@ -299,6 +299,28 @@ sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev,
                          const void *v_dev, const double *rho,
                          const double *gamma, void *stream);
 
+/* The quantities Algorithm adapt-rho-gamma saved at its last call ("save
+ * for next call"): v-hat, y and v at that iteration k0 (M' entries each, the
+ * layout of y, v above) and x^{k0} (N entries), from which the set pass
+ * forms s^{k0} = A_i x^{k0}.  With them a warm start continues the
+ * iteration as if it had not stopped: the next projection's first adapt
+ * call forms its differences against them instead of only saving.  (With
+ * sip_set_state alone it starts a fresh adapt history.)
+ * sip_get_adapt_state copies them out after a projection and sets *have to
+ * 1, or to 0 when no adapt call has saved anything yet (the arrays are then
+ * not written; NULL pointers are skipped); it synchronises `stream`.
+ * sip_set_adapt_state loads them for the next sip_project, together with a
+ * state loaded by sip_set_state (call that too: the adapt history belongs
+ * to the iterates it came with), copied into a staging buffer that the
+ * handle allocates on first use.  For handles whose adapt calls come more
+ * often than the x history is long (adapt_every < evol_hist, the default);
+ * single-level, single-instance handles with adapt != 0; SIP_ERR_INVALID_ARG
+ * otherwise. */
+sip_status sip_get_adapt_state(sip_handle *h, void *vhat_dev, void *y_dev, void *v_dev, void *xk0_dev,
+                               int *have, void *stream);
+sip_status sip_set_adapt_state(sip_handle *h, const void *vhat_dev, const void *y_dev, const void *v_dev,
+                               const void *xk0_dev, void *stream);
+
 const char *sip_last_error(const sip_handle *h);
 
 /* ---------------------------------------------------------------------

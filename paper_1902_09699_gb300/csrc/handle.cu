@@ -37,6 +37,10 @@ struct sip_handle {
   // the instances as built (before plan_build resolves them), for rebuilding
   // the plan with other launch-shape knobs; single-level and batched handles
   std::vector<InstLayout> layouts0;
+  // adapt-rho-gamma's saved quantities for the next warm start (v-hat, y, v
+  // at k0 and x^{k0}), staged until the projection's preparation
+  void *k0_stage = nullptr;
+  bool warm_k0 = false;
   bool tuned = false;     // the first projection's tuning has run (or was not asked for)
   sip_tuning report;      // what tuning measured
 };
@@ -214,6 +218,7 @@ sip_status sip_create(const sip_grid *grid, const sip_set *sets, int nsets, cons
 sip_status sip_destroy(sip_handle *h) {
   if (!h) return SIP_OK;
   if (h->dk_x) cudaFree(h->dk_x);
+  if (h->k0_stage) cudaFree(h->k0_stage);
   for (auto &P : h->lev) P.release();
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -274,6 +279,25 @@ static sip_status load_penalties(sip_handle *h, Plan &F, cudaStream_t st) {
     pen.gamma[b] = h->warm_gamma[b];
   }
   CKH(launch_load_penalties(st, F.d_insts, F.d_scal, pen));
+  return SIP_OK;
+}
+
+// The staged adapt-rho-gamma quantities into place after the preparation
+// (which clears them): the copies at k0, x^{k0} in the history-ring slot the
+// first adapt call reads, and the flag that makes that call form its
+// differences.
+static sip_status load_adapt_state(sip_handle *h, Plan &F, cudaStream_t st) {
+  const InstDev &d = F.h_insts[0];
+  const size_t W = esz(h->opts.dtype), M = (size_t)F.layouts[0].Mtot, N = (size_t)d.N;
+  const char *src = (const char *)h->k0_stage;
+  const int H = d.hist, ae = d.adapt_every;
+  const int slot = ((1 - ae) % H + H) % H;
+  CKH(cudaMemcpyAsync(d.k0vh, src, M * W, cudaMemcpyDeviceToDevice, st));
+  CKH(cudaMemcpyAsync(d.k0y, src + M * W, M * W, cudaMemcpyDeviceToDevice, st));
+  CKH(cudaMemcpyAsync(d.k0v, src + 2 * M * W, M * W, cudaMemcpyDeviceToDevice, st));
+  CKH(cudaMemcpyAsync((char *)d.ring + (size_t)slot * N * W, src + 3 * M * W, N * W, cudaMemcpyDeviceToDevice, st));
+  static const int32_t one = 1;
+  CKH(cudaMemcpyAsync(&F.d_scal->have_k0, &one, sizeof one, cudaMemcpyHostToDevice, st));
   return SIP_OK;
 }
 
@@ -501,7 +525,8 @@ static sip_status project_impl(sip_handle *h, const void *m_dev, void *x_dev, cu
                           cudaMemcpyHostToDevice, st));
     if ((s = plan_prepare(F, st, h->warm_next))) return s;
     if (h->warm_next && h->warm_pen && !o.rho_schedule && (s = load_penalties(h, F, st))) return s;
-    h->warm_next = h->warm_pen = false;
+    if (h->warm_next && h->warm_k0 && !o.rho_schedule && (s = load_adapt_state(h, F, st))) return s;
+    h->warm_next = h->warm_pen = h->warm_k0 = false;
   }
   sip_status s = run_iterations(F, st, h->cap, F.max_iter, o.stop != 0, h->pinned, tm);
   if (s) return s;
@@ -605,6 +630,65 @@ sip_status sip_set_state(sip_handle *h, const void *x_dev, const void *y_dev, co
     if (sip_status s2 = round_bf16(F0, d.v, (int64_t)M, st)) return keep(h, s2);
   }
   h->warm_next = true;
+  return SIP_OK;
+}
+
+static sip_status adapt_state_check(const sip_handle *h) {
+  if (sip_status s = state_check(h)) return s;
+  const InstDev &d = h->lev[0].h_insts[0];
+  if (!h->opts.adapt || h->dykstra) return fail(SIP_ERR_INVALID_ARG, "the handle does not adapt rho");
+  if (!d.k0_ring)
+    return fail(SIP_ERR_INVALID_ARG, "adapt state needs adapt_every < evol_hist (x^{k0} in the history ring)");
+  return SIP_OK;
+}
+
+sip_status sip_get_adapt_state(sip_handle *h, void *vhat_dev, void *y_dev, void *v_dev, void *xk0_dev, int *have,
+                               void *stream) {
+  if (sip_status s = adapt_state_check(h)) return h ? keep(h, s) : s;
+  if (!have) return keep(h, fail(SIP_ERR_INVALID_ARG, "have is NULL"));
+  const Plan &F = h->lev[0];
+  const InstDev &d = F.h_insts[0];
+  const size_t W = esz(h->opts.dtype), M = (size_t)F.layouts[0].Mtot, N = (size_t)d.N;
+  const cudaStream_t st = (cudaStream_t)stream;
+  CKH(cudaStreamSynchronize(st));
+  InstScal sc;
+  CKH(cudaMemcpy(&sc, F.d_scal, sizeof sc, cudaMemcpyDeviceToHost));
+  *have = 0;
+  // the last adapt iteration k0 <= iters (k0 % adapt_every == 1 % adapt_every)
+  const int ae = d.adapt_every, H = d.hist;
+  int k0 = sc.iters;
+  while (k0 >= 1 && k0 % ae != 1 % ae) --k0;
+  if (!sc.have_k0 || k0 < 1) return SIP_OK;
+  if (vhat_dev) CKH(cudaMemcpyAsync(vhat_dev, d.k0vh, M * W, cudaMemcpyDeviceToDevice, st));
+  if (y_dev) CKH(cudaMemcpyAsync(y_dev, d.k0y, M * W, cudaMemcpyDeviceToDevice, st));
+  if (v_dev) CKH(cudaMemcpyAsync(v_dev, d.k0v, M * W, cudaMemcpyDeviceToDevice, st));
+  if (xk0_dev)
+    CKH(cudaMemcpyAsync(xk0_dev, (const char *)d.ring + (size_t)(k0 % H) * N * W, N * W, cudaMemcpyDeviceToDevice,
+                        st));
+  CKH(cudaStreamSynchronize(st));
+  *have = 1;
+  return SIP_OK;
+}
+
+sip_status sip_set_adapt_state(sip_handle *h, const void *vhat_dev, const void *y_dev, const void *v_dev,
+                               const void *xk0_dev, void *stream) {
+  if (sip_status s = adapt_state_check(h)) return h ? keep(h, s) : s;
+  if (!vhat_dev || !y_dev || !v_dev || !xk0_dev) return keep(h, fail(SIP_ERR_INVALID_ARG, "NULL array"));
+  h->warm_k0 = false;
+  const Plan &F = h->lev[0];
+  const size_t W = esz(h->opts.dtype), M = (size_t)F.layouts[0].Mtot, N = (size_t)F.h_insts[0].N;
+  if (!h->k0_stage && (hook_alloc_fails() || cudaMalloc(&h->k0_stage, (3 * M + N) * W) != cudaSuccess)) {
+    cudaGetLastError();
+    h->k0_stage = nullptr;
+    return keep(h, fail(SIP_ERR_OOM, "adapt state staging: device allocation failed"));
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  char *dst = (char *)h->k0_stage;
+  CKH(cudaMemcpyAsync(dst, vhat_dev, M * W, cudaMemcpyDeviceToDevice, st));
+  CKH(cudaMemcpyAsync(dst + M * W, y_dev, M * W, cudaMemcpyDeviceToDevice, st));
+  CKH(cudaMemcpyAsync(dst + 2 * M * W, v_dev, M * W, cudaMemcpyDeviceToDevice, st));
+  CKH(cudaMemcpyAsync(dst + 3 * M * W, xk0_dev, N * W, cudaMemcpyDeviceToDevice, st));
+  h->warm_k0 = true;
   return SIP_OK;
 }
 

@@ -2008,8 +2008,13 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   // s^{k0} = A x^{k0} of the last adapt iteration, from x^{k0} in the x
   // history ring (k0ring) or from the stored copy k0s
   const bool k0ring = in.k0_ring != 0;
+  // (the slot of iteration k - adapt_every, taken modulo the ring length
+  // also when that iteration precedes this projection: a warm start that
+  // carries the adapt state puts x^{k0} there)
   const T *__restrict__ xk0 =
-      (k0ring && ad_dots) ? (const T *)in.ring + (int64_t)((k - in.adapt_every) % in.hist) * in.N : nullptr;
+      (k0ring && ad_dots)
+          ? (const T *)in.ring + (int64_t)(((k - in.adapt_every) % in.hist + in.hist) % in.hist) * in.N
+          : nullptr;
   // x gathers of one row: s = A x (Eq. FD_mat), m at the base sample and,
   // from the ring, s^{k0}
   auto gather = [&](int64_t row, T &sv, T &mv, T &kv0) {

@@ -92,6 +92,8 @@ SIGNATURES = {
     "sip_state_rows": (c_i64, [c_vp]),
     "sip_get_state": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "sip_set_state": (c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
+    "sip_get_adapt_state": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_int), c_vp]),
+    "sip_set_adapt_state": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "sip_last_error": (ctypes.c_char_p, [c_vp]),
     "sip_device_bytes": (c_i64, [c_vp]),
     "sip_bytes_per_iter": (c_dbl, [c_vp]),
@@ -367,6 +369,24 @@ class Projector:
                                    None if gh is None else gh.ctypes.data_as(ctypes.POINTER(c_dbl)),
                                    _stream_ptr(stream)), self.handle)
         self._state_keep = (x, y, v)  # the copies are stream-ordered: keep the sources alive
+
+    def get_adapt_state(self, device="cuda", stream=None):
+        """Algorithm adapt-rho-gamma's saved quantities after a projection:
+        (vhat, y, v, x_k0) at its last adapt call, or None before any."""
+        import torch
+        M = self.state_rows()
+        vh, y, v = (torch.empty(M, dtype=self.torch_dtype, device=device) for _ in range(3))
+        xk0 = torch.empty(self.N, dtype=self.torch_dtype, device=device)
+        have = c_int(0)
+        _check(lib().sip_get_adapt_state(self.handle, _ptr(vh), _ptr(y), _ptr(v), _ptr(xk0), ctypes.byref(have),
+                                         _stream_ptr(stream)), self.handle)
+        return (vh, y, v, xk0) if have.value else None
+
+    def set_adapt_state(self, vhat, y, v, xk0, stream=None):
+        """Load the saved quantities for the next (warm-started) projection."""
+        a = [_dev(t, self.code) for t in (vhat, y, v, xk0)]
+        _check(lib().sip_set_adapt_state(self.handle, *[_ptr(t) for t in a], _stream_ptr(stream)), self.handle)
+        self._adapt_keep = a
 
     def device_bytes(self):
         return int(lib().sip_device_bytes(self.handle))

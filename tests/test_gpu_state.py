@@ -115,3 +115,43 @@ def test_warm_start_carries_rho_and_gamma():
     with pytest.raises(sip.SipError):
         pr.set_state(xs, rho=[-1.0] * len(blocks))
     pr.close()
+
+
+@pytest.mark.parametrize("dt", ["f64"])
+def test_warm_start_with_adapt_state_continues_the_run(dt):
+    """K iterations, then a warm start that carries x, y_i, v_i, rho_i,
+    gamma_i and adapt-rho-gamma's saved quantities, for K more: the result of
+    2K uninterrupted iterations of the oracle (the oracle's own pin shows the
+    same continuity, and that without the saved quantities it is lost)."""
+    c = W.layered_2d(n=(48, 64), seed=77)
+    sets = [s_ for s_ in c["sets"] if s_["type"] != "card"]
+    K = 20
+    opts = dict(c["opts"], adapt=2, max_iter=K)
+    m = torch.as_tensor(c["m"], device="cuda")
+    full = P.parsdmm(c["m"], c["grid"], sets, P.options(**dict(opts, max_iter=2 * K)))
+    pr = sip.Projector(c["grid"], sets, dtype=dt, **opts)
+    _, info = pr.project(m)
+    x, y, v = pr.get_state()
+    st = pr.get_adapt_state()
+    assert st is not None
+    pr.set_state(x, y, v, rho=info["rho"], gamma=info["gamma"])
+    pr.set_adapt_state(*st)
+    x2, info2 = pr.project(m)
+    pr.close()
+    ref = full["x"]
+    e2 = float(np.linalg.norm(x2.cpu().numpy() - ref) / np.linalg.norm(ref))
+    assert e2 <= 1e-10, e2
+    np.testing.assert_allclose(info2["rho"], full["rho"], rtol=1e-9)
+    np.testing.assert_allclose(info2["gamma"], full["gamma"], rtol=1e-9)
+
+
+def test_adapt_state_rejected_without_adaptation_or_ring():
+    c = W.small_2d(n=(16, 16))
+    pr = sip.Projector(c["grid"], c["sets"], dtype="f64", **dict(c["opts"], adapt=0))
+    with pytest.raises(sip.SipError):
+        pr.get_adapt_state()
+    pr.close()
+    pr = sip.Projector(c["grid"], c["sets"], dtype="f64", **dict(c["opts"], adapt=1, adapt_every=5, evol_hist=5))
+    with pytest.raises(sip.SipError):
+        pr.get_adapt_state()
+    pr.close()
