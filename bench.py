@@ -650,6 +650,46 @@ def run_small(args):
     return 0
 
 
+def run_smallbatch(args):
+    """--count models of the 64 x 64 FP64 workload (own seeds) in one batched
+    handle, 200 iterations each: the throughput form of that workload, whose
+    binary64 arithmetic runs at 1/64 of the binary32 rate on this GPU."""
+    import numpy as np
+    import torch
+
+    from paper_1902_09699_gb300 import sip
+    from paper_1902_09699_gb300 import workloads as W
+    c = W.small_2d()
+    its = c["opts"]["max_iter"]
+    models = [c["m"]] + [W.small_2d(seed=3000 + i)["m"] for i in range(args.count - 1)]
+    bp = sip.BatchProjector([(c["grid"], c["sets"])] * args.count, dtype="f64", exec=args.exec,
+                            cluster_ctas=args.cluster_ctas, **c["opts"])
+    mp = bp.pack(models)
+    xb = torch.empty_like(mp)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bp.project(mp, xb, info=False)
+    clocks = Clocks()
+    clocks.start()
+    bms = _timed_steps(lambda: bp.project(mp, xb, info=False), args.steps, flush, st)
+    clk = clocks.stop()
+    ms = sum(bms) / args.steps
+    bpi = bp.bytes_per_iter()
+    bp.close()
+    peak, _ = peaks()
+    out = {"metric": METRIC, "value": args.count / (ms / 1000.0), "unit": "projections/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": c["name"] + "-batched", "instances": args.count, "iterations": its,
+                      "l2_between_steps": "flushed (512 MB write)"},
+           "instance_iter_per_s": args.count * its / (ms / 1000.0),
+           "us_per_iteration_of_the_batch": 1000.0 * ms / its,
+           "pct_hbm_peak": bpi * its / (ms / 1000.0) / 1e9 / peak, "clocks": clk}
+    print(json.dumps(out))
+    return 0
+
+
 def run_lines(args):
     """2D 512 x 1024 layered model with per-row and per-column cardinality
     sets next to whole-model ones, FP32, against the FP64 GPU loop; the
@@ -886,7 +926,8 @@ def main():
     ap.add_argument("--tune", action="store_true",
                     help="plan tuning on the first (untimed) projection; ragged: time the default and the tuned plan")
     ap.add_argument("--workload", default="layered",
-                    choices=["layered", "small", "ragged", "grf3d", "serving", "lines", "dykstra", "deblur"],
+                    choices=["layered", "small", "smallbatch", "ragged", "grf3d", "serving", "lines", "dykstra",
+                             "deblur"],
                     help="layered: 512 x 1024 five-set 2D model (default line); small: 64 x 64 FP64 "
                          "three-set model, single and batched; ragged: 512-instance batch; "
                          "grf3d: 256 x 256 x 128 multilevel; serving: Poisson request stream; lines: per-row "
@@ -906,6 +947,8 @@ def main():
         return run_ragged(args)
     if args.workload == "small":
         return run_small(args)
+    if args.workload == "smallbatch":
+        return run_smallbatch(args)
     if args.workload == "deblur":
         return run_deblur(args)
     if args.workload == "lines":
