@@ -3221,6 +3221,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_final(const Tile *__restrict__ 
 // gives the feasibility distance.
 // --------------------------------------------------------------------------
 constexpr int kLineMax = SIP_MAX_LINE;
+constexpr int kLineSmallK = 8;  // per-line top-k by per-thread lists up to this k
 template <typename T>
 constexpr size_t line_smem() {
   return (size_t)kLineMax * (sizeof(typename KeyOf<T>::K) + sizeof(uint32_t) + 1);
@@ -3284,12 +3285,17 @@ __device__ void line_project(const BlockDev &bd, const T *__restrict__ src, int6
   double scale = 1.0;
   double theta = 0.0;
   double ss = 0.0, sa = 0.0;
-  for (int64_t e = threadIdx.x; e < L; e += kThreads) {
-    const double x = (double)src[at(e)];
-    ss += x * x;
-    sa += fabs(x);
+  // ||line||^2: for the l2 / annulus scale and the feasibility pass;
+  // ||line||_1: for the l1 ball
+  const bool need_ss = lt == BT_L2 || lt == BT_ANNULUS || !out;
+  if (need_ss || lt == BT_L1) {
+    for (int64_t e = threadIdx.x; e < L; e += kThreads) {
+      const double x = (double)src[at(e)];
+      ss += x * x;
+      sa += fabs(x);
+    }
   }
-  ss = cta_sum_f64(ss, red);
+  if (need_ss) ss = cta_sum_f64(ss, red);
   if (lt == BT_L2 || lt == BT_ANNULUS) {
     const double nrm = sqrt(ss);
     const double hi = lt == BT_L2 ? sigma : bd.hi, lo = lt == BT_L2 ? 0.0 : bd.lo;
@@ -3357,6 +3363,88 @@ __device__ void line_project(const BlockDev &bd, const T *__restrict__ src, int6
   bool all_ties = true;
   const int per = (int)((L + kThreads - 1) / kThreads);
   const int e0 = (int)threadIdx.x * per, e1 = (int)(e0 + per < L ? e0 + per : L);
+  // small k (the paper's "at most a few nonzeros per row / column"): the
+  // line's k largest entries in the order (|w| descending, position
+  // ascending) -- the same set as the radix selection with its tie rule --
+  // from each thread's own top k over its positions, then k rounds of a
+  // CTA-wide maximum; the output keeps exactly the selected positions
+  __shared__ uint32_t s_sel[kLineSmallK];
+  if (mode == 1 && kk <= kLineSmallK) {
+    const int kq = (int)kk;
+    K tk[kLineSmallK];
+    uint32_t tp[kLineSmallK];
+#pragma unroll
+    for (int j = 0; j < kLineSmallK; ++j) {
+      tk[j] = 0;
+      tp[j] = 0xffffffffu;
+    }
+    // positions ascend within a thread: an entry enters only if its key is
+    // strictly larger than the current k-th
+    for (int e = e0; e < e1; ++e) {
+      const K key = KT::key(src[at(e)]);
+      if (tp[kq - 1] != 0xffffffffu && key <= tk[kq - 1]) continue;
+      K ck = key;
+      uint32_t cp = (uint32_t)e;
+#pragma unroll
+      for (int j = 0; j < kLineSmallK; ++j) {
+        if (j < kq && (tp[j] == 0xffffffffu || ck > tk[j])) {
+          const K t1 = tk[j];
+          const uint32_t t2 = tp[j];
+          tk[j] = ck;
+          tp[j] = cp;
+          ck = t1;
+          cp = t2;
+        }
+      }
+    }
+    constexpr int kWarps = kThreads / 32;
+    __shared__ K wk[kWarps];
+    __shared__ uint32_t wp[kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int head = 0;
+    for (int round = 0; round < kq; ++round) {
+      // this thread's next candidate; exhausted threads offer nothing
+      K bk = 0;
+      uint32_t bp = 0xffffffffu;
+#pragma unroll
+      for (int j = 0; j < kLineSmallK; ++j)
+        if (j == head) {
+          bk = tk[j];
+          bp = tp[j];
+        }
+      if (head >= kq) bp = 0xffffffffu;
+      K mk = bk;
+      uint32_t mp = bp;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const K ok2 = __shfl_xor_sync(0xffffffffu, mk, o);
+        const uint32_t op = __shfl_xor_sync(0xffffffffu, mp, o);
+        const bool better = op != 0xffffffffu && (mp == 0xffffffffu || ok2 > mk || (ok2 == mk && op < mp));
+        if (better) {
+          mk = ok2;
+          mp = op;
+        }
+      }
+      if (lane == 0) {
+        wk[wid] = mk;
+        wp[wid] = mp;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        K gk = wk[0];
+        uint32_t gp = wp[0];
+        for (int w2 = 1; w2 < kWarps; ++w2)
+          if (wp[w2] != 0xffffffffu && (gp == 0xffffffffu || wk[w2] > gk || (wk[w2] == gk && wp[w2] < gp))) {
+            gk = wk[w2];
+            gp = wp[w2];
+          }
+        s_sel[round] = gp;
+      }
+      __syncthreads();
+      if (bp != 0xffffffffu && bp == s_sel[round]) ++head;  // positions are unique
+    }
+    mode = 3;
+  }
   if (mode == 1) {
     constexpr int kWarps = kThreads / 32;
     uint32_t *h = (uint32_t *)smem;
@@ -3440,6 +3528,7 @@ __device__ void line_project(const BlockDev &bd, const T *__restrict__ src, int6
   double dd = 0.0;
   uint32_t tie = tie0;
   for (int64_t e = (mode == 1 ? e0 : threadIdx.x); e < (mode == 1 ? e1 : L); e += (mode == 1 ? 1 : kThreads)) {
+    // (mode 3 walks the line like the point-wise modes)
     const int64_t r = at(e);
     const T wv = src[r];
     T yn;
@@ -3447,6 +3536,10 @@ __device__ void line_project(const BlockDev &bd, const T *__restrict__ src, int6
       const K key = KT::key(wv);
       bool keep = key > kkey;
       if (key == kkey) keep = all_ties || tie++ < need;
+      yn = keep ? wv : T(0);
+    } else if (mode == 3) {
+      bool keep = false;
+      for (int j = 0; j < (int)kk; ++j) keep = keep || s_sel[j] == (uint32_t)e;
       yn = keep ? wv : T(0);
     } else if (mode == 2) {
       const T a = fabs(wv) - th;

@@ -3,8 +3,10 @@ its own) through the C ABI, against the FP64 oracle.
 
 Bars as in the loop parity tests: 1e-10 in FP64 (the GPU's own
 adapt-rho-gamma), 1e-4 in FP32 (fixed rho: no threshold decision can flip
-on one-ulp differences).  Per-line card and l1 sets sort each line in
-shared memory; lines longer than SIP_MAX_LINE are rejected.
+on one-ulp differences).  Per-line card sets keep the k largest entries of
+each line by per-thread lists for k <= 8 and by a radix selection in shared
+memory above; per-line l1 sets sort each line in shared memory; lines longer
+than SIP_MAX_LINE are rejected.
 """
 import math
 
@@ -44,6 +46,9 @@ LINE_CASES = {
     "card-dz-columns": ({"op": "DZ", "type": "card", "k": 3, "scope": "z"}, (48, 36)),
     "card-dx-rows": ({"op": "DX", "type": "card", "k": 2, "scope": "x"}, (48, 36)),
     "card-frac-columns": ({"op": "DZ", "type": "card", "k_frac": 0.1, "scope": "z"}, (40, 30)),
+    # k above the per-thread top-k path's limit: the radix selection per line
+    "card-dz-columns-k12": ({"op": "DZ", "type": "card", "k": 12, "scope": "z"}, (48, 36)),
+    "card-frac-rows-large": ({"op": "DX", "type": "card", "k_frac": 0.3, "scope": "x"}, (40, 30)),
     "l2-columns": ({"op": "I", "type": "l2", "sigma": 18.0, "scope": "z"}, (48, 36)),
     "l1-rows": ({"op": "DX", "type": "l1", "sigma": 0.6, "scope": "x"}, (48, 36)),
     "annulus-rows": ({"op": "I", "type": "annulus", "lo": 11.0, "hi": 13.0, "scope": "x"}, (48, 36)),
