@@ -1866,7 +1866,9 @@ struct RowOut {
 // update, adapt-rho-gamma and feasibility partial sums (Algorithm PARSDMM
 // FOR-body; Algorithm adapt-rho-gamma; Eq. feas_stop).
 // Partials: 0..5 adapt dots, 6 feasD2, 7 s2, 8 s1, 9 wnorm.
-template <typename T, typename A>
+// PW: 0 any block type (decided per row from q), 1 bounds, 2 the identity
+// block's distance prox (the block type fixed at compile time)
+template <int PW = 0, typename T, typename A>
 __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T y0, T v0, T mg, T ks, T kvh, T ky,
                                                  T kv, T lo, T hi, A (&acc)[10]) {
   RowOut<T> o;
@@ -1884,8 +1886,10 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
       acc[2] += dvh * dvh;
     }
   }
-  if (q.pointwise) {
-    o.yn = q.type == BT_BOUNDS ? fmin(fmax(o.w, lo), hi) : (mg + q.rho * o.w) * q.inv1p;  // Eq. prox_sq_dist
+  const bool pointwise = PW ? true : q.pointwise;
+  const bool bounds = PW ? PW == 1 : q.type == BT_BOUNDS;
+  if (pointwise) {
+    o.yn = bounds ? fmin(fmax(o.w, lo), hi) : (mg + q.rho * o.w) * q.inv1p;  // Eq. prox_sq_dist
     o.vn = v0 + q.rho * (o.yn - xbar);
     if (q.ad_dots) {
       const A dg = (A)ky - (A)o.yn;
@@ -1894,7 +1898,7 @@ __device__ __forceinline__ RowOut<T> setpass_row(const SetpassScal<T> &q, T s, T
       acc[4] += dg * dg;
       acc[5] += dv * dv;
     }
-    if (q.chk && q.type == BT_BOUNDS) {
+    if (q.chk && bounds) {
       const A d = (A)s - (A)fmin(fmax(s, lo), hi);
       acc[6] += d * d;
       acc[7] += (A)s * (A)s;
@@ -2048,6 +2052,8 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
   }
   if (vec) {
     if constexpr (sizeof(T) == 4) {
+      // the block type of the rows' prox, fixed for the whole work item
+      const int pwk = type == BT_BOUNDS ? 1 : (type == BT_DIST ? 2 : 0);
       // grouped x gathers of four rows (no blur segment): 1 = identity rows
       // or 2D x-difference rows with 16-byte aligned x (and m, x^{k0}) and
       // n_z % 4 == 0; 2 = z-difference rows; 0 = row by row
@@ -2145,8 +2151,15 @@ __device__ void setpass_block(const Tile &tl, const InstDev &in, InstScal &sc, c
         for (int c = 0; c < 4; ++c) {
           RowOut<float> o;
           if (r0 + c < end) {
-            o = setpass_row(q, sv[c], vat(Y, c), vat(V, c), mv[c], vat(KS, c), vat(KVH, c), vat(KY, c), vat(KV, c),
-                            q.lo, q.hi, acc);
+            if (pwk == 1)
+              o = setpass_row<1>(q, sv[c], vat(Y, c), vat(V, c), mv[c], vat(KS, c), vat(KVH, c), vat(KY, c),
+                                 vat(KV, c), q.lo, q.hi, acc);
+            else if (pwk == 2)
+              o = setpass_row<2>(q, sv[c], vat(Y, c), vat(V, c), mv[c], vat(KS, c), vat(KVH, c), vat(KY, c),
+                                 vat(KV, c), q.lo, q.hi, acc);
+            else
+              o = setpass_row<0>(q, sv[c], vat(Y, c), vat(V, c), mv[c], vat(KS, c), vat(KVH, c), vat(KY, c),
+                                 vat(KV, c), q.lo, q.hi, acc);
           } else {
             o.yn = o.vn = o.w = o.vh = 0.f;
           }
