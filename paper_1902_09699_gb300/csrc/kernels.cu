@@ -794,16 +794,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_rhs_tma(const Tile *__restrict_
   const int nz = in.nz;
   float a1 = 0.f;
   bool waited = false;
-  for (int64_t g = s0 + threadIdx.x; g < e0 + threadIdx.x; g += kThreads) {
-    // (every thread runs the same number of rounds; the first round waits)
-    const bool ok = g < e0;
-    GridPos pos;
-    Nbr<float> xn;
-    float b = 0.f;
-    if (ok) {
-      pos = grid_pos(in, g);
-      if (!alg1) b = m[g];
-      load_nbr<float>(in, pos, g, [&](int64_t i) { return x[i]; }, xn);
+  // U grid points per thread per round (g, g + kThreads, ...): their x
+  // stencils and m are requested together. Every thread runs the same
+  // rounds (at least one), and the first round waits for the copies.
+  constexpr int U = 4;
+  for (int64_t base = s0; base < e0 || !waited; base += (int64_t)kThreads * U) {
+    GridPos pos[U];
+    Nbr<float> xn[U];
+    float b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t g = base + threadIdx.x + (int64_t)u * kThreads;
+      b[u] = 0.f;
+      if (g < e0) {
+        pos[u] = grid_pos(in, g);
+        if (!alg1) b[u] = m[g];
+        load_nbr<float>(in, pos[u], g, [&](int64_t i) { return x[i]; }, xn[u]);
+      }
     }
     if (!waited) {
       __syncthreads();  // sbase_* written by thread 0
@@ -815,28 +822,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_rhs_tma(const Tile *__restrict_
       }
       waited = true;
     }
-    if (!ok) continue;
-    const int gi = (int)g;
-    const int rz = gi - (int)pos.t;  // D_z row base (iz + (nz-1) t)
-    for (int j = 0; j < nseg; ++j) {
-      const float *__restrict__ ys = sw + sbase_y[j];
-      const float *__restrict__ vs = sw + sbase_v[j];
-      const float rho = srs[j], ih = sih[j];
-      // (A^T u)[g] = u[ia] (if fa) - u[ib] (if fb), times 1/h
-      int ia = gi, ib = gi;
-      bool fa = true, fb = false;
-      switch (skind[j]) {
-        case SEG_DZ: ia = rz - 1; ib = rz; fa = pos.iz >= 1; fb = pos.iz <= nz - 2; break;
-        case SEG_DX: ia = gi - nz; ib = gi; fa = pos.ix >= 1; fb = pos.ix <= in.nx - 2; break;
-        default: break;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t g = base + threadIdx.x + (int64_t)u * kThreads;
+      if (g >= e0) continue;
+      const int gi = (int)g;
+      const int rz = gi - (int)pos[u].t;  // D_z row base (iz + (nz-1) t)
+      for (int j = 0; j < nseg; ++j) {
+        const float *__restrict__ ys = sw + sbase_y[j];
+        const float *__restrict__ vs = sw + sbase_v[j];
+        const float rho = srs[j], ih = sih[j];
+        // (A^T u)[g] = u[ia] (if fa) - u[ib] (if fb), times 1/h
+        int ia = gi, ib = gi;
+        bool fa = true, fb = false;
+        switch (skind[j]) {
+          case SEG_DZ: ia = rz - 1; ib = rz; fa = pos[u].iz >= 1; fb = pos[u].iz <= nz - 2; break;
+          case SEG_DX: ia = gi - nz; ib = gi; fa = pos[u].ix >= 1; fb = pos[u].ix <= in.nx - 2; break;
+          default: break;
+        }
+        const float ua = fa ? rho * ys[ia] + vs[ia] : 0.f;
+        const float ub = fb ? rho * ys[ib] + vs[ib] : 0.f;
+        b[u] += (ua - ub) * ih;
       }
-      const float ua = fa ? rho * ys[ia] + vs[ia] : 0.f;
-      const float ub = fb ? rho * ys[ib] + vs[ib] : 0.f;
-      b += (ua - ub) * ih;
+      const float rv = b[u] - apply_c(C, xn[u]);
+      r[g] = rv;
+      a1 += rv * rv;
     }
-    const float rv = b - apply_c(C, xn);
-    r[g] = rv;
-    a1 += rv * rv;
   }
   float acc[1] = {a1};
   block_sum<1>(acc);
@@ -3074,56 +3085,67 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   }
   if (vec) {
     if constexpr (sizeof(T) == 4) {
-      // 16-byte accesses, 4 consecutive rows per thread
-      for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4) {
-        const int64_t r0 = base + (int64_t)threadIdx.x * 4;
-        if (r0 >= end) continue;
-        const bool full = r0 + 4 <= end;
-        auto ld = [&](const float *p) {
-          if (full) return ld4(p, r0);
+      // 16-byte accesses, 4 consecutive rows per thread, two groups of 4
+      // per round (their loads requested together)
+      constexpr int FU = 2;
+      for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4 * FU) {
+        auto ld = [&](const float *p, int64_t r0) {
+          if (r0 + 4 <= end) return ld4(p, r0);
           float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
           for (int c = 0; c < 4; ++c)
             if (r0 + c < end) vset(t, c, p[r0 + c]);
           return t;
         };
-        auto st = [&](float *p, const float4 &t) {
-          if (full) {
+        auto st = [&](float *p, int64_t r0, const float4 &t) {
+          if (r0 + 4 <= end) {
             st4(p, r0, t);
           } else {
             for (int c = 0; c < 4; ++c)
               if (r0 + c < end) p[r0 + c] = vat(t, c);
           }
         };
-        const float4 W = ld(w);
-        float4 KY = make_float4(0.f, 0.f, 0.f, 0.f), KV = KY;
-        if (ad_dots) {
-          KY = ld(k0y);
-          KV = ld(k0v);
-        }
-        float4 YN, VN;
+        float4 W[FU], KY[FU], KV[FU];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float wc = vat(W, c);
-          const float yn = prox(wc), vn = rho * (yn - wc);
-          vset(YN, c, yn);
-          vset(VN, c, vn);
-          if (ad_dots && r0 + c < end) {
-            const A dg = (A)vat(KY, c) - (A)yn;
-            const A dv = (A)vn - (A)vat(KV, c);
-            acc[0] += dg * dv;
-            acc[1] += dg * dg;
-            acc[2] += dv * dv;
+        for (int h = 0; h < FU; ++h) {
+          const int64_t r0 = base + ((int64_t)h * kThreads + threadIdx.x) * 4;
+          W[h] = KY[h] = KV[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (r0 < end) {
+            W[h] = ld(w, r0);
+            if (ad_dots) {
+              KY[h] = ld(k0y, r0);
+              KV[h] = ld(k0v, r0);
+            }
           }
         }
-        if (in.bf16) {
-          YN = rbf4(YN);
-          VN = rbf4(VN);
-        }
-        st(y, YN);
-        st(v, VN);
-        if (ad) {
-          st(k0y, YN);
-          st(k0v, VN);
+#pragma unroll
+        for (int h = 0; h < FU; ++h) {
+          const int64_t r0 = base + ((int64_t)h * kThreads + threadIdx.x) * 4;
+          if (r0 >= end) continue;
+          float4 YN, VN;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float wc = vat(W[h], c);
+            const float yn = prox(wc), vn = rho * (yn - wc);
+            vset(YN, c, yn);
+            vset(VN, c, vn);
+            if (ad_dots && r0 + c < end) {
+              const A dg = (A)vat(KY[h], c) - (A)yn;
+              const A dv = (A)vn - (A)vat(KV[h], c);
+              acc[0] += dg * dv;
+              acc[1] += dg * dg;
+              acc[2] += dv * dv;
+            }
+          }
+          if (in.bf16) {
+            YN = rbf4(YN);
+            VN = rbf4(VN);
+          }
+          st(y, r0, YN);
+          st(v, r0, VN);
+          if (ad) {
+            st(k0y, r0, YN);
+            st(k0v, r0, VN);
+          }
         }
       }
     }
