@@ -438,7 +438,7 @@ double sip_bytes_per_iter(const sip_handle *h);
  * (see sip_kernel_name, 0..SIP_KERNEL_CATEGORIES-1), the summed device
  * milliseconds, the launch count since timing was switched on, and the
  * algorithmic bytes one launch moves (the roofline numerator). */
-#define SIP_KERNEL_CATEGORIES 8
+#define SIP_KERNEL_CATEGORIES 9
 sip_status sip_set_timing(sip_handle *h, int on);
 sip_status sip_kernel_times(const sip_handle *h, double *ms, int64_t *launches,
                             double *bytes_per_launch);

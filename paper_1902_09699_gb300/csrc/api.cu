@@ -440,7 +440,10 @@ double layout_bytes_per_iter(const InstLayout &L, int dtype) {
   const int ncg = L.opts.cg_iters > 0 ? L.opts.cg_iters : 5;
   const int rsel = select_passes(dtype);
   double words = 2 * Mp + 2 * N + (d.alg1 ? 0 : N);  // rhs: y, v, x read; r write (+ m)
-  words += 3.0 * N + ncg * 10.0 * N;                  // CG: w0 = C r0; per step p, x, r, w, s
+  // CG: w0 = C r0; per step p, x, r, w, s read and written, except in the
+  // iteration's last step, after which only x is read again (r, p, x read,
+  // x written)
+  words += 3.0 * N + (ncg > 0 ? (ncg - 1) * 10.0 * N + 4.0 * N : 0.0);
   words += 4 * Mp + N + (d.alg1 ? N : 0);             // set pass: x, y, v read, y, v write (+ m)
   double feas = 0.0;
   for (int b = 0; b < d.nb; ++b) {
@@ -1017,6 +1020,12 @@ static sip_status enqueue_iteration(Plan &P, cudaStream_t st, bool marks) {
   CK(launch_cg_w0(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, P.cg_one));  // w_0 = C r_0
   T1(KT_CG_W0);
   for (int j = 0; j < P.cg_launch; ++j) {
+    if (j == P.cg_launch - 1 && !P.blur) {  // the iteration's last step: x only
+      T0(KT_CG_LAST);
+      CK(launch_cg_last(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j, P.cg_one));
+      T1(KT_CG_LAST);
+      break;
+    }
     T0(KT_CG_STEP);
     if (!P.blur_all)
       CK(launch_cg_step(L, P.d_tn, P.nt_n, P.d_insts, P.d_scal, 2 + j, P.cg_one));  // one CG step

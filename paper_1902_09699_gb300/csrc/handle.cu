@@ -707,7 +707,8 @@ sip_status sip_project(sip_handle *h, const void *m_dev, void *x_dev, void *stre
 // ----------------------------------------------------------------------------
 // per-kernel timing
 // ----------------------------------------------------------------------------
-static const char *kKernelNames[KT_COUNT] = {"rhs", "cg_w0", "cg_step", "setpass", "select", "ties", "final", "tail"};
+static const char *kKernelNames[KT_COUNT] = {"rhs",   "cg_w0", "cg_step", "setpass", "select",
+                                             "ties",  "final", "tail",    "cg_last"};
 
 const char *sip_kernel_name(int i) { return (i >= 0 && i < KT_COUNT) ? kKernelNames[i] : ""; }
 
@@ -793,6 +794,7 @@ sip_status sip_kernel_times(const sip_handle *h, double *ms, int64_t *launches, 
   bytes[KT_TIES] = 0.0;
   bytes[KT_FINAL] = W * (3 * Mms + ad * 4 * Mms);
   bytes[KT_TAIL] = 0.0;
+  bytes[KT_CG_LAST] = W * 4 * N;  // read r, p, x; write x
   for (int c = 0; c < KT_COUNT; ++c) {
     if (ms) ms[c] = h->timer.ms[c];
     if (launches) launches[c] = h->timer.launches[c];

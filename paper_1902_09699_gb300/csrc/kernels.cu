@@ -1314,6 +1314,95 @@ __device__ __noinline__ void cg_step_call(const Tile &tl, const InstDev *insts, 
   body_cg_step<T>(tl, insts, scal, ph);
 }
 
+// The last step launch of an iteration.  The next iteration restarts the CG
+// from r_0 = b - C x, so of this launch's results only
+// x_{i+1} = x_i + alpha_i p_i, p_i = r_i + beta_i p_{i-1}, is read again: r, w,
+// s, p and the partial sums are not formed (4 words per grid point instead
+// of 10, no stencil).  alpha_i, beta_i and the CG state come from the same
+// gather as in a full step, so the iterate is the full step's.
+template <typename T, typename D>
+__device__ __forceinline__ void body_cg_last_in(const Tile &tl, const D &in, InstScal &sc, int ph) {
+  SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= in.N, 3u, tl.start + tl.len);
+  const int c = ph & 1;
+  const T *__restrict__ r = (const T *)in.cr[c];
+  const T *__restrict__ p = (const T *)in.cp;
+  T *__restrict__ x = (T *)in.x;
+  __shared__ T s_ab[2];
+  __shared__ int s_go;
+  const int64_t end = tl.start + tl.len;
+  T alpha = T(0), beta = T(0);
+  bool first = true;
+  if constexpr (sizeof(T) == 4) {
+    const uintptr_t al = (uintptr_t)(r + tl.start) | (uintptr_t)(p + tl.start) | (uintptr_t)(x + tl.start);
+    if ((al & 15) == 0 && (tl.len & 3) == 0) {
+      for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4) {
+        const int64_t g0 = base + 4 * (int64_t)threadIdx.x;
+        const bool ok = g0 < end;
+        float4 rv, pv, xv;
+        if (ok) {
+          rv = ld4(r, g0);
+          pv = ld4(p, g0);
+          xv = ld4(x, g0);
+        }
+        if (first) {
+          // the previous launch's sums, while this CTA's first loads are in flight
+          cg_scalars<T>(tl, in, sc, ph, s_ab, &s_go);
+          if (!s_go) return;
+          alpha = s_ab[0];
+          beta = s_ab[1];
+          first = false;
+        }
+        if (ok) {
+          const float4 Pn = make_float4(rv.x + beta * pv.x, rv.y + beta * pv.y, rv.z + beta * pv.z, rv.w + beta * pv.w);
+          st4(x, g0, make_float4(xv.x + alpha * Pn.x, xv.y + alpha * Pn.y, xv.z + alpha * Pn.z, xv.w + alpha * Pn.w));
+        }
+      }
+      return;
+    }
+  }
+  constexpr int PT = PerThread<T>::value;
+  for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * PT) {
+    T rv[PT], pv[PT], xv[PT];
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) {
+        rv[e] = r[g];
+        pv[e] = p[g];
+        xv[e] = x[g];
+      }
+    }
+    if (first) {
+      cg_scalars<T>(tl, in, sc, ph, s_ab, &s_go);
+      if (!s_go) return;
+      alpha = s_ab[0];
+      beta = s_ab[1];
+      first = false;
+    }
+#pragma unroll
+    for (int e = 0; e < PT; ++e) {
+      const int64_t g = base + threadIdx.x + (int64_t)e * kThreads;
+      if (g < end) {
+        const T pi = rv[e] + beta * pv[e];
+        x[g] = xv[e] + alpha * pi;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cg_last(const Tile *__restrict__ tiles, const InstDev *__restrict__ insts,
+                                                      InstScal *__restrict__ scal, int ph, unsigned long long *ts,
+                                                      const __grid_constant__ CgOne one) {
+  const Stamp stamp(ts);
+  if (one.on) {
+    body_cg_last_in<T>(one_tile(one), one.d, scal[0], ph);
+  } else {
+    const Tile tl = tiles[blockIdx.x];
+    body_cg_last_in<T>(tl, insts[tl.inst], scal[tl.inst], ph);
+  }
+}
+
 template <typename T, bool BL = false>
 __global__ void __launch_bounds__(kThreads, 3) k_cg_step(const Tile *__restrict__ tiles,
                                                          const InstDev *__restrict__ insts,
@@ -4417,6 +4506,11 @@ cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstD
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
                            const CgOne &one) {
   SIP_DISPATCH_BL(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_last(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
+                           const CgOne &one) {
+  SIP_DISPATCH(L, k_cg_last, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_blur_rhs(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, const InstScal *scal) {

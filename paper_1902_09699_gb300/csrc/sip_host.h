@@ -55,7 +55,7 @@ struct InstLayout {
 };
 
 // kernel categories of the per-kernel timer
-enum KernelCat { KT_RHS = 0, KT_CG_W0, KT_CG_STEP, KT_SETPASS, KT_SELECT, KT_TIES, KT_FINAL, KT_TAIL, KT_COUNT };
+enum KernelCat { KT_RHS = 0, KT_CG_W0, KT_CG_STEP, KT_SETPASS, KT_SELECT, KT_TIES, KT_FINAL, KT_TAIL, KT_CG_LAST, KT_COUNT };
 
 // Per-kernel device time by category (opt-in): the iterations run as a CUDA
 // graph whose kernels stamp their first CTA start and last CTA end with the

@@ -33,6 +33,9 @@ cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstD
 // ph: 2 for the first step launch of an iteration, then 3, 4, ...
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
                            const CgOne &one);
+// the last step launch of an iteration: x_{i+1} only (plans without a blur block)
+cudaError_t launch_cg_last(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
+                           const CgOne &one);
 // the blur block's right-hand side part F^T (rho y + v) - rho F^T F x, and
 // s = F x, at the blur instances' block work items (plans with a blur block)
 cudaError_t launch_cg_step_blur(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal,

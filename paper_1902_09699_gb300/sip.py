@@ -404,7 +404,7 @@ class Projector:
         _check(lib().sip_set_timing(self.handle, 1 if on else 0), self.handle)
 
     def kernel_times(self):
-        n = 8
+        n = 9  # SIP_KERNEL_CATEGORIES
         ms = (c_dbl * n)()
         la = (c_i64 * n)()
         by = (c_dbl * n)()
