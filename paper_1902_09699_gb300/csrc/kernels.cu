@@ -100,8 +100,21 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2)
   lo = (lo + l2) + err;
 }
 
+// This thread's entries of the first batch (entries threadIdx.x + u kThreads).
+template <int NQ>
+__device__ __forceinline__ void gather_first(const float *const (&p)[NQ], int nt, float (&v)[NQ][kGatherBatch]) {
+#pragma unroll
+  for (int u = 0; u < kGatherBatch; ++u) {
+    const int i = u * kThreads + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q][u] = i < nt ? __ldcg(p[q] + i) : 0.f;
+  }
+}
+
+// pre: the first batch, already loaded by gather_first (or null)
 template <int NQ, typename O>
-__device__ __forceinline__ void cta_gather(const float *const (&p)[NQ], int nt, O (&out)[NQ]) {
+__device__ __forceinline__ void cta_gather(const float *const (&p)[NQ], int nt, O (&out)[NQ],
+                                           const float (*pre)[kGatherBatch] = nullptr) {
   constexpr int NW = kThreads / 32;
   __shared__ float sh[NQ][NW], sl[NQ][NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -110,11 +123,18 @@ __device__ __forceinline__ void cta_gather(const float *const (&p)[NQ], int nt, 
   for (int q = 0; q < NQ; ++q) hi[q] = lo[q] = 0.f;
   for (int i0 = 0; i0 < nt; i0 += kThreads * kGatherBatch) {
     float v[NQ][kGatherBatch];
+    if (pre && i0 == 0) {
 #pragma unroll
-    for (int u = 0; u < kGatherBatch; ++u) {
-      const int i = i0 + u * kThreads + threadIdx.x;
+      for (int u = 0; u < kGatherBatch; ++u)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q][u] = i < nt ? __ldcg(p[q] + i) : 0.f;
+        for (int q = 0; q < NQ; ++q) v[q][u] = pre[q][u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u) {
+        const int i = i0 + u * kThreads + threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q][u] = i < nt ? __ldcg(p[q] + i) : 0.f;
+      }
     }
 #pragma unroll
     for (int u = 0; u < kGatherBatch; ++u)
@@ -1026,9 +1046,20 @@ template <> struct CgOf<float> {
 // threads add the partial sums, thread 0 updates the CG state (the same
 // values in every CTA) and the instance's first tile stores it for the next
 // launch.  Results in s_ab, s_go after the closing __syncthreads.
+// The partial sums a step launch of phase ph gathers (binary32 storage):
+// pointers of the two quantities.
+template <typename D>
+__device__ __forceinline__ void cg_gather_src(const D &in, int ph, const float *(&p)[2]) {
+  const int slot = 1 + ((ph - 1) & 1);
+  p[0] = ph == 2 ? cg_part<float>(in, 0, 0) : cg_part<float>(in, slot, 0);
+  p[1] = ph == 2 ? cg_part<float>(in, 2, 0) : cg_part<float>(in, slot, 1);
+}
+
+// pre (binary32): the first batch of the partial sums, requested by
+// gather_first before the launch's data loads (or null)
 template <typename T, typename D>
 __device__ __forceinline__ void cg_scalars(const Tile &tl, const D &in, InstScal &sc, int ph, T *s_ab,
-                                           int *s_go) {
+                                           int *s_go, const float (*pre)[kGatherBatch] = nullptr) {
   using A = typename AccOf<T>::type;
   using G = CgOf<T>;
   const int nt = in.nt_part;  // entries past a launch's own work items stay zero
@@ -1039,12 +1070,22 @@ __device__ __forceinline__ void cg_scalars(const Tile &tl, const D &in, InstScal
   if (ph == 2) {
     // r_0.r_0 from the right-hand side launch, delta_0 from the w_0 launch
     const A *const p[2] = {cg_part<A>(in, 0, 0), cg_part<A>(in, 2, 0)};
-    if (!done) cta_gather<2>(p, nt, t);
+    if (!done) {
+      if constexpr (sizeof(T) == 4)
+        cta_gather<2>(p, nt, t, pre);
+      else
+        cta_gather<2>(p, nt, t);
+    }
   } else {
     prev_active = __ldcg(&pv->active);
     const int slot = 1 + ((ph - 1) & 1);
     const A *const p[2] = {cg_part<A>(in, slot, 0), cg_part<A>(in, slot, 1)};
-    if (!done && prev_active) cta_gather<2>(p, nt, t);
+    if (!done && prev_active) {
+      if constexpr (sizeof(T) == 4)
+        cta_gather<2>(p, nt, t, pre);
+      else
+        cta_gather<2>(p, nt, t);
+    }
   }
   if (threadIdx.x == 0) {
     CgState st;
@@ -1103,9 +1144,9 @@ __device__ __forceinline__ void cg_scalars(const Tile &tl, const D &in, InstScal
 // 4 consecutive z samples of one column with 16-byte loads and stores; the
 // z neighbours beyond its 4 come from the adjacent lanes, or, at a warp or
 // tile edge, from single loads.  Same arithmetic per sample as the general
-// step.
-
-template <typename D>
+// step.  FIRST (the first step, beta = 0): p and s_{i-1} are taken as zero
+// instead of being read (beta times them is zero).
+template <bool FIRST, typename D>
 __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const D &in, InstScal &sc, int ph) {
   constexpr int SUB = kThreads * 4;
   const unsigned FULL = 0xffffffffu;
@@ -1134,31 +1175,32 @@ __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const D &in, Ins
     bool hzm = false, hzp = false, edge_p = false;
     if (ok) {
       const GridPos ps = grid_pos(in, g0);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       rc = ld4(r, g0);
       wc = ld4(w, g0);
-      sc4 = ld4(sp, g0);
-      pv = ld4(p, g0);
+      sc4 = FIRST ? z4 : ld4(sp, g0);
+      pv = FIRST ? z4 : ld4(p, g0);
       xv = ld4(x, g0);
       // a missing neighbour repeats the centre, so its difference is zero
       const bool hxm = ps.ix > 0, hxp = ps.ix < in.nx - 1;
       rxm = hxm ? ld4(r, g0 - in.nz) : rc;
       wxm = hxm ? ld4(w, g0 - in.nz) : wc;
-      sxm = hxm ? ld4(sp, g0 - in.nz) : sc4;
+      sxm = (hxm && !FIRST) ? ld4(sp, g0 - in.nz) : sc4;
       rxp = hxp ? ld4(r, g0 + in.nz) : rc;
       wxp = hxp ? ld4(w, g0 + in.nz) : wc;
-      sxp = hxp ? ld4(sp, g0 + in.nz) : sc4;
+      sxp = (hxp && !FIRST) ? ld4(sp, g0 + in.nz) : sc4;
       hzm = ps.iz > 0;
       hzp = ps.iz + 4 < in.nz;
       edge_p = lane == 31 || g0 + 4 >= end;
       if (hzm && lane == 0) {
         rzm = r[g0 - 1];
         wzm = w[g0 - 1];
-        szm = sp[g0 - 1];
+        szm = FIRST ? 0.f : sp[g0 - 1];
       }
       if (hzp && edge_p) {
         rzp = r[g0 + 4];
         wzp = w[g0 + 4];
-        szp = sp[g0 + 4];
+        szp = FIRST ? 0.f : sp[g0 + 4];
       }
     }
     if (base == tl.start) {
@@ -1210,7 +1252,7 @@ __device__ __forceinline__ void body_cg_step_v4(const Tile &tl, const D &in, Ins
   }
 }
 
-template <typename T, typename D>
+template <typename T, typename D, bool FIRST = false>
 __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, InstScal &sc, int ph) {
   using A = typename AccOf<T>::type;
   SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= in.N, 3u, tl.start + tl.len);
@@ -1222,7 +1264,7 @@ __device__ __forceinline__ void body_cg_step_in(const Tile &tl, const D &in, Ins
     const uintptr_t al = (uintptr_t)in.x | (uintptr_t)in.cp | (uintptr_t)in.cr[0] | (uintptr_t)in.cr[1] |
                          (uintptr_t)in.cw[0] | (uintptr_t)in.cw[1] | (uintptr_t)in.cs[0] | (uintptr_t)in.cs[1];
     if ((in.nz & 3) == 0 && in.ny == 1 && (al & 15) == 0) {
-      body_cg_step_v4(tl, in, sc, ph);
+      body_cg_step_v4<FIRST>(tl, in, sc, ph);  // FIRST (beta = 0): p and s_{i-1} are not read
       return;
     }
   }
@@ -1335,6 +1377,12 @@ __device__ __forceinline__ void body_cg_last_in(const Tile &tl, const D &in, Ins
   if constexpr (sizeof(T) == 4) {
     const uintptr_t al = (uintptr_t)(r + tl.start) | (uintptr_t)(p + tl.start) | (uintptr_t)(x + tl.start);
     if ((al & 15) == 0 && (tl.len & 3) == 0) {
+      // the partial sums are requested before the data, so that their sum
+      // is formed while the data loads are in flight
+      const float *gp[2];
+      cg_gather_src(in, ph, gp);
+      float pre[2][kGatherBatch];
+      gather_first<2>(gp, in.nt_part, pre);
       for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4) {
         const int64_t g0 = base + 4 * (int64_t)threadIdx.x;
         const bool ok = g0 < end;
@@ -1345,8 +1393,7 @@ __device__ __forceinline__ void body_cg_last_in(const Tile &tl, const D &in, Ins
           xv = ld4(x, g0);
         }
         if (first) {
-          // the previous launch's sums, while this CTA's first loads are in flight
-          cg_scalars<T>(tl, in, sc, ph, s_ab, &s_go);
+          cg_scalars<T>(tl, in, sc, ph, s_ab, &s_go, pre);
           if (!s_go) return;
           alpha = s_ab[0];
           beta = s_ab[1];
@@ -1400,6 +1447,26 @@ __global__ void __launch_bounds__(kThreads) k_cg_last(const Tile *__restrict__ t
   } else {
     const Tile tl = tiles[blockIdx.x];
     body_cg_last_in<T>(tl, insts[tl.inst], scal[tl.inst], ph);
+  }
+}
+
+// The first step launch of an iteration (phase 2): beta = 0, so p_0 = r_0 and
+// s_0 = w_0 without reading p or s; its own kernel keeps the other steps'
+// register allocation.
+template <typename T, bool BL = false>
+__global__ void __launch_bounds__(kThreads, 3) k_cg_first(const Tile *__restrict__ tiles,
+                                                         const InstDev *__restrict__ insts,
+                                                         InstScal *__restrict__ scal, int ph, unsigned long long *ts,
+                                                         const __grid_constant__ CgOne one) {
+  const Stamp stamp(ts);
+  if constexpr (BL) {
+    if (!one.on && tiles[blockIdx.x].item > 0) return;  // k_cg_step_blur's items
+  }
+  if (one.on) {
+    body_cg_step_in<T, CgDesc, true>(one_tile(one), one.d, scal[0], ph);
+  } else {
+    const Tile tl = tiles[blockIdx.x];
+    body_cg_step_in<T, InstDev, true>(tl, insts[tl.inst], scal[tl.inst], ph);
   }
 }
 
@@ -4505,7 +4572,10 @@ cudaError_t launch_cg_w0(const Launch &L, const Tile *tiles, int nt, const InstD
 }
 cudaError_t launch_cg_step(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
                            const CgOne &one) {
-  SIP_DISPATCH_BL(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
+  if (ph == 2)
+    SIP_DISPATCH_BL(L, k_cg_first, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
+  else
+    SIP_DISPATCH_BL(L, k_cg_step, nt, kThreads, 0, tiles, insts, scal, ph, L.ts, one);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_last(const Launch &L, const Tile *tiles, int nt, const InstDev *insts, InstScal *scal, int ph,
