@@ -55,6 +55,28 @@ def test_batch_matches_oracle_fixed_rho():
     bp.close()
 
 
+def test_batch_adaptive_cg_steps_match_oracle():
+    """Eq. cg_stop with at most 4 steps: the instances of one plan stop their
+    x-updates after different numbers of steps, so some are inactive at the
+    plan's last step launch (the x-only one) and others take it.  Each
+    instance must still match the oracle (FP64, 1e-10) with its own CG step
+    count."""
+    inst, models = mixed_instances()
+    opts = dict(max_iter=30, adapt=0, rho0=1.0, gamma0=1.5, cg_iters=0, cg_max=4)
+    bp = sip.BatchProjector(inst, dtype="f64", **opts)
+    xs, infos = bp.project(models)
+    steps = []
+    for i, ((grid, sets), m) in enumerate(zip(inst, models)):
+        ref = P.parsdmm(m, grid, sets, P.options(**opts))
+        assert infos[i]["cg_steps"] == ref["cg_steps"], i
+        assert rel(xs[i].cpu().numpy(), ref["x"]) <= 1e-10, i
+        steps.append(ref["cg_steps"])
+    bp.close()
+    # more than 3 steps per iteration on average: the 4th (x-only) launch was
+    # taken; fewer than 3: other x-updates stopped before it
+    assert max(steps) > 3 * 30 and min(steps) < 3 * 30, "the rule must vary the step count across instances"
+
+
 @pytest.mark.parametrize("dt,tol", [("f64", 1e-10), ("f32", 1e-5)])
 def test_batch_equals_one_at_a_time(dt, tol):
     """Each result alone and in the mix is the same.  Binary32 runs with

@@ -314,6 +314,33 @@ def test_adaptive_cg_rule_matches_oracle(case):
     assert rel(x, ref["x"]) <= 1e-10
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(36, 64), (37, 20)], ids=["nz4", "nz37"])
+@pytest.mark.parametrize("cg", [1, 2, 3])
+def test_cg_step_counts(cg, n, dt):
+    """The first step launch of an iteration (beta = 0: p and s are not read)
+    and the last (only x is formed) are kernels of their own.  With one step
+    the last launch is also the first (it takes the right-hand side's and
+    w_0's sums); with two the x-only launch follows the first directly.
+    n_z = 36 takes the four-sample kernels in binary32, n_z = 37 the general
+    ones.  Fixed rho: FP64 within 1e-10 of the oracle, FP32 within the
+    four-sample step test's 5e-5, and the same number of CG steps."""
+    g = np.random.default_rng(31 + cg)
+    m = 3.0 + g.standard_normal(n[0] * n[1])
+    grid = {"n": n}
+    sets = [{"op": "I", "type": "bounds", "lo": 2.5, "hi": 3.5},
+            {"op": "TV", "type": "l1", "sigma_rel": 0.4},
+            {"op": "DZ", "type": "bounds", "lo": -0.5, "hi": 0.5}]
+    opts = dict(max_iter=30, cg_iters=cg, adapt=0, rho0=1.0, gamma0=1.5)
+    mm = m_as(m, dt)
+    ref = oracle_run(mm, grid, sets, opts)
+    x, info, _ = run_gpu(mm, grid, sets, dt, opts)
+    # every iteration takes cg steps but the first (y = v = 0 there, so b and
+    # r_0 are zero and no step is taken)
+    assert info["cg_steps"] == ref["cg_steps"] == 29 * cg
+    assert rel(x, ref["x"]) <= (1e-10 if dt == "f64" else 5e-5)
+
+
 def test_full_size_fp32_tracks_fp64_while_supports_hold():
     """The 512 x 1024 five-set workload, FP32 against the FP64 GPU loop (each
     with its own adapt-rho-gamma) in the bench launch configuration.  The
