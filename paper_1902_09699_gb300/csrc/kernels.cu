@@ -842,30 +842,50 @@ __global__ void __launch_bounds__(kThreads, 2) k_rhs_tma(const Tile *__restrict_
       }
       waited = true;
     }
+    // segments outside, this thread's points inside: a segment's descriptor
+    // is read once per round and its kind decides the loop taken (each
+    // point still adds its segments in order)
+    int gi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) gi[u] = (int)(base + threadIdx.x + (int64_t)u * kThreads);
+    for (int j = 0; j < nseg; ++j) {
+      const float *__restrict__ ys = sw + sbase_y[j];
+      const float *__restrict__ vs = sw + sbase_v[j];
+      const float rho = srs[j], ih = sih[j];
+      const int kind = skind[j];
+      // (A^T u)[g] = u[ia] (if fa) - u[ib] (if fb), times 1/h
+      if (kind == SEG_DZ) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (gi[u] >= e0) continue;
+          const int rz = gi[u] - (int)pos[u].t;  // D_z row base (iz + (nz-1) t)
+          const float ua = pos[u].iz >= 1 ? rho * ys[rz - 1] + vs[rz - 1] : 0.f;
+          const float ub = pos[u].iz <= nz - 2 ? rho * ys[rz] + vs[rz] : 0.f;
+          b[u] += (ua - ub) * ih;
+        }
+      } else if (kind == SEG_DX) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (gi[u] >= e0) continue;
+          const int ia = gi[u] - nz;
+          const float ua = pos[u].ix >= 1 ? rho * ys[ia] + vs[ia] : 0.f;
+          const float ub = pos[u].ix <= in.nx - 2 ? rho * ys[gi[u]] + vs[gi[u]] : 0.f;
+          b[u] += (ua - ub) * ih;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (gi[u] >= e0) continue;
+          const float ua = rho * ys[gi[u]] + vs[gi[u]], ub = 0.f;
+          b[u] += (ua - ub) * ih;
+        }
+      }
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t g = base + threadIdx.x + (int64_t)u * kThreads;
-      if (g >= e0) continue;
-      const int gi = (int)g;
-      const int rz = gi - (int)pos[u].t;  // D_z row base (iz + (nz-1) t)
-      for (int j = 0; j < nseg; ++j) {
-        const float *__restrict__ ys = sw + sbase_y[j];
-        const float *__restrict__ vs = sw + sbase_v[j];
-        const float rho = srs[j], ih = sih[j];
-        // (A^T u)[g] = u[ia] (if fa) - u[ib] (if fb), times 1/h
-        int ia = gi, ib = gi;
-        bool fa = true, fb = false;
-        switch (skind[j]) {
-          case SEG_DZ: ia = rz - 1; ib = rz; fa = pos[u].iz >= 1; fb = pos[u].iz <= nz - 2; break;
-          case SEG_DX: ia = gi - nz; ib = gi; fa = pos[u].ix >= 1; fb = pos[u].ix <= in.nx - 2; break;
-          default: break;
-        }
-        const float ua = fa ? rho * ys[ia] + vs[ia] : 0.f;
-        const float ub = fb ? rho * ys[ib] + vs[ib] : 0.f;
-        b[u] += (ua - ub) * ih;
-      }
+      if (gi[u] >= e0) continue;
       const float rv = b[u] - apply_c(C, xn[u]);
-      r[g] = rv;
+      r[gi[u]] = rv;
       a1 += rv * rv;
     }
   }
