@@ -3197,10 +3197,33 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
   using A = typename AccOf<T>::type;
   const InstDev &in = insts[tl.inst];
   InstScal &sc = scal[tl.inst];
-  if (sc.done) return;
   const int b = tl.item;
   const BlockDev &bd = in.blk[b];
   SIP_GUARD_TILE(in.err, tl.start >= 0 && tl.start + tl.len <= bd.M, 9u, tl.start + tl.len);
+  // binary32: the first round's w is requested before the instance's and
+  // the job's state arrive (used by the 16-byte path, discarded otherwise)
+  constexpr int FU = 2;
+  float4 W0[FU];
+  bool w0_ok = false;
+  if constexpr (sizeof(T) == 4) {
+    const float *w0 = (const float *)in.w + bd.woff;
+    const int64_t e0 = tl.start + tl.len;
+    w0_ok = ((uintptr_t)(w0 + tl.start) & 15) == 0;
+    if (w0_ok) {
+#pragma unroll
+      for (int h = 0; h < FU; ++h) {
+        const int64_t r0 = tl.start + ((int64_t)h * kThreads + threadIdx.x) * 4;
+        W0[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r0 + 4 <= e0) {
+          W0[h] = ld4(w0, r0);
+        } else {
+          for (int c = 0; c < 4; ++c)
+            if (r0 + c < e0) vset(W0[h], c, w0[r0 + c]);
+        }
+      }
+    }
+  }
+  if (sc.done) return;
   const int k = sc.k;
   const bool ad = adapt_iter(in, k);
   const bool ad_dots = ad && sc.have_k0;
@@ -3263,7 +3286,6 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
     if constexpr (sizeof(T) == 4) {
       // 16-byte accesses, 4 consecutive rows per thread, two groups of 4
       // per round (their loads requested together)
-      constexpr int FU = 2;
       for (int64_t base = tl.start; base < end; base += (int64_t)kThreads * 4 * FU) {
         auto ld = [&](const float *p, int64_t r0) {
           if (r0 + 4 <= end) return ld4(p, r0);
@@ -3286,7 +3308,7 @@ __device__ __forceinline__ void body_final(const Tile &tl, const InstDev *__rest
           const int64_t r0 = base + ((int64_t)h * kThreads + threadIdx.x) * 4;
           W[h] = KY[h] = KV[h] = make_float4(0.f, 0.f, 0.f, 0.f);
           if (r0 < end) {
-            W[h] = ld(w, r0);
+            W[h] = (base == tl.start && w0_ok) ? W0[h] : ld(w, r0);
             if (ad_dots) {
               KY[h] = ld(k0y, r0);
               KV[h] = ld(k0v, r0);
